@@ -1,0 +1,369 @@
+#!/usr/bin/env python
+"""Benchmark: periodic Ewald-RPY Brownian-dynamics steps per second at
+N = 8000 beads (400 chains x 20 beads, theta solution at c/c* = 4, excluded
+volume off, overlap-corrected RPY, 16 Wiener vectors, N_Ch = 40).
+
+One step = the whole hot path on one configuration: forces, dense D(R)
+assembly (self + real-space images + reciprocal sum + M*), Lanczos bounds,
+the first product D.[F, dW], the Chebyshev terms and the Euler update.
+
+  python bench.py [--gpus N --steps K --warmup W] [--precision fp64|mixed_f16|mixed_bf16]
+  python bench.py --impl reference ...     # the CPU oracle on the host cores
+
+Prints one JSON line (rank 0).  N > 1 runs independent replicas, one per
+rank (weak scaling; the path has no data-path exchange).
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "BD steps/sec at N=8000 (D build + Chebyshev), FP64 vs mixed; % of roofline"
+WORKLOAD = ("theta solution N=8000 (400 chains x 20 beads), c/c*=4, EV off, overlap-corrected "
+            "RPY, dense D 24000x24000, 16 Wiener vectors, N_Ch=40")
+KERNEL_FILES = {"fp64": "paper_1203_6208_gb300/csrc/dense_f64.cu",
+                "mixed": "paper_1203_6208_gb300/csrc/tc_gemm.cu"}
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed_f16", "mixed_bf16"])
+    ap.add_argument("--nch", type=int, default=40)
+    ap.add_argument("--m", type=int, default=16)
+    ap.add_argument("--alpha-factor", type=float, default=1.0)
+    ap.add_argument("--lanczos", type=int, default=30)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--e2e-steps", type=int, default=3)
+    ap.add_argument("--chains", type=int, default=400,
+                    help="chains of 20 beads (400 = the N=8000 workload; smaller only for "
+                         "profiler captures)")
+    return ap.parse_args()
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def system(alpha_factor, chains=400):
+    from paper_1203_6208_gb300 import inputs
+    cfg, extra = inputs.preset("c4", alpha_factor=alpha_factor, n_chains=chains)
+    return cfg, cfg.params()
+
+
+# ---------------------------------------------------------------------------
+# CPU oracle timing (bounded sample of the same workload)
+
+def oracle_sample_step(p, R, m, nch, rows):
+    """Oracle work of one step restricted to `rows` bead rows: those rows of
+    D plus the N_Ch - 1 products restricted to them.  Returns seconds."""
+    import numpy as np
+    import oracle
+    n3 = 3 * p["n"]
+    X = np.random.default_rng(0).standard_normal((m, n3))
+    Y = np.zeros((m, n3))
+    t0 = time.perf_counter()
+    Drows = oracle.build_D_rows(p, R, 0, rows)
+    for _ in range(nch - 1):
+        oracle.lib().oracle_apply_rows(n3, 0, 3 * rows, oracle._ptr(Drows), oracle._ptr(X), m,
+                                       oracle._ptr(Y))
+    return time.perf_counter() - t0
+
+
+def cpu_baseline(p, R, m, nch, target_s=12.0):
+    import oracle
+    n = p["n"]
+    t_small = oracle_sample_step(p, R, m, nch, 32)
+    rows = int(min(n, max(32, 32 * target_s / max(t_small, 1e-3))))
+    t = oracle_sample_step(p, R, m, nch, rows)
+    step_s = t * n / rows
+    return {"value": 1.0 / step_s, "unit": "steps/s", "cores": oracle.num_threads(),
+            "kind": "oracle",
+            "sample": f"D rows and the {nch - 1} products for {rows} of {n} beads "
+                      f"({t:.1f} s), scaled by N/rows to one step ({step_s:.1f} s)"}
+
+
+def run_reference(args):
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return
+    from paper_1203_6208_gb300 import inputs
+    import oracle
+    oracle.build()
+    cfg, p = system(args.alpha_factor, args.chains)
+    R = inputs.make_chains(cfg)
+    n = p["n"]
+    rows = 64
+    for _ in range(args.warmup):
+        oracle_sample_step(p, R, args.m, args.nch, rows)
+    ts = [oracle_sample_step(p, R, args.m, args.nch, rows) for _ in range(args.steps)]
+    step_s = sum(ts) / len(ts) * n / rows
+    v = 1.0 / step_s
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "steps/s",
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": step_s * 1e3, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "precision": "fp64", "alpha_factor": args.alpha_factor},
+            "cpu_baseline": {"value": v, "unit": "steps/s", "cores": oracle.num_threads(),
+                             "kind": "oracle",
+                             "sample": f"each step: D rows + {args.nch - 1} products for {rows} "
+                                       f"of {n} beads, scaled by N/rows"},
+            "e2e": {"value": v, "unit": "steps/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ---------------------------------------------------------------------------
+# GPU clocks during the timed region
+
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self):
+        self.lines = []
+        self.proc = None
+
+    def start(self):
+        cmd = ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+               "-lms", "200"]
+        vis = os.environ.get("CUDA_VISIBLE_DEVICES", "")
+        if vis.strip().isdigit():
+            cmd += ["-i", vis.strip()]
+        try:
+            self.proc = subprocess.Popen(cmd, stdout=subprocess.PIPE, stderr=subprocess.DEVNULL,
+                                         text=True)
+        except OSError:
+            self.proc = None
+            return
+        self.t = threading.Thread(target=self._read, daemon=True)
+        self.t.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.t.join(timeout=2)
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        first_idx = None
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            if first_idx is None:
+                first_idx = f[0]
+            if f[0] != first_idx:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax.append(float(f[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ---------------------------------------------------------------------------
+
+def measured_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as f:
+            return json.load(f), "measured"
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}, "fallback"
+
+
+def probe_fp64_peak():
+    """FP64 DFMA throughput of this GPU (probe kernel), flop/s."""
+    import ctypes
+    from paper_1203_6208_gb300 import build
+    L = ctypes.CDLL(build.PROBE_LIB)
+    L.bd_probe_peak.restype = ctypes.c_double
+    L.bd_probe_peak.argtypes = [ctypes.c_int] * 4
+    sms = 152
+    best = 0.0
+    for blocks_per_sm in (4, 8):
+        best = max(best, L.bd_probe_peak(0, 4096, sms * blocks_per_sm, 256))
+    return best
+
+
+def traffic_per_launch(kind):
+    """DRAM bytes per launch of the dominant kernel from the committed ncu
+    summary, if it was taken on the current kernel source (else None)."""
+    path = os.path.join(ROOT, "profiles", f"traffic_{kind}.txt")
+    if not os.path.exists(path):
+        return None
+    src = os.path.join(ROOT, KERNEL_FILES["fp64" if kind == "fp64" else "mixed"])
+    h = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+    vals = {}
+    for line in open(path):
+        if ":" in line:
+            k, v = line.split(":", 1)
+            vals[k.strip()] = v.strip()
+    if vals.get("kernel_source_sha256_16") != h:
+        return None
+    try:
+        return float(vals["dram_bytes_per_launch"])
+    except (KeyError, ValueError):
+        return None
+
+
+def run_ours(args):
+    import torch
+    ws, rank, local = dist_env()
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+        torch.cuda.set_device(local)
+    else:
+        torch.cuda.set_device(0)
+    from paper_1203_6208_gb300 import binding as bnd, build, inputs
+    build.build()
+    cfg, p = system(args.alpha_factor, args.chains)
+    R0 = inputs.make_chains(cfg, seed=cfg.seed + 17 * rank)
+    plan = bnd.Plan(p, args.precision, max_rhs=args.m, max_cheb=max(args.nch, 2))
+    R = torch.tensor(R0, device="cuda")
+    D = plan.alloc_D()
+    stats = bnd.new_stats()
+    kw = dict(m=args.m, n_cheb=args.nch, lanczos_iters=args.lanczos, bound_safety=0.05,
+              dmin_fraction=0.5, seed=4242 + rank, stats=stats)
+    for w in range(args.warmup):
+        plan.step(R, D, None, step_index=w, **kw)
+    torch.cuda.synchronize()
+    stream = torch.cuda.current_stream()
+    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(7)] for _ in range(args.steps)]
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    clocks = ClockSampler()
+    clocks.start()
+    time.sleep(0.4)
+    if ws > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    l0 = bnd.kernel_launches()
+    e0.record(stream)
+    for k in range(args.steps):
+        plan.set_phase_events(evs[k])
+        plan.step(R, D, None, step_index=args.warmup + k, **kw)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    launches = bnd.kernel_launches() - l0
+    if ws > 1:
+        torch.distributed.barrier()
+    clk = clocks.stop()
+    plan.set_phase_events(None)
+    ms = e0.elapsed_time(e1)
+    if ws > 1:
+        t = torch.tensor([ms], device="cuda")
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        ms = float(t.item())
+    st = bnd.read_stats(stats)
+    phases = {name: sum(evs[k][i].elapsed_time(evs[k][i + 1]) for k in range(args.steps))
+              / args.steps for i, name in enumerate(bnd.PHASES)}
+
+    # roofline of the dominant kernel: the Chebyshev product (N_Ch - 2 launches per step)
+    n3 = 3 * p["n"]
+    cheb_launch_ms = phases["chebyshev"] / max(args.nch - 2, 1)
+    peaks, peak_src = measured_peaks()
+    if args.precision == "fp64":
+        flops = 2.0 * n3 * n3 * args.m
+        fp64_peak = probe_fp64_peak()
+        achieved = flops / (cheb_launch_ms * 1e-3) / 1e12
+        roof = {"bound": "alu", "kernel": "k_gemm_f64<16,cheb>", "achieved": achieved,
+                "peak": fp64_peak / 1e12, "unit": "TFLOP/s", "frac": achieved * 1e12 / fp64_peak,
+                "peak_source": "FP64 DFMA probe (probe/peaks.cu) on this GPU",
+                "traffic": traffic_per_launch("fp64"),
+                "algorithmic_per_launch": f"2*(3N)^2*m = {flops:.3e} flop"}
+    else:
+        bytes_ = n3 * n3 * 2.0 + n3 * args.m * (2 + 8 * 4)
+        achieved = bytes_ / (cheb_launch_ms * 1e-3) / 1e9
+        roof = {"bound": "hbm", "kernel": "tc_cheb", "achieved": achieved,
+                "peak": peaks["hbm_gbs"], "unit": "GB/s", "frac": achieved / peaks["hbm_gbs"],
+                "peak_source": f"hbm_gbs ({peak_src})", "traffic": traffic_per_launch("mixed"),
+                "algorithmic_per_launch": f"16-bit D + vectors = {bytes_:.3e} B"}
+
+    # end to end through the public API with host buffers
+    e2e = None
+    if args.e2e_steps > 0:
+        Rh = torch.tensor(R0, dtype=torch.float64).pin_memory()
+        sh = torch.empty(bnd.STATS_BYTES, dtype=torch.uint8).pin_memory()
+        t0 = time.perf_counter()
+        for k in range(args.e2e_steps):
+            R.copy_(Rh, non_blocking=True)
+            plan.step(R, D, None, step_index=10_000 + k, **kw)
+            Rh.copy_(R, non_blocking=True)
+            sh.copy_(stats, non_blocking=True)
+            stream.synchronize()
+        e2e_s = (time.perf_counter() - t0) / args.e2e_steps
+        e2e = {"value": ws / e2e_s, "unit": "steps/s", "h2d_bytes_per_step": 8 * n3,
+               "d2h_bytes_per_step": 8 * n3 + bnd.STATS_BYTES,
+               "note": "per step: positions H2D from pinned memory, bd_step, positions + "
+                       "stats D2H, stream sync (wall clock)"}
+
+    if rank != 0:
+        return
+    value = ws * args.steps / (ms * 1e-3)
+    line = {"metric": METRIC, "value": value, "unit": "steps/s", "n_gpus": ws,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f64" if args.precision == "fp64" else
+                     ("f16+f32+f64" if args.precision == "mixed_f16" else "bf16+f32+f64"),
+            "data": "synthetic",
+            "config": {"workload": WORKLOAD if args.chains == 400 else
+                       f"reduced: {args.chains} chains x 20 beads (profiling only)",
+                       "n_beads": p["n"], "box_L": p["L"],
+                       "alpha": p["alpha"], "alpha_factor": args.alpha_factor, "r_c": p["rc"],
+                       "n2max": p["n2max"], "n_kvec_half": plan.info.n_kvec, "m": args.m,
+                       "n_cheb": args.nch, "lanczos_iters": args.lanczos,
+                       "precision": args.precision,
+                       "l2": "inputs larger than L2 (D alone is %.2f GB)" % (plan.info.d_bytes / 1e9),
+                       "parallelism": "replicas" if ws > 1 else "single"},
+            "phases_ms": phases, "step_stats": st, "roofline": roof, "gpu_launches": launches,
+            "clocks": clk, "e2e": e2e}
+    if ws == 1 and not args.no_cpu_baseline:
+        import oracle
+        oracle.build()
+        line["cpu_baseline"] = cpu_baseline(p, R0, args.m, args.nch)
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,259 @@
+/*
+ * bd.h -- C ABI of libbdgb: one periodic Brownian-dynamics Euler step for
+ * bead-spring polymer solutions with Ewald-summed Rotne-Prager-Yamakawa
+ * hydrodynamics, on one NVIDIA GB300 (sm_103a).
+ *
+ * Method: Jain, Sunthar, Duenweg & Prakash, "Optimisation of a Brownian
+ * dynamics algorithm for semidilute polymer solutions" (paper sections and
+ * equations are cited per entry point below).
+ *
+ * Conventions shared by every entry point
+ * ----------------------------------------
+ *  * Plain pointers and sizes only.  "dev" pointers are CUDA device pointers
+ *    on the device that was current when the plan was created; "host"
+ *    pointers are ordinary host memory.
+ *  * Vectors of 3N numbers use the bead-major index 3*nu + s (s = x, y, z):
+ *    positions R, forces F, Wiener increments dW, drift D.F, noise dS.
+ *    A block of m such vectors is stored column-major, column j starting at
+ *    element j*3N.
+ *  * The diffusion matrix D (3N x 3N, symmetric) is stored row-major with the
+ *    leading dimension bd_plan_info.ld (>= 3N).  Its storage depends on the
+ *    plan precision:
+ *      BD_FP64        : double D[3N][ld]
+ *      BD_MIXED_F16 /
+ *      BD_MIXED_BF16  : float  D32[3N][ld] followed (at byte offset
+ *                       3N*ld*4) by a 16-bit copy D16[3N][ld] (IEEE half or
+ *                       bfloat16) that feeds the tensor cores.
+ *    The caller allocates bd_plan_info.d_bytes bytes for it (device memory,
+ *    256-byte aligned) and owns them.
+ *  * Ownership: every argument buffer is caller-owned; nothing is freed
+ *    across the ABI.  The plan owns its constant tables and its scratch.
+ *  * Asynchrony: compute entry points enqueue work on the given stream and
+ *    return without synchronising, unless stated otherwise.  A plan may be
+ *    used by one stream at a time (its scratch is shared by its calls).
+ *  * Errors: every entry point returns a bd_status; no C++ exception crosses
+ *    the ABI.  On an error the text is available from bd_last_error()
+ *    (thread-local).  Argument errors are detected before any work is
+ *    enqueued.  Errors that only the device can detect (FENE over-stretch,
+ *    non-positive bounds, a bounded wait that ran out) are written to
+ *    device-side status words that the caller reads when convenient.
+ */
+#ifndef BD_H
+#define BD_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct CUstream_st *bd_stream; /* a cudaStream_t; NULL = legacy default stream */
+
+typedef enum {
+    BD_OK = 0,
+    BD_ERR_INVALID = 1,       /* bad argument or plan/argument mismatch            */
+    BD_ERR_OOM = 2,           /* device allocation failed (plan creation only)     */
+    BD_ERR_CUDA = 3,          /* a CUDA runtime/driver call failed                 */
+    BD_ERR_NOT_PD = 4,        /* eigenvalue bound <= 0: D not positive definite    */
+    BD_ERR_FENE_STRETCH = 5,  /* a FENE spring reached |Q|^2 >= b                  */
+    BD_ERR_CHEB_NOCONV = 6,   /* adaptive Chebyshev did not reach the tolerance    */
+    BD_ERR_TIMEOUT = 7,       /* a bounded device-side wait gave up                */
+    BD_ERR_UNSUPPORTED = 8    /* request outside this build's supported range      */
+} bd_status;
+
+typedef enum {
+    BD_FP64 = 0,        /* FP64 everywhere                                          */
+    BD_MIXED_F16 = 1,   /* FP32 D assembly; products on tensor cores with IEEE-half
+                           operands and FP32 accumulation; FP64 vectors/scalars     */
+    BD_MIXED_BF16 = 2   /* as BD_MIXED_F16 with bfloat16 operands                  */
+} bd_precision;
+
+/* Model and method parameters.  Units: lengths in l_H = sqrt(kT/H), time in
+ * lambda_H = zeta/(4H) (Sec. II A). */
+typedef struct {
+    int32_t n_beads;          /* N; chains are contiguous in the bead index       */
+    int32_t beads_per_chain;  /* N_b (N % N_b == 0)                               */
+    double  box_L;            /* periodic cube edge L                             */
+    double  a;                /* bead radius a = sqrt(pi) h* (Sec. II A)           */
+    double  alpha;            /* Ewald splitting parameter alpha (Eq. DF)          */
+    double  r_c;              /* real-space cutoff: images with |r| <= r_c (Eq. rparameter) */
+    int32_t n2max;            /* reciprocal cutoff: k = 2 pi n / L, n.n <= n2max (Eq. kparameter) */
+    int32_t overlap_corr;     /* 1: add the overlap correction M* for |r| < 2a (Eq. DFmodified) */
+    int32_t spring;           /* 0 Hookean, 1 FENE (Sec. II A)                      */
+    double  fene_b;           /* FENE extensibility b                             */
+    int32_t ev_on;            /* 1: narrow-Gaussian excluded volume               */
+    double  z_star, d_star;   /* EV strength and range: U/kT = (z_star/d_star^3) exp(-r^2/(2 d_star^2)) */
+    double  r_ev;             /* EV cutoff over periodic images                   */
+    double  dt;               /* time step Delta t (Eq. sde)                      */
+    int32_t precision;        /* bd_precision                                     */
+    int32_t max_rhs;          /* largest m (Wiener columns) any call will use, 1..32 */
+    int32_t max_cheb;         /* largest number of Chebyshev terms N_Ch, 2..256   */
+} bd_params;
+
+typedef struct bd_plan bd_plan;
+
+typedef struct {
+    int32_t n3;               /* 3N                                               */
+    int32_t ld;               /* leading dimension of D in elements               */
+    int64_t d_bytes;          /* bytes of device memory D needs                   */
+    int32_t n_kvec;           /* half-space k-vectors of the reciprocal sum       */
+    int32_t precision;        /* bd_precision of the plan                          */
+    int64_t scratch_bytes;    /* device scratch owned by the plan                 */
+} bd_plan_info;
+
+/* Device-resident statistics of one step (the caller reads them back when it
+ * wants; bd_step writes them on the stream). */
+typedef struct {
+    double  d_min, d_max;     /* eigenvalue bounds used by the Chebyshev series   */
+    double  ef_max;           /* max over Wiener columns of E_f (Sec. IV)           */
+    int32_t n_cheb;           /* Chebyshev terms used                              */
+    int32_t n_overstretched;  /* FENE springs with |Q|^2 >= b in the proposal      */
+    int32_t accepted;         /* 1 if R was advanced, 0 if the step was rejected   */
+    int32_t status;           /* bd_status of the device-side checks              */
+} bd_step_stats;
+
+/* Options of bd_step. */
+typedef struct {
+    int32_t m;                /* Wiener columns (1..max_rhs); column 0 advances R  */
+    int32_t n_cheb;           /* Chebyshev terms N_Ch (2..max_cheb)                */
+    int32_t lanczos_iters;    /* Lanczos steps for the bounds (4..128)            */
+    double  bound_safety;     /* d_max = (1 + bound_safety) theta_max             */
+    double  dmin_fraction;    /* d_min = dmin_fraction theta_min (0 < f <= 1)     */
+    uint64_t seed;            /* Philox key when dW == NULL                        */
+    uint64_t step_index;      /* Philox counter high word when dW == NULL          */
+} bd_step_opts;
+
+/* ---------------------------------------------------------------------------
+ * Plan.  bd_plan_create validates the parameters, computes the reciprocal
+ * table (k-vectors and M2(k), Eq. M2) in FP64 on the current device and
+ * allocates the plan's scratch (Chebyshev and Lanczos vectors).
+ * Errors: BD_ERR_INVALID for inconsistent parameters, BD_ERR_OOM when the
+ * scratch cannot be allocated, BD_ERR_CUDA otherwise.  Synchronous.      */
+bd_status bd_plan_create(const bd_params *params, bd_plan **out_plan);
+/* Frees the plan and its scratch (synchronises the device first).  NULL ok. */
+void bd_plan_destroy(bd_plan *plan);
+/* Sizes and layout of the plan (host output). */
+bd_status bd_plan_query(const bd_plan *plan, bd_plan_info *out_info);
+
+/* ---------------------------------------------------------------------------
+ * bd_forces -- non-hydrodynamic forces F_mu = F_spr + F_exv (Sec. II A).
+ * Springs: F^c(Q_mu) - F^c(Q_{mu-1}) with Hookean F^c(Q) = Q or FENE
+ * F^c(Q) = Q/(1 - |Q|^2/b).  Excluded volume: narrow-Gaussian
+ * F = sum (z_star/d_star^5) r exp(-r^2/(2 d_star^2)) over all pairs and periodic images
+ * with |r| <= r_ev (not specified by the paper, which uses WCA; see DESIGN).
+ *   R       dev, 3N doubles (input positions, unwrapped)
+ *   F       dev, 3N doubles (output)
+ *   n_bad   dev, one int32 (output, may be NULL): FENE springs with
+ *           |Q|^2 >= b; their force is set to NaN.                      */
+bd_status bd_forces(bd_plan *plan, const double *R, double *F, int32_t *n_bad, bd_stream stream);
+
+/* ---------------------------------------------------------------------------
+ * bd_build_D -- assemble the dense periodic diffusion matrix D(R), Eq.
+ * (DFmodified): self term (1 - 6 a alpha/sqrt(pi) + 40 a^3 alpha^3/(3
+ * sqrt(pi))) I on the diagonal blocks, the real-space sum of M1 (Eq. M1)
+ * over periodic images with |r| <= r_c (n = 0 omitted for nu = mu), the
+ * reciprocal sum of M2(k) cos(k.(r_nu - r_mu)) over 0 < |k|, n.n <= n2max
+ * (Eq. M2), and, for the image of a pair nu != mu closer than 2a, the
+ * overlap correction M* = Omega_B - Omega_A (Eq. cor5).
+ *   R   dev, 3N doubles
+ *   D   dev, bd_plan_info.d_bytes bytes (output; layout in the header
+ *       comment).  Padding columns [3N, ld) are not written.            */
+bd_status bd_build_D(bd_plan *plan, const double *R, void *D, bd_stream stream);
+
+/* ---------------------------------------------------------------------------
+ * bd_apply_D -- Y = D X, the drift product of Eq. (sde) (and any product of
+ * Eqs. cheb2/cheb3).  X, Y: dev, 3N x m column-major doubles, 1 <= m <=
+ * max_rhs, X and Y must not overlap.  FP64 plan: FP64 product.  Mixed plan:
+ * tensor-core product of D16 with the columns of X scaled to 16 bits, FP32
+ * accumulation; with flags & BD_APPLY_REFINE, followed by one FP64-residual
+ * refinement step y += (D32 X - y) evaluated with the FP32 matrix and FP64
+ * accumulation.                                                           */
+#define BD_APPLY_REFINE 1
+bd_status bd_apply_D(bd_plan *plan, const void *D, const double *X, int32_t m, double *Y,
+                     int32_t flags, bd_stream stream);
+
+/* ---------------------------------------------------------------------------
+ * bd_eig_bounds -- bounds d_min <= lambda_min(D), d_max >= lambda_max(D)
+ * required by the Chebyshev series (Sec. IV).  The paper estimates them from
+ * Fixman's quadratic forms and empirical scalings (Eqs. lmax-lmin-dilute,
+ * fmax, fmin); here they come from `iters` Lanczos steps (FP64 vectors and
+ * recurrence, start vector from a fixed Philox stream) whose extreme Ritz
+ * values theta are widened: d_max = (1 + safety_max) theta_max,
+ * d_min = dmin_fraction theta_min.  theta_max converges to lambda_max from
+ * below within a few tens of steps; theta_min approaches lambda_min slowly
+ * (the bottom of the spectrum of D is clustered), which is why d_min takes a
+ * multiplicative fraction rather than a small margin.  The tridiagonal
+ * eigenvalues are found by bisection on the device; a Lanczos breakdown
+ * (beta ~ 0) truncates the tridiagonal matrix.  1 <= iters <= 128 (clamped
+ * to 3N).
+ *   bounds  dev, 2 doubles (output): {d_min, d_max}
+ *   status  dev, one int32 (output, may be NULL): BD_ERR_NOT_PD when
+ *           d_min <= 0, else BD_OK.                                       */
+bd_status bd_eig_bounds(bd_plan *plan, const void *D, int32_t iters, double safety_max,
+                        double dmin_fraction, double *bounds, int32_t *status, bd_stream stream);
+
+/* ---------------------------------------------------------------------------
+ * bd_chebyshev_sqrt -- Fixman's Chebyshev approximation of the Brownian
+ * term dS = sqrt(D) dW, Eqs. (cheb1)-(cheb3):
+ *   dS = sum_{p<N_Ch} c_p V_p - (c_0/2) dW,  V_0 = dW, V_1 = Y V_0,
+ *   V_p = 2 Y V_{p-1} - V_{p-2},  Y = (2 D - (d_max + d_min) I)/(d_max - d_min),
+ * with c_p the coefficients of the Chebyshev interpolant of sqrt on
+ * [d_min, d_max] (computed in FP64 on the device), and the error estimate
+ * E_f = sqrt(|dS.dS - dW.D.dW| / dW.D.dW) per column (Sec. IV).
+ *   bounds  dev, {d_min, d_max}
+ *   n_cheb  N_Ch, 2 <= n_cheb <= max_cheb
+ *   dW, dS  dev, 3N x m column-major doubles (dS output)
+ *   Ef      dev, m doubles (output, may be NULL)                         */
+bd_status bd_chebyshev_sqrt(bd_plan *plan, const void *D, const double *bounds, int32_t n_cheb,
+                            const double *dW, int32_t m, double *dS, double *Ef,
+                            bd_stream stream);
+
+/* ---------------------------------------------------------------------------
+ * bd_step -- one Euler step of Eq. (sde) with kappa = 0:
+ *   r(t+dt) = r + (dt/4) D.F + (1/sqrt 2) dS[:,0],
+ * i.e. bd_forces, bd_build_D, bd_eig_bounds, the product D.[F, dW] and
+ * bd_chebyshev_sqrt, then the update.  FENE systems reject a proposal with
+ * any |Q|^2 >= b (Sec. VII): R is then left unchanged, stats->accepted = 0
+ * and stats->status = BD_ERR_FENE_STRETCH.
+ *   R      dev, 3N doubles, advanced in place (only if accepted)
+ *   D      dev, bd_plan_info.d_bytes bytes of workspace for D (overwritten)
+ *   dW     dev, 3N x m Wiener increments, or NULL to draw them on the device:
+ *          element pair q from Philox4x32-10 with counter (q, step_index)
+ *          and key seed, Box-Muller, scaled by sqrt(dt)
+ *   DF, dS dev outputs (may be NULL): 3N drift D.F and 3N x m noise
+ *   stats  dev, one bd_step_stats (output, may be NULL)                   */
+bd_status bd_step(bd_plan *plan, double *R, void *D, const double *dW, const bd_step_opts *opts,
+                  double *DF, double *dS, bd_step_stats *stats, bd_stream stream);
+
+/* ---------------------------------------------------------------------------
+ * bd_wiener -- the device Wiener generator of bd_step on its own: count
+ * N(0, dt) numbers (see bd_step for the counter layout).  out: dev doubles. */
+bd_status bd_wiener(bd_plan *plan, uint64_t seed, uint64_t step_index, int64_t count,
+                    double *out, bd_stream stream);
+
+/* ---------------------------------------------------------------------------
+ * Phase timing.  When `events` is non-NULL, subsequent bd_step calls on this
+ * plan record the caller's CUDA events (cudaEvent_t values, created and
+ * owned by the caller) on the step's stream at the phase boundaries:
+ *   ev[0] start, ev[1] after the forces, ev[2] after the D assembly,
+ *   ev[3] after the eigenvalue bounds, ev[4] after the first product
+ *   D.[F, dW], ev[5] after the Chebyshev terms, ev[6] after the update.
+ * count must be 7.  The array is copied; NULL disables recording.        */
+#define BD_PHASE_EVENTS 7
+bd_status bd_set_phase_events(bd_plan *plan, void *const *events, int32_t count);
+
+/* Number of CUDA kernels this library has launched in the process so far
+ * (host-side counter; lets a caller count the launches of a region). */
+uint64_t bd_kernel_launches(void);
+
+/* Text of the last error on this thread ("" if none).  Never NULL. */
+const char *bd_last_error(void);
+/* Library version string. */
+const char *bd_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* BD_H */

@@ -22,6 +22,7 @@ from __future__ import annotations
 
 import ctypes
 import os
+import platform
 import subprocess
 import threading
 
@@ -42,7 +43,7 @@ def build(force: bool = False, defines=()) -> str:
     test, which builds variants with one deliberate mistake each."""
     os.makedirs(_BUILD, exist_ok=True)
     tag = "".join("_" + d.lower() for d in defines)
-    path = os.path.join(_BUILD, f"liboracle_bd{tag}.so")
+    path = os.path.join(_BUILD, f"liboracle_bd{tag}_{platform.machine()}.so")
     if (not force and os.path.exists(path)
             and os.path.getmtime(path) >= os.path.getmtime(_SRC)):
         return path

@@ -1,0 +1,436 @@
+// bd_api.cu -- the C ABI of libbdgb (include/bd.h): plan lifecycle, argument
+// validation, error text, and the orchestration of the step on one stream.
+#include <stdarg.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <new>
+
+#include "bd_internal.cuh"
+#include "tc_gemm.cuh"
+
+struct bd_plan {
+    bd::Plan P;
+};
+
+namespace bd {
+
+static thread_local char g_err[1024] = "";
+static unsigned long long g_launches = 0;
+
+void count_launches(int k) { __atomic_fetch_add(&g_launches, (unsigned long long)k, __ATOMIC_RELAXED); }
+
+bd_status set_error(bd_status st, const char *fmt, ...)
+{
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(g_err, sizeof(g_err), fmt, ap);
+    va_end(ap);
+    return st;
+}
+
+bd_status check_launch(const char *what)
+{
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return set_error(BD_ERR_CUDA, "%s: %s", what, cudaGetErrorString(e));
+    return BD_OK;
+}
+
+static bool is_mixed(const Plan &P) { return P.p.precision != BD_FP64; }
+
+template <typename T>
+static bd_status dmalloc(Plan &P, T **ptr, size_t count)
+{
+    size_t bytes = count * sizeof(T);
+    if (bytes == 0) bytes = 16;
+    cudaError_t e = cudaMalloc((void **)ptr, bytes);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        *ptr = nullptr;
+        return set_error(BD_ERR_OOM, "cudaMalloc(%zu bytes): %s", bytes, cudaGetErrorString(e));
+    }
+    P.scratch_bytes += (int64_t)bytes;
+    return BD_OK;
+}
+
+static void free_plan(Plan &P)
+{
+    void *ptrs[] = {P.d_kvec, P.d_ewc, P.d_cos, P.d_sin, P.d_cos32, P.d_sin32, P.d_F, P.d_DF,
+                    P.d_Rnew, P.d_V[0], P.d_V[1], P.d_V[2], P.d_X0, P.d_Y0, P.d_dS, P.d_dW,
+                    P.d_coef, P.d_wdw, P.d_red, P.d_bounds, P.d_status, P.d_lq[0], P.d_lq[1],
+                    P.d_lq[2], P.d_lab, P.d_x16, P.d_xscale, P.d_part, P.d_counters,
+                    P.d_stats_scratch, P.d_y32};
+    for (void *p : ptrs)
+        if (p) cudaFree(p);
+}
+
+static bd_status validate(const bd_params *p)
+{
+    if (!p) return set_error(BD_ERR_INVALID, "params is NULL");
+    if (p->n_beads < 1) return set_error(BD_ERR_INVALID, "n_beads must be >= 1");
+    if (p->beads_per_chain < 1 || p->n_beads % p->beads_per_chain != 0)
+        return set_error(BD_ERR_INVALID, "n_beads must be a multiple of beads_per_chain >= 1");
+    if ((int64_t)p->n_beads * 3 > (int64_t)1 << 20)
+        return set_error(BD_ERR_UNSUPPORTED, "3N = %lld exceeds this build's limit 2^20",
+                         (long long)p->n_beads * 3);
+    if (!(p->box_L > 0.0)) return set_error(BD_ERR_INVALID, "box_L must be > 0");
+    if (!(p->a >= 0.0) || !(2.0 * p->a < p->box_L))
+        return set_error(BD_ERR_INVALID, "need 0 <= a and 2a < L (a=%g, L=%g)", p->a, p->box_L);
+    if (!(p->alpha > 0.0)) return set_error(BD_ERR_INVALID, "alpha must be > 0");
+    if (!(p->r_c > 0.0) || p->r_c / p->box_L > 64.0)
+        return set_error(BD_ERR_INVALID, "r_c must satisfy 0 < r_c <= 64 L");
+    if (p->n2max < 0 || p->n2max > 4096)
+        return set_error(BD_ERR_INVALID, "n2max must be in [0, 4096]");
+    if (p->spring != 0 && p->spring != 1)
+        return set_error(BD_ERR_INVALID, "spring must be 0 (Hookean) or 1 (FENE)");
+    if (p->spring == 1 && !(p->fene_b > 0.0))
+        return set_error(BD_ERR_INVALID, "FENE needs fene_b > 0");
+    if (p->ev_on && (!(p->d_star > 0.0) || !(p->r_ev >= 0.0) || p->r_ev / p->box_L > 64.0))
+        return set_error(BD_ERR_INVALID, "excluded volume needs d_star > 0, 0 <= r_ev <= 64 L");
+    if (p->precision < BD_FP64 || p->precision > BD_MIXED_BF16)
+        return set_error(BD_ERR_INVALID, "unknown precision %d", p->precision);
+    if (p->max_rhs < 1 || p->max_rhs > kMaxRhs)
+        return set_error(BD_ERR_INVALID, "max_rhs must be in [1, %d]", kMaxRhs);
+    if (p->max_cheb < 2 || p->max_cheb > kMaxCheb)
+        return set_error(BD_ERR_INVALID, "max_cheb must be in [2, %d]", kMaxCheb);
+    if (!(p->dt >= 0.0)) return set_error(BD_ERR_INVALID, "dt must be >= 0");
+    return BD_OK;
+}
+
+}  // namespace bd
+
+using namespace bd;
+
+extern "C" {
+
+const char *bd_last_error(void) { return g_err; }
+
+const char *bd_version(void) { return "libbdgb 0.1 (sm_103a)"; }
+
+uint64_t bd_kernel_launches(void) { return __atomic_load_n(&g_launches, __ATOMIC_RELAXED); }
+
+bd_status bd_set_phase_events(bd_plan *plan, void *const *events, int32_t count)
+{
+    if (!plan) return set_error(BD_ERR_INVALID, "NULL plan");
+    Plan &P = plan->P;
+    if (!events) {
+        P.phase_on = 0;
+        return BD_OK;
+    }
+    if (count != BD_PHASE_EVENTS)
+        return set_error(BD_ERR_INVALID, "phase events: count must be %d", BD_PHASE_EVENTS);
+    for (int i = 0; i < BD_PHASE_EVENTS; i++) {
+        if (!events[i]) return set_error(BD_ERR_INVALID, "phase event %d is NULL", i);
+        P.phase_ev[i] = (cudaEvent_t)events[i];
+    }
+    P.phase_on = 1;
+    return BD_OK;
+}
+
+bd_status bd_plan_create(const bd_params *params, bd_plan **out_plan)
+{
+    g_err[0] = 0;
+    if (!out_plan) return set_error(BD_ERR_INVALID, "out_plan is NULL");
+    *out_plan = nullptr;
+    bd_status st = validate(params);
+    if (st != BD_OK) return st;
+    bd_plan *pl = new (std::nothrow) bd_plan();
+    if (!pl) return set_error(BD_ERR_OOM, "host allocation failed");
+    Plan &P = pl->P;
+    memset(&P, 0, sizeof(P));
+    P.p = *params;
+    cudaGetDevice(&P.device);
+    P.n = params->n_beads;
+    P.n3 = 3 * P.n;
+    P.ld = (P.n3 + kLdAlign - 1) / kLdAlign * kLdAlign;
+    const size_t n3 = P.n3, R = params->max_rhs;
+    const bool mixed = params->precision != BD_FP64;
+#define TRY(x)                       \
+    do {                             \
+        st = (x);                    \
+        if (st != BD_OK) goto fail;  \
+    } while (0)
+    TRY(dmalloc(P, &P.d_kvec, kMaxKvec));
+    TRY(dmalloc(P, &P.d_ewc, 1));
+    TRY(dmalloc(P, &P.d_F, n3));
+    TRY(dmalloc(P, &P.d_DF, n3));
+    TRY(dmalloc(P, &P.d_Rnew, n3));
+    for (int i = 0; i < 3; i++) TRY(dmalloc(P, &P.d_V[i], n3 * R));
+    TRY(dmalloc(P, &P.d_X0, n3 * (R + 1)));
+    TRY(dmalloc(P, &P.d_Y0, n3 * (R + 1)));
+    TRY(dmalloc(P, &P.d_dS, n3 * R));
+    TRY(dmalloc(P, &P.d_dW, n3 * R));
+    TRY(dmalloc(P, &P.d_coef, kMaxCheb));
+    TRY(dmalloc(P, &P.d_wdw, kMaxRhs));
+    TRY(dmalloc(P, &P.d_red, 4 * kMaxRhs));
+    TRY(dmalloc(P, &P.d_bounds, 2));
+    TRY(dmalloc(P, &P.d_status, 8));
+    for (int i = 0; i < 3; i++) TRY(dmalloc(P, &P.d_lq[i], n3));
+    TRY(dmalloc(P, &P.d_lab, 2 * kMaxLanczos));
+    TRY(dmalloc(P, &P.d_stats_scratch, 1));
+    {
+        cudaStream_t s = 0;
+        launch_kvec_table(P, s);
+        if (P.nk > kMaxKvec) {
+            st = set_error(BD_ERR_UNSUPPORTED, "%d half-space k-vectors exceed the limit %d",
+                           P.nk, kMaxKvec);
+            goto fail;
+        }
+        TRY(check_launch("plan tables"));
+        size_t nkn = (size_t)(P.nk > 0 ? P.nk : 1) * P.n;
+        TRY(dmalloc(P, &P.d_cos, nkn));
+        TRY(dmalloc(P, &P.d_sin, nkn));
+        if (mixed) {
+            TRY(dmalloc(P, &P.d_cos32, nkn));
+            TRY(dmalloc(P, &P.d_sin32, nkn));
+            TRY(tc_plan_init(P));
+        }
+        if (cudaDeviceSynchronize() != cudaSuccess) {
+            st = check_launch("plan creation");
+            goto fail;
+        }
+    }
+#undef TRY
+    *out_plan = pl;
+    return BD_OK;
+fail:
+    free_plan(P);
+    delete pl;
+    return st;
+}
+
+void bd_plan_destroy(bd_plan *plan)
+{
+    if (!plan) return;
+    cudaDeviceSynchronize();
+    free_plan(plan->P);
+    delete plan;
+}
+
+bd_status bd_plan_query(const bd_plan *plan, bd_plan_info *info)
+{
+    if (!plan || !info) return set_error(BD_ERR_INVALID, "NULL argument");
+    const Plan &P = plan->P;
+    info->n3 = P.n3;
+    info->ld = P.ld;
+    info->d_bytes = (int64_t)P.n3 * P.ld * (is_mixed(P) ? 6 : 8);
+    info->n_kvec = P.nk;
+    info->precision = P.p.precision;
+    info->scratch_bytes = P.scratch_bytes;
+    return BD_OK;
+}
+
+bd_status bd_forces(bd_plan *plan, const double *R, double *F, int32_t *n_bad, bd_stream stream)
+{
+    if (!plan || !R || !F) return set_error(BD_ERR_INVALID, "NULL argument");
+    if (n_bad) cudaMemsetAsync(n_bad, 0, sizeof(int32_t), stream);
+    launch_forces(plan->P, R, F, n_bad, stream);
+    return check_launch("bd_forces");
+}
+
+static void split_mixed(const Plan &P, void *D, float **D32, void **D16)
+{
+    *D32 = (float *)D;
+    *D16 = (void *)((char *)D + (size_t)P.n3 * P.ld * 4);
+}
+
+bd_status bd_build_D(bd_plan *plan, const double *R, void *D, bd_stream stream)
+{
+    if (!plan || !R || !D) return set_error(BD_ERR_INVALID, "NULL argument");
+    Plan &P = plan->P;
+    if (((uintptr_t)D & 255) != 0) return set_error(BD_ERR_INVALID, "D must be 256-byte aligned");
+    if (!is_mixed(P)) {
+        launch_build_D_f64(P, R, (double *)D, stream);
+    } else {
+        float *D32;
+        void *D16;
+        split_mixed(P, D, &D32, &D16);
+        launch_build_D_f32(P, R, D32, D16, P.p.precision == BD_MIXED_BF16, stream);
+    }
+    return check_launch("bd_build_D");
+}
+
+// Y = D X for the plan's precision (no refinement)
+static bd_status apply_core(Plan &P, const void *D, const double *X, int m, double *Y,
+                            int flags, cudaStream_t s)
+{
+    if (!is_mixed(P)) {
+        launch_gemm_f64(P, (const double *)D, X, m, Y, s);
+        return check_launch("gemm_f64");
+    }
+    float *D32;
+    void *D16;
+    split_mixed(P, (void *)D, &D32, &D16);
+    bd_status st = tc_apply(P, D16, X, m, Y, s);
+    if (st != BD_OK) return st;
+    if (flags & BD_APPLY_REFINE) {
+        launch_refine_f32(P, D32, X, m, Y, s);
+        return check_launch("refine");
+    }
+    return BD_OK;
+}
+
+bd_status bd_apply_D(bd_plan *plan, const void *D, const double *X, int32_t m, double *Y,
+                     int32_t flags, bd_stream stream)
+{
+    if (!plan || !D || !X || !Y) return set_error(BD_ERR_INVALID, "NULL argument");
+    Plan &P = plan->P;
+    if (m < 1 || m > P.p.max_rhs) return set_error(BD_ERR_INVALID, "m=%d outside [1, max_rhs=%d]", m, P.p.max_rhs);
+    const char *xb = (const char *)X, *yb = (const char *)Y;
+    size_t bytes = (size_t)P.n3 * m * sizeof(double);
+    if (xb < yb + bytes && yb < xb + bytes) return set_error(BD_ERR_INVALID, "X and Y overlap");
+    return apply_core(P, D, X, m, Y, flags, stream);
+}
+
+static bd_status eig_bounds_core(Plan &P, const void *D, int iters, double smax, double fmin_,
+                                 double *bounds, int32_t *status, cudaStream_t s)
+{
+    int k = iters < P.n3 ? iters : P.n3;
+    launch_lanczos_init(P, s);
+    for (int j = 0; j < k; j++) {
+        bd_status st = apply_core(P, D, P.d_lq[1], 1, P.d_lq[2], 0, s);
+        if (st != BD_OK) return st;
+        launch_lanczos_update(P, j, s);
+    }
+    launch_lanczos_finish(P, k, smax, fmin_, bounds, status, s);
+    return check_launch("bd_eig_bounds");
+}
+
+bd_status bd_eig_bounds(bd_plan *plan, const void *D, int32_t iters, double safety_max,
+                        double dmin_fraction, double *bounds, int32_t *status, bd_stream stream)
+{
+    if (!plan || !D || !bounds) return set_error(BD_ERR_INVALID, "NULL argument");
+    if (iters < 1 || iters > kMaxLanczos)
+        return set_error(BD_ERR_INVALID, "iters must be in [1, %d]", kMaxLanczos);
+    if (!(safety_max >= 0.0) || !(dmin_fraction > 0.0) || !(dmin_fraction <= 1.0))
+        return set_error(BD_ERR_INVALID, "need safety_max >= 0 and 0 < dmin_fraction <= 1");
+    return eig_bounds_core(plan->P, D, iters, safety_max, dmin_fraction, bounds, status, stream);
+}
+
+// Chebyshev recurrence given W = D dW; dS and E_f outputs
+static bd_status cheb_core(Plan &P, const void *D, const double *bounds, int nch,
+                           const double *dW, const double *W, int m, double *dS, double *Ef,
+                           bd_step_stats *stats, cudaStream_t s)
+{
+    launch_cheb_coeffs(P, bounds, nch, s);
+    double *A = P.d_V[0], *B = P.d_V[1];
+    launch_cheb_first(P, bounds, dW, W, m, A, B, dS, s);   // A = V0, B = V1
+    double *prev2 = A, *prev1 = B;
+    for (int p = 2; p < nch; p++) {
+        if (!is_mixed(P)) {
+            ChebEpi e{P.d_coef, bounds, p, prev2, prev1, dS};
+            launch_gemm_f64_cheb(P, (const double *)D, m, e, s);
+        } else {
+            float *D32;
+            void *D16;
+            split_mixed(P, (void *)D, &D32, &D16);
+            bd_status st = tc_cheb(P, D16, m, P.d_coef, bounds, p, prev2, prev1, dS, s);
+            if (st != BD_OK) return st;
+        }
+        double *t = prev2;   // prev2 now holds V_p
+        prev2 = prev1;
+        prev1 = t;
+    }
+    launch_ef(P, dW, W, dS, m, Ef, stats, s);
+    return check_launch("chebyshev");
+}
+
+bd_status bd_chebyshev_sqrt(bd_plan *plan, const void *D, const double *bounds, int32_t n_cheb,
+                            const double *dW, int32_t m, double *dS, double *Ef,
+                            bd_stream stream)
+{
+    if (!plan || !D || !bounds || !dW || !dS) return set_error(BD_ERR_INVALID, "NULL argument");
+    Plan &P = plan->P;
+    if (m < 1 || m > P.p.max_rhs) return set_error(BD_ERR_INVALID, "m=%d outside [1, max_rhs=%d]", m, P.p.max_rhs);
+    if (n_cheb < 2 || n_cheb > P.p.max_cheb)
+        return set_error(BD_ERR_INVALID, "n_cheb=%d outside [2, max_cheb=%d]", n_cheb, P.p.max_cheb);
+    bd_status st = apply_core(P, D, dW, m, P.d_V[2], 0, stream);
+    if (st != BD_OK) return st;
+    return cheb_core(P, D, bounds, n_cheb, dW, P.d_V[2], m, dS, Ef, nullptr, stream);
+}
+
+bd_status bd_wiener(bd_plan *plan, uint64_t seed, uint64_t step_index, int64_t count,
+                    double *out, bd_stream stream)
+{
+    if (!plan || !out || count < 0) return set_error(BD_ERR_INVALID, "bad argument");
+    if (count == 0) return BD_OK;
+    launch_wiener(plan->P, seed, step_index, count, out, stream);
+    return check_launch("bd_wiener");
+}
+
+bd_status bd_step(bd_plan *plan, double *R, void *D, const double *dW, const bd_step_opts *o,
+                  double *DF, double *dS, bd_step_stats *stats, bd_stream stream)
+{
+    if (!plan || !R || !D || !o) return set_error(BD_ERR_INVALID, "NULL argument");
+    Plan &P = plan->P;
+    const int m = o->m;
+    if (m < 1 || m > P.p.max_rhs) return set_error(BD_ERR_INVALID, "m=%d outside [1, max_rhs=%d]", m, P.p.max_rhs);
+    if (o->n_cheb < 2 || o->n_cheb > P.p.max_cheb)
+        return set_error(BD_ERR_INVALID, "n_cheb outside [2, max_cheb]");
+    if (o->lanczos_iters < 1 || o->lanczos_iters > kMaxLanczos)
+        return set_error(BD_ERR_INVALID, "lanczos_iters outside [1, %d]", kMaxLanczos);
+    if (!(o->bound_safety >= 0.0) || !(o->dmin_fraction > 0.0) || !(o->dmin_fraction <= 1.0))
+        return set_error(BD_ERR_INVALID, "need bound_safety >= 0, 0 < dmin_fraction <= 1");
+    if (((uintptr_t)D & 255) != 0) return set_error(BD_ERR_INVALID, "D must be 256-byte aligned");
+    cudaStream_t s = stream;
+    bd_step_stats *st_dev = stats ? stats : P.d_stats_scratch;
+    const size_t n3 = P.n3;
+    bd_status st;
+#define PHASE(i) \
+    do { if (P.phase_on) cudaEventRecord(P.phase_ev[i], s); } while (0)
+    PHASE(0);
+    launch_stats_begin(st_dev, o->n_cheb, s);
+    cudaMemsetAsync(P.d_status, 0, 8 * sizeof(int32_t), s);
+    // (a1) forces; input over-stretch count in status word 2
+    launch_forces(P, R, P.d_F, P.d_status + 2, s);
+    PHASE(1);
+    // (a2-a4) D(R)
+    st = bd_build_D(plan, R, D, s);
+    if (st != BD_OK) return st;
+    PHASE(2);
+    // (a6) bounds
+    st = eig_bounds_core(P, D, o->lanczos_iters, o->bound_safety, o->dmin_fraction, P.d_bounds,
+                         P.d_status + 3, s);
+    if (st != BD_OK) return st;
+    launch_stats_bounds(st_dev, P.d_bounds, P.d_status + 3, s);
+    PHASE(3);
+    // Wiener increments
+    const double *w = dW;
+    if (!w) {
+        launch_wiener(P, o->seed, o->step_index, (int64_t)n3 * m, P.d_dW, s);
+        w = P.d_dW;
+    }
+    // (a5) first product D [F, dW]  (one pass over D)
+    double *Wcols;
+    if (m + 1 <= kMaxRhs && m + 1 <= P.p.max_rhs + 1) {
+        cudaMemcpyAsync(P.d_X0, P.d_F, n3 * sizeof(double), cudaMemcpyDeviceToDevice, s);
+        cudaMemcpyAsync(P.d_X0 + n3, w, n3 * m * sizeof(double), cudaMemcpyDeviceToDevice, s);
+        st = apply_core(P, D, P.d_X0, m + 1, P.d_Y0, 0, s);
+        if (st != BD_OK) return st;
+        Wcols = P.d_Y0 + n3;
+        if (is_mixed(P)) {   // refine the drift column only
+            launch_refine_f32(P, (const float *)D, P.d_F, 1, P.d_Y0, s);
+        }
+    } else {
+        st = apply_core(P, D, P.d_F, 1, P.d_Y0, BD_APPLY_REFINE, s);
+        if (st != BD_OK) return st;
+        st = apply_core(P, D, w, m, P.d_Y0 + n3, 0, s);
+        if (st != BD_OK) return st;
+        Wcols = P.d_Y0 + n3;
+    }
+    const double *DFd = P.d_Y0;
+    PHASE(4);
+    // (a7) Chebyshev
+    double *dSd = dS ? dS : P.d_dS;
+    st = cheb_core(P, D, P.d_bounds, o->n_cheb, w, Wcols, m, dSd, nullptr, st_dev, s);
+    if (st != BD_OK) return st;
+    PHASE(5);
+    // (a8) Euler update with FENE rejection
+    launch_euler(P, R, DFd, dSd, st_dev, s);
+    PHASE(6);
+#undef PHASE
+    if (DF) cudaMemcpyAsync(DF, DFd, n3 * sizeof(double), cudaMemcpyDeviceToDevice, s);
+    return check_launch("bd_step");
+}
+
+}  // extern "C"

@@ -1,0 +1,130 @@
+// bd_internal.cuh -- internal declarations shared by the CUDA translation
+// units of libbdgb (plan layout, launch helpers, error plumbing).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cuda_fp16.h>
+#include <cuda_bf16.h>
+#include <stdint.h>
+
+#include "../../include/bd.h"
+
+namespace bd {
+
+// Half-space reciprocal vector with its M2 tensor folded with the +/-k pair:
+// m[0..5] = 2 f(k) (delta_ab - khat_a khat_b) for ab = xx, xy, xz, yy, yz, zz.
+struct KVec {
+    double k[3];
+    double m[6];
+};
+
+// Ewald coefficients of Eq. (M1) with 1/sqrt(pi) folded in, in the form
+//   c1 = erfc(alpha r)/r (A1 + A3/r^2) + e^{-alpha^2 r^2} (P0 + P1 r^2 + P2 r^4 + Q/r^2)
+//   c2 = erfc(alpha r)/r (A1 - 3 A3/r^2) + e^{-alpha^2 r^2} (R0 + R1 r^2 + R2 r^4 + S/r^2)
+// computed once per plan on the device in FP64.
+struct EwaldCoef {
+    double alpha, alpha2, a, L, invL, rc2, four_a2;
+    double A1, A3, P0, P1, P2, Q, R0, R1, R2, S;
+    double self;                 // 1 - 6 a alpha/sqrt(pi) + 40 a^3 alpha^3/(3 sqrt(pi))
+    double g1a, g1b, g2a, g2b;   // a alpha, a^3 alpha^3, a alpha^3, a^3 alpha^5 (each / sqrt(pi))
+    double inv_a;
+};
+
+constexpr int kMaxKvec = 4096;        // half-space k-vectors a plan may use
+constexpr int kMaxRhs = 32;           // Wiener columns per product
+constexpr int kMaxCheb = 256;         // Chebyshev terms
+constexpr int kMaxLanczos = 128;      // Lanczos steps
+constexpr int kLdAlign = 64;          // D leading dimension multiple (elements)
+
+struct Plan {
+    bd_params p;
+    int device;
+    int n, n3, ld;
+    int nk;                            // half-space k-vectors in use
+    double self_coeff;                 // self term of Eq. (DF)
+    KVec *d_kvec;                      // [nk], device
+    EwaldCoef *d_ewc;                  // Eq. (M1) coefficients, device
+    // per-bead trig tables for the reciprocal sum: cos/sin(k_t . r_nu),
+    // stored [t][nu] (FP64) for the current R
+    double *d_cos, *d_sin;
+    float *d_cos32, *d_sin32;
+    // scratch vectors (3N x max_rhs, column-major, FP64)
+    double *d_F, *d_DF;                // forces and drift (3N)
+    double *d_Rnew;                    // proposed positions (3N)
+    double *d_V[3];                    // Chebyshev recurrence buffers (3N x max_rhs)
+    double *d_X0, *d_Y0;               // first product [F, dW] and its image (3N x (max_rhs+1))
+    double *d_dS;                      // noise when the caller passes no dS
+    double *d_dW;                      // Wiener block when generated on device
+    double *d_coef;                    // Chebyshev coefficients [kMaxCheb]
+    double *d_wdw;                     // dW.D.dW per column [kMaxRhs]
+    double *d_red;                     // reduction scratch [4*kMaxRhs]
+    double *d_bounds;                  // {d_min, d_max}
+    int32_t *d_status;                 // device status words [8]
+    // Lanczos
+    double *d_lq[3];                   // q_{j-1}, q_j, w (3N each)
+    double *d_lab;                     // alpha_j [kMaxLanczos], beta_j [kMaxLanczos]
+    // mixed precision operand scratch: X^T in 16 bits, [kMaxRhsPad][ldx]
+    void *d_x16;
+    float *d_xscale;                   // per-column power-of-two scale
+    float *d_part;                     // split-K partial sums
+    int32_t *d_counters;               // split-K arrival counters
+    int ldx;                           // leading dimension of d_x16 (elements)
+    int64_t scratch_bytes;
+    bd_step_stats *d_stats_scratch;
+    cudaEvent_t phase_ev[BD_PHASE_EVENTS];
+    int phase_on;
+    float *d_y32;                      // FP32 product scratch (mixed plans)
+};
+
+// host-side count of kernel launches (bd_kernel_launches)
+void count_launches(int k);
+
+// error plumbing (thread-local message)
+bd_status set_error(bd_status st, const char *fmt, ...);
+bd_status check_launch(const char *what);
+
+// ---- launchers (defined in the .cu files) ---------------------------------
+// ewald_build.cu
+void launch_kvec_table(Plan &P, cudaStream_t s);
+void launch_trig_tables(Plan &P, const double *R, cudaStream_t s);
+void launch_build_D_f64(Plan &P, const double *R, double *D, cudaStream_t s);
+void launch_build_D_f32(Plan &P, const double *R, float *D32, void *D16, int is_bf16,
+                        cudaStream_t s);
+
+// dense_f64.cu : Y = D X (FP64), epilogue variants
+struct ChebEpi {
+    const double *coef;       // device coefficients
+    const double *bounds;     // device {dmin, dmax}
+    int p;                    // term index being produced (>= 2)
+    double *Vprev2;           // in: V_{p-2}, out: V_p (in place)
+    const double *Vprev1;     // V_{p-1} (also the B operand)
+    double *dS;               // accumulated sum
+};
+void launch_gemm_f64(const Plan &P, const double *D, const double *X, int m, double *Y,
+                     cudaStream_t s);
+void launch_gemm_f64_cheb(const Plan &P, const double *D, int m, const ChebEpi &e,
+                          cudaStream_t s);
+
+// vec_kernels.cu
+void launch_forces(Plan &P, const double *R, double *F, int32_t *n_bad, cudaStream_t s);
+void launch_cheb_coeffs(Plan &P, const double *bounds, int nch, cudaStream_t s);
+void launch_cheb_first(Plan &P, const double *bounds, const double *dW, const double *DW, int m,
+                       double *V0, double *V1, double *dS, cudaStream_t s);
+void launch_ef(Plan &P, const double *dW, const double *DW, const double *dS, int m,
+               double *Ef, bd_step_stats *stats, cudaStream_t s);
+void launch_wiener(Plan &P, uint64_t seed, uint64_t step, int64_t count, double *out,
+                   cudaStream_t s);
+void launch_lanczos_init(Plan &P, cudaStream_t s);
+void launch_lanczos_update(Plan &P, int j, cudaStream_t s);
+void launch_lanczos_finish(Plan &P, int k, double safety_max, double dmin_fraction,
+                           double *bounds, int32_t *status, cudaStream_t s);
+void launch_stats_begin(bd_step_stats *st, int nch, cudaStream_t s);
+void launch_stats_bounds(bd_step_stats *st, const double *bounds, const int32_t *bstatus,
+                         cudaStream_t s);
+void launch_euler(Plan &P, double *R, const double *DF, const double *dS, bd_step_stats *stats,
+                  cudaStream_t s);
+void launch_dot_cols(const double *A, const double *B, int n3, int m, double *out,
+                     cudaStream_t s);
+void launch_zero_i32(int32_t *p, int n, cudaStream_t s);
+
+}  // namespace bd

@@ -1,0 +1,495 @@
+// vec_kernels.cu -- the O(N) and O(N m) parts of the step: forces (Sec. II A),
+// Chebyshev coefficients and first term (Eqs. cheb1-cheb3), the error
+// estimate E_f (Sec. IV), Lanczos bounds (FP64 recurrence, bisection on the
+// tridiagonal matrix), the device Wiener generator (Philox4x32-10 + Box-
+// Muller) and the Euler update with FENE rejection (Eq. sde, Sec. VII).
+#include <math.h>
+
+#include "bd_internal.cuh"
+
+namespace bd {
+
+constexpr double kPi = 3.14159265358979323846;
+
+__device__ __forceinline__ double warp_sum(double v)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// block-wide sum, result valid in thread 0
+__device__ double block_sum(double v)
+{
+    __shared__ double sh[32];
+    int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    v = warp_sum(v);
+    if (lane == 0) sh[w] = v;
+    __syncthreads();
+    int nw = (blockDim.x + 31) >> 5;
+    v = threadIdx.x < nw ? sh[threadIdx.x] : 0.0;
+    if (w == 0) v = warp_sum(v);
+    __syncthreads();
+    return v;
+}
+
+// ---------------------------------------------------------------------------
+// Forces
+
+// springs: F^c(Q_mu) - F^c(Q_{mu-1}), Hookean F^c = Q, FENE F^c = Q/(1-Q^2/b)
+__global__ void k_springs(const double *R, int n, int nb, int fene, double b, double *F,
+                          int32_t *n_bad)
+{
+    int nu = blockIdx.x * blockDim.x + threadIdx.x;
+    if (nu >= n) return;
+    int j = nu % nb;
+    double f[3] = {0.0, 0.0, 0.0};
+    int bad = 0;
+    if (j + 1 < nb) {            // spring to the next bead: +F^c(Q_nu)
+        double Q[3], q2 = 0.0;
+        for (int s = 0; s < 3; s++) { Q[s] = R[3 * (nu + 1) + s] - R[3 * nu + s]; q2 += Q[s] * Q[s]; }
+        double g = 1.0;
+        if (fene) {
+            if (q2 >= b) { g = NAN; bad = 1; }
+            else g = 1.0 / (1.0 - q2 / b);
+        }
+        for (int s = 0; s < 3; s++) f[s] += g * Q[s];
+    }
+    if (j > 0) {                 // spring from the previous bead: -F^c(Q_{nu-1})
+        double Q[3], q2 = 0.0;
+        for (int s = 0; s < 3; s++) { Q[s] = R[3 * nu + s] - R[3 * (nu - 1) + s]; q2 += Q[s] * Q[s]; }
+        double g = 1.0;
+        if (fene) g = (q2 >= b) ? NAN : 1.0 / (1.0 - q2 / b);
+        for (int s = 0; s < 3; s++) f[s] -= g * Q[s];
+    }
+    for (int s = 0; s < 3; s++) F[3 * nu + s] = f[s];
+    if (bad && n_bad) atomicAdd(n_bad, 1);
+}
+
+// narrow-Gaussian excluded volume over all pairs and periodic images with
+// |r| <= r_ev: F_nu += (z*/d*^5) r exp(-r^2/(2 d*^2))
+__global__ void k_ev(const double *R, int n, double L, double pref, double inv2d2, double rev2,
+                     int nmax, double *F)
+{
+    __shared__ double sr[3 * 128];
+    int nu = blockIdx.x * blockDim.x + threadIdx.x;
+    double rn[3] = {0, 0, 0};
+    if (nu < n) for (int s = 0; s < 3; s++) rn[s] = R[3 * nu + s];
+    double acc[3] = {0.0, 0.0, 0.0};
+    const double invL = 1.0 / L;
+    for (int base = 0; base < n; base += 128) {
+        __syncthreads();
+        for (int i = threadIdx.x; i < 3 * 128; i += blockDim.x) {
+            int b = base * 3 + i;
+            sr[i] = b < 3 * n ? R[b] : 0.0;
+        }
+        __syncthreads();
+        if (nu < n) {
+            int lim = min(128, n - base);
+            for (int q = 0; q < lim; q++) {
+                int mu = base + q;
+                if (mu == nu) continue;
+                double d[3];
+                for (int s = 0; s < 3; s++) {
+                    double x = rn[s] - sr[3 * q + s];
+                    d[s] = x - L * rint(x * invL);
+                }
+                for (int ix = -nmax; ix <= nmax; ix++) {
+                    double vx = d[0] + ix * L;
+                    if (vx * vx > rev2) continue;
+                    for (int iy = -nmax; iy <= nmax; iy++) {
+                        double vy = d[1] + iy * L;
+                        if (vx * vx + vy * vy > rev2) continue;
+                        for (int iz = -nmax; iz <= nmax; iz++) {
+                            double vz = d[2] + iz * L;
+                            double u = vx * vx + vy * vy + vz * vz;
+                            if (u > rev2) continue;
+                            double w = pref * exp(-u * inv2d2);
+                            acc[0] += w * vx; acc[1] += w * vy; acc[2] += w * vz;
+                        }
+                    }
+                }
+            }
+        }
+    }
+    if (nu < n) for (int s = 0; s < 3; s++) F[3 * nu + s] += acc[s];
+}
+
+void launch_forces(Plan &P, const double *R, double *F, int32_t *n_bad, cudaStream_t s)
+{
+    int n = P.n;
+    k_springs<<<(n + 127) / 128, 128, 0, s>>>(R, n, P.p.beads_per_chain, P.p.spring == 1,
+                                               P.p.fene_b, F, n_bad);
+    count_launches(1);
+    if (P.p.ev_on) {
+        double d = P.p.d_star;
+        double pref = P.p.z_star / (d * d * d * d * d);
+        int nmax = (int)floor(P.p.r_ev / P.p.box_L + 0.5) + 1;
+        k_ev<<<(n + 127) / 128, 128, 0, s>>>(R, n, P.p.box_L, pref, 1.0 / (2.0 * d * d),
+                                              P.p.r_ev * P.p.r_ev, nmax, F);
+        count_launches(1);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Chebyshev (Sec. IV)
+
+// c_p = (2/N) sum_j sqrt(h cos t_j + mid) cos(p t_j), t_j = pi (j + 1/2)/N:
+// the coefficients of the Chebyshev interpolant of sqrt on [d_min, d_max].
+__global__ void k_cheb_coeffs(const double *bounds, int nch, double *c)
+{
+    int p = threadIdx.x;
+    double dmin = bounds[0], dmax = bounds[1];
+    double h = 0.5 * (dmax - dmin), mid = 0.5 * (dmax + dmin);
+    for (; p < nch; p += blockDim.x) {
+        double s = 0.0;
+        for (int j = 0; j < nch; j++) {
+            double t = kPi * (j + 0.5) / nch;
+            s += sqrt(h * cos(t) + mid) * cos(p * t);
+        }
+        c[p] = 2.0 * s / nch;
+    }
+}
+
+void launch_cheb_coeffs(Plan &P, const double *bounds, int nch, cudaStream_t s)
+{
+    k_cheb_coeffs<<<1, 256, 0, s>>>(bounds, nch, P.d_coef);
+    count_launches(1);
+}
+
+// V0 = dW, V1 = Y V0 = s (D dW) - t dW, dS = (c0/2) dW + c1 V1
+__global__ void k_cheb_first(const double *dW, const double *DW, long len, const double *bounds,
+                             const double *coef, double *V0, double *V1, double *dS)
+{
+    long i = (long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= len) return;
+    double dmin = bounds[0], dmax = bounds[1];
+    double ys = 2.0 / (dmax - dmin), yt = (dmax + dmin) / (dmax - dmin);
+    double w = dW[i];
+    double v1 = ys * DW[i] - yt * w;
+    V0[i] = w;
+    V1[i] = v1;
+    dS[i] = coef[0] * w - 0.5 * coef[0] * w + coef[1] * v1;
+}
+
+void launch_cheb_first(Plan &P, const double *bounds, const double *dW, const double *DW, int m,
+                       double *V0, double *V1, double *dS, cudaStream_t s)
+{
+    long len = (long)P.n3 * m;
+    k_cheb_first<<<(unsigned)((len + 255) / 256), 256, 0, s>>>(dW, DW, len, bounds, P.d_coef, V0,
+                                                               V1, dS);
+    count_launches(1);
+}
+
+// out[j] += sum_i A[j n3 + i] B[j n3 + i]  (out zeroed by the caller)
+__global__ void k_dot_cols(const double *A, const double *B, int n3, double *out)
+{
+    int j = blockIdx.y;
+    double v = 0.0;
+    for (long i = (long)blockIdx.x * blockDim.x + threadIdx.x; i < n3;
+         i += (long)gridDim.x * blockDim.x)
+        v += A[(long)j * n3 + i] * B[(long)j * n3 + i];
+    v = block_sum(v);
+    if (threadIdx.x == 0) atomicAdd(&out[j], v);
+}
+
+void launch_dot_cols(const double *A, const double *B, int n3, int m, double *out,
+                     cudaStream_t s)
+{
+    cudaMemsetAsync(out, 0, sizeof(double) * m, s);
+    int bx = min(64, (n3 + 255) / 256);
+    k_dot_cols<<<dim3(bx, m), 256, 0, s>>>(A, B, n3, out);
+    count_launches(1);
+}
+
+// E_f = sqrt(|dS.dS - dW.D.dW| / dW.D.dW) per column; stats->ef_max
+__global__ void k_ef(const double *ss, const double *wdw, int m, double *Ef, bd_step_stats *st)
+{
+    if (threadIdx.x != 0) return;
+    double mx = 0.0;
+    for (int j = 0; j < m; j++) {
+        double e = sqrt(fabs(ss[j] - wdw[j]) / wdw[j]);
+        if (Ef) Ef[j] = e;
+        mx = fmax(mx, e);
+    }
+    if (st) st->ef_max = mx;
+}
+
+void launch_ef(Plan &P, const double *dW, const double *DW, const double *dS, int m, double *Ef,
+               bd_step_stats *stats, cudaStream_t s)
+{
+    launch_dot_cols(dW, DW, P.n3, m, P.d_wdw, s);
+    launch_dot_cols(dS, dS, P.n3, m, P.d_red, s);
+    k_ef<<<1, 32, 0, s>>>(P.d_red, P.d_wdw, m, Ef, stats);
+    count_launches(1);
+}
+
+// ---------------------------------------------------------------------------
+// Philox4x32-10 (Salmon et al., SC'11) and Box-Muller
+
+__device__ __forceinline__ void philox4x32_10(uint32_t c[4], uint32_t k0, uint32_t k1)
+{
+#pragma unroll
+    for (int r = 0; r < 10; r++) {
+        uint32_t lo0 = 0xD2511F53u * c[0], hi0 = __umulhi(0xD2511F53u, c[0]);
+        uint32_t lo1 = 0xCD9E8D57u * c[2], hi1 = __umulhi(0xCD9E8D57u, c[2]);
+        uint32_t y0 = hi1 ^ c[1] ^ k0, y2 = hi0 ^ c[3] ^ k1;
+        c[0] = y0; c[1] = lo1; c[2] = y2; c[3] = lo0;
+        k0 += 0x9E3779B9u; k1 += 0xBB67AE85u;
+    }
+}
+
+__global__ void k_wiener(uint64_t seed, uint64_t step, int64_t count, double sdt, double *out)
+{
+    int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (2 * q >= count) return;
+    uint32_t c[4] = {(uint32_t)q, (uint32_t)((uint64_t)q >> 32), (uint32_t)step,
+                     (uint32_t)(step >> 32)};
+    philox4x32_10(c, (uint32_t)seed, (uint32_t)(seed >> 32));
+    uint64_t b1 = ((uint64_t)c[0] << 32) | c[1];
+    uint64_t b2 = ((uint64_t)c[2] << 32) | c[3];
+    double u1 = ((double)(b1 >> 11) + 0.5) * (1.0 / 9007199254740992.0);
+    double u2 = ((double)(b2 >> 11) + 0.5) * (1.0 / 9007199254740992.0);
+    double rr = sqrt(-2.0 * log(u1));
+    double sn, cs;
+    sincospi(2.0 * u2, &sn, &cs);
+    out[2 * q] = sdt * rr * cs;
+    if (2 * q + 1 < count) out[2 * q + 1] = sdt * rr * sn;
+}
+
+void launch_wiener(Plan &P, uint64_t seed, uint64_t step, int64_t count, double *out,
+                   cudaStream_t s)
+{
+    int64_t pairs = (count + 1) / 2;
+    k_wiener<<<(unsigned)((pairs + 255) / 256), 256, 0, s>>>(seed, step, count, sqrt(P.p.dt), out);
+    count_launches(1);
+}
+
+// ---------------------------------------------------------------------------
+// Lanczos: q_1 from a fixed Philox stream, then
+//   w = D q_j; alpha_j = q_j.w; w -= alpha_j q_j + beta_{j-1} q_{j-1};
+//   beta_j = |w|; q_{j+1} = w / beta_j.
+// d_lq[0] = q_{j-1}, d_lq[1] = q_j, d_lq[2] = w;  d_lab = {alpha[], beta[]}
+// d_red[0] = q_j.w, d_red[1] = |w|^2 (after the update)
+
+__global__ void k_lanczos_start(double *q, double *qprev, int n3)
+{
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n3) return;
+    uint32_t c[4] = {(uint32_t)i, 0u, 0x4C414E43u, 0u};
+    philox4x32_10(c, 0x5EEDu, 0xB0u);
+    q[i] = ((double)c[0] + 0.5) * (1.0 / 4294967296.0) - 0.5;
+    qprev[i] = 0.0;
+}
+
+__global__ void k_scale_by_inv_sqrt(double *q, int n3, const double *nrm2)
+{
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n3) q[i] *= rsqrt(*nrm2);
+}
+
+void launch_lanczos_init(Plan &P, cudaStream_t s)
+{
+    int n3 = P.n3;
+    k_lanczos_start<<<(n3 + 255) / 256, 256, 0, s>>>(P.d_lq[1], P.d_lq[0], n3);
+    count_launches(1);
+    launch_dot_cols(P.d_lq[1], P.d_lq[1], n3, 1, P.d_red + 2, s);
+    k_scale_by_inv_sqrt<<<(n3 + 255) / 256, 256, 0, s>>>(P.d_lq[1], n3, P.d_red + 2);
+    count_launches(1);
+}
+
+// w -= alpha q - beta_prev qprev; accumulate |w|^2
+__global__ void k_lanczos_orth(double *w, const double *q, const double *qprev, int n3,
+                               const double *alpha, const double *beta_prev, double *nrm2)
+{
+    double a = *alpha, b = beta_prev ? *beta_prev : 0.0;
+    double v = 0.0;
+    for (long i = (long)blockIdx.x * blockDim.x + threadIdx.x; i < n3;
+         i += (long)gridDim.x * blockDim.x) {
+        double x = w[i] - a * q[i] - b * qprev[i];
+        w[i] = x;
+        v += x * x;
+    }
+    v = block_sum(v);
+    if (threadIdx.x == 0) atomicAdd(nrm2, v);
+}
+
+// beta_j = sqrt(nrm2); qprev <- q; q <- w / beta_j
+__global__ void k_lanczos_shift(double *qprev, double *q, const double *w, int n3,
+                                const double *nrm2, double *beta)
+{
+    double bj = sqrt(*nrm2);
+    long i = (long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i == 0) *beta = bj;
+    if (i >= n3) return;
+    qprev[i] = q[i];
+    q[i] = bj > 0.0 ? w[i] / bj : 0.0;
+}
+
+// called after d_lq[2] = D q_j
+void launch_lanczos_update(Plan &P, int j, cudaStream_t s)
+{
+    int n3 = P.n3;
+    double *alpha = P.d_lab + j, *beta = P.d_lab + kMaxLanczos + j;
+    double *beta_prev = j > 0 ? P.d_lab + kMaxLanczos + j - 1 : nullptr;
+    launch_dot_cols(P.d_lq[1], P.d_lq[2], n3, 1, alpha, s);
+    cudaMemsetAsync(P.d_red + 1, 0, sizeof(double), s);
+    int bx = min(128, (n3 + 255) / 256);
+    k_lanczos_orth<<<bx, 256, 0, s>>>(P.d_lq[2], P.d_lq[1], P.d_lq[0], n3, alpha, beta_prev,
+                                      P.d_red + 1);
+    count_launches(1);
+    k_lanczos_shift<<<(n3 + 255) / 256, 256, 0, s>>>(P.d_lq[0], P.d_lq[1], P.d_lq[2], n3,
+                                                     P.d_red + 1, beta);
+    count_launches(1);
+}
+
+// number of eigenvalues of the k x k tridiagonal (alpha, beta) below x
+__device__ int sturm_count(const double *al, const double *be, int k, double x)
+{
+    int cnt = 0;
+    double q = al[0] - x;
+    if (q < 0) cnt++;
+    for (int i = 1; i < k; i++) {
+        double b2 = be[i - 1] * be[i - 1];
+        if (q == 0.0) q = 1e-300;
+        q = al[i] - x - b2 / q;
+        if (q < 0) cnt++;
+    }
+    return cnt;
+}
+
+// extreme Ritz values by bisection (Gershgorin bracket), then the widened
+// bounds {d_min, d_max} and a status word
+__global__ void k_lanczos_finish(const double *lab, int k, double smax, double fmin_,
+                                 double *bounds, int32_t *status)
+{
+    if (threadIdx.x != 0) return;
+    const double *al = lab, *be = lab + kMaxLanczos;
+    // stop at a breakdown (beta ~ 0: the Krylov space became invariant)
+    double scale = 0.0;
+    for (int i = 0; i < k; i++) scale = fmax(scale, fabs(al[i]));
+    for (int i = 0; i + 1 < k; i++)
+        if (!(fabs(be[i]) > 1e-13 * scale)) { k = i + 1; break; }
+    double lo = 1e300, hi = -1e300;
+    for (int i = 0; i < k; i++) {
+        double rad = (i > 0 ? fabs(be[i - 1]) : 0.0) + (i + 1 < k ? fabs(be[i]) : 0.0);
+        lo = fmin(lo, al[i] - rad);
+        hi = fmax(hi, al[i] + rad);
+    }
+    double th[2];
+    for (int w = 0; w < 2; w++) {
+        int target = (w == 0) ? 1 : k;        // count(x) >= target
+        double a = lo, b = hi;
+        for (int it = 0; it < 200 && b - a > 1e-15 * fmax(fabs(a), fabs(b)); it++) {
+            double mid = 0.5 * (a + b);
+            if (sturm_count(al, be, k, mid) >= target) b = mid;
+            else a = mid;
+        }
+        th[w] = 0.5 * (a + b);
+    }
+    double dmin = fmin_ * th[0], dmax = (1.0 + smax) * th[1];
+    bounds[0] = dmin;
+    bounds[1] = dmax;
+    if (status) *status = (dmin > 0.0 && dmax > dmin) ? BD_OK : BD_ERR_NOT_PD;
+}
+
+void launch_lanczos_finish(Plan &P, int k, double safety_max, double dmin_fraction,
+                           double *bounds, int32_t *status, cudaStream_t s)
+{
+    k_lanczos_finish<<<1, 32, 0, s>>>(P.d_lab, k, safety_max, dmin_fraction, bounds, status);
+    count_launches(1);
+}
+
+// stats bookkeeping for bd_step
+__global__ void k_stats_begin(bd_step_stats *st, int nch)
+{
+    st->d_min = 0.0; st->d_max = 0.0; st->ef_max = 0.0;
+    st->n_cheb = nch; st->n_overstretched = 0; st->accepted = 0; st->status = BD_OK;
+}
+
+__global__ void k_stats_bounds(bd_step_stats *st, const double *bounds, const int32_t *bstatus)
+{
+    st->d_min = bounds[0];
+    st->d_max = bounds[1];
+    if (*bstatus != BD_OK) st->status = *bstatus;
+}
+
+void launch_stats_begin(bd_step_stats *st, int nch, cudaStream_t s)
+{
+    k_stats_begin<<<1, 1, 0, s>>>(st, nch);
+    count_launches(1);
+}
+
+void launch_stats_bounds(bd_step_stats *st, const double *bounds, const int32_t *bstatus,
+                         cudaStream_t s)
+{
+    k_stats_bounds<<<1, 1, 0, s>>>(st, bounds, bstatus);
+    count_launches(1);
+}
+
+// ---------------------------------------------------------------------------
+// Euler update, Eq. (sde) with kappa = 0, and FENE rejection
+
+__global__ void k_euler_propose(const double *R, const double *DF, const double *dS, int n3,
+                                double dt, double *Rn)
+{
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n3) return;
+    Rn[i] = R[i] + 0.25 * dt * DF[i] + dS[i] * 0.70710678118654752440;
+}
+
+__global__ void k_fene_check(const double *Rn, int n, int nb, double b, int32_t *over)
+{
+    int nu = blockIdx.x * blockDim.x + threadIdx.x;
+    if (nu >= n || (nu % nb) + 1 >= nb) return;
+    double q2 = 0.0;
+    for (int s = 0; s < 3; s++) {
+        double q = Rn[3 * (nu + 1) + s] - Rn[3 * nu + s];
+        q2 += q * q;
+    }
+    if (q2 >= b) atomicAdd(over, 1);
+}
+
+__global__ void k_commit(double *R, const double *Rn, int n3, const int32_t *over,
+                         const int32_t *in_bad, bd_step_stats *st)
+{
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    bool ok = (*over == 0) && (*in_bad == 0);
+    if (ok && i < n3) R[i] = Rn[i];
+    if (i == 0 && st) {
+        st->n_overstretched = *over;
+        st->accepted = ok ? 1 : 0;
+        if (!ok) st->status = BD_ERR_FENE_STRETCH;
+    }
+}
+
+void launch_euler(Plan &P, double *R, const double *DF, const double *dS, bd_step_stats *stats,
+                  cudaStream_t s)
+{
+    int n3 = P.n3;
+    k_euler_propose<<<(n3 + 255) / 256, 256, 0, s>>>(R, DF, dS, n3, P.p.dt, P.d_Rnew);
+    count_launches(1);
+    int32_t *over = P.d_status + 1;
+    cudaMemsetAsync(over, 0, sizeof(int32_t), s);
+    if (P.p.spring == 1) {
+        k_fene_check<<<(P.n + 127) / 128, 128, 0, s>>>(P.d_Rnew, P.n, P.p.beads_per_chain,
+                                                      P.p.fene_b, over);
+        count_launches(1);
+    }
+    k_commit<<<(n3 + 255) / 256, 256, 0, s>>>(R, P.d_Rnew, n3, over, P.d_status + 2, stats);
+    count_launches(1);
+}
+
+__global__ void k_zero_i32(int32_t *p, int n)
+{
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) p[i] = 0;
+}
+
+void launch_zero_i32(int32_t *p, int n, cudaStream_t s)
+{
+    k_zero_i32<<<(n + 255) / 256, 256, 0, s>>>(p, n);
+    count_launches(1);
+}
+
+}  // namespace bd
