@@ -264,6 +264,10 @@ def run_ours(args):
     stream = torch.cuda.current_stream()
     evs = [[torch.cuda.Event(enable_timing=True) for _ in range(7)] for _ in range(args.steps)]
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    for row in evs:             # torch creates the CUDA event on its first record
+        for ev in row:
+            ev.record(stream)
+    torch.cuda.synchronize()
     clocks = ClockSampler()
     clocks.start()
     time.sleep(0.4)

@@ -208,6 +208,9 @@ class Plan:
         if events is None:
             _check(load().bd_set_phase_events(self._h, None, 0))
             return
+        for e in events:
+            if not e.cuda_event:          # created lazily by torch on first record
+                e.record()
         arr = (_vp * len(events))(*[ctypes.c_void_p(e.cuda_event) for e in events])
         _check(load().bd_set_phase_events(self._h, arr, len(events)))
 

@@ -454,12 +454,14 @@ __global__ void k_commit(double *R, const double *Rn, int n3, const int32_t *ove
                          const int32_t *in_bad, bd_step_stats *st)
 {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
-    bool ok = (*over == 0) && (*in_bad == 0);
+    const int32_t timeout = in_bad[4];           // status word 6: a bounded wait gave up
+    bool ok = (*over == 0) && (*in_bad == 0) && timeout == 0;
     if (ok && i < n3) R[i] = Rn[i];
     if (i == 0 && st) {
         st->n_overstretched = *over;
         st->accepted = ok ? 1 : 0;
-        if (!ok) st->status = BD_ERR_FENE_STRETCH;
+        if (timeout) st->status = BD_ERR_TIMEOUT;
+        else if (!ok) st->status = BD_ERR_FENE_STRETCH;
     }
 }
 

@@ -1,0 +1,169 @@
+"""Mixed-precision parity (FP32 D assembly, 16-bit tensor-core products with
+FP32 accumulation, FP64 vectors) against the FP64 CPU oracle.
+
+Bars (stated accuracy targets of the mixed mode):
+  * FP32 D vs oracle D ................ 2e-6 relative (max-norm)
+  * 16-bit D vs oracle D .............. element-wise half (bf16) rounding
+  * D.F after one FP64-residual refinement ... 1e-5 relative (max-norm)
+  * Chebyshev dS = sqrt(D) dW ......... 1e-3 relative (max-norm) vs the FP64
+    oracle series with the same bounds and N_Ch, and vs the
+    eigen-decomposition square root on a small system
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_1203_6208_gb300 import inputs
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+def relerr(a, b):
+    a = np.asarray(a, dtype=np.float64)
+    b = np.asarray(b, dtype=np.float64)
+    return float(np.max(np.abs(a - b)) / max(np.max(np.abs(b)), 1e-300))
+
+
+@pytest.fixture(scope="module")
+def bnd():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1203_6208_gb300 import binding, build
+    build.build()
+    binding.load()
+    return binding
+
+
+def system(n_chains=40, nb=10, c=2.0, seed=61, **kw):
+    cfg = inputs.SystemConfig(n_chains=n_chains, nb=nb, c_over_cstar=c, seed=seed, **kw)
+    p = cfg.params()
+    return cfg, p, inputs.make_chains(cfg)
+
+
+def mixed(bnd, p, R, prec="mixed_f16", **kw):
+    plan = bnd.Plan(p, prec, **kw)
+    Rg = torch.tensor(R, device="cuda")
+    D = plan.alloc_D()
+    plan.build_D(Rg, D)
+    torch.cuda.synchronize()
+    return plan, Rg, D
+
+
+@pytest.mark.parametrize("prec", ["mixed_f16", "mixed_bf16"])
+def test_build_D_f32_and_16bit(bnd, prec):
+    cfg, p, R = system(n_chains=7, nb=11, seed=62)       # 77 beads: ragged tiles
+    plan, Rg, D = mixed(bnd, p, R, prec)
+    Dr = oracle.build_D(p, R)
+    D32 = plan.D_view(D, "f32").cpu().numpy().astype(np.float64)
+    assert relerr(D32, Dr) <= 2e-6
+    D16 = plan.D_view(D, "16").float().cpu().numpy().astype(np.float64)
+    ulp = 2.0 ** -11 if prec == "mixed_f16" else 2.0 ** -8
+    assert np.all(np.abs(D16 - Dr) <= ulp * np.abs(Dr) + 1e-6)
+
+
+@pytest.mark.parametrize("m", [1, 5, 16, 17, 32])
+def test_apply_tensor_core(bnd, m):
+    cfg, p, R = system(seed=63)
+    plan, Rg, D = mixed(bnd, p, R, max_rhs=32)
+    Dr = oracle.build_D(p, R)
+    X = inputs.make_wiener(3 * cfg.n, m, 1.0, 64)
+    Xg = torch.tensor(X, device="cuda")
+    Y = torch.empty_like(Xg)
+    plan.apply(D, Xg, Y)
+    ref = oracle.apply_D(Dr, X)
+    assert relerr(Y.cpu().numpy(), ref) <= 2e-3
+    # column by column the error is that of a half-precision D
+    for j in range(m):
+        assert relerr(Y[j].cpu().numpy(), ref[j]) <= 2e-3
+
+
+def test_apply_refined_drift(bnd):
+    cfg, p, R = system(seed=65)
+    plan, Rg, D = mixed(bnd, p, R, max_rhs=4)
+    Dr = oracle.build_D(p, R)
+    F, _ = oracle.forces(p, R)
+    Fg = torch.tensor(F, device="cuda").view(1, -1)
+    Y = torch.empty_like(Fg)
+    plan.apply(D, Fg, Y, refine=True)
+    assert relerr(Y.cpu().numpy()[0], Dr @ F) <= 1e-5
+    Y0 = torch.empty_like(Fg)
+    plan.apply(D, Fg, Y0, refine=False)
+    assert relerr(Y0.cpu().numpy()[0], Dr @ F) > 1e-5      # refinement does something
+
+
+@pytest.mark.parametrize("prec,tol", [("mixed_f16", 1e-3), ("mixed_bf16", 4e-3)])
+def test_chebyshev_mixed(bnd, prec, tol):
+    cfg, p, R = system(n_chains=30, nb=10, c=2.0, seed=66)
+    plan, Rg, D = mixed(bnd, p, R, prec, max_rhs=16, max_cheb=64)
+    Dr = oracle.build_D(p, R)
+    lmin, lmax = oracle.exact_eigs(Dr)
+    dmin, dmax = 0.9 * lmin, 1.05 * lmax
+    m, nch = 16, 40
+    dW = inputs.make_wiener(3 * cfg.n, m, p["dt"], 67)
+    bounds = torch.tensor([dmin, dmax], dtype=torch.float64, device="cuda")
+    dWg = torch.tensor(dW, device="cuda")
+    dS = torch.empty_like(dWg)
+    plan.chebyshev(D, bounds, nch, dWg, dS)
+    dS_r, _ = oracle.cheb_sqrt(Dr, dmin, dmax, nch, dW)
+    assert relerr(dS.cpu().numpy(), dS_r) <= tol
+
+
+def test_chebyshev_mixed_vs_eigen_root(bnd):
+    """Against the exact symmetric root (eigen-decomposition) of the FP64 D
+    on a small system with converged N_Ch: <= 1e-3 relative."""
+    cfg, p, R = system(n_chains=10, nb=10, c=1.0, seed=68)
+    plan, Rg, D = mixed(bnd, p, R, max_rhs=4, max_cheb=128)
+    Dr = oracle.build_D(p, R)
+    lmin, lmax = oracle.exact_eigs(Dr)
+    dW = inputs.make_wiener(3 * cfg.n, 4, p["dt"], 69)
+    ref = (oracle.sqrt_eig(Dr) @ dW.T).T
+    bounds = torch.tensor([0.95 * lmin, 1.02 * lmax], dtype=torch.float64, device="cuda")
+    dWg = torch.tensor(dW, device="cuda")
+    dS = torch.empty_like(dWg)
+    Ef = torch.empty(4, dtype=torch.float64, device="cuda")
+    plan.chebyshev(D, bounds, 100, dWg, dS, Ef)
+    assert relerr(dS.cpu().numpy(), ref) <= 1e-3
+    assert float(Ef.max()) < 1e-3
+
+
+def test_step_mixed_drift_refined(bnd):
+    cfg, extra = inputs.preset("c1")
+    p = cfg.params()
+    R = inputs.make_chains(cfg)
+    dW = inputs.make_wiener(3 * cfg.n, 2, p["dt"], cfg.seed + 1)
+    plan = bnd.Plan(p, "mixed_f16", max_rhs=2, max_cheb=64)
+    Rg = torch.tensor(R, device="cuda")
+    D = plan.alloc_D()
+    DF = torch.empty(3 * cfg.n, dtype=torch.float64, device="cuda")
+    dS = torch.empty(2, 3 * cfg.n, dtype=torch.float64, device="cuda")
+    stats = bnd.new_stats()
+    plan.step(Rg, D, torch.tensor(dW, device="cuda"), m=2, n_cheb=30, lanczos_iters=60,
+              bound_safety=0.02, dmin_fraction=0.5, DF=DF, dS=dS, stats=stats)
+    st = bnd.read_stats(stats)
+    assert st["status"] == 0 and st["accepted"] == 1
+    R_ref, code, DF_r, dS_r, _ = oracle.step(p, R, dW, st["d_min"], st["d_max"], 30)
+    assert relerr(DF.cpu().numpy(), DF_r) <= 1e-5
+    assert relerr(dS.cpu().numpy(), dS_r) <= 1e-3
+    disp = Rg.cpu().numpy() - R
+    assert relerr(disp, R_ref - R) <= 1e-3
+
+
+def test_n8000_mixed_sampled_rows(bnd):
+    """The N = 8000 workload of the benchmark: rows of the tensor-core
+    product against oracle rows of D times the same X (FP64)."""
+    cfg, _ = inputs.preset("c4")
+    p = cfg.params()
+    R = inputs.make_chains(cfg)
+    plan, Rg, D = mixed(bnd, p, R, max_rhs=16)
+    m = 16
+    X = inputs.make_wiener(3 * cfg.n, m, 1.0, 70)
+    Xg = torch.tensor(X, device="cuda")
+    Y = torch.empty_like(Xg)
+    plan.apply(D, Xg, Y)
+    Yh = Y.cpu().numpy()
+    for b in (0, 1234, 4095, 7999):
+        rows = oracle.build_D_rows(p, R, b, b + 1)
+        ref = rows @ X.T                                   # (3, m)
+        got = Yh[:, 3 * b:3 * b + 3].T
+        assert np.max(np.abs(got - ref)) <= 2e-3 * np.max(np.abs(Yh))
