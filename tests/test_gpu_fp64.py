@@ -157,7 +157,7 @@ def test_fene_overstretch_counted(bnd):
     nbad = torch.zeros(1, dtype=torch.int32, device="cuda")
     plan.forces(torch.tensor(R, device="cuda"), F, nbad)
     _, bad = oracle.forces(p, R)
-    assert int(nbad.item()) == bad == 1
+    assert bad >= 1 and int(nbad.item()) == bad
 
 
 @pytest.mark.parametrize("m,nch", [(1, 20), (4, 40), (16, 12)])
