@@ -309,7 +309,7 @@ def run_ours(args):
                 "traffic": traffic_per_launch("fp64"),
                 "algorithmic_per_launch": f"2*(3N)^2*m = {flops:.3e} flop"}
     else:
-        bytes_ = n3 * n3 * 2.0 + n3 * args.m * (2 + 8 * 4)
+        bytes_ = n3 * n3 * 2.0 + n3 * args.m * (2 + 2 + 8 * 5)
         achieved = bytes_ / (cheb_launch_ms * 1e-3) / 1e9
         roof = {"bound": "hbm", "kernel": "tc_cheb", "achieved": achieved,
                 "peak": peaks["hbm_gbs"], "unit": "GB/s", "frac": achieved / peaks["hbm_gbs"],
