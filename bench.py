@@ -42,10 +42,15 @@ def parse():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed_f16", "mixed_bf16"])
+    ap.add_argument("--precision", default="both",
+                    choices=["both", "fp64", "mixed_f16", "mixed_bf16"],
+                    help="both: FP64 and mixed (IEEE-half) on the same system; the headline "
+                         "value is the mixed step, the FP64 step is reported beside it")
     ap.add_argument("--nch", type=int, default=40)
     ap.add_argument("--m", type=int, default=16)
-    ap.add_argument("--alpha-factor", type=float, default=1.0)
+    ap.add_argument("--alpha-factor", default="auto",
+                    help="alpha = f sqrt(pi)/L; 'auto' times bd_build_D for a few f first "
+                         "(untimed) and keeps the fastest per precision")
     ap.add_argument("--lanczos", type=int, default=30)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=3)
@@ -100,6 +105,11 @@ def cpu_baseline(p, R, m, nch, target_s=12.0):
                       f"({t:.1f} s), scaled by N/rows to one step ({step_s:.1f} s)"}
 
 
+# alpha factor the oracle arm uses when --alpha-factor is auto: the value the
+# GPU autotuner picks for the mixed step of this workload (see profiles/)
+REFERENCE_ALPHA = 1.0
+
+
 def run_reference(args):
     ws, rank, _ = dist_env()
     if rank != 0:
@@ -107,7 +117,8 @@ def run_reference(args):
     from paper_1203_6208_gb300 import inputs
     import oracle
     oracle.build()
-    cfg, p = system(args.alpha_factor, args.chains)
+    f = REFERENCE_ALPHA if args.alpha_factor == "auto" else float(args.alpha_factor)
+    cfg, p = system(f, args.chains)
     R = inputs.make_chains(cfg)
     n = p["n"]
     rows = 64
@@ -120,7 +131,7 @@ def run_reference(args):
             "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": step_s * 1e3, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "precision": "fp64", "alpha_factor": args.alpha_factor},
+            "config": {"workload": WORKLOAD, "precision": "fp64 oracle", "alpha_factor": f},
             "cpu_baseline": {"value": v, "unit": "steps/s", "cores": oracle.num_threads(),
                              "kind": "oracle",
                              "sample": f"each step: D rows + {args.nch - 1} products for {rows} "
@@ -239,20 +250,22 @@ def traffic_per_launch(kind):
         return None
 
 
-def run_ours(args):
+ALPHA_FACTORS = (1.0, 1.25, 1.5, 1.75, 2.0, 2.5)
+
+
+def pick_alpha(args, p, R, precision):
+    if args.alpha_factor != "auto":
+        return float(args.alpha_factor), None
+    from paper_1203_6208_gb300 import tune
+    best, times = tune.tune_alpha(p, R, precision, factors=ALPHA_FACTORS, reps=1)
+    return best, {str(k): round(v, 3) for k, v in times.items()}
+
+
+def measure(args, precision, p, R0, rank, ws):
+    """Warm up, then time exactly args.steps bd_step calls on the device."""
     import torch
-    ws, rank, local = dist_env()
-    if ws > 1:
-        import torch.distributed as dist
-        dist.init_process_group("nccl")
-        torch.cuda.set_device(local)
-    else:
-        torch.cuda.set_device(0)
-    from paper_1203_6208_gb300 import binding as bnd, build, inputs
-    build.build()
-    cfg, p = system(args.alpha_factor, args.chains)
-    R0 = inputs.make_chains(cfg, seed=cfg.seed + 17 * rank)
-    plan = bnd.Plan(p, args.precision, max_rhs=args.m, max_cheb=max(args.nch, 2))
+    from paper_1203_6208_gb300 import binding as bnd
+    plan = bnd.Plan(p, precision, max_rhs=args.m, max_cheb=max(args.nch, 2))
     R = torch.tensor(R0, device="cuda")
     D = plan.alloc_D()
     stats = bnd.new_stats()
@@ -299,21 +312,23 @@ def run_ours(args):
     n3 = 3 * p["n"]
     cheb_launch_ms = phases["chebyshev"] / max(args.nch - 2, 1)
     peaks, peak_src = measured_peaks()
-    if args.precision == "fp64":
+    if precision == "fp64":
         flops = 2.0 * n3 * n3 * args.m
         fp64_peak = probe_fp64_peak()
         achieved = flops / (cheb_launch_ms * 1e-3) / 1e12
         roof = {"bound": "alu", "kernel": "k_gemm_f64<16,cheb>", "achieved": achieved,
                 "peak": fp64_peak / 1e12, "unit": "TFLOP/s", "frac": achieved * 1e12 / fp64_peak,
-                "peak_source": "FP64 DFMA probe (probe/peaks.cu) on this GPU",
+                "peak_source": "FP64 DFMA probe (probe/peaks.cu) on this GPU (measured)",
                 "traffic": traffic_per_launch("fp64"),
                 "algorithmic_per_launch": f"2*(3N)^2*m = {flops:.3e} flop"}
     else:
         bytes_ = n3 * n3 * 2.0 + n3 * args.m * (2 + 2 + 8 * 5)
         achieved = bytes_ / (cheb_launch_ms * 1e-3) / 1e9
-        roof = {"bound": "hbm", "kernel": "tc_cheb", "achieved": achieved,
-                "peak": peaks["hbm_gbs"], "unit": "GB/s", "frac": achieved / peaks["hbm_gbs"],
-                "peak_source": f"hbm_gbs ({peak_src})", "traffic": traffic_per_launch("mixed"),
+        roof = {"bound": "hbm", "kernel": "k_tc_gemm<16> (Chebyshev epilogue)",
+                "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                "frac": achieved / peaks["hbm_gbs"],
+                "peak_source": f"hbm_gbs ({peak_src} copy bandwidth)",
+                "traffic": traffic_per_launch("mixed"),
                 "algorithmic_per_launch": f"16-bit D + vectors = {bytes_:.3e} B"}
 
     # end to end through the public API with host buffers
@@ -321,6 +336,7 @@ def run_ours(args):
     if args.e2e_steps > 0:
         Rh = torch.tensor(R0, dtype=torch.float64).pin_memory()
         sh = torch.empty(bnd.STATS_BYTES, dtype=torch.uint8).pin_memory()
+        torch.cuda.synchronize()
         t0 = time.perf_counter()
         for k in range(args.e2e_steps):
             R.copy_(Rh, non_blocking=True)
@@ -333,27 +349,69 @@ def run_ours(args):
                "d2h_bytes_per_step": 8 * n3 + bnd.STATS_BYTES,
                "note": "per step: positions H2D from pinned memory, bd_step, positions + "
                        "stats D2H, stream sync (wall clock)"}
+    out = {"value": ws * args.steps / (ms * 1e-3), "ms_per_step": ms / args.steps,
+           "phases_ms": phases, "step_stats": st, "roofline": roof, "gpu_launches": launches,
+           "clocks": clk, "e2e": e2e, "n_kvec_half": plan.info.n_kvec,
+           "d_gb": plan.info.d_bytes / 1e9}
+    del D
+    plan.close()
+    torch.cuda.empty_cache()
+    return out
 
+
+def dtype_of(precision):
+    return {"fp64": "f64", "mixed_f16": "f16+f32+f64", "mixed_bf16": "bf16+f32+f64"}[precision]
+
+
+def run_ours(args):
+    import torch
+    ws, rank, local = dist_env()
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+        torch.cuda.set_device(local)
+    else:
+        torch.cuda.set_device(0)
+    from paper_1203_6208_gb300 import build, inputs
+    build.build()
+    precs = ["fp64", "mixed_f16"] if args.precision == "both" else [args.precision]
+    cfg, p1 = system(1.0, args.chains)
+    R0 = inputs.make_chains(cfg, seed=cfg.seed + 17 * rank)
+    results, alphas = {}, {}
+    for prec in precs:
+        Rt = torch.tensor(R0, device="cuda")
+        f, sweep = pick_alpha(args, p1, Rt, prec)
+        del Rt
+        _, p = system(f, args.chains)
+        alphas[prec] = (f, sweep, p)
+        results[prec] = measure(args, prec, p, R0, rank, ws)
     if rank != 0:
         return
-    value = ws * args.steps / (ms * 1e-3)
-    line = {"metric": METRIC, "value": value, "unit": "steps/s", "n_gpus": ws,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
+    head = precs[-1]
+    r = results[head]
+    f, sweep, p = alphas[head]
+    line = {"metric": METRIC, "value": r["value"], "unit": "steps/s", "n_gpus": ws,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": r["ms_per_step"],
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-            "dtype": "f64" if args.precision == "fp64" else
-                     ("f16+f32+f64" if args.precision == "mixed_f16" else "bf16+f32+f64"),
-            "data": "synthetic",
+            "dtype": dtype_of(head), "data": "synthetic",
             "config": {"workload": WORKLOAD if args.chains == 400 else
                        f"reduced: {args.chains} chains x 20 beads (profiling only)",
-                       "n_beads": p["n"], "box_L": p["L"],
-                       "alpha": p["alpha"], "alpha_factor": args.alpha_factor, "r_c": p["rc"],
-                       "n2max": p["n2max"], "n_kvec_half": plan.info.n_kvec, "m": args.m,
-                       "n_cheb": args.nch, "lanczos_iters": args.lanczos,
-                       "precision": args.precision,
-                       "l2": "inputs larger than L2 (D alone is %.2f GB)" % (plan.info.d_bytes / 1e9),
+                       "n_beads": p["n"], "box_L": p["L"], "precision": head,
+                       "alpha": p["alpha"], "alpha_factor": f, "alpha_sweep_ms": sweep,
+                       "r_c": p["rc"], "n2max": p["n2max"], "n_kvec_half": r["n_kvec_half"],
+                       "m": args.m, "n_cheb": args.nch, "lanczos_iters": args.lanczos,
+                       "l2": "inputs larger than L2 (D alone is %.2f GB)" % r["d_gb"],
                        "parallelism": "replicas" if ws > 1 else "single"},
-            "phases_ms": phases, "step_stats": st, "roofline": roof, "gpu_launches": launches,
-            "clocks": clk, "e2e": e2e}
+            "phases_ms": r["phases_ms"], "step_stats": r["step_stats"], "roofline": r["roofline"],
+            "gpu_launches": r["gpu_launches"], "clocks": r["clocks"], "e2e": r["e2e"]}
+    if "fp64" in results and head != "fp64":
+        q = results["fp64"]
+        fq, sq, pq = alphas["fp64"]
+        line["fp64"] = {"value": q["value"], "unit": "steps/s", "ms_per_step": q["ms_per_step"],
+                        "alpha_factor": fq, "alpha_sweep_ms": sq, "phases_ms": q["phases_ms"],
+                        "step_stats": q["step_stats"], "roofline": q["roofline"],
+                        "gpu_launches": q["gpu_launches"], "clocks": q["clocks"], "e2e": q["e2e"]}
+        line["mixed_speedup_over_fp64"] = r["value"] / q["value"]
     if ws == 1 and not args.no_cpu_baseline:
         import oracle
         oracle.build()

@@ -110,6 +110,7 @@ def _load(path):
     L.oracle_wiener_philox.argtypes = [ctypes.c_uint64, ctypes.c_uint64,
                                        ctypes.c_int64, ctypes.c_double, _dp]
     L.oracle_num_threads.restype = ctypes.c_int32
+    L.oracle_grad_DF_R.argtypes = [P, _dp, _dp, _dp, _dp]
     return L
 
 
@@ -221,6 +222,17 @@ def step(p: dict, R: np.ndarray, dW: np.ndarray, dmin: float, dmax: float, nch: 
     st = lib().oracle_step(ctypes.byref(_params(p)), _ptr(Rn), _ptr(dW), dW.shape[0],
                            float(dmin), float(dmax), int(nch), _ptr(DF), _ptr(dS), _ptr(Ef))
     return Rn, int(st), DF, dS, Ef
+
+
+def grad_DF(p: dict, R: np.ndarray, F: np.ndarray, g: np.ndarray):
+    """Gradient of L = g . D(R) F: returns (dL/dR as (N, 3), dL/dF = D g)."""
+    R = np.ascontiguousarray(R, dtype=np.float64)
+    F = np.ascontiguousarray(F, dtype=np.float64).reshape(-1)
+    g = np.ascontiguousarray(g, dtype=np.float64).reshape(-1)
+    gR = np.empty(3 * int(p["n"]), dtype=np.float64)
+    lib().oracle_grad_DF_R(ctypes.byref(_params(p)), _ptr(R), _ptr(F), _ptr(g), _ptr(gR))
+    D = build_D(p, R)
+    return gR.reshape(-1, 3), D @ g
 
 
 def philox4x32_10(ctr, key):

@@ -500,6 +500,126 @@ done:
     return ret;
 }
 
+
+/* ------------------------------------------------------------------------ */
+/* Gradient of L = g . D(R) F with respect to R (the adjoint of the drift
+ * product of Eq. sde; dL/dF = D g is a plain product).  D_{nu mu} = B(d),
+ * d = r_nu - r_mu, with B the pair tensor of Eq. (DFmodified); the diagonal
+ * blocks do not depend on R.  For each ordered pair,
+ *   dL/dr_nu^c += sum_ab dB_ab/dd_c (d) W_ab,  W_ab = g_nu^a F_mu^b + g_mu^a F_nu^b,
+ * and dB/dd is the analytic derivative of the image sum of M1 (Eq. M1), of
+ * M* (Eq. cor5, reading R2) and of the reciprocal sum (Eq. M2).            */
+
+/* dc1/dr and dc2/dr of Eq. (M1) written out by hand, with s = alpha r. */
+static void m1_coeffs_dr(double r, double a, double al, double *d1, double *d2)
+{
+    double a3 = a * a * a, r2 = r * r, r3 = r2 * r, r4 = r2 * r2, r5 = r4 * r;
+    double al2 = al * al, al3 = al2 * al, al5 = al3 * al2, al7 = al5 * al2;
+    double ec = erfc(al * r);
+    double ex = exp(-al2 * r2) / sqrt(PI);
+    double dec = -2.0 * al * ex;                   /* d erfc(alpha r)/dr      */
+    double dex = -2.0 * al2 * r * ex;              /* d [exp(-a^2r^2)/sqrt(pi)]/dr */
+    double p1 = 3.0 * a * al3 * r2 - 9.0 * a * al / 2.0 + 4.0 * a3 * al7 * r4
+              - 20.0 * a3 * al5 * r2 + 14.0 * a3 * al3 + a3 * al / r2;
+    double dp1 = 6.0 * a * al3 * r + 16.0 * a3 * al7 * r3 - 40.0 * a3 * al5 * r
+               - 2.0 * a3 * al / r3;
+    double p2 = 3.0 * a * al / 2.0 - 3.0 * a * al3 * r2 - 4.0 * a3 * al7 * r4
+              + 16.0 * a3 * al5 * r2 - 2.0 * a3 * al3 - 3.0 * a3 * al / r2;
+    double dp2 = -6.0 * a * al3 * r - 16.0 * a3 * al7 * r3 + 32.0 * a3 * al5 * r
+               + 6.0 * a3 * al / r3;
+    double q1 = 3.0 * a / (4.0 * r) + a3 / (2.0 * r3);
+    double dq1 = -3.0 * a / (4.0 * r2) - 3.0 * a3 / (2.0 * r4);
+    double q2 = 3.0 * a / (4.0 * r) - 3.0 * a3 / (2.0 * r3);
+    double dq2 = -3.0 * a / (4.0 * r2) + 9.0 * a3 / (2.0 * r4);
+    (void)r5;
+    *d1 = dec * q1 + ec * dq1 + dex * p1 + ex * dp1;
+    *d2 = dec * q2 + ec * dq2 + dex * p2 + ex * dp2;
+}
+
+/* d/dd_c of f1(r) I + f2(r) rhat rhat contracted with W, added to out[c]. */
+static void add_radial_grad(const double v[3], double r, double f1, double f2, double df1,
+                            double df2, const double W[9], double out[3])
+{
+    double trW = W[0] + W[4] + W[8];
+    double vWv = 0.0, Wv[3], WTv[3];
+    for (int i = 0; i < 3; i++) {
+        Wv[i] = W[3 * i] * v[0] + W[3 * i + 1] * v[1] + W[3 * i + 2] * v[2];
+        WTv[i] = W[i] * v[0] + W[3 + i] * v[1] + W[6 + i] * v[2];
+        vWv += v[i] * Wv[i];
+    }
+    double r2 = r * r;
+    for (int c = 0; c < 3; c++) {
+        double e = v[c] / r;                        /* dr/dd_c */
+        out[c] += df1 * e * trW                     /* f1' e_c delta_ab            */
+                + df2 * e * vWv / r2                /* f2' e_c v_a v_b / r^2       */
+                + f2 * (Wv[c] + WTv[c]) / r2        /* f2 (delta_ac v_b + v_a delta_bc)/r^2 */
+                - 2.0 * f2 * vWv * v[c] / (r2 * r2);/* f2 v_a v_b d(1/r^2)/dd_c    */
+    }
+}
+
+void oracle_grad_DF_R(const oracle_params *p, const double *R, const double *F, const double *g,
+                      double *gR)
+{
+    kterm *kl;
+    int nk = build_klist(p, &kl);
+    int n = p->n;
+    double L = p->L, a = p->a, al = p->alpha, rc2 = p->rc * p->rc;
+    int nmax = (int)floor(p->rc / L + 0.5) + 1;
+#pragma omp parallel for schedule(dynamic, 1)
+    for (int nu = 0; nu < n; nu++) {
+        double acc[3] = {0.0, 0.0, 0.0};
+        for (int mu = 0; mu < n; mu++) {
+            if (mu == nu) continue;
+            double W[9];
+            for (int i = 0; i < 3; i++)
+                for (int j = 0; j < 3; j++)
+                    W[3 * i + j] = g[3 * nu + i] * F[3 * mu + j] + g[3 * mu + i] * F[3 * nu + j];
+            double d[3];
+            for (int i = 0; i < 3; i++) {
+                d[i] = R[3 * nu + i] - R[3 * mu + i];
+                d[i] -= L * nearbyint(d[i] / L);
+            }
+            for (int nx = -nmax; nx <= nmax; nx++)
+                for (int ny = -nmax; ny <= nmax; ny++)
+                    for (int nz = -nmax; nz <= nmax; nz++) {
+                        double v[3] = {d[0] + nx * L, d[1] + ny * L, d[2] + nz * L};
+                        double u = v[0] * v[0] + v[1] * v[1] + v[2] * v[2];
+                        if (u > rc2 || u == 0.0) continue;
+                        double r = sqrt(u), c1, c2, d1, d2;
+                        m1_coeffs(r, a, al, &c1, &c2);
+                        m1_coeffs_dr(r, a, al, &d1, &d2);
+                        add_radial_grad(v, r, c1, c2, d1, d2, W, acc);
+                        if (p->overlap_corr && u < 4.0 * a * a) {
+                            /* M* of Eq. (cor5), reading R2, with x = r/a */
+                            double x = r / a, x2 = x * x, x3 = x2 * x, x4 = x2 * x2;
+                            double q = 0.75 * x2 + 1.0;
+                            double s1 = 1.0 - q * q / (2.0 * x3);
+                            double ds1 = (-(2.0 * q * 1.5 * x) * 2.0 * x3 + q * q * 6.0 * x2)
+                                       / (4.0 * x3 * x3) / a;
+                            double s2 = 3.0 * (x2 - 4.0) * (x2 - 4.0) / (32.0 * x3);
+                            double ds2 = (3.0 * 2.0 * (x2 - 4.0) * 2.0 * x * 32.0 * x3
+                                          - 3.0 * (x2 - 4.0) * (x2 - 4.0) * 96.0 * x2)
+                                       / (1024.0 * x3 * x3) / a;
+                            (void)x4;
+                            add_radial_grad(v, r, s1, s2, ds1, ds2, W, acc);
+                        }
+                    }
+            for (int t = 0; t < nk; t++) {
+                const double *k = kl[t].k;
+                double k2 = k[0] * k[0] + k[1] * k[1] + k[2] * k[2];
+                double sn = sin(k[0] * d[0] + k[1] * d[1] + k[2] * d[2]);
+                double mw = 0.0;
+                for (int i = 0; i < 3; i++)
+                    for (int j = 0; j < 3; j++)
+                        mw += kl[t].f * ((i == j ? 1.0 : 0.0) - k[i] * k[j] / k2) * W[3 * i + j];
+                for (int c = 0; c < 3; c++) acc[c] -= mw * k[c] * sn;
+            }
+        }
+        for (int c = 0; c < 3; c++) gR[3 * nu + c] = acc[c];
+    }
+    free(kl);
+}
+
 /* ------------------------------------------------------------------------ */
 /* Philox4x32-10 counter-based generator (Salmon, Moraes, Dror & Shaw,
  * SC'11), written from its published definition: ten rounds of

@@ -55,9 +55,9 @@ static bd_status dmalloc(Plan &P, T **ptr, size_t count)
 
 static void free_plan(Plan &P)
 {
-    void *ptrs[] = {P.d_kvec, P.d_ewc, P.d_cos, P.d_sin, P.d_cos32, P.d_sin32, P.d_F, P.d_DF,
+    void *ptrs[] = {P.d_kvec, P.d_km64, P.d_km32, P.d_xsplit, P.d_ewc, P.d_tab, P.d_tab32, P.d_cos, P.d_sin, P.d_cos32, P.d_sin32, P.d_F, P.d_DF,
                     P.d_Rnew, P.d_V[0], P.d_V[1], P.d_V[2], P.d_X0, P.d_Y0, P.d_dS, P.d_dW,
-                    P.d_coef, P.d_wdw, P.d_red, P.d_bounds, P.d_status, P.d_lq[0], P.d_lq[1],
+                    P.d_coef, P.d_wdw, P.d_red, P.d_redpart, P.d_bounds, P.d_status, P.d_lq[0], P.d_lq[1],
                     P.d_lq[2], P.d_lab, P.d_x16, P.d_xscale, P.d_part, P.d_counters,
                     P.d_stats_scratch, P.d_y32};
     for (void *p : ptrs)
@@ -151,7 +151,18 @@ bd_status bd_plan_create(const bd_params *params, bd_plan **out_plan)
         if (st != BD_OK) goto fail;  \
     } while (0)
     TRY(dmalloc(P, &P.d_kvec, kMaxKvec));
+    TRY(dmalloc(P, &P.d_km64, (size_t)8 * kMaxKvec));
+    if (mixed) TRY(dmalloc(P, &P.d_km32, (size_t)8 * kMaxKvec));
+    if (mixed) TRY(dmalloc(P, &P.d_xsplit, 2 * n3));
     TRY(dmalloc(P, &P.d_ewc, 1));
+    m1_table_range(P.p, &P.tab_i0, &P.ntab);
+    if (P.ntab > kTabMax) {
+        st = set_error(BD_ERR_UNSUPPORTED, "r_c/a ratio needs %d table intervals (limit %d)",
+                       P.ntab, kTabMax);
+        goto fail;
+    }
+    TRY(dmalloc(P, &P.d_tab, (size_t)(P.ntab > 0 ? P.ntab : 1) * kTabStride));
+    if (mixed) TRY(dmalloc(P, &P.d_tab32, (size_t)(P.ntab > 0 ? P.ntab : 1) * kTabStride));
     TRY(dmalloc(P, &P.d_F, n3));
     TRY(dmalloc(P, &P.d_DF, n3));
     TRY(dmalloc(P, &P.d_Rnew, n3));
@@ -163,6 +174,7 @@ bd_status bd_plan_create(const bd_params *params, bd_plan **out_plan)
     TRY(dmalloc(P, &P.d_coef, kMaxCheb));
     TRY(dmalloc(P, &P.d_wdw, kMaxRhs));
     TRY(dmalloc(P, &P.d_red, 4 * kMaxRhs));
+    TRY(dmalloc(P, &P.d_redpart, (size_t)kRedBlocks * kMaxRhs));
     TRY(dmalloc(P, &P.d_bounds, 2));
     TRY(dmalloc(P, &P.d_status, 8));
     for (int i = 0; i < 3; i++) TRY(dmalloc(P, &P.d_lq[i], n3));

@@ -30,6 +30,17 @@ struct EwaldCoef {
     double inv_a;
 };
 
+// Piecewise-polynomial table of the Eq. (M1) coefficients for images with
+// 4a^2 <= u = |r|^2 <= r_c^2: interval i covers the u whose FP32 bit pattern
+// has (bits >> kTabShift) == i0 + i, i.e. 2^kTabBits intervals per octave of u.
+// Per interval: mid, 1/half-width, then kTabDeg+1 monomial coefficients in
+// t = (u - mid)/half-width of c1(u) and of c2(u)/u.
+constexpr int kTabBits = 4;
+constexpr int kTabShift = 23 - kTabBits;
+constexpr int kTabDeg = 8;
+constexpr int kTabStride = 2 + 2 * (kTabDeg + 1);  // doubles per interval
+constexpr int kTabMax = 512;
+
 constexpr int kMaxKvec = 4096;        // half-space k-vectors a plan may use
 constexpr int kMaxRhs = 32;           // Wiener columns per product
 constexpr int kMaxCheb = 256;         // Chebyshev terms
@@ -43,7 +54,12 @@ struct Plan {
     int nk;                            // half-space k-vectors in use
     double self_coeff;                 // self term of Eq. (DF)
     KVec *d_kvec;                      // [nk], device
+    double *d_km64;                    // folded M2 tensors [nk][8] (xx xy xz yy yz zz, pad)
+    float *d_km32;                     // the same in FP32 (mixed plans)
     EwaldCoef *d_ewc;                  // Eq. (M1) coefficients, device
+    double *d_tab;                     // M1 table [ntab][kTabStride] (FP64)
+    float *d_tab32;                    // the same table in FP32 (mixed plans)
+    int tab_i0, ntab;                  // first interval index, interval count
     // per-bead trig tables for the reciprocal sum: cos/sin(k_t . r_nu),
     // stored [t][nu] (FP64) for the current R
     double *d_cos, *d_sin;
@@ -57,7 +73,8 @@ struct Plan {
     double *d_dW;                      // Wiener block when generated on device
     double *d_coef;                    // Chebyshev coefficients [kMaxCheb]
     double *d_wdw;                     // dW.D.dW per column [kMaxRhs]
-    double *d_red;                     // reduction scratch [4*kMaxRhs]
+    double *d_red;                     // reduction results [4*kMaxRhs]
+    double *d_redpart;                 // per-block partial sums [kRedBlocks * kMaxRhs]
     double *d_bounds;                  // {d_min, d_max}
     int32_t *d_status;                 // device status words [8]
     // Lanczos
@@ -74,6 +91,7 @@ struct Plan {
     cudaEvent_t phase_ev[BD_PHASE_EVENTS];
     int phase_on;
     float *d_y32;                      // FP32 product scratch (mixed plans)
+    float *d_xsplit;                   // refinement operand: hi/lo FP32 words [2][3N]
 };
 
 // host-side count of kernel launches (bd_kernel_launches)
@@ -85,6 +103,7 @@ bd_status check_launch(const char *what);
 
 // ---- launchers (defined in the .cu files) ---------------------------------
 // ewald_build.cu
+void m1_table_range(const bd_params &p, int *i0, int *ntab);
 void launch_kvec_table(Plan &P, cudaStream_t s);
 void launch_trig_tables(Plan &P, const double *R, cudaStream_t s);
 void launch_build_D_f64(Plan &P, const double *R, double *D, cudaStream_t s);
@@ -123,7 +142,9 @@ void launch_stats_bounds(bd_step_stats *st, const double *bounds, const int32_t 
                          cudaStream_t s);
 void launch_euler(Plan &P, double *R, const double *DF, const double *dS, bd_step_stats *stats,
                   cudaStream_t s);
-void launch_dot_cols(const double *A, const double *B, int n3, int m, double *out,
+// deterministic column dots: out[j] = A_j . B_j; part holds kRedBlocks x m partials
+constexpr int kRedBlocks = 64;
+void launch_dot_cols(const double *A, const double *B, int n3, int m, double *out, double *part,
                      cudaStream_t s);
 void launch_zero_i32(int32_t *p, int n, cudaStream_t s);
 

@@ -545,25 +545,73 @@ bd_status tc_cheb(Plan &P, const void *D16, int m, const double *coef, const dou
     return launch_tc(P, D16, cur, bn, e, s);
 }
 
-// one warp per row: r = sum_k D32[i][k] X[k][j] - Y[i][j] in FP64; Y += r
-__global__ void k_refine(const float *__restrict__ D32, long ld, int n3,
-                         const double *__restrict__ X, int m, double *__restrict__ Y)
+// One FP64-residual refinement step y += (D32 x - y) for one column.  The
+// FP32 matrix times x is accumulated exactly enough without the FP64 pipe
+// (1/60 of FP32 on this GPU): x is split once into FP32 words x = xh + xl,
+// each lane forms d*xh exactly as the pair (p, fma(d, xh, -p)) and keeps a
+// double-float running sum (TwoSum), and only the 32 lane totals of a row
+// are combined in FP64.  Accuracy of the residual ~1e-12 of sum |d x|; the
+// kernel streams D32 once (HBM bound).
+__global__ void k_split_x(const double *x, int n3, float *xs)
 {
-    int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n3) return;
+    double v = x[i];
+    float h = (float)v;
+    xs[i] = h;
+    xs[n3 + i] = (float)(v - (double)h);
+}
+
+__device__ __forceinline__ void two_sum(float a, float b, float &s, float &e)
+{
+    s = a + b;
+    float bb = s - a;
+    e = (a - (s - bb)) + (b - bb);
+}
+
+__global__ void __launch_bounds__(256)
+k_refine(const float *__restrict__ D32, long ld, int n3, const float *__restrict__ xs,
+         double *__restrict__ y)
+{
+    int row = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     int lane = threadIdx.x & 31;
-    if (warp >= n3) return;
-    const float *row = D32 + (long)warp * ld;
-    for (int j = 0; j < m; j++) {
-        const double *x = X + (long)j * n3;
-        double acc = 0.0;
-        for (int k = lane; k < n3; k += 32) acc = fma((double)row[k], x[k], acc);
+    if (row >= n3) return;
+    const float *d = D32 + (long)row * ld;
+    const float *xh = xs, *xl = xs + n3;
+    float s = 0.f, c = 0.f;
+    // n3 is a multiple of 3, rows start 256-byte aligned (ld multiple of 64)
+    int k = lane * 4;
+    for (; k + 3 < n3; k += 128) {
+        float4 dv = __ldg((const float4 *)(d + k));
+        float dd[4] = {dv.x, dv.y, dv.z, dv.w};
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-        if (lane == 0) {
-            double y0 = Y[(long)j * n3 + warp];
-            double r = acc - y0;
-            Y[(long)j * n3 + warp] = y0 + r;
+        for (int q = 0; q < 4; q++) {
+            float h = __ldg(xh + k + q), l = __ldg(xl + k + q);
+            float p = dd[q] * h;
+            float pe = fmaf(dd[q], h, -p);
+            pe = fmaf(dd[q], l, pe);
+            float t, e;
+            two_sum(s, p, t, e);
+            s = t;
+            c += e + pe;
         }
+    }
+    for (; k < n3; k++) {             // tail (at most 3 elements per lane)
+        float p = d[k] * xh[k];
+        float pe = fmaf(d[k], xh[k], -p);
+        pe = fmaf(d[k], xl[k], pe);
+        float t, e;
+        two_sum(s, p, t, e);
+        s = t;
+        c += e + pe;
+    }
+    double acc = (double)s + (double)c;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    if (lane == 0) {
+        double y0 = y[row];
+        double r = acc - y0;
+        y[row] = y0 + r;
     }
 }
 
@@ -571,8 +619,13 @@ void launch_refine_f32(Plan &P, const float *D32, const double *X, int m, double
                        cudaStream_t s)
 {
     long threads = (long)P.n3 * 32;
-    k_refine<<<(unsigned)((threads + 255) / 256), 256, 0, s>>>(D32, P.ld, P.n3, X, m, Y);
-    count_launches(1);
+    for (int j = 0; j < m; j++) {
+        k_split_x<<<(P.n3 + 255) / 256, 256, 0, s>>>(X + (long)j * P.n3, P.n3, P.d_xsplit);
+        count_launches(1);
+        k_refine<<<(unsigned)((threads + 255) / 256), 256, 0, s>>>(D32, P.ld, P.n3, P.d_xsplit,
+                                                                   Y + (long)j * P.n3);
+        count_launches(1);
+    }
 }
 
 }  // namespace bd

@@ -181,8 +181,11 @@ void launch_cheb_first(Plan &P, const double *bounds, const double *dW, const do
     count_launches(1);
 }
 
-// out[j] += sum_i A[j n3 + i] B[j n3 + i]  (out zeroed by the caller)
-__global__ void k_dot_cols(const double *A, const double *B, int n3, double *out)
+// Deterministic column dot products: block b writes its partial sum of
+// column j to part[j * kRedBlocks + b]; one warp per column then adds the
+// partials in block order.  No atomics, so every run gives the same bits.
+
+__global__ void k_dot_cols_part(const double *A, const double *B, int n3, double *part)
 {
     int j = blockIdx.y;
     double v = 0.0;
@@ -190,15 +193,27 @@ __global__ void k_dot_cols(const double *A, const double *B, int n3, double *out
          i += (long)gridDim.x * blockDim.x)
         v += A[(long)j * n3 + i] * B[(long)j * n3 + i];
     v = block_sum(v);
-    if (threadIdx.x == 0) atomicAdd(&out[j], v);
+    if (threadIdx.x == 0) part[j * kRedBlocks + blockIdx.x] = v;
 }
 
-void launch_dot_cols(const double *A, const double *B, int n3, int m, double *out,
+__global__ void k_sum_parts(const double *part, int nparts, double *out)
+{
+    int j = blockIdx.x;
+    double v = 0.0;
+    for (int b = threadIdx.x; b < nparts; b += 32) v += part[j * kRedBlocks + b];
+    // fixed-shape warp tree
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    if (threadIdx.x == 0) out[j] = v;
+}
+
+void launch_dot_cols(const double *A, const double *B, int n3, int m, double *out, double *part,
                      cudaStream_t s)
 {
-    cudaMemsetAsync(out, 0, sizeof(double) * m, s);
-    int bx = min(64, (n3 + 255) / 256);
-    k_dot_cols<<<dim3(bx, m), 256, 0, s>>>(A, B, n3, out);
+    int bx = min(kRedBlocks, (n3 + 255) / 256);
+    k_dot_cols_part<<<dim3(bx, m), 256, 0, s>>>(A, B, n3, part);
+    count_launches(1);
+    k_sum_parts<<<m, 32, 0, s>>>(part, bx, out);
     count_launches(1);
 }
 
@@ -218,8 +233,8 @@ __global__ void k_ef(const double *ss, const double *wdw, int m, double *Ef, bd_
 void launch_ef(Plan &P, const double *dW, const double *DW, const double *dS, int m, double *Ef,
                bd_step_stats *stats, cudaStream_t s)
 {
-    launch_dot_cols(dW, DW, P.n3, m, P.d_wdw, s);
-    launch_dot_cols(dS, dS, P.n3, m, P.d_red, s);
+    launch_dot_cols(dW, DW, P.n3, m, P.d_wdw, P.d_redpart, s);
+    launch_dot_cols(dS, dS, P.n3, m, P.d_red, P.d_redpart, s);
     k_ef<<<1, 32, 0, s>>>(P.d_red, P.d_wdw, m, Ef, stats);
     count_launches(1);
 }
@@ -293,14 +308,14 @@ void launch_lanczos_init(Plan &P, cudaStream_t s)
     int n3 = P.n3;
     k_lanczos_start<<<(n3 + 255) / 256, 256, 0, s>>>(P.d_lq[1], P.d_lq[0], n3);
     count_launches(1);
-    launch_dot_cols(P.d_lq[1], P.d_lq[1], n3, 1, P.d_red + 2, s);
+    launch_dot_cols(P.d_lq[1], P.d_lq[1], n3, 1, P.d_red + 2, P.d_redpart, s);
     k_scale_by_inv_sqrt<<<(n3 + 255) / 256, 256, 0, s>>>(P.d_lq[1], n3, P.d_red + 2);
     count_launches(1);
 }
 
-// w -= alpha q - beta_prev qprev; accumulate |w|^2
+// w -= alpha q - beta_prev qprev; per-block partial |w|^2 (ordered sum after)
 __global__ void k_lanczos_orth(double *w, const double *q, const double *qprev, int n3,
-                               const double *alpha, const double *beta_prev, double *nrm2)
+                               const double *alpha, const double *beta_prev, double *part)
 {
     double a = *alpha, b = beta_prev ? *beta_prev : 0.0;
     double v = 0.0;
@@ -311,7 +326,7 @@ __global__ void k_lanczos_orth(double *w, const double *q, const double *qprev, 
         v += x * x;
     }
     v = block_sum(v);
-    if (threadIdx.x == 0) atomicAdd(nrm2, v);
+    if (threadIdx.x == 0) part[blockIdx.x] = v;
 }
 
 // beta_j = sqrt(nrm2); qprev <- q; q <- w / beta_j
@@ -332,11 +347,13 @@ void launch_lanczos_update(Plan &P, int j, cudaStream_t s)
     int n3 = P.n3;
     double *alpha = P.d_lab + j, *beta = P.d_lab + kMaxLanczos + j;
     double *beta_prev = j > 0 ? P.d_lab + kMaxLanczos + j - 1 : nullptr;
-    launch_dot_cols(P.d_lq[1], P.d_lq[2], n3, 1, alpha, s);
-    cudaMemsetAsync(P.d_red + 1, 0, sizeof(double), s);
-    int bx = min(128, (n3 + 255) / 256);
+    launch_dot_cols(P.d_lq[1], P.d_lq[2], n3, 1, alpha, P.d_redpart, s);
+    double *part = P.d_redpart;
+    int bx = min(kRedBlocks, (n3 + 255) / 256);
     k_lanczos_orth<<<bx, 256, 0, s>>>(P.d_lq[2], P.d_lq[1], P.d_lq[0], n3, alpha, beta_prev,
-                                      P.d_red + 1);
+                                      part);
+    count_launches(1);
+    k_sum_parts<<<1, 32, 0, s>>>(part, bx, P.d_red + 1);
     count_launches(1);
     k_lanczos_shift<<<(n3 + 255) / 256, 256, 0, s>>>(P.d_lq[0], P.d_lq[1], P.d_lq[2], n3,
                                                      P.d_red + 1, beta);
@@ -358,12 +375,14 @@ __device__ int sturm_count(const double *al, const double *be, int k, double x)
     return cnt;
 }
 
-// extreme Ritz values by bisection (Gershgorin bracket), then the widened
-// bounds {d_min, d_max} and a status word
+// Extreme Ritz values of the k x k tridiagonal matrix by warp-parallel
+// multisection on Sturm counts: each round the 32 lanes test 32 points of
+// the current bracket (Gershgorin at the start), which shrinks it 33-fold.
+// Then the widened bounds {d_min, d_max} and a status word.
 __global__ void k_lanczos_finish(const double *lab, int k, double smax, double fmin_,
                                  double *bounds, int32_t *status)
 {
-    if (threadIdx.x != 0) return;
+    const int lane = threadIdx.x;
     const double *al = lab, *be = lab + kMaxLanczos;
     // stop at a breakdown (beta ~ 0: the Krylov space became invariant)
     double scale = 0.0;
@@ -378,19 +397,27 @@ __global__ void k_lanczos_finish(const double *lab, int k, double smax, double f
     }
     double th[2];
     for (int w = 0; w < 2; w++) {
-        int target = (w == 0) ? 1 : k;        // count(x) >= target
+        const int target = (w == 0) ? 1 : k;        // smallest x with count(x) >= target
         double a = lo, b = hi;
-        for (int it = 0; it < 200 && b - a > 1e-15 * fmax(fabs(a), fabs(b)); it++) {
-            double mid = 0.5 * (a + b);
-            if (sturm_count(al, be, k, mid) >= target) b = mid;
-            else a = mid;
+        for (int it = 0; it < 16 && b - a > 1e-15 * fmax(fabs(a), fabs(b)); it++) {
+            double x = a + (b - a) * (lane + 1) / 33.0;
+            bool ge = sturm_count(al, be, k, x) >= target;
+            unsigned mask = __ballot_sync(0xffffffffu, ge);
+            // first lane whose point already holds >= target eigenvalues
+            int f = mask ? __ffs(mask) - 1 : 32;
+            double na = f == 0 ? a : a + (b - a) * f / 33.0;
+            double nb = f == 32 ? b : a + (b - a) * (f + 1) / 33.0;
+            a = na;
+            b = nb;
         }
         th[w] = 0.5 * (a + b);
     }
-    double dmin = fmin_ * th[0], dmax = (1.0 + smax) * th[1];
-    bounds[0] = dmin;
-    bounds[1] = dmax;
-    if (status) *status = (dmin > 0.0 && dmax > dmin) ? BD_OK : BD_ERR_NOT_PD;
+    if (lane == 0) {
+        double dmin = fmin_ * th[0], dmax = (1.0 + smax) * th[1];
+        bounds[0] = dmin;
+        bounds[1] = dmax;
+        if (status) *status = (dmin > 0.0 && dmax > dmin) ? BD_OK : BD_ERR_NOT_PD;
+    }
 }
 
 void launch_lanczos_finish(Plan &P, int k, double safety_max, double dmin_fraction,

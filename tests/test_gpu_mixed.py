@@ -113,7 +113,9 @@ def test_chebyshev_mixed(bnd, prec, tol):
 
 def test_chebyshev_mixed_vs_eigen_root(bnd):
     """Against the exact symmetric root (eigen-decomposition) of the FP64 D
-    on a small system with converged N_Ch: <= 1e-3 relative."""
+    on a small system with converged N_Ch: <= 1e-3 relative.  E_f is the
+    square root of a relative error in |dS|^2, so half-precision D sets its
+    floor near sqrt(1e-5) ~ 3e-3; it is held to 1e-2 here."""
     cfg, p, R = system(n_chains=10, nb=10, c=1.0, seed=68)
     plan, Rg, D = mixed(bnd, p, R, max_rhs=4, max_cheb=128)
     Dr = oracle.build_D(p, R)
@@ -126,7 +128,7 @@ def test_chebyshev_mixed_vs_eigen_root(bnd):
     Ef = torch.empty(4, dtype=torch.float64, device="cuda")
     plan.chebyshev(D, bounds, 100, dWg, dS, Ef)
     assert relerr(dS.cpu().numpy(), ref) <= 1e-3
-    assert float(Ef.max()) < 1e-3
+    assert float(Ef.max()) < 1e-2
 
 
 def test_step_mixed_drift_refined(bnd):
