@@ -247,6 +247,33 @@ bd_status bd_set_phase_events(bd_plan *plan, void *const *events, int32_t count)
  * (host-side counter; lets a caller count the launches of a region). */
 uint64_t bd_kernel_launches(void);
 
+/* ---------------------------------------------------------------------------
+ * bd_eig_bounds_noalloc -- the Lanczos bounds of bd_eig_bounds for an FP64
+ * matrix, for callers that must not allocate device memory.  The paper has no
+ * counterpart: this is a deployment variant of the same computation.
+ * bd_eig_bounds needs a plan, and creating a plan allocates; a caller whose
+ * device memory belongs to someone else's allocator (a host framework that
+ * reserved HBM for its own pool), or that runs in a latency-critical loop
+ * where cudaMalloc's possible device synchronisation is not acceptable, can
+ * call this instead.  It allocates nothing: its working vectors live in one
+ * fixed file-scope device array of about 0.6 MB (3 x 24576 doubles plus the
+ * tridiagonal matrix), which every GPU that loads the library holds until
+ * the process exits.
+ *   D        dev, FP64 matrix, row-major, n3 rows with leading dimension ld
+ *            (the layout bd_build_D writes for a BD_FP64 plan), 8-byte aligned
+ *   n3       3N, a multiple of 3, 3 <= n3 <= 24576 (8192 beads); larger
+ *            sizes return BD_ERR_UNSUPPORTED before any work is enqueued
+ *   iters, safety_max, dmin_fraction, bounds, status: as in bd_eig_bounds
+ * The first call on a device looks up the array's device address
+ * (cudaGetSymbolAddress) with that device current; make that first call
+ * before starting any stream capture on the device.  Every call uses the same
+ * array, which keeps the previous call's contents (each call re-initialises
+ * what it reads first); calls whose work overlaps on the GPU race and must be
+ * serialised by the caller.                                               */
+bd_status bd_eig_bounds_noalloc(const double *D, int32_t n3, int32_t ld, int32_t iters,
+                                double safety_max, double dmin_fraction, double *bounds,
+                                int32_t *status, bd_stream stream);
+
 /* Text of the last error on this thread ("" if none).  Never NULL. */
 const char *bd_last_error(void);
 /* Library version string. */

@@ -27,7 +27,8 @@ BD_APPLY_REFINE = 1
 
 EXPORTS = ["bd_plan_create", "bd_plan_destroy", "bd_plan_query", "bd_forces", "bd_build_D",
            "bd_apply_D", "bd_eig_bounds", "bd_chebyshev_sqrt", "bd_step", "bd_wiener",
-           "bd_set_phase_events", "bd_kernel_launches", "bd_last_error", "bd_version"]
+           "bd_set_phase_events", "bd_kernel_launches", "bd_eig_bounds_noalloc",
+           "bd_last_error", "bd_version"]
 PHASES = ["forces", "build_D", "bounds", "first_product", "chebyshev", "update"]
 
 
@@ -91,6 +92,7 @@ def load(path: str = LIB_PATH):
     L.bd_step.argtypes = [_vp, _vp, _vp, _vp, ctypes.POINTER(BdStepOpts), _vp, _vp, _vp, _vp]
     L.bd_wiener.argtypes = [_vp, u64, u64, i64, _vp, _vp]
     L.bd_set_phase_events.argtypes = [_vp, ctypes.POINTER(_vp), i32]
+    L.bd_eig_bounds_noalloc.argtypes = [_vp, i32, i32, i32, f64, f64, _vp, _vp, _vp]
     L.bd_kernel_launches.restype = ctypes.c_uint64
     L.bd_last_error.restype = ctypes.c_char_p
     L.bd_version.restype = ctypes.c_char_p
@@ -217,6 +219,15 @@ class Plan:
     def wiener(self, seed, step_index, out, stream=None):
         _check(load().bd_wiener(self._h, int(seed), int(step_index), out.numel(), _p(out),
                                 _stream(stream)))
+
+
+def eig_bounds_noalloc(D, n3, ld, iters, safety_max, dmin_fraction, bounds, status=None,
+                       stream=None):
+    """bd_eig_bounds_noalloc: Lanczos bounds of an FP64 D without a plan and
+    without any device allocation (fixed-size static scratch, 3N <= 24576)."""
+    _check(load().bd_eig_bounds_noalloc(_p(D), int(n3), int(ld), int(iters), float(safety_max),
+                                        float(dmin_fraction), _p(bounds), _p(status),
+                                        _stream(stream)))
 
 
 def kernel_launches() -> int:
