@@ -52,6 +52,9 @@ def parse():
                     help="alpha = f sqrt(pi)/L; 'auto' times bd_build_D for a few f first "
                          "(untimed) and keeps the fastest per precision")
     ap.add_argument("--lanczos", type=int, default=30)
+    ap.add_argument("--bounds", default="lagged", choices=["lagged", "fresh"],
+                    help="mixed plans: lagged = bounds from the previous step's Lanczos "
+                         "carried in the products; fresh = --lanczos products per step")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--chains", type=int, default=400,
@@ -269,8 +272,11 @@ def measure(args, precision, p, R0, rank, ws):
     R = torch.tensor(R0, device="cuda")
     D = plan.alloc_D()
     stats = bnd.new_stats()
+    # mixed steps take their bounds from the previous step's Lanczos recurrence,
+    # which rides as one extra column of the products (no extra pass over D)
+    bounds_mode = 1 if (precision != "fp64" and args.bounds == "lagged") else 0
     kw = dict(m=args.m, n_cheb=args.nch, lanczos_iters=args.lanczos, bound_safety=0.05,
-              dmin_fraction=0.5, seed=4242 + rank, stats=stats)
+              dmin_fraction=0.5, seed=4242 + rank, stats=stats, bounds_mode=bounds_mode)
     for w in range(args.warmup):
         plan.step(R, D, None, step_index=w, **kw)
     torch.cuda.synchronize()
@@ -400,6 +406,7 @@ def run_ours(args):
                        "alpha": p["alpha"], "alpha_factor": f, "alpha_sweep_ms": sweep,
                        "r_c": p["rc"], "n2max": p["n2max"], "n_kvec_half": r["n_kvec_half"],
                        "m": args.m, "n_cheb": args.nch, "lanczos_iters": args.lanczos,
+                       "bounds": args.bounds if head != "fp64" else "fresh",
                        "l2": "inputs larger than L2 (D alone is %.2f GB)" % r["d_gb"],
                        "parallelism": "replicas" if ws > 1 else "single"},
             "phases_ms": r["phases_ms"], "step_stats": r["step_stats"], "roofline": r["roofline"],

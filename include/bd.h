@@ -122,7 +122,14 @@ typedef struct {
     double  dmin_fraction;    /* d_min = dmin_fraction theta_min (0 < f <= 1)     */
     uint64_t seed;            /* Philox key when dW == NULL                        */
     uint64_t step_index;      /* Philox counter high word when dW == NULL          */
+    int32_t bounds_mode;      /* BD_BOUNDS_FRESH or BD_BOUNDS_LAGGED (see bd_step)  */
+    int32_t reserved;
 } bd_step_opts;
+
+#define BD_BOUNDS_FRESH 0     /* lanczos_iters Lanczos products every step          */
+#define BD_BOUNDS_LAGGED 1    /* mixed plans: the Lanczos vector rides as one extra
+                                 column of this step's products; its bounds serve
+                                 the next step (the first step runs fresh)          */
 
 /* ---------------------------------------------------------------------------
  * Plan.  bd_plan_create validates the parameters, computes the reciprocal
@@ -213,7 +220,13 @@ bd_status bd_chebyshev_sqrt(bd_plan *plan, const void *D, const double *bounds, 
  * bd_step -- one Euler step of Eq. (sde) with kappa = 0:
  *   r(t+dt) = r + (dt/4) D.F + (1/sqrt 2) dS[:,0],
  * i.e. bd_forces, bd_build_D, bd_eig_bounds, the product D.[F, dW] and
- * bd_chebyshev_sqrt, then the update.  FENE systems reject a proposal with
+ * bd_chebyshev_sqrt, then the update.  With opts->bounds_mode =
+ * BD_BOUNDS_LAGGED on a mixed plan, the bounds of step t come from the
+ * Lanczos recurrence run inside the products of step t-1 (the Lanczos vector
+ * is one extra column of D.[F, dW] and of every Chebyshev product, so it costs
+ * no extra pass over D; N_Ch - 1 Lanczos steps), widened by the same
+ * margins; the plan keeps them between calls.  FP64 plans, the first step of
+ * a plan, m + 2 > 32, n_cheb < 8 and n_cheb > 129 use fresh bounds.  FENE systems reject a proposal with
  * any |Q|^2 >= b (Sec. VII): R is then left unchanged, stats->accepted = 0
  * and stats->status = BD_ERR_FENE_STRETCH.
  *   R      dev, 3N doubles, advanced in place (only if accepted)
@@ -225,6 +238,32 @@ bd_status bd_chebyshev_sqrt(bd_plan *plan, const void *D, const double *bounds, 
  *   stats  dev, one bd_step_stats (output, may be NULL)                   */
 bd_status bd_step(bd_plan *plan, double *R, void *D, const double *dW, const bd_step_opts *opts,
                   double *DF, double *dS, bd_step_stats *stats, bd_stream stream);
+
+/* ---------------------------------------------------------------------------
+ * Reverse mode.  D(R) enters the step through D_{nu mu} = B(r_nu - r_mu)
+ * (Eq. DFmodified); the derivative of each block is recomputed per pair from
+ * R (image sum, overlap branch and reciprocal sum), nothing like dD/dR is
+ * stored.  Bounds d_min, d_max and N_Ch are held fixed (their derivative is
+ * not taken).  gR is overwritten (3N doubles).
+ *
+ * bd_apply_D_backward -- for L with dL/dY = gY, Y = D(R) F:
+ *   gF = D gY (may be NULL; needs D, the matrix built from the same R),
+ *   gR = dL/dR = sum_mu dB(d_{nu mu})/dd : (gY_nu F_mu^T + gY_mu F_nu^T).  */
+bd_status bd_apply_D_backward(bd_plan *plan, const double *R, const void *D, const double *F,
+                              const double *gY, double *gR, double *gF, bd_stream stream);
+/* bd_chebyshev_backward -- for L with dL/ddS = gS, dS = P(D(R)) dW the
+ * Chebyshev series of bd_chebyshev_sqrt (same bounds, n_cheb, dW, m):
+ * replays the forward terms V_p, runs the adjoint recurrence
+ *   U_{N-1} = c_{N-1} gS,  U_p = c_p gS + 2 Y U_{p+1} - U_{p+2},
+ *   gdW = U_0 = (c_0/2) gS + Y U_1 - U_2   (equal to P(D) gS),
+ * and contracts dL/dD = (2/(d_max - d_min)) (U_1 V_0^T + 2 sum_{p>=2} U_p V_{p-1}^T)
+ * with the pair derivative of D(R) into gR.  gdW may be NULL.  The first
+ * backward call on a plan allocates its history buffers (2 (max_cheb - 1)
+ * max_rhs 3N doubles) and so synchronises; later calls do not allocate.   */
+bd_status bd_chebyshev_backward(bd_plan *plan, const double *R, const void *D,
+                                const double *bounds, int32_t n_cheb, const double *dW,
+                                int32_t m, const double *gS, double *gR, double *gdW,
+                                bd_stream stream);
 
 /* ---------------------------------------------------------------------------
  * bd_wiener -- the device Wiener generator of bd_step on its own: count

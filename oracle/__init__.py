@@ -111,6 +111,7 @@ def _load(path):
                                        ctypes.c_int64, ctypes.c_double, _dp]
     L.oracle_num_threads.restype = ctypes.c_int32
     L.oracle_grad_DF_R.argtypes = [P, _dp, _dp, _dp, _dp]
+    L.oracle_grad_pairs_R.argtypes = [P, _dp, _dp, _dp, ctypes.c_int32, _dp]
     return L
 
 
@@ -233,6 +234,55 @@ def grad_DF(p: dict, R: np.ndarray, F: np.ndarray, g: np.ndarray):
     lib().oracle_grad_DF_R(ctypes.byref(_params(p)), _ptr(R), _ptr(F), _ptr(g), _ptr(gR))
     D = build_D(p, R)
     return gR.reshape(-1, 3), D @ g
+
+
+def grad_pairs(p: dict, R: np.ndarray, X: np.ndarray, Y: np.ndarray) -> np.ndarray:
+    """dL/dR when dL/dD = sum_q x_q y_q^T (X, Y of shape (Q, 3N)); (N, 3)."""
+    R = np.ascontiguousarray(R, dtype=np.float64)
+    X = np.ascontiguousarray(np.atleast_2d(X), dtype=np.float64)
+    Y = np.ascontiguousarray(np.atleast_2d(Y), dtype=np.float64)
+    gR = np.empty(3 * int(p["n"]), dtype=np.float64)
+    lib().oracle_grad_pairs_R(ctypes.byref(_params(p)), _ptr(R), _ptr(X), _ptr(Y), X.shape[0],
+                              _ptr(gR))
+    return gR.reshape(-1, 3)
+
+
+def cheb_adjoint(D: np.ndarray, dmin: float, dmax: float, nch: int, dW: np.ndarray,
+                 h: np.ndarray):
+    """Reverse pass of the Chebyshev series of Sec. IV for L(dS) with
+    dL/ddS = h (both (m, 3N)), bounds and N_Ch held fixed.  Forward:
+    V_0 = dW, V_1 = Y V_0, V_p = 2 Y V_{p-1} - V_{p-2}, dS = sum c_p V_p - c_0/2 V_0,
+    Y = s D - t I.  Adjoints U_p = dL/dV_p run the recurrence backwards:
+    U_{N-1} = c_{N-1} h, U_p = c_p h + 2 Y U_{p+1} - U_{p+2} (p >= 1), and
+    dL/dD = s (U_1 V_0^T + 2 sum_{p>=2} U_p V_{p-1}^T),  dL/ddW = U_0.
+    Returns (X, Y) with dL/dD = sum_q X_q Y_q^T, and dL/ddW."""
+    dW = np.atleast_2d(dW).astype(np.float64)
+    h = np.atleast_2d(h).astype(np.float64)
+    c = cheb_coeffs(nch, dmin, dmax)
+    s = 2.0 / (dmax - dmin)
+    t = (dmax + dmin) / (dmax - dmin)
+    Yop = lambda V: s * (V @ D.T) - t * V          # rows are vectors; D symmetric
+    V = [dW]
+    if nch > 1:
+        V.append(Yop(dW))
+    for p_ in range(2, nch):
+        V.append(2.0 * Yop(V[-1]) - V[-2])
+    U = [None] * (nch + 2)
+    U[nch] = np.zeros_like(h)
+    U[nch + 1] = np.zeros_like(h)
+    for p_ in range(nch - 1, 0, -1):
+        U[p_] = c[p_] * h + 2.0 * Yop(U[p_ + 1]) - U[p_ + 2]
+    # V_1 = Y V_0 has coefficient 1, so U_0 gets Y U_1 (not 2 Y U_1)
+    U0 = 0.5 * c[0] * h + (Yop(U[1]) if nch > 1 else 0.0) - (U[2] if nch > 2 else 0.0)
+    Xs, Ys = [], []
+    if nch > 1:
+        Xs.append(s * U[1]); Ys.append(V[0])
+    for p_ in range(2, nch):
+        Xs.append(2.0 * s * U[p_]); Ys.append(V[p_ - 1])
+    m = dW.shape[0]
+    X = np.concatenate(Xs, axis=0) if Xs else np.zeros((0, dW.shape[1]))
+    Yv = np.concatenate(Ys, axis=0) if Ys else np.zeros((0, dW.shape[1]))
+    return X, Yv, U0
 
 
 def philox4x32_10(ctr, key):

@@ -557,8 +557,19 @@ static void add_radial_grad(const double v[3], double r, double f1, double f2, d
     }
 }
 
+/* General form: dL/dR for dL/dD = G = sum_q x_q y_q^T (Q pairs of 3N-vectors,
+ * X and Y stored [q][3N]); the drift adjoint is Q = 1 with x = g, y = F. */
+void oracle_grad_pairs_R(const oracle_params *p, const double *R, const double *X, const double *Y,
+                         int32_t Q, double *gR);
+
 void oracle_grad_DF_R(const oracle_params *p, const double *R, const double *F, const double *g,
                       double *gR)
+{
+    oracle_grad_pairs_R(p, R, g, F, 1, gR);
+}
+
+void oracle_grad_pairs_R(const oracle_params *p, const double *R, const double *X, const double *Y,
+                         int32_t Q, double *gR)
 {
     kterm *kl;
     int nk = build_klist(p, &kl);
@@ -571,9 +582,15 @@ void oracle_grad_DF_R(const oracle_params *p, const double *R, const double *F, 
         for (int mu = 0; mu < n; mu++) {
             if (mu == nu) continue;
             double W[9];
+            long n3 = 3L * n;
             for (int i = 0; i < 3; i++)
-                for (int j = 0; j < 3; j++)
-                    W[3 * i + j] = g[3 * nu + i] * F[3 * mu + j] + g[3 * mu + i] * F[3 * nu + j];
+                for (int j = 0; j < 3; j++) {
+                    double w = 0.0;
+                    for (int q = 0; q < Q; q++)
+                        w += X[q * n3 + 3 * nu + i] * Y[q * n3 + 3 * mu + j]
+                           + X[q * n3 + 3 * mu + i] * Y[q * n3 + 3 * nu + j];
+                    W[3 * i + j] = w;
+                }
             double d[3];
             for (int i = 0; i < 3; i++) {
                 d[i] = R[3 * nu + i] - R[3 * mu + i];

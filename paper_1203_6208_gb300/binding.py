@@ -28,6 +28,7 @@ BD_APPLY_REFINE = 1
 EXPORTS = ["bd_plan_create", "bd_plan_destroy", "bd_plan_query", "bd_forces", "bd_build_D",
            "bd_apply_D", "bd_eig_bounds", "bd_chebyshev_sqrt", "bd_step", "bd_wiener",
            "bd_set_phase_events", "bd_kernel_launches", "bd_eig_bounds_noalloc",
+           "bd_apply_D_backward", "bd_chebyshev_backward",
            "bd_last_error", "bd_version"]
 PHASES = ["forces", "build_D", "bounds", "first_product", "chebyshev", "update"]
 
@@ -61,7 +62,8 @@ class BdStepOpts(ctypes.Structure):
     _fields_ = [("m", ctypes.c_int32), ("n_cheb", ctypes.c_int32),
                 ("lanczos_iters", ctypes.c_int32), ("bound_safety", ctypes.c_double),
                 ("dmin_fraction", ctypes.c_double), ("seed", ctypes.c_uint64),
-                ("step_index", ctypes.c_uint64)]
+                ("step_index", ctypes.c_uint64), ("bounds_mode", ctypes.c_int32),
+                ("reserved", ctypes.c_int32)]
 
 
 STATS_BYTES = ctypes.sizeof(BdStepStats)
@@ -92,6 +94,8 @@ def load(path: str = LIB_PATH):
     L.bd_step.argtypes = [_vp, _vp, _vp, _vp, ctypes.POINTER(BdStepOpts), _vp, _vp, _vp, _vp]
     L.bd_wiener.argtypes = [_vp, u64, u64, i64, _vp, _vp]
     L.bd_set_phase_events.argtypes = [_vp, ctypes.POINTER(_vp), i32]
+    L.bd_apply_D_backward.argtypes = [_vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp]
+    L.bd_chebyshev_backward.argtypes = [_vp, _vp, _vp, _vp, i32, _vp, i32, _vp, _vp, _vp, _vp]
     L.bd_eig_bounds_noalloc.argtypes = [_vp, i32, i32, i32, f64, f64, _vp, _vp, _vp]
     L.bd_kernel_launches.restype = ctypes.c_uint64
     L.bd_last_error.restype = ctypes.c_char_p
@@ -198,12 +202,22 @@ class Plan:
                                         _p(dS), _p(Ef), _stream(stream)))
 
     def step(self, R, D, dW=None, *, m=1, n_cheb=20, lanczos_iters=30, bound_safety=0.05,
-             dmin_fraction=0.5, seed=0, step_index=0, DF=None, dS=None, stats=None, stream=None):
+             dmin_fraction=0.5, seed=0, step_index=0, DF=None, dS=None, stats=None,
+             bounds_mode=0, stream=None):
         o = BdStepOpts(m=int(m), n_cheb=int(n_cheb), lanczos_iters=int(lanczos_iters),
                        bound_safety=float(bound_safety), dmin_fraction=float(dmin_fraction),
-                       seed=int(seed), step_index=int(step_index))
+                       seed=int(seed), step_index=int(step_index), bounds_mode=int(bounds_mode))
         _check(load().bd_step(self._h, _p(R), _p(D), _p(dW), ctypes.byref(o), _p(DF), _p(dS),
                               _p(stats), _stream(stream)))
+
+    def apply_backward(self, R, D, F, gY, gR, gF=None, stream=None):
+        _check(load().bd_apply_D_backward(self._h, _p(R), _p(D), _p(F), _p(gY), _p(gR), _p(gF),
+                                          _stream(stream)))
+
+    def chebyshev_backward(self, R, D, bounds, n_cheb, dW, gS, gR, gdW=None, stream=None):
+        m = dW.shape[0] if dW.dim() == 2 else 1
+        _check(load().bd_chebyshev_backward(self._h, _p(R), _p(D), _p(bounds), int(n_cheb),
+                                            _p(dW), m, _p(gS), _p(gR), _p(gdW), _stream(stream)))
 
     def set_phase_events(self, events):
         """events: list of 7 torch.cuda.Event (enable_timing) or None."""

@@ -8,6 +8,7 @@
 
 #include "bd_internal.cuh"
 #include "tc_gemm.cuh"
+#include "adjoint.cuh"
 
 struct bd_plan {
     bd::Plan P;
@@ -55,11 +56,13 @@ static bd_status dmalloc(Plan &P, T **ptr, size_t count)
 
 static void free_plan(Plan &P)
 {
-    void *ptrs[] = {P.d_kvec, P.d_km64, P.d_km32, P.d_xsplit, P.d_ewc, P.d_tab, P.d_tab32, P.d_cos, P.d_sin, P.d_cos32, P.d_sin32, P.d_F, P.d_DF,
+    void *ptrs[] = {P.d_kvec, P.d_km64, P.d_km32, P.d_xsplit, P.d_ewc, P.d_ew64, P.d_ew32,
+                    P.d_pw64, P.d_pw32, P.d_tab, P.d_tab32, P.d_cos, P.d_sin, P.d_cos32, P.d_sin32, P.d_F, P.d_DF,
                     P.d_Rnew, P.d_V[0], P.d_V[1], P.d_V[2], P.d_X0, P.d_Y0, P.d_dS, P.d_dW,
                     P.d_coef, P.d_wdw, P.d_red, P.d_redpart, P.d_bounds, P.d_status, P.d_lq[0], P.d_lq[1],
                     P.d_lq[2], P.d_lab, P.d_x16, P.d_xscale, P.d_part, P.d_counters,
-                    P.d_stats_scratch, P.d_y32};
+                    P.d_stats_scratch, P.d_y32, P.d_lag_bounds, P.d_vhist, P.d_xhist, P.d_ubuf[0], P.d_ubuf[1],
+                    P.d_ubuf[2], P.d_ubuf[3]};
     for (void *p : ptrs)
         if (p) cudaFree(p);
 }
@@ -151,10 +154,14 @@ bd_status bd_plan_create(const bd_params *params, bd_plan **out_plan)
         if (st != BD_OK) goto fail;  \
     } while (0)
     TRY(dmalloc(P, &P.d_kvec, kMaxKvec));
-    TRY(dmalloc(P, &P.d_km64, (size_t)8 * kMaxKvec));
-    if (mixed) TRY(dmalloc(P, &P.d_km32, (size_t)8 * kMaxKvec));
+    TRY(dmalloc(P, &P.d_km64, (size_t)12 * kMaxKvec));
+    if (mixed) TRY(dmalloc(P, &P.d_km32, (size_t)12 * kMaxKvec));
     if (mixed) TRY(dmalloc(P, &P.d_xsplit, 2 * n3));
     TRY(dmalloc(P, &P.d_ewc, 1));
+    TRY(dmalloc(P, &P.d_ew64, 1));
+    if (mixed) TRY(dmalloc(P, &P.d_ew32, 1));
+    TRY(dmalloc(P, &P.d_pw64, n3));
+    if (mixed) TRY(dmalloc(P, &P.d_pw32, 2 * n3));
     m1_table_range(P.p, &P.tab_i0, &P.ntab);
     if (P.ntab > kTabMax) {
         st = set_error(BD_ERR_UNSUPPORTED, "r_c/a ratio needs %d table intervals (limit %d)",
@@ -167,8 +174,9 @@ bd_status bd_plan_create(const bd_params *params, bd_plan **out_plan)
     TRY(dmalloc(P, &P.d_DF, n3));
     TRY(dmalloc(P, &P.d_Rnew, n3));
     for (int i = 0; i < 3; i++) TRY(dmalloc(P, &P.d_V[i], n3 * R));
-    TRY(dmalloc(P, &P.d_X0, n3 * (R + 1)));
-    TRY(dmalloc(P, &P.d_Y0, n3 * (R + 1)));
+    TRY(dmalloc(P, &P.d_X0, n3 * (R + 2)));
+    TRY(dmalloc(P, &P.d_Y0, n3 * (R + 2)));
+    TRY(dmalloc(P, &P.d_lag_bounds, 2));
     TRY(dmalloc(P, &P.d_dS, n3 * R));
     TRY(dmalloc(P, &P.d_dW, n3 * R));
     TRY(dmalloc(P, &P.d_coef, kMaxCheb));
@@ -322,8 +330,10 @@ bd_status bd_eig_bounds(bd_plan *plan, const void *D, int32_t iters, double safe
 // Chebyshev recurrence given W = D dW; dS and E_f outputs
 static bd_status cheb_core(Plan &P, const void *D, const double *bounds, int nch,
                            const double *dW, const double *W, int m, double *dS, double *Ef,
-                           bd_step_stats *stats, cudaStream_t s)
+                           bd_step_stats *stats, cudaStream_t s, int lanczos_from = -1)
 {
+    // lanczos_from >= 0: a Lanczos recurrence (its step lanczos_from already
+    // taken) rides as an extra column of every product (mixed plans only)
     launch_cheb_coeffs(P, bounds, nch, s);
     double *A = P.d_V[0], *B = P.d_V[1];
     launch_cheb_first(P, bounds, dW, W, m, A, B, dS, s);   // A = V0, B = V1
@@ -336,8 +346,11 @@ static bd_status cheb_core(Plan &P, const void *D, const double *bounds, int nch
             float *D32;
             void *D16;
             split_mixed(P, (void *)D, &D32, &D16);
-            bd_status st = tc_cheb(P, D16, m, P.d_coef, bounds, p, prev2, prev1, dS, s);
+            const bool lan = lanczos_from >= 0;
+            bd_status st = tc_cheb(P, D16, m, P.d_coef, bounds, p, prev2, prev1, dS, s,
+                                   lan ? P.d_lq[1] : nullptr, lan ? P.d_lq[2] : nullptr);
             if (st != BD_OK) return st;
+            if (lan) launch_lanczos_update(P, lanczos_from + (p - 1), s);
         }
         double *t = prev2;   // prev2 now holds V_p
         prev2 = prev1;
@@ -400,10 +413,17 @@ bd_status bd_step(bd_plan *plan, double *R, void *D, const double *dW, const bd_
     st = bd_build_D(plan, R, D, s);
     if (st != BD_OK) return st;
     PHASE(2);
-    // (a6) bounds
-    st = eig_bounds_core(P, D, o->lanczos_iters, o->bound_safety, o->dmin_fraction, P.d_bounds,
-                         P.d_status + 3, s);
-    if (st != BD_OK) return st;
+    // (a6) bounds: fresh Lanczos, or the previous step's lagged recurrence
+    const bool lag = o->bounds_mode == BD_BOUNDS_LAGGED && is_mixed(P) && o->n_cheb >= 8 &&
+                     o->n_cheb - 1 <= kMaxLanczos && m + 2 <= kMaxRhs;
+    if (lag && P.lag_valid) {
+        cudaMemcpyAsync(P.d_bounds, P.d_lag_bounds, 2 * sizeof(double), cudaMemcpyDeviceToDevice, s);
+        launch_check_bounds(P.d_bounds, P.d_status + 3, s);
+    } else {
+        st = eig_bounds_core(P, D, o->lanczos_iters, o->bound_safety, o->dmin_fraction,
+                             P.d_bounds, P.d_status + 3, s);
+        if (st != BD_OK) return st;
+    }
     launch_stats_bounds(st_dev, P.d_bounds, P.d_status + 3, s);
     PHASE(3);
     // Wiener increments
@@ -415,13 +435,24 @@ bd_status bd_step(bd_plan *plan, double *R, void *D, const double *dW, const bd_
     // (a5) first product D [F, dW]  (one pass over D)
     double *Wcols;
     if (m + 1 <= kMaxRhs && m + 1 <= P.p.max_rhs + 1) {
+        const int extra = lag ? 1 : 0;     // the Lanczos start vector q_1
         cudaMemcpyAsync(P.d_X0, P.d_F, n3 * sizeof(double), cudaMemcpyDeviceToDevice, s);
         cudaMemcpyAsync(P.d_X0 + n3, w, n3 * m * sizeof(double), cudaMemcpyDeviceToDevice, s);
-        st = apply_core(P, D, P.d_X0, m + 1, P.d_Y0, 0, s);
+        if (lag) {
+            launch_lanczos_init(P, s);
+            cudaMemcpyAsync(P.d_X0 + n3 * (m + 1), P.d_lq[1], n3 * sizeof(double),
+                            cudaMemcpyDeviceToDevice, s);
+        }
+        st = apply_core(P, D, P.d_X0, m + 1 + extra, P.d_Y0, 0, s);
         if (st != BD_OK) return st;
         Wcols = P.d_Y0 + n3;
         if (is_mixed(P)) {   // refine the drift column only
             launch_refine_f32(P, (const float *)D, P.d_F, 1, P.d_Y0, s);
+        }
+        if (lag) {           // Lanczos step 0 from the product's last column
+            cudaMemcpyAsync(P.d_lq[2], P.d_Y0 + n3 * (m + 1), n3 * sizeof(double),
+                            cudaMemcpyDeviceToDevice, s);
+            launch_lanczos_update(P, 0, s);
         }
     } else {
         st = apply_core(P, D, P.d_F, 1, P.d_Y0, BD_APPLY_REFINE, s);
@@ -434,8 +465,14 @@ bd_status bd_step(bd_plan *plan, double *R, void *D, const double *dW, const bd_
     PHASE(4);
     // (a7) Chebyshev
     double *dSd = dS ? dS : P.d_dS;
-    st = cheb_core(P, D, P.d_bounds, o->n_cheb, w, Wcols, m, dSd, nullptr, st_dev, s);
+    st = cheb_core(P, D, P.d_bounds, o->n_cheb, w, Wcols, m, dSd, nullptr, st_dev, s,
+                   lag ? 0 : -1);
     if (st != BD_OK) return st;
+    if (lag) {               // N_Ch - 1 Lanczos steps -> bounds of the next step
+        launch_lanczos_finish(P, o->n_cheb - 1, o->bound_safety, o->dmin_fraction,
+                              P.d_lag_bounds, nullptr, s);
+        P.lag_valid = 1;
+    }
     PHASE(5);
     // (a8) Euler update with FENE rejection
     launch_euler(P, R, DFd, dSd, st_dev, s);
@@ -443,6 +480,85 @@ bd_status bd_step(bd_plan *plan, double *R, void *D, const double *dW, const bd_
 #undef PHASE
     if (DF) cudaMemcpyAsync(DF, DFd, n3 * sizeof(double), cudaMemcpyDeviceToDevice, s);
     return check_launch("bd_step");
+}
+
+static bd_status ensure_backward_scratch(Plan &P)
+{
+    if (P.d_vhist) return BD_OK;
+    size_t blk = (size_t)P.n3 * P.p.max_rhs;
+    size_t hist = (size_t)(P.p.max_cheb - 1) * blk;
+    bd_status st = dmalloc(P, &P.d_vhist, hist);
+    if (st == BD_OK) st = dmalloc(P, &P.d_xhist, hist);
+    for (int i = 0; i < 4 && st == BD_OK; i++) st = dmalloc(P, &P.d_ubuf[i], blk);
+    return st;
+}
+
+bd_status bd_apply_D_backward(bd_plan *plan, const double *R, const void *D, const double *F,
+                              const double *gY, double *gR, double *gF, bd_stream stream)
+{
+    if (!plan || !R || !F || !gY || !gR) return set_error(BD_ERR_INVALID, "NULL argument");
+    Plan &P = plan->P;
+    if (gF) {
+        if (!D) return set_error(BD_ERR_INVALID, "gF requested without D");
+        bd_status st = apply_core(P, D, gY, 1, gF, BD_APPLY_REFINE, stream);
+        if (st != BD_OK) return st;
+    }
+    launch_pair_adjoint(P, R, gY, F, 1, gR, stream);
+    return check_launch("bd_apply_D_backward");
+}
+
+bd_status bd_chebyshev_backward(bd_plan *plan, const double *R, const void *D,
+                                const double *bounds, int32_t n_cheb, const double *dW,
+                                int32_t m, const double *gS, double *gR, double *gdW,
+                                bd_stream stream)
+{
+    if (!plan || !R || !D || !bounds || !dW || !gS || !gR)
+        return set_error(BD_ERR_INVALID, "NULL argument");
+    Plan &P = plan->P;
+    if (m < 1 || m > P.p.max_rhs) return set_error(BD_ERR_INVALID, "m=%d outside [1, max_rhs=%d]", m, P.p.max_rhs);
+    if (n_cheb < 2 || n_cheb > P.p.max_cheb)
+        return set_error(BD_ERR_INVALID, "n_cheb=%d outside [2, max_cheb=%d]", n_cheb, P.p.max_cheb);
+    bd_status st = ensure_backward_scratch(P);
+    if (st != BD_OK) return st;
+    cudaStream_t s = stream;
+    const long len = (long)P.n3 * m;
+    const int N = n_cheb;
+    double *W = P.d_ubuf[3];
+    launch_cheb_coeffs(P, bounds, N, s);
+    // forward history V_0 .. V_{N-2} (V_0 = dW, V_1 = Y V_0, V_p = 2 Y V_{p-1} - V_{p-2})
+    double *Vh = P.d_vhist;
+    cudaMemcpyAsync(Vh, dW, len * sizeof(double), cudaMemcpyDeviceToDevice, s);
+    for (int p = 1; p <= N - 2; p++) {
+        st = apply_core(P, D, Vh + (long)(p - 1) * len, m, W, 0, s);
+        if (st != BD_OK) return st;
+        launch_cheb_hist(W, Vh + (long)(p - 1) * len, p >= 2 ? Vh + (long)(p - 2) * len : nullptr,
+                         len, bounds, p == 1 ? 1.0 : 2.0, 1.0, Vh + (long)p * len, s);
+    }
+    // adjoint recurrence: U_{N-1} = c_{N-1} h, U_p = c_p h + 2 Y U_{p+1} - U_{p+2},
+    // X_{p-1} = (p == 1 ? 1 : 2) s U_p pairs with V_{p-1}
+    double *Uq2 = nullptr, *Uq1 = nullptr;      // U_{p+2}, U_{p+1}
+    double *bufs[3] = {P.d_ubuf[0], P.d_ubuf[1], P.d_ubuf[2]};
+    for (int p = N - 1; p >= 1; p--) {
+        double *Up = bufs[p % 3];
+        if (p == N - 1) {
+            launch_cheb_adj(gS, nullptr, nullptr, nullptr, len, bounds, P.d_coef, p, 0.0, 1.0, Up, s);
+        } else {
+            st = apply_core(P, D, Uq1, m, W, 0, s);
+            if (st != BD_OK) return st;
+            launch_cheb_adj(gS, W, Uq1, Uq2, len, bounds, P.d_coef, p, 2.0, 1.0, Up, s);
+        }
+        launch_scale_copy(Up, len, bounds, p == 1 ? 1.0 : 2.0, P.d_xhist + (long)(p - 1) * len, s);
+        Uq2 = Uq1;
+        Uq1 = Up;
+    }
+    if (gdW) {
+        // U_0 = (c_0/2) h + Y U_1 - U_2
+        st = apply_core(P, D, Uq1, m, W, 0, s);
+        if (st != BD_OK) return st;
+        launch_cheb_adj(gS, W, Uq1, Uq2, len, bounds, P.d_coef, 0, 1.0, 0.5, gdW, s);
+    }
+    launch_pair_adjoint(P, R, P.d_xhist, Vh, (N - 1) * m, gR, s);
+    return check_launch("bd_chebyshev_backward");
 }
 
 }  // extern "C"

@@ -41,6 +41,16 @@ constexpr int kTabDeg = 8;
 constexpr int kTabStride = 2 + 2 * (kTabDeg + 1);  // doubles per interval
 constexpr int kTabMax = 512;
 
+// the Eq. (M1) coefficients and the box constants in the working precision of
+// a pair kernel (converted once per plan: on this GPU a double-to-float
+// conversion issues on the FP64 pipe, which must stay out of FP32 loops)
+template <typename T> struct EwaldT {
+    T alpha, alpha2, A1, A3, P0, P1, P2, Q, R0, R1, R2, S;
+    T g1a, g1b, g2a, g2b, inv_a, rc2, four_a2, self;
+    T L, Llo, halfL;     // box edge as T plus its low-order remainder (FP32: L - (float)L)
+    float Lf, invLf;     // box edge and its inverse for the FP32 image cursor
+};
+
 constexpr int kMaxKvec = 4096;        // half-space k-vectors a plan may use
 constexpr int kMaxRhs = 32;           // Wiener columns per product
 constexpr int kMaxCheb = 256;         // Chebyshev terms
@@ -54,9 +64,13 @@ struct Plan {
     int nk;                            // half-space k-vectors in use
     double self_coeff;                 // self term of Eq. (DF)
     KVec *d_kvec;                      // [nk], device
-    double *d_km64;                    // folded M2 tensors [nk][8] (xx xy xz yy yz zz, pad)
+    double *d_km64;                    // folded M2 tensors and k: [nk][12] (6 tensor, 3 k, pad)
     float *d_km32;                     // the same in FP32 (mixed plans)
     EwaldCoef *d_ewc;                  // Eq. (M1) coefficients, device
+    EwaldT<double> *d_ew64;            // the same per working precision
+    EwaldT<float> *d_ew32;
+    double *d_pw64;                    // positions wrapped into [0, L), FP64 [3N]
+    float *d_pw32;                     // the same as FP32 hi/lo words [2][3N]
     double *d_tab;                     // M1 table [ntab][kTabStride] (FP64)
     float *d_tab32;                    // the same table in FP32 (mixed plans)
     int tab_i0, ntab;                  // first interval index, interval count
@@ -89,9 +103,15 @@ struct Plan {
     int64_t scratch_bytes;
     bd_step_stats *d_stats_scratch;
     cudaEvent_t phase_ev[BD_PHASE_EVENTS];
+    double *d_lag_bounds;              // bounds from the previous step's lagged Lanczos
+    int lag_valid;                     // host flag: d_lag_bounds was produced
     int phase_on;
     float *d_y32;                      // FP32 product scratch (mixed plans)
     float *d_xsplit;                   // refinement operand: hi/lo FP32 words [2][3N]
+    // reverse mode (allocated by the first backward call)
+    double *d_vhist;                   // V_0..V_{N_Ch-2}, [max_cheb-1][max_rhs][3N]
+    double *d_xhist;                   // scaled adjoints X_q, same shape
+    double *d_ubuf[4];                 // rolling adjoint vectors and D U products
 };
 
 // host-side count of kernel launches (bd_kernel_launches)
@@ -138,6 +158,7 @@ void launch_lanczos_update(Plan &P, int j, cudaStream_t s);
 void launch_lanczos_finish(Plan &P, int k, double safety_max, double dmin_fraction,
                            double *bounds, int32_t *status, cudaStream_t s);
 void launch_stats_begin(bd_step_stats *st, int nch, cudaStream_t s);
+void launch_check_bounds(const double *bounds, int32_t *status, cudaStream_t s);
 void launch_stats_bounds(bd_step_stats *st, const double *bounds, const int32_t *bstatus,
                          cudaStream_t s);
 void launch_euler(Plan &P, double *R, const double *DF, const double *dS, bd_step_stats *stats,

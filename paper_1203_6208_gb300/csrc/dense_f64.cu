@@ -102,6 +102,30 @@ k_gemm_f64(const double *__restrict__ D, long ld, int n3, const double *__restri
     }
 }
 
+// m = 1 (Lanczos and single products): one warp per row, each lane streams
+// a strided slice of the row with two independent FP64 accumulators; the
+// FP64 pipe (one FMA per 8 bytes) and HBM are then both near their limits
+__global__ void __launch_bounds__(256)
+k_gemv_f64(const double *__restrict__ D, long ld, int n3, const double *__restrict__ x,
+           double *__restrict__ y)
+{
+    const long row = ((long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (row >= n3) return;
+    const double *d = D + row * ld;
+    double a0 = 0.0, a1 = 0.0;
+    int k = lane;
+    for (; k + 32 < n3; k += 64) {
+        a0 = fma(__ldg(d + k), __ldg(x + k), a0);
+        a1 = fma(__ldg(d + k + 32), __ldg(x + k + 32), a1);
+    }
+    if (k < n3) a0 = fma(__ldg(d + k), __ldg(x + k), a0);
+    double a = a0 + a1;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) a += __shfl_xor_sync(0xffffffffu, a, o);
+    if (lane == 0) y[row] = a;
+}
+
 template <bool CHEB>
 static void dispatch(const Plan &P, const double *D, const double *X, int m, double *Y,
                      const ChebEpi &e, cudaStream_t s)
@@ -122,6 +146,12 @@ static void dispatch(const Plan &P, const double *D, const double *X, int m, dou
 void launch_gemm_f64(const Plan &P, const double *D, const double *X, int m, double *Y,
                      cudaStream_t s)
 {
+    if (m == 1) {
+        long threads = (long)P.n3 * 32;
+        k_gemv_f64<<<(unsigned)((threads + 255) / 256), 256, 0, s>>>(D, P.ld, P.n3, X, Y);
+        count_launches(1);
+        return;
+    }
     ChebEpi e{};
     dispatch<false>(P, D, X, m, Y, e, s);
 }

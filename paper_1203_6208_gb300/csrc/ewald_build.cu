@@ -15,46 +15,11 @@
 #include <string.h>
 
 #include "bd_internal.cuh"
+#include "pair_common.cuh"
 
 namespace bd {
 
 
-
-// Taylor coefficients (in s^2, s = alpha r) of sqrt(pi) times the brackets of
-// the smooth remainder G = Omega_A - M1; generated by gen_overlap_series.py.
-constexpr int kNT = 22;
-__constant__ double c_A1[kNT] = {
-    6.0, -8.0, 5.4, -2.2857142857142856, 0.6944444444444444, -0.16363636363636364,
-    0.03141025641025641, -0.005079365079365079, 0.0007090336134453781,
-    -8.702311333890281e-05, 9.526958931720837e-06, -9.410878976096367e-07,
-    8.467612634279301e-08, -6.994605760037859e-09, 5.33982984721901e-10,
-    -3.7890462877662056e-11, 2.511398089199917e-12, -1.5615636864136263e-13,
-    9.143568187556154e-15, -5.058852459461126e-16, 2.6526586417765823e-17,
-    -1.3218562987927494e-18};
-__constant__ double c_B1[kNT] = {
-    -13.333333333333334, 33.6, -30.857142857142858, 16.296296296296298,
-    -5.909090909090909, 1.6153846153846154, -0.35259259259259257, 0.06386554621848739,
-    -0.009868421052631578, 0.0013280003359368439, -0.0001581550494593973,
-    1.6883116883116884e-05, -1.6324077538069307e-06, 1.4419913845201202e-07,
-    -1.1722361952776699e-08, 8.824363482051473e-10, -6.184370555118855e-11,
-    4.053969390103844e-12, -2.495869175082804e-13, 1.4484358297954673e-14,
-    -7.949163105921851e-16, 4.137632749951742e-17};
-__constant__ double c_A2s[kNT] = {
-    4.0, -3.6, 1.7142857142857142, -0.5555555555555556, 0.13636363636363635,
-    -0.026923076923076925, 0.0044444444444444444, -0.0006302521008403362,
-    7.832080200501253e-05, -8.660871756109852e-06, 8.62663906142167e-07,
-    -7.816257816257817e-08, 6.494991062892297e-09, -4.983841190737743e-10,
-    3.552230894780818e-11, -2.363668789835216e-12, 1.474810148279536e-13,
-    -8.662327756632145e-15, 4.80590983648807e-16, -2.526341563596745e-17,
-    1.261771921574897e-18, -6.00236859277332e-20};
-__constant__ double c_B2s[kNT] = {
-    -16.8, 20.571428571428573, -12.222222222222221, 4.7272727272727275,
-    -1.3461538461538463, 0.3022222222222222, -0.05588235294117647, 0.008771929824561403,
-    -0.0011952003023431594, 0.00014377731769036118, -1.5476190476190476e-05,
-    1.506837926591013e-06, -1.3389919999115402e-07, 1.0940871155924919e-08,
-    -8.272840764423256e-10, 5.820584051876569e-11, -3.8287488684314084e-12,
-    2.3645076395521305e-13, -1.376014038305694e-14, 7.570631529449383e-16,
-    -3.949558534044845e-17, 1.958959888557287e-18};
 
 // ---------------------------------------------------------------------------
 // Plan-time tables (FP64, on the device)
@@ -81,6 +46,43 @@ __global__ void k_ewald_coef(double a, double alpha, double L, double rc, EwaldC
     c.g2a = a * al3 * rpi; c.g2b = a3 * al5 * rpi;
     c.inv_a = 1.0 / a;
     *out = c;
+}
+
+template <typename T>
+__device__ void fill_ewt(const EwaldCoef &c, EwaldT<T> *o)
+{
+    o->alpha = (T)c.alpha; o->alpha2 = (T)c.alpha2; o->A1 = (T)c.A1; o->A3 = (T)c.A3;
+    o->P0 = (T)c.P0; o->P1 = (T)c.P1; o->P2 = (T)c.P2; o->Q = (T)c.Q;
+    o->R0 = (T)c.R0; o->R1 = (T)c.R1; o->R2 = (T)c.R2; o->S = (T)c.S;
+    o->g1a = (T)c.g1a; o->g1b = (T)c.g1b; o->g2a = (T)c.g2a; o->g2b = (T)c.g2b;
+    o->inv_a = (T)c.inv_a; o->rc2 = (T)c.rc2; o->four_a2 = (T)c.four_a2; o->self = (T)c.self;
+    o->L = (T)c.L;
+    o->Llo = (T)(c.L - (double)(T)c.L);
+    o->halfL = (T)(0.5 * c.L);
+    o->Lf = (float)c.L;
+    o->invLf = (float)c.invL;
+}
+
+__global__ void k_ewald_typed(const EwaldCoef *c, EwaldT<double> *o64, EwaldT<float> *o32)
+{
+    fill_ewt<double>(*c, o64);
+    if (o32) fill_ewt<float>(*c, o32);
+}
+
+// positions wrapped into [0, L): FP64, and as FP32 hi/lo words
+__global__ void k_wrap(const double *R, int n3, double L, double *pw, float *pw32)
+{
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n3) return;
+    double x = R[i];
+    x -= L * floor(x / L);
+    if (x >= L) x -= L;
+    pw[i] = x;
+    if (pw32) {
+        float h = (float)x;
+        pw32[i] = h;
+        pw32[n3 + i] = (float)(x - (double)h);
+    }
 }
 
 // M2(k) of Eq. (M2) for the half-space vectors n (integers from the host),
@@ -169,15 +171,16 @@ __global__ void k_m1_table(const EwaldCoef *ewc, int i0, int ntab, double *tab, 
     }
 }
 
-// the six folded tensor components per k in the working precision, [nk][8]
+// per k in the working precision, [nk][12]: the six folded tensor components
+// (xx xy xz yy yz zz), then k (x y z), then padding
 __global__ void k_kvec_m(const KVec *kv, int nk, double *m64, float *m32)
 {
     int t = blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= nk) return;
-    for (int i = 0; i < 8; i++) {
-        double v = i < 6 ? kv[t].m[i] : 0.0;
-        m64[8 * t + i] = v;
-        if (m32) m32[8 * t + i] = (float)v;
+    for (int i = 0; i < 12; i++) {
+        double v = i < 6 ? kv[t].m[i] : (i < 9 ? kv[t].k[i - 6] : 0.0);
+        m64[12 * t + i] = v;
+        if (m32) m32[12 * t + i] = (float)v;
     }
 }
 
@@ -201,64 +204,6 @@ __global__ void k_trig(const double *R, int n, const KVec *kv, int nk, double *c
     }
 }
 
-// ---------------------------------------------------------------------------
-// Per-thread image cursor.  Enumerates integer n with |d + n L| <= r_c using
-// FP32 range bounds widened by a margin (a superset of the exact set); the
-// exact inclusion test |v|^2 <= r_c^2 is then taken in the working precision
-// at the evaluation site.  Every loop index only increases, so the cursor
-// always terminates.
-struct ImageCursor {
-    float dx, dy, dz, L, invL, rc2, margin;
-    int nx, ny, nz, nxh, nyh, nzh;
-    float remx;
-    bool done;
-
-    __device__ __forceinline__ static int lo_of(float rho, float c, float invL)
-    {
-        return (int)ceilf((-rho - c) * invL - 1e-4f);
-    }
-    __device__ __forceinline__ static int hi_of(float rho, float c, float invL)
-    {
-        return (int)floorf((rho - c) * invL + 1e-4f);
-    }
-
-    __device__ void start(float dx_, float dy_, float dz_, float L_, float invL_, float rc_)
-    {
-        dx = dx_; dy = dy_; dz = dz_; L = L_; invL = invL_;
-        rc2 = rc_ * rc_;
-        margin = rc2 * 1e-5f + 1e-6f;
-        nx = lo_of(rc_, dx, invL) - 1;
-        nxh = hi_of(rc_, dx, invL);
-        ny = 0; nyh = -1;
-        nz = 0; nzh = -1;
-        done = false;
-        advance();
-    }
-
-    __device__ void advance()
-    {
-        nz++;
-        while (nz > nzh) {
-            ny++;
-            while (ny > nyh) {
-                nx++;
-                if (nx > nxh) { done = true; return; }
-                float vx = fmaf((float)nx, L, dx);
-                remx = rc2 - vx * vx;
-                float t = remx + margin;
-                float rho = t > 0.f ? sqrtf(t) : -1.f;
-                ny = lo_of(rho, dy, invL);
-                nyh = hi_of(rho, dy, invL);
-            }
-            float vy = fmaf((float)ny, L, dy);
-            float t = remx - vy * vy + margin;
-            float rho = t > 0.f ? sqrtf(t) : -1.f;
-            nz = lo_of(rho, dz, invL);
-            nzh = hi_of(rho, dz, invL);
-        }
-    }
-};
-
 template <typename T> struct Math;
 template <> struct Math<double> {
     __device__ static double rsqrt_(double x) { return rsqrt(x); }
@@ -273,23 +218,10 @@ template <> struct Math<float> {
     __device__ static float exp_(float x) { return expf(x); }
 };
 
-template <typename T> struct CoefT {
-    T alpha, alpha2, A1, A3, P0, P1, P2, Q, R0, R1, R2, S, g1a, g1b, g2a, g2b, inv_a;
-    __device__ void load(const EwaldCoef &c_ew)
-    {
-        alpha = (T)c_ew.alpha; alpha2 = (T)c_ew.alpha2;
-        A1 = (T)c_ew.A1; A3 = (T)c_ew.A3;
-        P0 = (T)c_ew.P0; P1 = (T)c_ew.P1; P2 = (T)c_ew.P2; Q = (T)c_ew.Q;
-        R0 = (T)c_ew.R0; R1 = (T)c_ew.R1; R2 = (T)c_ew.R2; S = (T)c_ew.S;
-        g1a = (T)c_ew.g1a; g1b = (T)c_ew.g1b; g2a = (T)c_ew.g2a; g2b = (T)c_ew.g2b;
-        inv_a = (T)c_ew.inv_a;
-    }
-};
-
 // Eq. (M1) for one image vector v (u = |v|^2 > 0); accumulates the six
 // independent components (xx, xy, xz, yy, yz, zz).
 template <typename T>
-__device__ __forceinline__ void add_m1(T vx, T vy, T vz, T u, const CoefT<T> &c, T acc[6])
+__device__ __forceinline__ void add_m1(T vx, T vy, T vz, T u, const EwaldT<T> &c, T acc[6])
 {
     T rinv = Math<T>::rsqrt_(u);
     T r = u * rinv;
@@ -348,7 +280,7 @@ __device__ __forceinline__ T horner(const double *cf, T x)
 // avoids the (a/r)^3 cancellation between M1 and M*.  For s^2 > 1 (only
 // reachable with alpha > 1/(2a)) the direct sum M1 + M* is used instead.
 template <typename T>
-__device__ void add_overlap(T vx, T vy, T vz, T u, const CoefT<T> &c, T acc[6])
+__device__ void add_overlap(T vx, T vy, T vz, T u, const EwaldT<T> &c, T acc[6])
 {
     T s2 = c.alpha2 * u;
     T d1, d2;
@@ -398,65 +330,110 @@ template <> struct Store<float> {
     }
 };
 
+template <typename T> struct Sep;
+template <> struct Sep<double> {
+    __device__ static void get(const double *pw, const float *, long, int nu, int mu,
+                               const EwaldT<double> &c, double d[3])
+    {
+#pragma unroll
+        for (int s = 0; s < 3; s++) {
+            double x = pw[3 * nu + s] - pw[3 * mu + s];
+            x = x > c.halfL ? x - c.L : (x < -c.halfL ? x + c.L : x);
+            d[s] = x;
+        }
+    }
+};
+template <> struct Sep<float> {
+    __device__ static void get(const double *, const float *pw32, long n3, int nu, int mu,
+                               const EwaldT<float> &c, float d[3])
+    {
+#pragma unroll
+        for (int s = 0; s < 3; s++) {
+            float a = pw32[3 * nu + s], b = -pw32[3 * mu + s];
+            float hs = a + b;                                  // TwoSum(a, b)
+            float bb = hs - a;
+            float he = (a - (hs - bb)) + (b - bb);
+            he += pw32[n3 + 3 * nu + s] - pw32[n3 + 3 * mu + s];
+            if (hs > c.halfL) { hs -= c.L; he -= c.Llo; }
+            else if (hs < -c.halfL) { hs += c.L; he += c.Llo; }
+            d[s] = hs + he;
+        }
+    }
+};
+
+constexpr int KC = 64;                 // k-vectors per shared-memory chunk
+
 template <typename T>
 __global__ void __launch_bounds__(TB *TB)
-k_build_D(const double *__restrict__ R, int n, const EwaldCoef *__restrict__ ewc,
+k_build_D(const double *__restrict__ pw, const float *__restrict__ pw32, int n,
+          const EwaldT<T> *__restrict__ ewt, const EwaldCoef *__restrict__ ewc,
           const T *__restrict__ tab, int tab_i0, int ntab, const T *__restrict__ km, int nk,
           const T *__restrict__ cs, const T *__restrict__ sn, int overlap_corr, float rc,
           T *__restrict__ D, void *__restrict__ D16, int is_bf16, long ld)
 {
     __shared__ T tile[TS * TSP];
-    // tile pair (I <= J) from the linear index over the upper triangle
+    __shared__ T s_tr[4][KC][TB];      // cos nu, sin nu, cos mu, sin mu for one k chunk
+    __shared__ T s_km[KC][6];
+    // tile pair (I <= J) from the linear index over the upper triangle (FP32
+    // estimate, integer correction: no FP64 instruction)
     long idx = blockIdx.x;
-    int J = (int)((sqrt(8.0 * (double)idx + 1.0) - 1.0) * 0.5);
+    int J = (int)((sqrtf(8.0f * (float)idx + 1.0f) - 1.0f) * 0.5f);
     while ((long)J * (J + 1) / 2 > idx) J--;
     while ((long)(J + 1) * (J + 2) / 2 <= idx) J++;
     int I = (int)(idx - (long)J * (J + 1) / 2);
-    const EwaldCoef &c_ew = *ewc;
+    const EwaldT<T> c = *ewt;
+    (void)ewc;
     int ty = threadIdx.x / TB, tx = threadIdx.x % TB;
     int nu = I * TB + ty, mu = J * TB + tx;
     T acc[6] = {0, 0, 0, 0, 0, 0};
     // diagonal tiles compute nu <= mu only; the rest is mirrored on write,
     // which keeps D exactly symmetric
-    if (nu < n && mu < n && !(I == J && ty > tx)) {
-        CoefT<T> c;
-        c.load(c_ew);
-        const double L = c_ew.L, invL = c_ew.invL;
-        double d[3];
-        for (int s = 0; s < 3; s++) {
-            double x = R[3 * nu + s] - R[3 * mu + s];
-            d[s] = x - L * rint(x * invL);       // minimum image
-        }
+    const bool active = nu < n && mu < n && !(I == J && ty > tx);
+    const long n3 = 3L * n;
+    if (active) {
+        T d[3];
+        Sep<T>::get(pw, pw32, n3, nu, mu, c, d);
         const bool same = (nu == mu);
-        const T rc2 = (T)c_ew.rc2, four_a2 = (T)c_ew.four_a2;
-        const T Lt = (T)L;
-        const T dx = (T)d[0], dy = (T)d[1], dz = (T)d[2];
         ImageCursor cur;
-        cur.start((float)d[0], (float)d[1], (float)d[2], (float)L, (float)invL, rc);
+        cur.start((float)d[0], (float)d[1], (float)d[2], c.Lf, c.invLf, rc);
         while (!cur.done) {
-            T vx = dx + (T)cur.nx * Lt, vy = dy + (T)cur.ny * Lt, vz = dz + (T)cur.nz * Lt;
+            T vx = d[0] + (T)cur.nx * c.L, vy = d[1] + (T)cur.ny * c.L,
+              vz = d[2] + (T)cur.nz * c.L;
             T u = vx * vx + vy * vy + vz * vz;
             bool zero_image = same && cur.nx == 0 && cur.ny == 0 && cur.nz == 0;
-            if (u <= rc2 && !zero_image) {
-                if (u >= four_a2) add_m1_tab<T>(vx, vy, vz, u, tab, tab_i0, ntab, acc);
+            if (u <= c.rc2 && !zero_image) {
+                if (u >= c.four_a2) add_m1_tab<T>(vx, vy, vz, u, tab, tab_i0, ntab, acc);
                 else if (!same && overlap_corr) add_overlap<T>(vx, vy, vz, u, c, acc);
                 else add_m1<T>(vx, vy, vz, u, c, acc);
             }
             cur.advance();
         }
-        // reciprocal sum over half-space k (each folded with -k)
-        for (int t = 0; t < nk; t++) {
-            T cf = cs[(size_t)t * n + nu] * cs[(size_t)t * n + mu]
-                 + sn[(size_t)t * n + nu] * sn[(size_t)t * n + mu];
-            const T *mk = km + 8 * t;
-#pragma unroll
-            for (int i = 0; i < 6; i++) acc[i] += __ldg(mk + i) * cf;
-        }
         if (same) {
-            T sc = (T)c_ew.self;
-            acc[0] += sc; acc[3] += sc; acc[5] += sc;
+            acc[0] += c.self; acc[3] += c.self; acc[5] += c.self;
         }
     }
+    // reciprocal sum over half-space k (each folded with -k), staged per chunk
+    for (int t0 = 0; t0 < nk; t0 += KC) {
+        const int kc = min(KC, nk - t0);
+        __syncthreads();
+        for (int e = threadIdx.x; e < 4 * kc * TB; e += TB * TB) {
+            int w = e / (kc * TB), r = e % (kc * TB), t = r / TB, b = r % TB;
+            int bead = (w < 2 ? I : J) * TB + b;
+            const T *src = (w & 1) ? sn : cs;
+            s_tr[w][t][b] = bead < n ? src[(size_t)(t0 + t) * n + bead] : (T)0;
+        }
+        for (int e = threadIdx.x; e < 6 * kc; e += TB * TB)
+            s_km[e / 6][e % 6] = km[12 * (t0 + e / 6) + e % 6];
+        __syncthreads();
+        if (active) {
+            for (int t = 0; t < kc; t++) {
+                T cf = s_tr[0][t][ty] * s_tr[2][t][tx] + s_tr[1][t][ty] * s_tr[3][t][tx];
+#pragma unroll
+                for (int i = 0; i < 6; i++) acc[i] += s_km[t][i] * cf;
+            }
+        }
+    }
+    __syncthreads();
     // stage the 3x3 block: rows 3ty+a, cols 3tx+b
     {
         T *b = &tile[(3 * ty) * TSP + 3 * tx];
@@ -465,7 +442,6 @@ k_build_D(const double *__restrict__ R, int n, const EwaldCoef *__restrict__ ewc
         b[2 * TSP] = acc[2]; b[2 * TSP + 1] = acc[4]; b[2 * TSP + 2] = acc[5];
     }
     __syncthreads();
-    const long n3 = 3L * n;
     const long r0 = 3L * TB * I, c0 = 3L * TB * J;
     for (int e = threadIdx.x; e < TS * TS; e += TB * TB) {
         int r = e / TS, cc = e % TS;
@@ -520,6 +496,8 @@ void launch_kvec_table(Plan &P, cudaStream_t s)
     P.nk = nk;
     k_ewald_coef<<<1, 1, 0, s>>>(P.p.a, P.p.alpha, P.p.box_L, P.p.r_c, P.d_ewc);
     count_launches(1);
+    k_ewald_typed<<<1, 1, 0, s>>>(P.d_ewc, P.d_ew64, P.d_ew32);
+    count_launches(1);
     if (P.ntab > 0) {
         k_m1_table<<<(2 * P.ntab + 63) / 64, 64, 0, s>>>(P.d_ewc, P.tab_i0, P.ntab, P.d_tab,
                                                         P.d_tab32);
@@ -555,13 +533,20 @@ static long tile_pairs(int n)
     return T * (T + 1) / 2;
 }
 
+static void launch_wrap(Plan &P, const double *R, cudaStream_t s)
+{
+    k_wrap<<<(P.n3 + 255) / 256, 256, 0, s>>>(R, P.n3, P.p.box_L, P.d_pw64, P.d_pw32);
+    count_launches(1);
+}
+
 void launch_build_D_f64(Plan &P, const double *R, double *D, cudaStream_t s)
 {
     launch_trig_tables(P, R, s);
+    launch_wrap(P, R, s);
     long nb = tile_pairs(P.n);
     k_build_D<double><<<(unsigned)nb, TB * TB, 0, s>>>(
-        R, P.n, P.d_ewc, P.d_tab, P.tab_i0, P.ntab, P.d_km64, P.nk, P.d_cos, P.d_sin,
-        P.p.overlap_corr,
+        P.d_pw64, P.d_pw32, P.n, P.d_ew64, P.d_ewc, P.d_tab, P.tab_i0, P.ntab, P.d_km64, P.nk,
+        P.d_cos, P.d_sin, P.p.overlap_corr,
         (float)P.p.r_c, D, nullptr, 0, P.ld);
     count_launches(1);
 }
@@ -570,10 +555,11 @@ void launch_build_D_f32(Plan &P, const double *R, float *D32, void *D16, int is_
                         cudaStream_t s)
 {
     launch_trig_tables(P, R, s);
+    launch_wrap(P, R, s);
     long nb = tile_pairs(P.n);
     k_build_D<float><<<(unsigned)nb, TB * TB, 0, s>>>(
-        R, P.n, P.d_ewc, P.d_tab32, P.tab_i0, P.ntab, P.d_km32, P.nk, P.d_cos32, P.d_sin32,
-        P.p.overlap_corr,
+        P.d_pw64, P.d_pw32, P.n, P.d_ew32, P.d_ewc, P.d_tab32, P.tab_i0, P.ntab, P.d_km32, P.nk,
+        P.d_cos32, P.d_sin32, P.p.overlap_corr,
         (float)P.p.r_c, D32, D16, is_bf16, P.ld);
     count_launches(1);
 }

@@ -157,6 +157,8 @@ struct Epi {
     void *X16next;              // next operand (mode 1), [BN][ldx]
     int ldx;
     int is_bf16;
+    int lan_col;                // mode 1: column carrying an extra vector (-1: none)
+    double *lan_w;              // its product, FP64
 };
 
 template <int BN>
@@ -304,6 +306,7 @@ k_tc_gemm(const __grid_constant__ CUtensorMap mapD, const __grid_constant__ CUte
                     const double cp = e.coef[e.p];
 #pragma unroll
                     for (int c = 0; c < BN; c++) {
+                        if (c == e.lan_col) e.lan_w[row] = y[c] * (double)e.inv_scale[c];
                         if (c < e.m) {
                             long o = (long)c * n3 + row;
                             double w = y[c] * (double)e.inv_scale[c];
@@ -480,6 +483,36 @@ static void prepare_operand(Plan &P, const double *X, int m, int bn, void *X16, 
     count_launches(1);
 }
 
+// one extra column: scale from its own max and the 16-bit copy in row `col`
+__global__ void k_scale_one(const unsigned long long *bits, float *scale, float *inv_scale)
+{
+    float sc = 1.f;
+    double mx = __longlong_as_double((long long)*bits);
+    if (mx > 0.0 && isfinite(mx)) {
+        int e;
+        frexp(mx, &e);
+        sc = ldexpf(1.f, -e);
+    }
+    *scale = sc;
+    *inv_scale = 1.f / sc;
+}
+
+static void prepare_column(Plan &P, const double *x, int col, void *X16, cudaStream_t s)
+{
+    unsigned long long *bits = (unsigned long long *)(P.d_xscale + 2 * kMaxRhs) + col;
+    cudaMemsetAsync(bits, 0, sizeof(unsigned long long), s);
+    k_col_absmax<<<dim3(64, 1), 256, 0, s>>>(x, P.n3, 1, bits);
+    count_launches(1);
+    k_scale_one<<<1, 1, 0, s>>>(bits, P.d_xscale + col, P.d_xscale + kMaxRhs + col);
+    count_launches(1);
+    // k_to16 converts column 0 of x into row 0 of the buffer it is given: offset
+    // the destination to row `col` and the scale to entry `col`
+    k_to16<<<dim3((P.n3 + 255) / 256, 1), 256, 0, s>>>(
+        x, P.n3, 1, 1, P.d_xscale + col, (char *)X16 + (size_t)col * P.ldx * 2, P.ldx,
+        P.p.precision == BD_MIXED_BF16);
+    count_launches(1);
+}
+
 static bd_status launch_tc(Plan &P, const void *D16, const void *X16, int bn, const tc::Epi &e,
                            cudaStream_t s)
 {
@@ -513,21 +546,25 @@ bd_status tc_apply(Plan &P, const void *D16, const double *X, int m, double *Y, 
     e.mode = 0;
     e.m = m;
     e.Y = Y;
+    e.lan_col = -1;
     e.inv_scale = P.d_xscale + kMaxRhs;
     e.is_bf16 = P.p.precision == BD_MIXED_BF16;
     return launch_tc(P, D16, X16, bn, e, s);
 }
 
 bd_status tc_cheb(Plan &P, const void *D16, int m, const double *coef, const double *bounds, int p,
-                  double *Vprev2, const double *Vprev1, double *dS, cudaStream_t s)
+                  double *Vprev2, const double *Vprev1, double *dS, cudaStream_t s,
+                  const double *lan_q, double *lan_w)
 {
-    const int bn = m <= 16 ? 16 : 32;
+    const int cols = m + (lan_q ? 1 : 0);
+    const int bn = cols <= 16 ? 16 : 32;
     // operand of V_{p-1}: buffer (p & 1); the epilogue writes V_p into the other
     void *cur = x16_buf(P, p & 1), *nxt = x16_buf(P, (p + 1) & 1);
     if (p == 2) {
         // scales from V_1's block (kept for the whole recurrence); 16-bit V_1
         prepare_operand(P, Vprev1, m, bn, cur, s);
     }
+    if (lan_q) prepare_column(P, lan_q, m, cur, s);
     tc::Epi e{};
     e.mode = 1;
     e.m = m;
@@ -542,6 +579,8 @@ bd_status tc_cheb(Plan &P, const void *D16, int m, const double *coef, const dou
     e.X16next = nxt;
     e.ldx = P.ldx;
     e.is_bf16 = P.p.precision == BD_MIXED_BF16;
+    e.lan_col = lan_q ? m : -1;
+    e.lan_w = lan_w;
     return launch_tc(P, D16, cur, bn, e, s);
 }
 

@@ -11,8 +11,11 @@ bd_status tc_plan_init(Plan &P);
 bd_status tc_apply(Plan &P, const void *D16, const double *X, int m, double *Y, cudaStream_t s);
 // one Chebyshev term: V_p = 2 (s D16 V_{p-1} - t V_{p-1}) - V_{p-2} (in place
 // over V_{p-2}), dS += c_p V_p
+// lan_q (optional): a vector carried as column m of the operand; its product
+// D16 lan_q is written (FP64) to lan_w
 bd_status tc_cheb(Plan &P, const void *D16, int m, const double *coef, const double *bounds, int p,
-                  double *Vprev2, const double *Vprev1, double *dS, cudaStream_t s);
+                  double *Vprev2, const double *Vprev1, double *dS, cudaStream_t s,
+                  const double *lan_q = nullptr, double *lan_w = nullptr);
 // one step of FP64-residual refinement: Y += (D32 X - Y), with the residual
 // accumulated in FP64 from the FP32 matrix
 void launch_refine_f32(Plan &P, const float *D32, const double *X, int m, double *Y,

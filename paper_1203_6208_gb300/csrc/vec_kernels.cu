@@ -427,6 +427,18 @@ void launch_lanczos_finish(Plan &P, int k, double safety_max, double dmin_fracti
     count_launches(1);
 }
 
+// status of given bounds (lagged mode)
+__global__ void k_check_bounds(const double *b, int32_t *status)
+{
+    *status = (b[0] > 0.0 && b[1] > b[0]) ? BD_OK : BD_ERR_NOT_PD;
+}
+
+void launch_check_bounds(const double *bounds, int32_t *status, cudaStream_t s)
+{
+    k_check_bounds<<<1, 1, 0, s>>>(bounds, status);
+    count_launches(1);
+}
+
 // stats bookkeeping for bd_step
 __global__ void k_stats_begin(bd_step_stats *st, int nch)
 {

@@ -293,3 +293,22 @@ def test_invalid_arguments_raise(bnd):
         plan.apply(D, X, torch.empty_like(X))
     with pytest.raises(bnd.BDError):
         plan.build_D(torch.zeros(cfg.n, 3, dtype=torch.float64, device="cuda"), D[8:])
+
+
+@pytest.mark.parametrize("prec,tol", [("fp64", TOL), ("mixed_f16", 2e-6)])
+def test_build_D_periodic_images_of_beads(bnd, prec, tol):
+    """Shifting each bead by its own integer multiple of L (unwrapped
+    trajectories) leaves D unchanged: the wrap into the box and the
+    separation of close pairs across the boundary keep full precision."""
+    cfg = inputs.SystemConfig(n_chains=6, nb=10, c_over_cstar=3.0, seed=33)
+    p = cfg.params()
+    R = inputs.make_chains(cfg)
+    shifts = np.random.default_rng(34).integers(-40, 40, size=R.shape) * p["L"]
+    plan = bnd.Plan(p, prec, max_rhs=1)
+    Dr = oracle.build_D(p, R)
+    for Rx in (R, R + shifts):
+        Rg = torch.tensor(Rx, device="cuda")
+        D = plan.alloc_D()
+        plan.build_D(Rg, D)
+        Dg = plan.D_view(D).double().cpu().numpy()
+        assert relerr(Dg, Dr) <= tol

@@ -171,3 +171,35 @@ def test_n8000_mixed_sampled_rows(bnd):
         ref = rows @ X.T                                   # (3, m)
         got = Yh[:, 3 * b:3 * b + 3].T
         assert np.max(np.abs(got - ref)) <= 2e-3 * np.max(np.abs(Yh))
+
+
+def test_lagged_bounds_mode(bnd):
+    """BD_BOUNDS_LAGGED: step 2 uses the bounds of the Lanczos recurrence
+    carried as an extra column of step 1's products.  They bracket the
+    spectrum of the new D like fresh ones, and the step matches the oracle
+    step taken with those bounds."""
+    cfg, p, R = system(n_chains=20, nb=10, c=2.0, seed=71)
+    plan = bnd.Plan(p, "mixed_f16", max_rhs=4, max_cheb=64)
+    Rg = torch.tensor(R, device="cuda")
+    D = plan.alloc_D()
+    stats = bnd.new_stats()
+    kw = dict(m=4, n_cheb=40, lanczos_iters=60, bound_safety=0.05, dmin_fraction=0.5,
+              bounds_mode=1, stats=stats)
+    plan.step(Rg, D, None, seed=5, step_index=0, **kw)     # fresh bounds, primes the lag
+    R1 = Rg.cpu().numpy().copy()
+    dW = inputs.make_wiener(3 * cfg.n, 4, p["dt"], 72)
+    dS = torch.empty(4, 3 * cfg.n, dtype=torch.float64, device="cuda")
+    plan.step(Rg, D, torch.tensor(dW, device="cuda"), dS=dS, **kw)
+    st = bnd.read_stats(stats)
+    assert st["status"] == 0 and st["accepted"] == 1
+    D1 = oracle.build_D(p, R1)
+    lmin, lmax = oracle.exact_eigs(D1)
+    assert lmax <= st["d_max"] <= 1.1 * lmax
+    # same margins as fresh bounds on this D (which step 2 built from R1)
+    fresh = torch.empty(2, dtype=torch.float64, device="cuda")
+    plan.eig_bounds(D, 39, 0.05, 0.5, fresh)
+    fmin, fmax = fresh.cpu().numpy()
+    assert abs(st["d_max"] / fmax - 1) < 0.02
+    assert 0.5 < st["d_min"] / fmin < 2.0
+    _, _, _, dS_r, _ = oracle.step(p, R1, dW, st["d_min"], st["d_max"], 40)
+    assert relerr(dS.cpu().numpy(), dS_r) <= 1e-3

@@ -476,3 +476,34 @@ def test_grad_DF_matches_central_differences():
             fd[i, c] = (g @ oracle.build_D(p, Rp) @ F - g @ oracle.build_D(p, Rm) @ F) / (2 * h)
     assert np.max(np.abs(gR - fd)) < 2e-7 * max(1.0, np.max(np.abs(fd)))
     assert np.max(np.abs(gR.sum(axis=0))) < 1e-12     # pair forces: action = reaction
+
+
+def test_cheb_adjoint_matches_central_differences():
+    """Reverse pass of the Chebyshev series (bounds and N_Ch fixed): dL/ddW
+    equals P(D) h (the series is symmetric in D), and dL/dR through D(R)
+    matches central differences of L = h . dS(R)."""
+    R = small_system(seed=23, n=6, L=5.0)
+    p = mkparams(len(R), 5.0, M=4.5)
+    D = oracle.build_D(p, R)
+    lmin, lmax = oracle.exact_eigs(D)
+    dmin, dmax, nch = 0.8 * lmin, 1.1 * lmax, 12
+    rng = np.random.default_rng(8)
+    dW = rng.standard_normal((2, 3 * len(R)))
+    h = rng.standard_normal((2, 3 * len(R)))
+    X, Y, U0 = oracle.cheb_adjoint(D, dmin, dmax, nch, dW, h)
+    Ph, _ = oracle.cheb_sqrt(D, dmin, dmax, nch, h)
+    assert np.max(np.abs(U0 - Ph)) < 1e-12 * np.max(np.abs(Ph))
+    gR = oracle.grad_pairs(p, R, X, Y)
+
+    def L(Rx):
+        dS, _ = oracle.cheb_sqrt(oracle.build_D(p, Rx), dmin, dmax, nch, dW)
+        return float(np.sum(h * dS))
+    hh = 1e-6
+    fd = np.zeros_like(R)
+    for i in range(len(R)):
+        for c in range(3):
+            Rp, Rm = R.copy(), R.copy()
+            Rp[i, c] += hh
+            Rm[i, c] -= hh
+            fd[i, c] = (L(Rp) - L(Rm)) / (2 * hh)
+    assert np.max(np.abs(gR - fd)) < 2e-7 * max(1.0, np.max(np.abs(fd)))
