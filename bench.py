@@ -32,8 +32,6 @@ sys.path.insert(0, ROOT)
 METRIC = "BD steps/sec at N=8000 (D build + Chebyshev), FP64 vs mixed; % of roofline"
 WORKLOAD = ("theta solution N=8000 (400 chains x 20 beads), c/c*=4, EV off, overlap-corrected "
             "RPY, dense D 24000x24000, 16 Wiener vectors, N_Ch=40")
-KERNEL_FILES = {"fp64": "paper_1203_6208_gb300/csrc/dense_f64.cu",
-                "mixed": "paper_1203_6208_gb300/csrc/tc_gemm.cu"}
 
 
 def parse():
@@ -57,6 +55,10 @@ def parse():
                          "carried in the products; fresh = --lanczos products per step")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=3)
+    ap.add_argument("--workload", default="n8000", choices=["n8000", "batch"],
+                    help="batch: 64 replicas, N ~ U[200, 2000], mixed, one graph launch "
+                         "per step (replica-steps/s)")
+    ap.add_argument("--replicas", type=int, default=64)
     ap.add_argument("--chains", type=int, default=400,
                     help="chains of 20 beads (400 = the N=8000 workload; smaller only for "
                          "profiler captures)")
@@ -232,20 +234,30 @@ def probe_fp64_peak():
     return best
 
 
+def kernel_source_hash(path, name):
+    """sha256 (16 hex) of the source between the kernel's begin/end markers."""
+    txt = open(os.path.join(ROOT, path)).read()
+    a = txt.index(f"// -- kernel begin: {name}")
+    b = txt.index(f"// -- kernel end: {name}")
+    return hashlib.sha256(txt[a:b].encode()).hexdigest()[:16]
+
+
+KERNELS = {"fp64": ("paper_1203_6208_gb300/csrc/dense_f64.cu", "k_gemm_f64"),
+           "mixed": ("paper_1203_6208_gb300/csrc/tc_gemm.cu", "k_tc_gemm")}
+
+
 def traffic_per_launch(kind):
     """DRAM bytes per launch of the dominant kernel from the committed ncu
     summary, if it was taken on the current kernel source (else None)."""
     path = os.path.join(ROOT, "profiles", f"traffic_{kind}.txt")
     if not os.path.exists(path):
         return None
-    src = os.path.join(ROOT, KERNEL_FILES["fp64" if kind == "fp64" else "mixed"])
-    h = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
     vals = {}
     for line in open(path):
-        if ":" in line:
+        if ":" in line and not line.startswith("#"):
             k, v = line.split(":", 1)
             vals[k.strip()] = v.strip()
-    if vals.get("kernel_source_sha256_16") != h:
+    if vals.get("kernel_source_sha256_16") != kernel_source_hash(*KERNELS[kind]):
         return None
     try:
         return float(vals["dram_bytes_per_launch"])
@@ -294,12 +306,14 @@ def measure(args, precision, p, R0, rank, ws):
         torch.distributed.barrier()
     torch.cuda.synchronize()
     l0 = bnd.kernel_launches()
+    plan.product_timing(True)
     e0.record(stream)
     for k in range(args.steps):
         plan.set_phase_events(evs[k])
         plan.step(R, D, None, step_index=args.warmup + k, **kw)
     e1.record(stream)
     torch.cuda.synchronize()
+    prod_ms, prod_n = plan.product_timing(False)
     launches = bnd.kernel_launches() - l0
     if ws > 1:
         torch.distributed.barrier()
@@ -314,9 +328,10 @@ def measure(args, precision, p, R0, rank, ws):
     phases = {name: sum(evs[k][i].elapsed_time(evs[k][i + 1]) for k in range(args.steps))
               / args.steps for i, name in enumerate(bnd.PHASES)}
 
-    # roofline of the dominant kernel: the Chebyshev product (N_Ch - 2 launches per step)
+    # roofline of the dominant kernel: the Chebyshev product (N_Ch - 2 launches
+    # per step), its average launch duration from events around each launch
     n3 = 3 * p["n"]
-    cheb_launch_ms = phases["chebyshev"] / max(args.nch - 2, 1)
+    cheb_launch_ms = prod_ms / max(prod_n, 1)
     peaks, peak_src = measured_peaks()
     if precision == "fp64":
         flops = 2.0 * n3 * n3 * args.m
@@ -326,7 +341,8 @@ def measure(args, precision, p, R0, rank, ws):
                 "peak": fp64_peak / 1e12, "unit": "TFLOP/s", "frac": achieved * 1e12 / fp64_peak,
                 "peak_source": "FP64 DFMA probe (probe/peaks.cu) on this GPU (measured)",
                 "traffic": traffic_per_launch("fp64"),
-                "algorithmic_per_launch": f"2*(3N)^2*m = {flops:.3e} flop"}
+                "algorithmic_per_launch": f"2*(3N)^2*m = {flops:.3e} flop",
+                "launch_ms": cheb_launch_ms, "launches_timed": prod_n}
     else:
         bytes_ = n3 * n3 * 2.0 + n3 * args.m * (2 + 2 + 8 * 5)
         achieved = bytes_ / (cheb_launch_ms * 1e-3) / 1e9
@@ -335,7 +351,8 @@ def measure(args, precision, p, R0, rank, ws):
                 "frac": achieved / peaks["hbm_gbs"],
                 "peak_source": f"hbm_gbs ({peak_src} copy bandwidth)",
                 "traffic": traffic_per_launch("mixed"),
-                "algorithmic_per_launch": f"16-bit D + vectors = {bytes_:.3e} B"}
+                "algorithmic_per_launch": f"16-bit D + vectors = {bytes_:.3e} B",
+                "launch_ms": cheb_launch_ms, "launches_timed": prod_n}
 
     # end to end through the public API with host buffers
     e2e = None
@@ -426,10 +443,69 @@ def run_ours(args):
     print(json.dumps(line), flush=True)
 
 
+def run_batch(args):
+    """Batched replicas: one bd_batch_step (a single CUDA-graph launch after the
+    first two calls) advances every replica; value = replica steps per second."""
+    import torch
+    torch.cuda.set_device(0)
+    import numpy as np
+    from paper_1203_6208_gb300 import binding as bnd, build, inputs
+    build.build()
+    cfgs = inputs.batch_systems(count=args.replicas)
+    plist = []
+    for c in cfgs:
+        c.alpha_factor = 1.5
+        plist.append(c.params())
+    m = 1
+    nch = 30
+    b = bnd.Batch(plist, "mixed_f16", max_rhs=m, max_cheb=nch)
+    R = torch.tensor(np.concatenate([inputs.make_chains(c).reshape(-1) for c in cfgs]),
+                     device="cuda")
+    D = b.alloc_D()
+    stats = torch.zeros(b.count * bnd.STATS_BYTES, dtype=torch.uint8, device="cuda")
+    kw = dict(m=m, n_cheb=nch, lanczos_iters=30, seed=77, step_index=0, stats=stats,
+              bounds_mode=1)
+    for _ in range(max(args.warmup, 3)):
+        b.step(R, D, **kw)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    clocks = ClockSampler()
+    clocks.start()
+    time.sleep(0.4)
+    l0 = bnd.kernel_launches()
+    e0.record()
+    for _ in range(args.steps):
+        b.step(R, D, **kw)
+    e1.record()
+    torch.cuda.synchronize()
+    host_launches = bnd.kernel_launches() - l0
+    clk = clocks.stop()
+    ms = e0.elapsed_time(e1)
+    st = [bnd.BdStepStats.from_buffer_copy(bytes(stats[i * bnd.STATS_BYTES:(i + 1) * bnd.STATS_BYTES]
+                                                 .cpu().numpy().tobytes())) for i in range(b.count)]
+    nbeads = sum(c.n for c in cfgs)
+    line = {"metric": "batched replica steps/sec (64 replicas, N ~ U[200, 2000], mixed)",
+            "value": b.count * args.steps / (ms * 1e-3), "unit": "replica-steps/s",
+            "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f16+f32+f64", "data": "synthetic",
+            "config": {"workload": "batch", "replicas": b.count, "beads_total": nbeads,
+                       "n_range": [min(c.n for c in cfgs), max(c.n for c in cfgs)],
+                       "m": m, "n_cheb": nch, "bounds": "lagged", "alpha_factor": 1.5,
+                       "d_arena_gb": b.d_total / 1e9},
+            "bead_steps_per_s": nbeads * args.steps / (ms * 1e-3),
+            "graph_launches": host_launches,
+            "accepted": sum(x.accepted for x in st), "max_ef": max(x.ef_max for x in st),
+            "clocks": clk}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         run_reference(args)
+    elif args.workload == "batch":
+        run_batch(args)
     else:
         run_ours(args)
 

@@ -123,8 +123,14 @@ typedef struct {
     uint64_t seed;            /* Philox key when dW == NULL                        */
     uint64_t step_index;      /* Philox counter high word when dW == NULL          */
     int32_t bounds_mode;      /* BD_BOUNDS_FRESH or BD_BOUNDS_LAGGED (see bd_step)  */
-    int32_t reserved;
+    int32_t flags;            /* BD_STEP_DEVICE_COUNTER or 0                        */
 } bd_step_opts;
+
+#define BD_STEP_DEVICE_COUNTER 1  /* with dW == NULL: the Philox counter high word is
+                                     the plan's device step counter (set by
+                                     bd_plan_set_step_counter) and the step advances
+                                     it, so a captured graph draws new noise on
+                                     every replay; step_index is ignored           */
 
 #define BD_BOUNDS_FRESH 0     /* lanczos_iters Lanczos products every step          */
 #define BD_BOUNDS_LAGGED 1    /* mixed plans: the Lanczos vector rides as one extra
@@ -265,6 +271,42 @@ bd_status bd_chebyshev_backward(bd_plan *plan, const double *R, const void *D,
                                 int32_t m, const double *gS, double *gR, double *gdW,
                                 bd_stream stream);
 
+/* Autotuner: for a mixed plan, times the tensor-core product on D (its
+ * contents do not matter) for K-split counts 1, 2, 4, 8 and 16 and keeps the
+ * fastest for all later products of this plan; returns the split and the time
+ * per product (ms).  Synchronous.  FP64 plans: no-op (split 0).          */
+bd_status bd_plan_autotune(bd_plan *plan, void *D, int32_t *split_out, float *ms_out,
+                           bd_stream stream);
+
+/* Set the plan's device step counter used by BD_STEP_DEVICE_COUNTER (stream-
+ * ordered write of one uint64). */
+bd_status bd_plan_set_step_counter(bd_plan *plan, uint64_t value, bd_stream stream);
+
+/* ---------------------------------------------------------------------------
+ * Batched replicas.  A batch holds `count` independent systems (each with
+ * its own bd_params: uneven N, box, spring model, ...), one plan per replica.
+ * Positions are packed: replica i owns 3 N_i doubles at r_offset(i); the D
+ * workspace is one caller-owned arena, replica i at d_offset(i) (each
+ * offset 256-byte aligned).  bd_batch_step advances every replica by one
+ * step (bd_step semantics per replica, Wiener increments drawn on the device
+ * with replica i keyed by opts->seed + i).  The first call runs the steps
+ * directly and primes lagged bounds; the second call records the whole
+ * batched step into one CUDA graph (one branch per replica on its own stream,
+ * forked from and joined back to `stream`), and every later call with the
+ * same arguments is a single graph launch.  Changing R, D, opts or stats
+ * pointers re-records the graph.  Not thread-safe per batch.            */
+typedef struct bd_batch bd_batch;
+bd_status bd_batch_create(const bd_params *params, int32_t count, bd_batch **out_batch);
+void bd_batch_destroy(bd_batch *batch);
+/* sizes: total packed position doubles, total D arena bytes; per replica
+ * (index >= 0) its plan info and offsets (doubles into R, bytes into D). */
+bd_status bd_batch_query(const bd_batch *batch, int32_t index, bd_plan_info *info,
+                         int64_t *r_offset, int64_t *d_offset, int64_t *r_total,
+                         int64_t *d_total);
+/* stats: dev, count bd_step_stats (may be NULL). */
+bd_status bd_batch_step(bd_batch *batch, double *R, void *D, const bd_step_opts *opts,
+                        bd_step_stats *stats, bd_stream stream);
+
 /* ---------------------------------------------------------------------------
  * bd_wiener -- the device Wiener generator of bd_step on its own: count
  * N(0, dt) numbers (see bd_step for the counter layout).  out: dev doubles. */
@@ -281,6 +323,14 @@ bd_status bd_wiener(bd_plan *plan, uint64_t seed, uint64_t step_index, int64_t c
  * count must be 7.  The array is copied; NULL disables recording.        */
 #define BD_PHASE_EVENTS 7
 bd_status bd_set_phase_events(bd_plan *plan, void *const *events, int32_t count);
+
+/* Kernel timing of the Chebyshev products.  enable = 1: from now on the
+ * plan records a pair of CUDA events on the launch stream around each
+ * Chebyshev-product kernel (FP64 product or tensor-core product with the
+ * recurrence epilogue), up to 1024 launches.  enable = 0: waits for the last
+ * recorded event, returns the summed kernel time (ms) and the number of
+ * launches timed, and stops recording.                                    */
+bd_status bd_product_timing(bd_plan *plan, int32_t enable, float *total_ms, int32_t *launches);
 
 /* Number of CUDA kernels this library has launched in the process so far
  * (host-side counter; lets a caller count the launches of a region). */

@@ -24,11 +24,14 @@ STATUS_NAMES = {0: "BD_OK", 1: "BD_ERR_INVALID", 2: "BD_ERR_OOM", 3: "BD_ERR_CUD
                 7: "BD_ERR_TIMEOUT", 8: "BD_ERR_UNSUPPORTED"}
 PRECISIONS = {"fp64": 0, "mixed_f16": 1, "mixed_bf16": 2}
 BD_APPLY_REFINE = 1
+BD_STEP_DEVICE_COUNTER = 1
 
 EXPORTS = ["bd_plan_create", "bd_plan_destroy", "bd_plan_query", "bd_forces", "bd_build_D",
            "bd_apply_D", "bd_eig_bounds", "bd_chebyshev_sqrt", "bd_step", "bd_wiener",
            "bd_set_phase_events", "bd_kernel_launches", "bd_eig_bounds_noalloc",
-           "bd_apply_D_backward", "bd_chebyshev_backward",
+           "bd_apply_D_backward", "bd_chebyshev_backward", "bd_plan_autotune", "bd_product_timing",
+           "bd_plan_set_step_counter", "bd_batch_create", "bd_batch_destroy", "bd_batch_query",
+           "bd_batch_step",
            "bd_last_error", "bd_version"]
 PHASES = ["forces", "build_D", "bounds", "first_product", "chebyshev", "update"]
 
@@ -63,7 +66,7 @@ class BdStepOpts(ctypes.Structure):
                 ("lanczos_iters", ctypes.c_int32), ("bound_safety", ctypes.c_double),
                 ("dmin_fraction", ctypes.c_double), ("seed", ctypes.c_uint64),
                 ("step_index", ctypes.c_uint64), ("bounds_mode", ctypes.c_int32),
-                ("reserved", ctypes.c_int32)]
+                ("flags", ctypes.c_int32)]
 
 
 STATS_BYTES = ctypes.sizeof(BdStepStats)
@@ -95,13 +98,24 @@ def load(path: str = LIB_PATH):
     L.bd_wiener.argtypes = [_vp, u64, u64, i64, _vp, _vp]
     L.bd_set_phase_events.argtypes = [_vp, ctypes.POINTER(_vp), i32]
     L.bd_apply_D_backward.argtypes = [_vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp]
+    L.bd_plan_autotune.argtypes = [_vp, _vp, ctypes.POINTER(i32), ctypes.POINTER(ctypes.c_float),
+                                   _vp]
+    L.bd_plan_set_step_counter.argtypes = [_vp, u64, _vp]
+    L.bd_product_timing.argtypes = [_vp, i32, ctypes.POINTER(ctypes.c_float), ctypes.POINTER(i32)]
+    L.bd_batch_create.argtypes = [ctypes.POINTER(BdParams), i32, ctypes.POINTER(_vp)]
+    L.bd_batch_destroy.argtypes = [_vp]
+    L.bd_batch_destroy.restype = None
+    L.bd_batch_query.argtypes = [_vp, i32, ctypes.POINTER(BdPlanInfo), ctypes.POINTER(i64),
+                                 ctypes.POINTER(i64), ctypes.POINTER(i64), ctypes.POINTER(i64)]
+    L.bd_batch_step.argtypes = [_vp, _vp, _vp, ctypes.POINTER(BdStepOpts), _vp, _vp]
     L.bd_chebyshev_backward.argtypes = [_vp, _vp, _vp, _vp, i32, _vp, i32, _vp, _vp, _vp, _vp]
     L.bd_eig_bounds_noalloc.argtypes = [_vp, i32, i32, i32, f64, f64, _vp, _vp, _vp]
     L.bd_kernel_launches.restype = ctypes.c_uint64
     L.bd_last_error.restype = ctypes.c_char_p
     L.bd_version.restype = ctypes.c_char_p
     for name in EXPORTS:
-        if name not in ("bd_plan_destroy", "bd_last_error", "bd_version", "bd_kernel_launches"):
+        if name not in ("bd_plan_destroy", "bd_last_error", "bd_version", "bd_kernel_launches",
+                        "bd_batch_destroy"):
             getattr(L, name).restype = ctypes.c_int
     _lib = L
     return L
@@ -203,10 +217,11 @@ class Plan:
 
     def step(self, R, D, dW=None, *, m=1, n_cheb=20, lanczos_iters=30, bound_safety=0.05,
              dmin_fraction=0.5, seed=0, step_index=0, DF=None, dS=None, stats=None,
-             bounds_mode=0, stream=None):
+             bounds_mode=0, flags=0, stream=None):
         o = BdStepOpts(m=int(m), n_cheb=int(n_cheb), lanczos_iters=int(lanczos_iters),
                        bound_safety=float(bound_safety), dmin_fraction=float(dmin_fraction),
-                       seed=int(seed), step_index=int(step_index), bounds_mode=int(bounds_mode))
+                       seed=int(seed), step_index=int(step_index), bounds_mode=int(bounds_mode),
+                       flags=int(flags))
         _check(load().bd_step(self._h, _p(R), _p(D), _p(dW), ctypes.byref(o), _p(DF), _p(dS),
                               _p(stats), _stream(stream)))
 
@@ -218,6 +233,24 @@ class Plan:
         m = dW.shape[0] if dW.dim() == 2 else 1
         _check(load().bd_chebyshev_backward(self._h, _p(R), _p(D), _p(bounds), int(n_cheb),
                                             _p(dW), m, _p(gS), _p(gR), _p(gdW), _stream(stream)))
+
+    def product_timing(self, enable: bool):
+        """enable=True starts recording; enable=False returns (total_ms, launches)."""
+        ms = ctypes.c_float()
+        n = ctypes.c_int32()
+        _check(load().bd_product_timing(self._h, 1 if enable else 0, ctypes.byref(ms),
+                                        ctypes.byref(n)))
+        return float(ms.value), int(n.value)
+
+    def set_step_counter(self, value, stream=None):
+        _check(load().bd_plan_set_step_counter(self._h, int(value), _stream(stream)))
+
+    def autotune(self, D, stream=None):
+        sp = ctypes.c_int32()
+        ms = ctypes.c_float()
+        _check(load().bd_plan_autotune(self._h, _p(D), ctypes.byref(sp), ctypes.byref(ms),
+                                       _stream(stream)))
+        return int(sp.value), float(ms.value)
 
     def set_phase_events(self, events):
         """events: list of 7 torch.cuda.Event (enable_timing) or None."""
@@ -242,6 +275,54 @@ def eig_bounds_noalloc(D, n3, ld, iters, safety_max, dmin_fraction, bounds, stat
     _check(load().bd_eig_bounds_noalloc(_p(D), int(n3), int(ld), int(iters), float(safety_max),
                                         float(dmin_fraction), _p(bounds), _p(status),
                                         _stream(stream)))
+
+
+class Batch:
+    """bd_batch: independent replicas (uneven N), one graph launch per step."""
+
+    def __init__(self, plist, precision: str = "mixed_f16", max_rhs: int = 1, max_cheb: int = 64):
+        L = load()
+        arr = (BdParams * len(plist))(*[make_params(p, precision, max_rhs, max_cheb)
+                                        for p in plist])
+        h = _vp()
+        _check(L.bd_batch_create(arr, len(plist), ctypes.byref(h)))
+        self._h = h
+        self.count = len(plist)
+        rt, dt = ctypes.c_int64(), ctypes.c_int64()
+        _check(L.bd_batch_query(h, -1, None, None, None, ctypes.byref(rt), ctypes.byref(dt)))
+        self.r_total, self.d_total = int(rt.value), int(dt.value)
+        self.r_off, self.d_off, self.n3 = [], [], []
+        for i in range(self.count):
+            info = BdPlanInfo()
+            ro, do = ctypes.c_int64(), ctypes.c_int64()
+            _check(L.bd_batch_query(h, i, ctypes.byref(info), ctypes.byref(ro), ctypes.byref(do),
+                                    None, None))
+            self.r_off.append(int(ro.value))
+            self.d_off.append(int(do.value))
+            self.n3.append(int(info.n3))
+
+    def close(self):
+        if getattr(self, "_h", None):
+            load().bd_batch_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def alloc_D(self):
+        return torch.empty(self.d_total, dtype=torch.uint8, device="cuda")
+
+    def step(self, R, D, *, m=1, n_cheb=20, lanczos_iters=30, bound_safety=0.05,
+             dmin_fraction=0.5, seed=0, step_index=0, stats=None, bounds_mode=1, stream=None):
+        o = BdStepOpts(m=int(m), n_cheb=int(n_cheb), lanczos_iters=int(lanczos_iters),
+                       bound_safety=float(bound_safety), dmin_fraction=float(dmin_fraction),
+                       seed=int(seed), step_index=int(step_index), bounds_mode=int(bounds_mode),
+                       flags=0)
+        _check(load().bd_batch_step(self._h, _p(R), _p(D), ctypes.byref(o), _p(stats),
+                                    _stream(stream)))
 
 
 def kernel_launches() -> int:

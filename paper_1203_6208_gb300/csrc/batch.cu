@@ -1,0 +1,175 @@
+// batch.cu -- many independent replicas (uneven N) advanced together.
+//
+// One plan per replica.  A step of the batch forks `count` branches from the
+// caller's stream (one non-blocking stream per replica), runs bd_step for
+// each replica on its branch and joins them back.  From the second call on,
+// that whole fork/step/join sequence is recorded once into a CUDA graph and
+// replayed with a single cudaGraphLaunch per step, so the host issues one
+// launch per batched step and the GPU runs the replicas' kernels
+// concurrently (small replicas do not fill the GPU on their own).  Wiener
+// increments are drawn on the device with the plan's device step counter,
+// so every replay draws new noise.
+#include <string.h>
+
+#include <new>
+#include <vector>
+
+#include "bd_internal.cuh"
+
+struct bd_batch {
+    int count = 0;
+    std::vector<bd_plan *> plans;
+    std::vector<int64_t> r_off, d_off;
+    int64_t r_total = 0, d_total = 0;
+    std::vector<cudaStream_t> streams;
+    std::vector<cudaEvent_t> join_ev;
+    cudaEvent_t fork_ev = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    // arguments the recorded graph was made with
+    double *key_R = nullptr;
+    void *key_D = nullptr;
+    bd_step_stats *key_stats = nullptr;
+    bd_step_opts key_opts;
+    int calls = 0;
+};
+
+using namespace bd;
+
+static void destroy_batch(bd_batch *b)
+{
+    if (!b) return;
+    cudaDeviceSynchronize();
+    if (b->exec) cudaGraphExecDestroy(b->exec);
+    for (auto s : b->streams) if (s) cudaStreamDestroy(s);
+    for (auto e : b->join_ev) if (e) cudaEventDestroy(e);
+    if (b->fork_ev) cudaEventDestroy(b->fork_ev);
+    for (auto p : b->plans) bd_plan_destroy(p);
+    delete b;
+}
+
+extern "C" {
+
+bd_status bd_batch_create(const bd_params *params, int32_t count, bd_batch **out_batch)
+{
+    if (!params || !out_batch || count < 1 || count > 4096)
+        return set_error(BD_ERR_INVALID, "need params, out_batch and 1 <= count <= 4096");
+    *out_batch = nullptr;
+    bd_batch *b = new (std::nothrow) bd_batch();
+    if (!b) return set_error(BD_ERR_OOM, "host allocation failed");
+    b->count = count;
+    b->plans.assign(count, nullptr);
+    b->streams.assign(count, nullptr);
+    b->join_ev.assign(count, nullptr);
+    memset(&b->key_opts, 0, sizeof(b->key_opts));
+    for (int i = 0; i < count; i++) {
+        bd_status st = bd_plan_create(&params[i], &b->plans[i]);
+        if (st != BD_OK) {
+            destroy_batch(b);
+            return st;
+        }
+        bd_plan_info info;
+        bd_plan_query(b->plans[i], &info);
+        b->r_off.push_back(b->r_total);
+        b->d_off.push_back(b->d_total);
+        b->r_total += info.n3;
+        b->d_total += (info.d_bytes + 255) / 256 * 256;
+        if (cudaStreamCreateWithFlags(&b->streams[i], cudaStreamNonBlocking) != cudaSuccess ||
+            cudaEventCreateWithFlags(&b->join_ev[i], cudaEventDisableTiming) != cudaSuccess) {
+            destroy_batch(b);
+            return set_error(BD_ERR_CUDA, "stream/event creation failed");
+        }
+    }
+    if (cudaEventCreateWithFlags(&b->fork_ev, cudaEventDisableTiming) != cudaSuccess) {
+        destroy_batch(b);
+        return set_error(BD_ERR_CUDA, "event creation failed");
+    }
+    *out_batch = b;
+    return BD_OK;
+}
+
+void bd_batch_destroy(bd_batch *batch) { destroy_batch(batch); }
+
+bd_status bd_batch_query(const bd_batch *b, int32_t index, bd_plan_info *info, int64_t *r_offset,
+                         int64_t *d_offset, int64_t *r_total, int64_t *d_total)
+{
+    if (!b) return set_error(BD_ERR_INVALID, "NULL batch");
+    if (r_total) *r_total = b->r_total;
+    if (d_total) *d_total = b->d_total;
+    if (index < 0) return BD_OK;
+    if (index >= b->count) return set_error(BD_ERR_INVALID, "index %d >= count %d", index, b->count);
+    if (info) bd_plan_query(b->plans[index], info);
+    if (r_offset) *r_offset = b->r_off[index];
+    if (d_offset) *d_offset = b->d_off[index];
+    return BD_OK;
+}
+
+// fork from `stream`, one bd_step per replica on its branch, join back
+static bd_status batch_body(bd_batch *b, double *R, void *D, const bd_step_opts *opts,
+                            bd_step_stats *stats, cudaStream_t stream)
+{
+    if (cudaEventRecord(b->fork_ev, stream) != cudaSuccess) return check_launch("batch fork");
+    for (int i = 0; i < b->count; i++) {
+        cudaStreamWaitEvent(b->streams[i], b->fork_ev, 0);
+        bd_step_opts o = *opts;
+        o.seed = opts->seed + (uint64_t)i;
+        o.flags |= BD_STEP_DEVICE_COUNTER;
+        bd_status st = bd_step(b->plans[i], R + b->r_off[i], (char *)D + b->d_off[i], nullptr, &o,
+                               nullptr, nullptr, stats ? stats + i : nullptr, b->streams[i]);
+        if (st != BD_OK) return st;
+        cudaEventRecord(b->join_ev[i], b->streams[i]);
+        cudaStreamWaitEvent(stream, b->join_ev[i], 0);
+    }
+    return check_launch("batch step");
+}
+
+bd_status bd_batch_step(bd_batch *b, double *R, void *D, const bd_step_opts *opts,
+                        bd_step_stats *stats, bd_stream stream)
+{
+    if (!b || !R || !D || !opts) return set_error(BD_ERR_INVALID, "NULL argument");
+    if (((uintptr_t)D & 255) != 0) return set_error(BD_ERR_INVALID, "D must be 256-byte aligned");
+    cudaStream_t s = stream;
+    if (b->calls == 0) {
+        // direct run: set the device counters, prime lagged bounds
+        for (int i = 0; i < b->count; i++) {
+            bd_status st = bd_plan_set_step_counter(b->plans[i], opts->step_index, s);
+            if (st != BD_OK) return st;
+        }
+        b->calls = 1;
+        return batch_body(b, R, D, opts, stats, s);
+    }
+    const bool same = b->exec && b->key_R == R && b->key_D == D && b->key_stats == stats &&
+                      memcmp(&b->key_opts, opts, sizeof(*opts)) == 0;
+    if (!same) {
+        if (b->exec) {
+            cudaGraphExecDestroy(b->exec);
+            b->exec = nullptr;
+        }
+        cudaGraph_t g = nullptr;
+        if (cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal) != cudaSuccess)
+            return check_launch("batch capture begin");
+        bd_status st = batch_body(b, R, D, opts, stats, s);
+        cudaError_t e = cudaStreamEndCapture(s, &g);
+        if (st != BD_OK) {
+            if (g) cudaGraphDestroy(g);
+            return st;
+        }
+        if (e != cudaSuccess || !g)
+            return set_error(BD_ERR_CUDA, "batch capture: %s", cudaGetErrorString(e));
+        e = cudaGraphInstantiate(&b->exec, g, 0);
+        cudaGraphDestroy(g);
+        if (e != cudaSuccess) {
+            b->exec = nullptr;
+            return set_error(BD_ERR_CUDA, "graph instantiate: %s", cudaGetErrorString(e));
+        }
+        b->key_R = R;
+        b->key_D = D;
+        b->key_stats = stats;
+        b->key_opts = *opts;
+    }
+    b->calls++;
+    if (cudaGraphLaunch(b->exec, s) != cudaSuccess) return check_launch("batch graph launch");
+    count_launches(1);
+    return BD_OK;
+}
+
+}  // extern "C"

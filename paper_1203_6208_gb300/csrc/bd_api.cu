@@ -21,6 +21,13 @@ static unsigned long long g_launches = 0;
 
 void count_launches(int k) { __atomic_fetch_add(&g_launches, (unsigned long long)k, __ATOMIC_RELAXED); }
 
+void prod_mark(Plan &P, int end, cudaStream_t s)
+{
+    if (!P.prod_on || P.prod_n >= P.prod_cap) return;
+    cudaEventRecord(P.prod_ev[2 * P.prod_n + end], s);
+    if (end) P.prod_n++;
+}
+
 bd_status set_error(bd_status st, const char *fmt, ...)
 {
     va_list ap;
@@ -56,12 +63,17 @@ static bd_status dmalloc(Plan &P, T **ptr, size_t count)
 
 static void free_plan(Plan &P)
 {
+    if (P.prod_ev) {
+        for (int i = 0; i < 2 * P.prod_cap; i++) cudaEventDestroy(P.prod_ev[i]);
+        delete[] P.prod_ev;
+        P.prod_ev = nullptr;
+    }
     void *ptrs[] = {P.d_kvec, P.d_km64, P.d_km32, P.d_xsplit, P.d_ewc, P.d_ew64, P.d_ew32,
                     P.d_pw64, P.d_pw32, P.d_tab, P.d_tab32, P.d_cos, P.d_sin, P.d_cos32, P.d_sin32, P.d_F, P.d_DF,
                     P.d_Rnew, P.d_V[0], P.d_V[1], P.d_V[2], P.d_X0, P.d_Y0, P.d_dS, P.d_dW,
                     P.d_coef, P.d_wdw, P.d_red, P.d_redpart, P.d_bounds, P.d_status, P.d_lq[0], P.d_lq[1],
                     P.d_lq[2], P.d_lab, P.d_x16, P.d_xscale, P.d_part, P.d_counters,
-                    P.d_stats_scratch, P.d_y32, P.d_lag_bounds, P.d_vhist, P.d_xhist, P.d_ubuf[0], P.d_ubuf[1],
+                    P.d_stats_scratch, P.d_y32, P.d_lag_bounds, P.d_step_ctr, P.d_vhist, P.d_xhist, P.d_ubuf[0], P.d_ubuf[1],
                     P.d_ubuf[2], P.d_ubuf[3]};
     for (void *p : ptrs)
         if (p) cudaFree(p);
@@ -177,6 +189,7 @@ bd_status bd_plan_create(const bd_params *params, bd_plan **out_plan)
     TRY(dmalloc(P, &P.d_X0, n3 * (R + 2)));
     TRY(dmalloc(P, &P.d_Y0, n3 * (R + 2)));
     TRY(dmalloc(P, &P.d_lag_bounds, 2));
+    TRY(dmalloc(P, &P.d_step_ctr, 1));
     TRY(dmalloc(P, &P.d_dS, n3 * R));
     TRY(dmalloc(P, &P.d_dW, n3 * R));
     TRY(dmalloc(P, &P.d_coef, kMaxCheb));
@@ -205,6 +218,7 @@ bd_status bd_plan_create(const bd_params *params, bd_plan **out_plan)
             TRY(dmalloc(P, &P.d_sin32, nkn));
             TRY(tc_plan_init(P));
         }
+        cudaMemset(P.d_step_ctr, 0, sizeof(unsigned long long));
         if (cudaDeviceSynchronize() != cudaSuccess) {
             st = check_launch("plan creation");
             goto fail;
@@ -374,6 +388,68 @@ bd_status bd_chebyshev_sqrt(bd_plan *plan, const void *D, const double *bounds, 
     return cheb_core(P, D, bounds, n_cheb, dW, P.d_V[2], m, dS, Ef, nullptr, stream);
 }
 
+bd_status bd_product_timing(bd_plan *plan, int32_t enable, float *total_ms, int32_t *launches)
+{
+    if (!plan) return set_error(BD_ERR_INVALID, "NULL plan");
+    Plan &P = plan->P;
+    if (enable) {
+        if (!P.prod_ev) {
+            P.prod_cap = 1024;
+            P.prod_ev = new (std::nothrow) cudaEvent_t[2 * P.prod_cap];
+            if (!P.prod_ev) return set_error(BD_ERR_OOM, "host allocation failed");
+            for (int i = 0; i < 2 * P.prod_cap; i++) cudaEventCreate(&P.prod_ev[i]);
+        }
+        P.prod_n = 0;
+        P.prod_on = 1;
+        return check_launch("bd_product_timing");
+    }
+    float tot = 0.f;
+    int n = P.prod_on ? P.prod_n : 0;
+    if (n > 0) {
+        cudaEventSynchronize(P.prod_ev[2 * n - 1]);
+        for (int i = 0; i < n; i++) {
+            float ms = 0.f;
+            cudaEventElapsedTime(&ms, P.prod_ev[2 * i], P.prod_ev[2 * i + 1]);
+            tot += ms;
+        }
+    }
+    P.prod_on = 0;
+    if (total_ms) *total_ms = tot;
+    if (launches) *launches = n;
+    return check_launch("bd_product_timing");
+}
+
+bd_status bd_plan_autotune(bd_plan *plan, void *D, int32_t *split_out, float *ms_out,
+                           bd_stream stream)
+{
+    if (!plan || !D) return set_error(BD_ERR_INVALID, "NULL argument");
+    Plan &P = plan->P;
+    if (!is_mixed(P)) {
+        if (split_out) *split_out = 0;
+        if (ms_out) *ms_out = 0.f;
+        return BD_OK;
+    }
+    float *D32;
+    void *D16;
+    split_mixed(P, D, &D32, &D16);
+    int best = 0;
+    float ms = 0.f;
+    bd_status st = tc_autotune(P, D16, stream, &best, &ms);
+    if (split_out) *split_out = best;
+    if (ms_out) *ms_out = ms;
+    return st;
+}
+
+bd_status bd_plan_set_step_counter(bd_plan *plan, uint64_t value, bd_stream stream)
+{
+    if (!plan) return set_error(BD_ERR_INVALID, "NULL plan");
+    static thread_local unsigned long long hv;
+    hv = value;
+    cudaMemcpyAsync(plan->P.d_step_ctr, &hv, sizeof(hv), cudaMemcpyHostToDevice, stream);
+    cudaStreamSynchronize(stream);
+    return check_launch("bd_plan_set_step_counter");
+}
+
 bd_status bd_wiener(bd_plan *plan, uint64_t seed, uint64_t step_index, int64_t count,
                     double *out, bd_stream stream)
 {
@@ -429,7 +505,10 @@ bd_status bd_step(bd_plan *plan, double *R, void *D, const double *dW, const bd_
     // Wiener increments
     const double *w = dW;
     if (!w) {
-        launch_wiener(P, o->seed, o->step_index, (int64_t)n3 * m, P.d_dW, s);
+        const bool dev_ctr = (o->flags & BD_STEP_DEVICE_COUNTER) != 0;
+        launch_wiener(P, o->seed, o->step_index, (int64_t)n3 * m, P.d_dW, s,
+                      dev_ctr ? P.d_step_ctr : nullptr);
+        if (dev_ctr) launch_counter_add(P.d_step_ctr, s);
         w = P.d_dW;
     }
     // (a5) first product D [F, dW]  (one pass over D)

@@ -100,10 +100,14 @@ struct Plan {
     float *d_part;                     // split-K partial sums
     int32_t *d_counters;               // split-K arrival counters
     int ldx;                           // leading dimension of d_x16 (elements)
+    int tc_split;                      // K-splits of the tensor-core product (0: heuristic)
     int64_t scratch_bytes;
     bd_step_stats *d_stats_scratch;
     cudaEvent_t phase_ev[BD_PHASE_EVENTS];
+    cudaEvent_t *prod_ev;              // product timing: event pairs around each
+    int prod_cap, prod_n, prod_on;     //   Chebyshev-product kernel launch
     double *d_lag_bounds;              // bounds from the previous step's lagged Lanczos
+    unsigned long long *d_step_ctr;    // device step counter (BD_STEP_DEVICE_COUNTER)
     int lag_valid;                     // host flag: d_lag_bounds was produced
     int phase_on;
     float *d_y32;                      // FP32 product scratch (mixed plans)
@@ -116,6 +120,8 @@ struct Plan {
 
 // host-side count of kernel launches (bd_kernel_launches)
 void count_launches(int k);
+// product timing marks (end = 0 before the launch, 1 after)
+void prod_mark(Plan &P, int end, cudaStream_t s);
 
 // error plumbing (thread-local message)
 bd_status set_error(bd_status st, const char *fmt, ...);
@@ -152,7 +158,8 @@ void launch_cheb_first(Plan &P, const double *bounds, const double *dW, const do
 void launch_ef(Plan &P, const double *dW, const double *DW, const double *dS, int m,
                double *Ef, bd_step_stats *stats, cudaStream_t s);
 void launch_wiener(Plan &P, uint64_t seed, uint64_t step, int64_t count, double *out,
-                   cudaStream_t s);
+                   cudaStream_t s, const unsigned long long *step_dev = nullptr);
+void launch_counter_add(unsigned long long *ctr, cudaStream_t s);
 void launch_lanczos_init(Plan &P, cudaStream_t s);
 void launch_lanczos_update(Plan &P, int j, cudaStream_t s);
 void launch_lanczos_finish(Plan &P, int k, double safety_max, double dmin_fraction,

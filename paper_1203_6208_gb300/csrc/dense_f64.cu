@@ -25,6 +25,7 @@ struct Shape {
     static constexpr int KG = NT / (BM * CG);        // k groups
 };
 
+// -- kernel begin: k_gemm_f64
 template <int MC, bool CHEB>
 __global__ void __launch_bounds__(NT)
 k_gemm_f64(const double *__restrict__ D, long ld, int n3, const double *__restrict__ X, int m,
@@ -102,6 +103,8 @@ k_gemm_f64(const double *__restrict__ D, long ld, int n3, const double *__restri
     }
 }
 
+// -- kernel end: k_gemm_f64
+
 // m = 1 (Lanczos and single products): one warp per row, each lane streams
 // a strided slice of the row with two independent FP64 accumulators; the
 // FP64 pipe (one FMA per 8 bytes) and HBM are then both near their limits
@@ -159,7 +162,9 @@ void launch_gemm_f64(const Plan &P, const double *D, const double *X, int m, dou
 void launch_gemm_f64_cheb(const Plan &P, const double *D, int m, const ChebEpi &e,
                           cudaStream_t s)
 {
+    prod_mark(const_cast<Plan &>(P), 0, s);
     dispatch<true>(P, D, e.Vprev1, m, nullptr, e, s);
+    prod_mark(const_cast<Plan &>(P), 1, s);
 }
 
 }  // namespace bd

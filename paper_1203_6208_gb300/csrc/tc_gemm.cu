@@ -161,6 +161,7 @@ struct Epi {
     double *lan_w;              // its product, FP64
 };
 
+// -- kernel begin: k_tc_gemm
 template <int BN>
 __global__ void __launch_bounds__(THREADS, 2)
 k_tc_gemm(const __grid_constant__ CUtensorMap mapD, const __grid_constant__ CUtensorMap mapX,
@@ -334,6 +335,8 @@ k_tc_gemm(const __grid_constant__ CUtensorMap mapD, const __grid_constant__ CUte
     }
 }
 
+// -- kernel end: k_tc_gemm
+
 template <int BN>
 constexpr int smem_bytes()
 {
@@ -461,9 +464,10 @@ static void *x16_buf(Plan &P, int which)
 
 static int n_split(const Plan &P, int ktiles)
 {
-    // enough CTAs for ~5 waves of two CTAs per SM on 152 SMs
+    // enough CTAs for ~5 waves of two CTAs per SM on 152 SMs, unless the
+    // autotuner measured a better split for this plan
     int mbk = mblocks(P);
-    int s = (5 * 2 * 152 + mbk - 1) / mbk;
+    int s = P.tc_split > 0 ? P.tc_split : (5 * 2 * 152 + mbk - 1) / mbk;
     if (s > tc::kMaxSplit) s = tc::kMaxSplit;
     if (s > ktiles) s = ktiles;
     return s < 1 ? 1 : s;
@@ -527,6 +531,7 @@ static bd_status launch_tc(Plan &P, const void *D16, const void *X16, int bn, co
     dim3 grid(mblocks(P), ns);
     cudaMemsetAsync(P.d_counters, 0, sizeof(int32_t) * mblocks(P), s);
     int32_t *err = P.d_status + 6;
+    if (e.mode == 1) prod_mark(P, 0, s);
     if (bn == 16)
         tc::k_tc_gemm<16><<<grid, tc::THREADS, tc::smem_bytes<16>(), s>>>(
             mapD, mapX, P.n3, ktiles, ns, P.d_part, P.d_counters, err, e);
@@ -534,6 +539,7 @@ static bd_status launch_tc(Plan &P, const void *D16, const void *X16, int bn, co
         tc::k_tc_gemm<32><<<grid, tc::THREADS, tc::smem_bytes<32>(), s>>>(
             mapD, mapX, P.n3, ktiles, ns, P.d_part, P.d_counters, err, e);
     count_launches(1);
+    if (e.mode == 1) prod_mark(P, 1, s);
     return check_launch("tc_gemm");
 }
 
@@ -550,6 +556,42 @@ bd_status tc_apply(Plan &P, const void *D16, const double *X, int m, double *Y, 
     e.inv_scale = P.d_xscale + kMaxRhs;
     e.is_bf16 = P.p.precision == BD_MIXED_BF16;
     return launch_tc(P, D16, X16, bn, e, s);
+}
+
+// Autotuner of the product's tile decomposition: time Y = D16 X (m = the
+// plan's max_rhs, up to 16 columns) for K-split counts 1, 2, 4, 8, 16 on this
+// plan's own matrix and keep the fastest.  Synchronous.
+bd_status tc_autotune(Plan &P, const void *D16, cudaStream_t s, int *best_out, float *ms_out)
+{
+    const int m = P.p.max_rhs < 16 ? P.p.max_rhs : 16;
+    double *X = P.d_V[0], *Y = P.d_V[1];
+    cudaMemsetAsync(X, 0, sizeof(double) * (size_t)P.n3 * m, s);
+    const int ktiles = (P.n3 + tc::BK - 1) / tc::BK;
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    int best = 0;
+    float best_ms = 1e30f;
+    const int saved = P.tc_split;
+    for (int sp : {1, 2, 4, 8, 16}) {
+        if (sp > ktiles) break;
+        P.tc_split = sp;
+        bd_status st = tc_apply(P, D16, X, m, Y, s);      // warm-up
+        if (st != BD_OK) { P.tc_split = saved; cudaEventDestroy(e0); cudaEventDestroy(e1); return st; }
+        cudaEventRecord(e0, s);
+        for (int r = 0; r < 3; r++) tc_apply(P, D16, X, m, Y, s);
+        cudaEventRecord(e1, s);
+        cudaEventSynchronize(e1);
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        if (ms < best_ms) { best_ms = ms; best = sp; }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    P.tc_split = best;
+    if (best_out) *best_out = best;
+    if (ms_out) *ms_out = best_ms / 3.f;
+    return check_launch("tc_autotune");
 }
 
 bd_status tc_cheb(Plan &P, const void *D16, int m, const double *coef, const double *bounds, int p,

@@ -9,6 +9,8 @@ namespace bd {
 bd_status tc_plan_init(Plan &P);
 // Y = D16 X (FP32 accumulation, FP64 output)
 bd_status tc_apply(Plan &P, const void *D16, const double *X, int m, double *Y, cudaStream_t s);
+// measure the fastest K-split of the product for this plan (synchronous)
+bd_status tc_autotune(Plan &P, const void *D16, cudaStream_t s, int *best, float *ms);
 // one Chebyshev term: V_p = 2 (s D16 V_{p-1} - t V_{p-1}) - V_{p-2} (in place
 // over V_{p-2}), dS += c_p V_p
 // lan_q (optional): a vector carried as column m of the operand; its product

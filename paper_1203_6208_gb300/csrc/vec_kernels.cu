@@ -254,10 +254,12 @@ __device__ __forceinline__ void philox4x32_10(uint32_t c[4], uint32_t k0, uint32
     }
 }
 
-__global__ void k_wiener(uint64_t seed, uint64_t step, int64_t count, double sdt, double *out)
+__global__ void k_wiener(uint64_t seed, uint64_t step, int64_t count, double sdt, double *out,
+                         const unsigned long long *step_dev)
 {
     int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (2 * q >= count) return;
+    if (step_dev) step = *step_dev;
     uint32_t c[4] = {(uint32_t)q, (uint32_t)((uint64_t)q >> 32), (uint32_t)step,
                      (uint32_t)(step >> 32)};
     philox4x32_10(c, (uint32_t)seed, (uint32_t)(seed >> 32));
@@ -273,10 +275,11 @@ __global__ void k_wiener(uint64_t seed, uint64_t step, int64_t count, double sdt
 }
 
 void launch_wiener(Plan &P, uint64_t seed, uint64_t step, int64_t count, double *out,
-                   cudaStream_t s)
+                   cudaStream_t s, const unsigned long long *step_dev)
 {
     int64_t pairs = (count + 1) / 2;
-    k_wiener<<<(unsigned)((pairs + 255) / 256), 256, 0, s>>>(seed, step, count, sqrt(P.p.dt), out);
+    k_wiener<<<(unsigned)((pairs + 255) / 256), 256, 0, s>>>(seed, step, count, sqrt(P.p.dt), out,
+                                                             step_dev);
     count_launches(1);
 }
 
@@ -518,6 +521,14 @@ void launch_euler(Plan &P, double *R, const double *DF, const double *dS, bd_ste
         count_launches(1);
     }
     k_commit<<<(n3 + 255) / 256, 256, 0, s>>>(R, P.d_Rnew, n3, over, P.d_status + 2, stats);
+    count_launches(1);
+}
+
+__global__ void k_counter_add(unsigned long long *c) { *c += 1ull; }
+
+void launch_counter_add(unsigned long long *ctr, cudaStream_t s)
+{
+    k_counter_add<<<1, 1, 0, s>>>(ctr);
     count_launches(1);
 }
 

@@ -127,3 +127,18 @@ def preset(name: str, **overrides) -> tuple[SystemConfig, dict]:
     cfg = replace(d["cfg"], **overrides) if overrides else d["cfg"]
     extra = {k: v for k, v in d.items() if k != "cfg"}
     return cfg, extra
+
+
+def batch_systems(count: int = 64, seed: int = 1003, n_min: int = 200, n_max: int = 2000):
+    """Replica systems of the batched workload: N_b ~ U{10..20}, N ~ U[n_min,
+    n_max] rounded to a multiple of N_b, c/c* ~ U[1, 4], Hookean theta
+    chains; replica i's chains are seeded with seed * 1000 + i."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    out = []
+    for i in range(count):
+        nb = int(rng.integers(10, 21))
+        n = int(rng.integers(n_min, n_max + 1))
+        nc = max(1, int(round(n / nb)))
+        c = float(rng.uniform(1.0, 4.0))
+        out.append(SystemConfig(n_chains=nc, nb=nb, c_over_cstar=c, seed=seed * 1000 + i))
+    return out
