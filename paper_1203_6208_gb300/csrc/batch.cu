@@ -24,6 +24,7 @@ struct bd_batch {
     std::vector<cudaStream_t> streams;
     std::vector<cudaEvent_t> join_ev;
     cudaEvent_t fork_ev = nullptr;
+    cudaStream_t origin = nullptr;   // capture origin (the legacy stream cannot capture)
     cudaGraphExec_t exec = nullptr;
     // arguments the recorded graph was made with
     double *key_R = nullptr;
@@ -43,6 +44,7 @@ static void destroy_batch(bd_batch *b)
     for (auto s : b->streams) if (s) cudaStreamDestroy(s);
     for (auto e : b->join_ev) if (e) cudaEventDestroy(e);
     if (b->fork_ev) cudaEventDestroy(b->fork_ev);
+    if (b->origin) cudaStreamDestroy(b->origin);
     for (auto p : b->plans) bd_plan_destroy(p);
     delete b;
 }
@@ -79,7 +81,8 @@ bd_status bd_batch_create(const bd_params *params, int32_t count, bd_batch **out
             return set_error(BD_ERR_CUDA, "stream/event creation failed");
         }
     }
-    if (cudaEventCreateWithFlags(&b->fork_ev, cudaEventDisableTiming) != cudaSuccess) {
+    if (cudaEventCreateWithFlags(&b->fork_ev, cudaEventDisableTiming) != cudaSuccess ||
+        cudaStreamCreateWithFlags(&b->origin, cudaStreamNonBlocking) != cudaSuccess) {
         destroy_batch(b);
         return set_error(BD_ERR_CUDA, "event creation failed");
     }
@@ -144,11 +147,13 @@ bd_status bd_batch_step(bd_batch *b, double *R, void *D, const bd_step_opts *opt
             cudaGraphExecDestroy(b->exec);
             b->exec = nullptr;
         }
+        // recorded on the batch's own stream; the graph is then launched on
+        // the caller's stream, which may be the legacy default stream
         cudaGraph_t g = nullptr;
-        if (cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal) != cudaSuccess)
+        if (cudaStreamBeginCapture(b->origin, cudaStreamCaptureModeThreadLocal) != cudaSuccess)
             return check_launch("batch capture begin");
-        bd_status st = batch_body(b, R, D, opts, stats, s);
-        cudaError_t e = cudaStreamEndCapture(s, &g);
+        bd_status st = batch_body(b, R, D, opts, stats, b->origin);
+        cudaError_t e = cudaStreamEndCapture(b->origin, &g);
         if (st != BD_OK) {
             if (g) cudaGraphDestroy(g);
             return st;

@@ -9,6 +9,7 @@
 #include "bd_internal.cuh"
 #include "tc_gemm.cuh"
 #include "adjoint.cuh"
+#include "recip_tc.cuh"
 
 struct bd_plan {
     bd::Plan P;
@@ -74,7 +75,7 @@ static void free_plan(Plan &P)
                     P.d_coef, P.d_wdw, P.d_red, P.d_redpart, P.d_bounds, P.d_status, P.d_lq[0], P.d_lq[1],
                     P.d_lq[2], P.d_lab, P.d_x16, P.d_xscale, P.d_part, P.d_counters,
                     P.d_stats_scratch, P.d_y32, P.d_lag_bounds, P.d_step_ctr, P.d_vhist, P.d_xhist, P.d_ubuf[0], P.d_ubuf[1],
-                    P.d_ubuf[2], P.d_ubuf[3]};
+                    P.d_ubuf[2], P.d_ubuf[3], P.d_Uh, P.d_Ul, P.d_rtiles};
     for (void *p : ptrs)
         if (p) cudaFree(p);
 }
@@ -217,6 +218,7 @@ bd_status bd_plan_create(const bd_params *params, bd_plan **out_plan)
             TRY(dmalloc(P, &P.d_cos32, nkn));
             TRY(dmalloc(P, &P.d_sin32, nkn));
             TRY(tc_plan_init(P));
+            TRY(recip_tc_init(P));
         }
         cudaMemset(P.d_step_ctr, 0, sizeof(unsigned long long));
         if (cudaDeviceSynchronize() != cudaSuccess) {
@@ -279,7 +281,8 @@ bd_status bd_build_D(bd_plan *plan, const double *R, void *D, bd_stream stream)
         float *D32;
         void *D16;
         split_mixed(P, D, &D32, &D16);
-        launch_build_D_f32(P, R, D32, D16, P.p.precision == BD_MIXED_BF16, stream);
+        bd_status st = launch_build_D_f32(P, R, D32, D16, P.p.precision == BD_MIXED_BF16, stream);
+        if (st != BD_OK) return st;
     }
     return check_launch("bd_build_D");
 }

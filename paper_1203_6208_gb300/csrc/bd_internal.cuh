@@ -116,6 +116,12 @@ struct Plan {
     double *d_vhist;                   // V_0..V_{N_Ch-2}, [max_cheb-1][max_rhs][3N]
     double *d_xhist;                   // scaled adjoints X_q, same shape
     double *d_ubuf[4];                 // rolling adjoint vectors and D U products
+    // reciprocal sum as a tensor-core product (mixed plans, recip_tc.cu)
+    int recip_tc;                      // 1: D32's upper tiles are filled by U U^T first
+    int recip_kp;                      // columns of U (4 per k-vector, padded to 32)
+    int recip_ntiles;                  // 128 x 128 tiles on and above the diagonal
+    float *d_Uh, *d_Ul;                // U as TF32 hi/lo words [3N][recip_kp]
+    int2 *d_rtiles;                    // tile list
 };
 
 // host-side count of kernel launches (bd_kernel_launches)
@@ -133,7 +139,7 @@ void m1_table_range(const bd_params &p, int *i0, int *ntab);
 void launch_kvec_table(Plan &P, cudaStream_t s);
 void launch_trig_tables(Plan &P, const double *R, cudaStream_t s);
 void launch_build_D_f64(Plan &P, const double *R, double *D, cudaStream_t s);
-void launch_build_D_f32(Plan &P, const double *R, float *D32, void *D16, int is_bf16,
+bd_status launch_build_D_f32(Plan &P, const double *R, float *D32, void *D16, int is_bf16,
                         cudaStream_t s);
 
 // dense_f64.cu : Y = D X (FP64), epilogue variants

@@ -16,6 +16,7 @@
 
 #include "bd_internal.cuh"
 #include "pair_common.cuh"
+#include "recip_tc.cuh"
 
 namespace bd {
 
@@ -369,7 +370,7 @@ k_build_D(const double *__restrict__ pw, const float *__restrict__ pw32, int n,
           const EwaldT<T> *__restrict__ ewt, const EwaldCoef *__restrict__ ewc,
           const T *__restrict__ tab, int tab_i0, int ntab, const T *__restrict__ km, int nk,
           const T *__restrict__ cs, const T *__restrict__ sn, int overlap_corr, float rc,
-          T *__restrict__ D, void *__restrict__ D16, int is_bf16, long ld)
+          T *__restrict__ D, void *__restrict__ D16, int is_bf16, long ld, int recip_in_D)
 {
     __shared__ T tile[TS * TSP];
     __shared__ T s_tr[4][KC][TB];      // cos nu, sin nu, cos mu, sin mu for one k chunk
@@ -390,6 +391,13 @@ k_build_D(const double *__restrict__ pw, const float *__restrict__ pw32, int n,
     // which keeps D exactly symmetric
     const bool active = nu < n && mu < n && !(I == J && ty > tx);
     const long n3 = 3L * n;
+    if (active && recip_in_D) {
+        // the reciprocal sum is already in D (row <= column for every
+        // component read: this tile is on or above the diagonal)
+        const T *b = D + (size_t)(3 * nu) * ld + 3 * mu;
+        acc[0] = b[0]; acc[1] = b[1]; acc[2] = b[2];
+        acc[3] = b[ld + 1]; acc[4] = b[ld + 2]; acc[5] = b[2 * ld + 2];
+    }
     if (active) {
         T d[3];
         Sep<T>::get(pw, pw32, n3, nu, mu, c, d);
@@ -547,21 +555,28 @@ void launch_build_D_f64(Plan &P, const double *R, double *D, cudaStream_t s)
     k_build_D<double><<<(unsigned)nb, TB * TB, 0, s>>>(
         P.d_pw64, P.d_pw32, P.n, P.d_ew64, P.d_ewc, P.d_tab, P.tab_i0, P.ntab, P.d_km64, P.nk,
         P.d_cos, P.d_sin, P.p.overlap_corr,
-        (float)P.p.r_c, D, nullptr, 0, P.ld);
+        (float)P.p.r_c, D, nullptr, 0, P.ld, 0);
     count_launches(1);
 }
 
-void launch_build_D_f32(Plan &P, const double *R, float *D32, void *D16, int is_bf16,
+bd_status launch_build_D_f32(Plan &P, const double *R, float *D32, void *D16, int is_bf16,
                         cudaStream_t s)
 {
     launch_trig_tables(P, R, s);
     launch_wrap(P, R, s);
+    int nk = P.nk;
+    if (P.recip_tc) {
+        bd_status st = launch_recip_tc(P, D32, s);
+        if (st != BD_OK) return st;
+        nk = 0;
+    }
     long nb = tile_pairs(P.n);
     k_build_D<float><<<(unsigned)nb, TB * TB, 0, s>>>(
-        P.d_pw64, P.d_pw32, P.n, P.d_ew32, P.d_ewc, P.d_tab32, P.tab_i0, P.ntab, P.d_km32, P.nk,
+        P.d_pw64, P.d_pw32, P.n, P.d_ew32, P.d_ewc, P.d_tab32, P.tab_i0, P.ntab, P.d_km32, nk,
         P.d_cos32, P.d_sin32, P.p.overlap_corr,
-        (float)P.p.r_c, D32, D16, is_bf16, P.ld);
+        (float)P.p.r_c, D32, D16, is_bf16, P.ld, P.recip_tc);
     count_launches(1);
+    return BD_OK;
 }
 
 }  // namespace bd

@@ -1,0 +1,384 @@
+// recip_tc.cu -- the reciprocal part of D (Eq. DF, Eq. M2) for the mixed
+// (FP32) assembly as a tensor-core product.
+//
+// The folded tensor of a half-space vector k is 2 f(k) (I - khat khat) =
+// 2 f(k) (u1 u1^T + u2 u2^T) with u1, u2 orthonormal and perpendicular to k,
+// so with cos(k.(r_nu - r_mu)) = c_nu c_mu + s_nu s_mu the whole reciprocal sum
+// is one symmetric product D_rec = U U^T,
+//   U[3 nu + a][4 t + 2 (c-1) + s] = sqrt(2 f_t) u_c^a(k_t) {cos, sin}(k_t . r_nu),
+// a rank-4 N_k contraction over all bead pairs -- dense work for the tensor
+// cores.  U is split into TF32 words U = Uh + Ul (each exactly representable
+// in TF32) and D_rec = Uh Uh^T + Uh Ul^T + Ul Uh^T is accumulated in FP32 in
+// TMEM (kind::tf32, M = N = 128, K = 8 per MMA): about 2^-21 relative per
+// term, below the FP32 assembly's own rounding.  The product fills the
+// 128 x 128 tiles of D32 on and above the diagonal; the pair kernel reads the
+// six components (a <= b) of each 3 x 3 block it owns there (always row <=
+// column), adds the real-space, self and overlap terms and writes the final
+// D32 / D16 over them.
+#include <cuda.h>
+#include <cudaTypedefs.h>
+#include <math.h>
+
+#include "recip_tc.cuh"
+
+namespace bd {
+
+namespace rt {
+
+constexpr int BM = 128, BN = 128, BK = 32;     // BK in TF32 elements (128 bytes)
+constexpr int STAGES = 3;
+constexpr int THREADS = 192;
+constexpr int TILE_BYTES = BM * BK * 4;        // 16 KB per operand tile
+constexpr uint32_t kWaitLimit = 1u << 22;
+
+__device__ __forceinline__ uint32_t smem_u32(const void *p)
+{
+    return (uint32_t)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes)
+                 : "memory");
+}
+__device__ __forceinline__ bool mbar_try(uint32_t bar, uint32_t parity)
+{
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(bar), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, volatile int *abort_flag)
+{
+    for (uint32_t i = 0; i < kWaitLimit; i++) {
+        if (mbar_try(bar, parity)) return true;
+        if ((i & 1023u) == 1023u && *abort_flag) return false;
+    }
+    *abort_flag = 1;
+    return false;
+}
+__device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap *map, int x, int y,
+                                            uint32_t bar)
+{
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes"
+        " [%0], [%1, {%2, %3}], [%4];" ::"r"(dst),
+        "l"((uint64_t)map), "r"(x), "r"(y), "r"(bar)
+        : "memory");
+}
+__device__ __forceinline__ uint64_t sw128_desc(uint32_t addr)
+{
+    uint64_t d = 0;
+    d |= (uint64_t)((addr & 0x3FFFFu) >> 4);
+    d |= (uint64_t)1 << 16;
+    d |= (uint64_t)(1024 >> 4) << 32;
+    d |= (uint64_t)1 << 46;
+    d |= (uint64_t)2 << 61;
+    return d;
+}
+// kind::tf32: F32 accumulator, TF32 A and B, K-major, M = N = 128
+constexpr uint32_t kIdesc = (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(BN >> 3) << 17) |
+                            ((uint32_t)(BM >> 4) << 24);
+
+__device__ __forceinline__ void mma_tf32(uint32_t tmem_d, uint64_t da, uint64_t db,
+                                         uint32_t accumulate)
+{
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "setp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem_d),
+        "l"(da), "l"(db), "r"(kIdesc), "r"(accumulate)
+        : "memory");
+}
+__device__ __forceinline__ void mma_commit(uint32_t bar)
+{
+    asm volatile(
+        "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar)
+        : "memory");
+}
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float *v)
+{
+    uint32_t r[16];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 "
+        "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+          "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]),
+          "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+        : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+    for (int i = 0; i < 16; i++) v[i] = __uint_as_float(r[i]);
+}
+
+// -- kernel begin: k_recip_syrk
+// One CTA per 128 x 128 tile (ti, tj), ti <= tj; the K loop
+// runs over three segments (Uh.Uh, Uh.Ul, Ul.Uh) of nkt k-tiles each.
+__global__ void __launch_bounds__(THREADS, 2)
+k_recip_syrk(const __grid_constant__ CUtensorMap mapH, const __grid_constant__ CUtensorMap mapL,
+             const int2 *__restrict__ tiles, int n3, int nkt, float *__restrict__ D32, long ld,
+             int32_t *__restrict__ err)
+{
+    constexpr int STAGE = 2 * TILE_BYTES;
+    extern __shared__ __align__(1024) uint8_t smem_raw[];
+    uint8_t *smem = (uint8_t *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+    __shared__ __align__(8) uint64_t full_bar[STAGES], empty_bar[STAGES], accum_bar, drain_bar;
+    __shared__ uint32_t tmem_base_sh;
+    __shared__ volatile int abort_flag;
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int2 t2 = tiles[blockIdx.x];
+    const int ti = t2.x, tj = t2.y;
+    const int nsteps = 3 * nkt;
+    if (threadIdx.x == 0) {
+        abort_flag = 0;
+        for (int s = 0; s < STAGES; s++) {
+            mbar_init(smem_u32(&full_bar[s]), 1);
+            mbar_init(smem_u32(&empty_bar[s]), 1);
+        }
+        mbar_init(smem_u32(&accum_bar), 1);
+        mbar_init(smem_u32(&drain_bar), 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    }
+    if (warp == 1) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                         smem_u32(&tmem_base_sh)),
+                     "r"(BN)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const uint32_t tmem = tmem_base_sh;
+
+    if (warp == 0 && lane == 0) {
+        int issued = 0;
+        for (int i = 0; i < nsteps; i++) {
+            int s = i % STAGES;
+            uint32_t ph = (uint32_t)(i / STAGES) & 1u;
+            if (!mbar_wait(smem_u32(&empty_bar[s]), ph ^ 1u, &abort_flag)) break;
+            const int seg = i / nkt, kk = i % nkt;
+            const CUtensorMap *ma = seg == 2 ? &mapL : &mapH;   // Ul.Uh in segment 2
+            const CUtensorMap *mb = seg == 1 ? &mapL : &mapH;   // Uh.Ul in segment 1
+            uint32_t a = smem_u32(smem + s * STAGE), b = a + TILE_BYTES;
+            uint32_t fb = smem_u32(&full_bar[s]);
+            mbar_expect_tx(fb, STAGE);
+            tma_load_2d(a, ma, kk * BK, ti * BM, fb);
+            tma_load_2d(b, mb, kk * BK, tj * BN, fb);
+            issued = i + 1;
+        }
+        if (abort_flag) {
+            for (int i = (issued > STAGES ? issued - STAGES : 0); i < issued; i++) {
+                int s = i % STAGES;
+                uint32_t ph = (uint32_t)(i / STAGES) & 1u;
+                for (uint32_t t = 0; t < kWaitLimit && !mbar_try(smem_u32(&full_bar[s]), ph); t++) {}
+            }
+        }
+    } else if (warp == 1 && lane == 0) {
+        bool ok = true;
+        for (int i = 0; i < nsteps && ok; i++) {
+            int s = i % STAGES;
+            uint32_t ph = (uint32_t)(i / STAGES) & 1u;
+            if (!mbar_wait(smem_u32(&full_bar[s]), ph, &abort_flag)) { ok = false; break; }
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            uint32_t a = smem_u32(smem + s * STAGE), b = a + TILE_BYTES;
+            uint64_t da = sw128_desc(a), db = sw128_desc(b);
+#pragma unroll
+            for (int k = 0; k < BK / 8; k++)      // 8 TF32 = 32 bytes per MMA along K
+                mma_tf32(tmem, da + (uint64_t)(2 * k), db + (uint64_t)(2 * k),
+                         (i > 0 || k > 0) ? 1u : 0u);
+            mma_commit(smem_u32(&empty_bar[s]));
+        }
+        mma_commit(smem_u32(&accum_bar));
+        if (!ok) {
+            mma_commit(smem_u32(&drain_bar));
+            for (uint32_t t = 0; t < kWaitLimit && !mbar_try(smem_u32(&drain_bar), 0); t++) {}
+        }
+    } else if (warp >= 2) {
+        const int q = warp & 3;
+        const long row = (long)ti * BM + q * 32 + lane;
+        bool ok = mbar_wait(smem_u32(&accum_bar), 0, &abort_flag);
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        if (ok) {
+            for (int c0 = 0; c0 < BN; c0 += 16) {
+                float v[16];
+                tmem_ld16(tmem + ((uint32_t)(q * 32) << 16) + c0, v);
+                const long col = (long)tj * BN + c0;
+                if (row < n3) {
+                    float *dst = D32 + row * ld + col;
+                    if (col + 16 <= n3) {
+#pragma unroll
+                        for (int c = 0; c < 16; c += 4)
+                            *(float4 *)(dst + c) = make_float4(v[c], v[c + 1], v[c + 2], v[c + 3]);
+                    } else {
+                        for (int c = 0; c < 16; c++)
+                            if (col + c < n3) dst[c] = v[c];
+                    }
+                }
+            }
+        }
+    }
+    if (threadIdx.x == 0 && abort_flag) atomicExch(err, (int32_t)BD_ERR_TIMEOUT);
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    if (warp == 1) {
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(BN)
+                     : "memory");
+    }
+}
+// -- kernel end: k_recip_syrk
+
+}  // namespace rt
+
+// U = Uh + Ul for one bead and one half-space k: the columns (c, s) of Eq. DF
+// written as a product; u1, u2 from the k vector (FP64), each word rounded to
+// TF32 (cvt.rna) so that the tensor cores use it exactly.
+__device__ __forceinline__ float to_tf32(float x)
+{
+    uint32_t r;
+    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+    return __uint_as_float(r);
+}
+
+__global__ void k_build_U(const double *__restrict__ cs, const double *__restrict__ sn,
+                          const KVec *__restrict__ kv, int n, int nk, int Kp, float *__restrict__ Uh,
+                          float *__restrict__ Ul)
+{
+    const int nu = blockIdx.x * blockDim.x + threadIdx.x;
+    const int t = blockIdx.y;
+    if (nu >= n) return;
+    if (t >= nk) {                       // zero padding columns of this k group
+        for (int a = 0; a < 3; a++)
+            for (int j = 0; j < 4; j++) {
+                size_t o = (size_t)(3 * nu + a) * Kp + 4 * t + j;
+                if (4 * t + j < Kp) { Uh[o] = 0.f; Ul[o] = 0.f; }
+            }
+        return;
+    }
+    const KVec &K = kv[t];
+    double k2 = K.k[0] * K.k[0] + K.k[1] * K.k[1] + K.k[2] * K.k[2];
+    double kn = sqrt(k2);
+    double kh[3] = {K.k[0] / kn, K.k[1] / kn, K.k[2] / kn};
+    // 2f = trace(m)/2, m = 2 f (I - khat khat)
+    double twof = 0.5 * (K.m[0] + K.m[3] + K.m[5]);
+    double w = sqrt(twof > 0.0 ? twof : 0.0);
+    // u1 = normalise(e x khat) with e the axis least aligned with khat; u2 = khat x u1
+    int ax = fabs(kh[0]) <= fabs(kh[1]) ? (fabs(kh[0]) <= fabs(kh[2]) ? 0 : 2)
+                                        : (fabs(kh[1]) <= fabs(kh[2]) ? 1 : 2);
+    double e[3] = {0, 0, 0};
+    e[ax] = 1.0;
+    double u1[3] = {e[1] * kh[2] - e[2] * kh[1], e[2] * kh[0] - e[0] * kh[2], e[0] * kh[1] - e[1] * kh[0]};
+    double n1 = sqrt(u1[0] * u1[0] + u1[1] * u1[1] + u1[2] * u1[2]);
+    for (int i = 0; i < 3; i++) u1[i] /= n1;
+    double u2[3] = {kh[1] * u1[2] - kh[2] * u1[1], kh[2] * u1[0] - kh[0] * u1[2], kh[0] * u1[1] - kh[1] * u1[0]};
+    double c = cs[(size_t)t * n + nu], s = sn[(size_t)t * n + nu];
+    for (int a = 0; a < 3; a++) {
+        double vals[4] = {w * u1[a] * c, w * u1[a] * s, w * u2[a] * c, w * u2[a] * s};
+        for (int j = 0; j < 4; j++) {
+            float h = to_tf32((float)vals[j]);
+            float l = to_tf32((float)(vals[j] - (double)h));
+            size_t o = (size_t)(3 * nu + a) * Kp + 4 * t + j;
+            Uh[o] = h;
+            Ul[o] = l;
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+
+static PFN_cuTensorMapEncodeTiled_v12000 g_enc = nullptr;
+
+static int upper_tiles(int T, std::vector<int2> *out)
+{
+    int cnt = 0;
+    for (int j = 0; j < T; j++)
+        for (int i = 0; i <= j; i++) {
+            if (out) out->push_back(make_int2(i, j));
+            cnt++;
+        }
+    return cnt;
+}
+
+bd_status recip_tc_init(Plan &P)
+{
+    P.recip_tc = 0;
+    if (P.p.precision == BD_FP64 || P.nk == 0) return BD_OK;
+    // needs f(k) >= 0 on every k (a - a^3 k^2/3 > 0): k_max^2 = (2 pi/L)^2 n2max < 3/a^2
+    double kmax2 = (2.0 * 3.14159265358979323846 / P.p.box_L) *
+                   (2.0 * 3.14159265358979323846 / P.p.box_L) * P.p.n2max;
+    if (!(kmax2 * P.p.a * P.p.a < 3.0)) return BD_OK;
+    if (!g_enc) {
+        cudaDriverEntryPointQueryResult q;
+        void *fn = nullptr;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault,
+                                             &q) != cudaSuccess || !fn)
+            return set_error(BD_ERR_CUDA, "cuTensorMapEncodeTiled unavailable");
+        g_enc = (PFN_cuTensorMapEncodeTiled_v12000)fn;
+    }
+    P.recip_kp = (4 * P.nk + rt::BK - 1) / rt::BK * rt::BK;
+    const int T = (P.n3 + rt::BM - 1) / rt::BM;
+    std::vector<int2> tiles;
+    P.recip_ntiles = upper_tiles(T, &tiles);
+    size_t ub = (size_t)P.n3 * P.recip_kp * sizeof(float);
+    cudaError_t e = cudaMalloc(&P.d_Uh, ub);
+    if (e == cudaSuccess) e = cudaMalloc(&P.d_Ul, ub);
+    if (e == cudaSuccess) e = cudaMalloc(&P.d_rtiles, tiles.size() * sizeof(int2));
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return set_error(BD_ERR_OOM, "reciprocal product scratch: %s", cudaGetErrorString(e));
+    }
+    P.scratch_bytes += (int64_t)(2 * ub + tiles.size() * sizeof(int2));
+    cudaMemcpy(P.d_rtiles, tiles.data(), tiles.size() * sizeof(int2), cudaMemcpyHostToDevice);
+    const int sm = rt::STAGES * 2 * rt::TILE_BYTES + 1024;
+    if (cudaFuncSetAttribute(rt::k_recip_syrk, cudaFuncAttributeMaxDynamicSharedMemorySize, sm) !=
+        cudaSuccess)
+        return set_error(BD_ERR_CUDA, "smem attribute (reciprocal product)");
+    P.recip_tc = 1;
+    return BD_OK;
+}
+
+static bd_status map_U(CUtensorMap *m, const float *base, int Kp, int n3)
+{
+    cuuint64_t dims[2] = {(cuuint64_t)Kp, (cuuint64_t)n3};
+    cuuint64_t strides[1] = {(cuuint64_t)Kp * 4};
+    cuuint32_t box[2] = {rt::BK, rt::BM};
+    cuuint32_t es[2] = {1, 1};
+    CUresult r = g_enc(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<float *>(base), dims,
+                       strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                       CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) return set_error(BD_ERR_CUDA, "tensor map for U (%d)", (int)r);
+    return BD_OK;
+}
+
+// D32 (band tiles) = U U^T, after the per-bead trig tables of this R are built
+bd_status launch_recip_tc(Plan &P, float *D32, cudaStream_t s)
+{
+    const int nkgroups = P.recip_kp / 4;             // >= nk, the rest zero
+    dim3 gu((P.n + 127) / 128, nkgroups);
+    k_build_U<<<gu, 128, 0, s>>>(P.d_cos, P.d_sin, P.d_kvec, P.n, P.nk, P.recip_kp, P.d_Uh, P.d_Ul);
+    count_launches(1);
+    CUtensorMap mh, ml;
+    bd_status st = map_U(&mh, P.d_Uh, P.recip_kp, P.n3);
+    if (st != BD_OK) return st;
+    st = map_U(&ml, P.d_Ul, P.recip_kp, P.n3);
+    if (st != BD_OK) return st;
+    const int sm = rt::STAGES * 2 * rt::TILE_BYTES + 1024;
+    rt::k_recip_syrk<<<P.recip_ntiles, rt::THREADS, sm, s>>>(mh, ml, P.d_rtiles, P.n3,
+                                                            P.recip_kp / rt::BK, D32, P.ld,
+                                                            P.d_status + 6);
+    count_launches(1);
+    return check_launch("reciprocal product");
+}
+
+}  // namespace bd

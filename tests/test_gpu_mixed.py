@@ -153,6 +153,37 @@ def test_step_mixed_drift_refined(bnd):
     assert relerr(disp, R_ref - R) <= 1e-3
 
 
+@pytest.mark.parametrize("n_chains,nb,alpha_factor", [(70, 10, 1.0), (7, 11, 3.0)])
+def test_build_D_f32_reciprocal_paths(bnd, n_chains, nb, alpha_factor):
+    """FP32 D over several 128-row tiles with a ragged tail (700 beads: the
+    reciprocal sum as the TF32 hi/lo tensor-core product U U^T), and with a
+    wide k sphere (alpha = 3 sqrt(pi)/L: a - a^3 k^2/3 < 0 for the largest k,
+    so the reciprocal sum stays in the pair kernel)."""
+    cfg, p, R = system(n_chains=n_chains, nb=nb, seed=63, alpha_factor=alpha_factor)
+    if alpha_factor > 1:
+        assert p["kc"] ** 2 * p["a"] ** 2 > 3.0
+    plan, Rg, D = mixed(bnd, p, R)
+    Dr = oracle.build_D(p, R)
+    D32 = plan.D_view(D, "f32").cpu().numpy().astype(np.float64)
+    assert relerr(D32, Dr) <= 2e-6
+    assert np.array_equal(D32, D32.T)
+
+
+def test_n8000_D32_sampled_rows(bnd):
+    """FP32 D of the N = 8000 workload (16,000+ tensor-core tiles of the
+    reciprocal product) against oracle rows of D."""
+    cfg, _ = inputs.preset("c4", alpha_factor=1.5)
+    p = cfg.params()
+    R = inputs.make_chains(cfg)
+    plan, Rg, D = mixed(bnd, p, R, max_rhs=1)
+    D32 = plan.D_view(D, "f32")
+    scale = float(D32.abs().max())
+    for b in (0, 1, 2047, 4096, 7999):
+        ref = oracle.build_D_rows(p, R, b, b + 1)
+        got = D32[3 * b:3 * b + 3].cpu().numpy().astype(np.float64)
+        assert np.max(np.abs(got - ref)) <= 2e-6 * scale
+
+
 def test_n8000_mixed_sampled_rows(bnd):
     """The N = 8000 workload of the benchmark: rows of the tensor-core
     product against oracle rows of D times the same X (FP64)."""
