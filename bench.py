@@ -110,8 +110,8 @@ def cpu_baseline(p, R, m, nch, target_s=12.0):
                       f"({t:.1f} s), scaled by N/rows to one step ({step_s:.1f} s)"}
 
 
-# alpha factor the oracle arm uses when --alpha-factor is auto: the value the
-# GPU autotuner picks for the mixed step of this workload (see profiles/)
+# alpha factor the oracle arm uses when --alpha-factor is auto: the balanced
+# split f = 1 of the input recipe (the oracle is timed as it stands, untuned)
 REFERENCE_ALPHA = 1.0
 
 
@@ -289,8 +289,13 @@ def measure(args, precision, p, R0, rank, ws):
     bounds_mode = 1 if (precision != "fp64" and args.bounds == "lagged") else 0
     kw = dict(m=args.m, n_cheb=args.nch, lanczos_iters=args.lanczos, bound_safety=0.05,
               dmin_fraction=0.5, seed=4242 + rank, stats=stats, bounds_mode=bounds_mode)
+    shape = None
     for w in range(args.warmup):
         plan.step(R, D, None, step_index=w, **kw)
+        if w == 0 and precision != "fp64":
+            # launch shape of the tensor-core product, timed on this D
+            cps, pms = plan.autotune(D)
+            shape = {"ctas_per_sm": cps, "autotune_ms": round(pms, 4)}
     torch.cuda.synchronize()
     stream = torch.cuda.current_stream()
     evs = [[torch.cuda.Event(enable_timing=True) for _ in range(7)] for _ in range(args.steps)]
@@ -375,7 +380,7 @@ def measure(args, precision, p, R0, rank, ws):
     out = {"value": ws * args.steps / (ms * 1e-3), "ms_per_step": ms / args.steps,
            "phases_ms": phases, "step_stats": st, "roofline": roof, "gpu_launches": launches,
            "clocks": clk, "e2e": e2e, "n_kvec_half": plan.info.n_kvec,
-           "d_gb": plan.info.d_bytes / 1e9}
+           "d_gb": plan.info.d_bytes / 1e9, "product_shape": shape}
     del D
     plan.close()
     torch.cuda.empty_cache()
@@ -425,7 +430,8 @@ def run_ours(args):
                        "m": args.m, "n_cheb": args.nch, "lanczos_iters": args.lanczos,
                        "bounds": args.bounds if head != "fp64" else "fresh",
                        "l2": "inputs larger than L2 (D alone is %.2f GB)" % r["d_gb"],
-                       "parallelism": "replicas" if ws > 1 else "single"},
+                       "parallelism": "replicas" if ws > 1 else "single",
+                       "product_shape": r["product_shape"]},
             "phases_ms": r["phases_ms"], "step_stats": r["step_stats"], "roofline": r["roofline"],
             "gpu_launches": r["gpu_launches"], "clocks": r["clocks"], "e2e": r["e2e"]}
     if "fp64" in results and head != "fp64":

@@ -116,14 +116,17 @@ typedef struct {
 /* Options of bd_step. */
 typedef struct {
     int32_t m;                /* Wiener columns (1..max_rhs); column 0 advances R  */
-    int32_t n_cheb;           /* Chebyshev terms N_Ch (2..max_cheb)                */
+    int32_t n_cheb;           /* Chebyshev terms N_Ch (2..max_cheb); 0 = adaptive  */
     int32_t lanczos_iters;    /* Lanczos steps for the bounds (4..128)            */
     double  bound_safety;     /* d_max = (1 + bound_safety) theta_max             */
     double  dmin_fraction;    /* d_min = dmin_fraction theta_min (0 < f <= 1)     */
     uint64_t seed;            /* Philox key when dW == NULL                        */
     uint64_t step_index;      /* Philox counter high word when dW == NULL          */
-    int32_t bounds_mode;      /* BD_BOUNDS_FRESH or BD_BOUNDS_LAGGED (see bd_step)  */
+    int32_t bounds_mode;      /* BD_BOUNDS_FRESH, _LAGGED, _FIXMAN_DILUTE or
+                                 _FIXMAN_SEMIDILUTE (see bd_step)                  */
     int32_t flags;            /* BD_STEP_DEVICE_COUNTER or 0                        */
+    double  ef_tol;           /* n_cheb == 0: adaptive N_Ch until E_f < ef_tol      */
+    double  fixman_c;         /* BD_BOUNDS_FIXMAN_SEMIDILUTE: C of Eq. (fmin)       */
 } bd_step_opts;
 
 #define BD_STEP_DEVICE_COUNTER 1  /* with dW == NULL: the Philox counter high word is
@@ -133,6 +136,14 @@ typedef struct {
                                      every replay; step_index is ignored           */
 
 #define BD_BOUNDS_FRESH 0     /* lanczos_iters Lanczos products every step          */
+#define BD_BOUNDS_FIXMAN_DILUTE 2     /* Eq. (lmax-lmin-dilute): lambda^F_max,min =
+                                 U+-.D.U+- / 3N with U+ all ones and U- alternating
+                                 +1, -1 (two extra columns of the first product);
+                                 d_max = 2 lambda^F_max, d_min = lambda^F_min / 2  */
+#define BD_BOUNDS_FIXMAN_SEMIDILUTE 3 /* Eqs. (fmax), (fmin): lambda_max = 0.35 N^0.6
+                                 lambda^F_max, lambda_min = lambda_max / (C N^0.6)
+                                 with C = fixman_c, N the number of beads;
+                                 d_max = lambda_max, d_min = lambda_min            */
 #define BD_BOUNDS_LAGGED 1    /* mixed plans: the Lanczos vector rides as one extra
                                  column of this step's products; its bounds serve
                                  the next step (the first step runs fresh)          */
@@ -222,6 +233,25 @@ bd_status bd_chebyshev_sqrt(bd_plan *plan, const void *D, const double *bounds, 
                             const double *dW, int32_t m, double *dS, double *Ef,
                             bd_stream stream);
 
+/* bd_chebyshev_sqrt_adaptive -- the same series with N_Ch chosen as in
+ * Sec. IV: N_Ch starts at Eq. (nint), nint(sqrt(d_max / d_min)) + 1 (the
+ * bounds stand in for the extreme eigenvalues), and grows by one term until
+ * E_f < ef_tol in every column, at most to the plan's max_cheb.  The
+ * recurrence vectors V_p are kept (they do not depend on N_Ch) and E_f of
+ * each candidate N_Ch is evaluated from the Chebyshev moments dW.T_j(Y)dW,
+ * so every V_p is computed once; dS is then formed with the coefficients of
+ * the chosen N_Ch and Ef recomputed from it.  Synchronises the stream (the
+ * host reads the bounds and one number per candidate; not for graph
+ * capture).  The first call allocates (max_cheb - 1) x 3N x max_rhs doubles
+ * of history.
+ *   ef_tol  > 0
+ *   n_used  host, one int32 (output, may be NULL): the N_Ch used
+ * Returns BD_ERR_CHEB_NOCONV if E_f >= ef_tol at max_cheb terms; dS and Ef
+ * then hold the max_cheb-term result.                                   */
+bd_status bd_chebyshev_sqrt_adaptive(bd_plan *plan, const void *D, const double *bounds,
+                                     double ef_tol, const double *dW, int32_t m, double *dS,
+                                     double *Ef, int32_t *n_used, bd_stream stream);
+
 /* ---------------------------------------------------------------------------
  * bd_step -- one Euler step of Eq. (sde) with kappa = 0:
  *   r(t+dt) = r + (dt/4) D.F + (1/sqrt 2) dS[:,0],
@@ -232,7 +262,12 @@ bd_status bd_chebyshev_sqrt(bd_plan *plan, const void *D, const double *bounds, 
  * is one extra column of D.[F, dW] and of every Chebyshev product, so it costs
  * no extra pass over D; N_Ch - 1 Lanczos steps), widened by the same
  * margins; the plan keeps them between calls.  FP64 plans, the first step of
- * a plan, m + 2 > 32, n_cheb < 8 and n_cheb > 129 use fresh bounds.  FENE systems reject a proposal with
+ * a plan, m + 2 > 32, n_cheb < 8 and n_cheb > 129 use fresh bounds.
+ * opts->n_cheb == 0 selects the adaptive series of
+ * bd_chebyshev_sqrt_adaptive with opts->ef_tol (fresh bounds; the call then
+ * synchronises the stream); stats->n_cheb reports the N_Ch used and
+ * stats->status = BD_ERR_CHEB_NOCONV if max_cheb terms did not reach ef_tol
+ * (the step is still taken with them).  FENE systems reject a proposal with
  * any |Q|^2 >= b (Sec. VII): R is then left unchanged, stats->accepted = 0
  * and stats->status = BD_ERR_FENE_STRETCH.
  *   R      dev, 3N doubles, advanced in place (only if accepted)
@@ -272,9 +307,11 @@ bd_status bd_chebyshev_backward(bd_plan *plan, const double *R, const void *D,
                                 bd_stream stream);
 
 /* Autotuner: for a mixed plan, times the tensor-core product on D (its
- * contents do not matter) for K-split counts 1, 2, 4, 8 and 16 and keeps the
- * fastest for all later products of this plan; returns the split and the time
- * per product (ms).  Synchronous.  FP64 plans: no-op (split 0).          */
+ * contents do not matter) with 1 and 2 resident CTAs per SM (the product is a
+ * persistent stream-K kernel with one grid of that many CTAs) and keeps the
+ * faster for all later products of this plan; returns the choice in
+ * *split_out and the time per product (ms).  Synchronous.  FP64 plans: no-op
+ * (0).                                                                   */
 bd_status bd_plan_autotune(bd_plan *plan, void *D, int32_t *split_out, float *ms_out,
                            bd_stream stream);
 

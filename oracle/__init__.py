@@ -26,6 +26,8 @@ import platform
 import subprocess
 import threading
 
+import math
+
 import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
@@ -210,6 +212,46 @@ def cheb_sqrt(D: np.ndarray, dmin: float, dmax: float, nch: int, dW: np.ndarray)
     lib().oracle_cheb_sqrt(D.shape[0], _ptr(D), float(dmin), float(dmax), int(nch),
                            _ptr(dW), dW.shape[0], _ptr(dS), _ptr(Ef))
     return dS, Ef
+
+
+def fixman_bounds(D: np.ndarray, nbeads: int, mode: str, C: float = 0.0):
+    """Sec. IV: lambda^F_max = U+.D.U+ / 3N, lambda^F_min = U-.D.U- / 3N
+    (Eq. lmax-lmin-dilute; U+ all ones, U- alternating +1, -1).  mode
+    'dilute': (d_min, d_max) = (lambda^F_min / 2, 2 lambda^F_max); mode
+    'semidilute': lambda_max = 0.35 N^0.6 lambda^F_max (Eq. fmax),
+    lambda_min = lambda_max / (C N^0.6) (Eq. fmin), used as the bounds.
+    Returns (d_min, d_max, lambda^F_max, lambda^F_min)."""
+    n3 = D.shape[0]
+    up = np.ones(n3)
+    um = np.where(np.arange(n3) % 2 == 0, 1.0, -1.0)
+    lmaxF = float(up @ D @ up) / n3
+    lminF = float(um @ D @ um) / n3
+    if mode == "dilute":
+        return 0.5 * lminF, 2.0 * lmaxF, lmaxF, lminF
+    n06 = float(nbeads) ** 0.6
+    lmax = 0.35 * n06 * lmaxF
+    return lmax / (C * n06), lmax, lmaxF, lminF
+
+
+def nch_initial(dmin: float, dmax: float) -> int:
+    """Eq. (nint): N_Ch = nint(sqrt(lambda_max / lambda_min)) + 1, with the
+    bounds standing in for the extreme eigenvalues (nint rounds halves up)."""
+    return int(math.floor(math.sqrt(dmax / dmin) + 0.5)) + 1
+
+
+def cheb_sqrt_adaptive(D: np.ndarray, dmin: float, dmax: float, dW: np.ndarray, tol: float,
+                       nch_max: int):
+    """Sec. IV: start from Eq. (nint) and raise N_Ch by one until E_f < tol in
+    every column (at most nch_max).  Each candidate is the full series of
+    cheb_sqrt.  Returns (dS, Ef, N_Ch, converged)."""
+    n = max(2, min(nch_initial(dmin, dmax), nch_max))
+    while True:
+        dS, Ef = cheb_sqrt(D, dmin, dmax, n, dW)
+        if float(np.max(Ef)) < tol:
+            return dS, Ef, n, True
+        if n >= nch_max:
+            return dS, Ef, n, False
+        n += 1
 
 
 def step(p: dict, R: np.ndarray, dW: np.ndarray, dmin: float, dmax: float, nch: int):

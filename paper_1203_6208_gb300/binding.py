@@ -25,13 +25,14 @@ STATUS_NAMES = {0: "BD_OK", 1: "BD_ERR_INVALID", 2: "BD_ERR_OOM", 3: "BD_ERR_CUD
 PRECISIONS = {"fp64": 0, "mixed_f16": 1, "mixed_bf16": 2}
 BD_APPLY_REFINE = 1
 BD_STEP_DEVICE_COUNTER = 1
+BOUNDS_MODES = {"fresh": 0, "lagged": 1, "fixman_dilute": 2, "fixman_semidilute": 3}
 
 EXPORTS = ["bd_plan_create", "bd_plan_destroy", "bd_plan_query", "bd_forces", "bd_build_D",
            "bd_apply_D", "bd_eig_bounds", "bd_chebyshev_sqrt", "bd_step", "bd_wiener",
            "bd_set_phase_events", "bd_kernel_launches", "bd_eig_bounds_noalloc",
            "bd_apply_D_backward", "bd_chebyshev_backward", "bd_plan_autotune", "bd_product_timing",
            "bd_plan_set_step_counter", "bd_batch_create", "bd_batch_destroy", "bd_batch_query",
-           "bd_batch_step",
+           "bd_batch_step", "bd_chebyshev_sqrt_adaptive",
            "bd_last_error", "bd_version"]
 PHASES = ["forces", "build_D", "bounds", "first_product", "chebyshev", "update"]
 
@@ -66,7 +67,8 @@ class BdStepOpts(ctypes.Structure):
                 ("lanczos_iters", ctypes.c_int32), ("bound_safety", ctypes.c_double),
                 ("dmin_fraction", ctypes.c_double), ("seed", ctypes.c_uint64),
                 ("step_index", ctypes.c_uint64), ("bounds_mode", ctypes.c_int32),
-                ("flags", ctypes.c_int32)]
+                ("flags", ctypes.c_int32), ("ef_tol", ctypes.c_double),
+                ("fixman_c", ctypes.c_double)]
 
 
 STATS_BYTES = ctypes.sizeof(BdStepStats)
@@ -109,6 +111,8 @@ def load(path: str = LIB_PATH):
                                  ctypes.POINTER(i64), ctypes.POINTER(i64), ctypes.POINTER(i64)]
     L.bd_batch_step.argtypes = [_vp, _vp, _vp, ctypes.POINTER(BdStepOpts), _vp, _vp]
     L.bd_chebyshev_backward.argtypes = [_vp, _vp, _vp, _vp, i32, _vp, i32, _vp, _vp, _vp, _vp]
+    L.bd_chebyshev_sqrt_adaptive.argtypes = [_vp, _vp, _vp, f64, _vp, i32, _vp, _vp,
+                                             ctypes.POINTER(i32), _vp]
     L.bd_eig_bounds_noalloc.argtypes = [_vp, i32, i32, i32, f64, f64, _vp, _vp, _vp]
     L.bd_kernel_launches.restype = ctypes.c_uint64
     L.bd_last_error.restype = ctypes.c_char_p
@@ -215,13 +219,27 @@ class Plan:
         _check(load().bd_chebyshev_sqrt(self._h, _p(D), _p(bounds), int(n_cheb), _p(dW), m,
                                         _p(dS), _p(Ef), _stream(stream)))
 
+    def chebyshev_adaptive(self, D, bounds, ef_tol, dW, dS, Ef=None, stream=None):
+        """Adaptive N_Ch (synchronising); returns (n_used, converged)."""
+        m = dW.shape[0] if dW.dim() == 2 else 1
+        n = ctypes.c_int32()
+        st = load().bd_chebyshev_sqrt_adaptive(self._h, _p(D), _p(bounds), float(ef_tol), _p(dW),
+                                               m, _p(dS), _p(Ef), ctypes.byref(n),
+                                               _stream(stream))
+        if st == 6:                     # BD_ERR_CHEB_NOCONV: outputs hold max_cheb terms
+            return int(n.value), False
+        _check(st)
+        return int(n.value), True
+
     def step(self, R, D, dW=None, *, m=1, n_cheb=20, lanczos_iters=30, bound_safety=0.05,
              dmin_fraction=0.5, seed=0, step_index=0, DF=None, dS=None, stats=None,
-             bounds_mode=0, flags=0, stream=None):
+             bounds_mode=0, flags=0, ef_tol=0.0, fixman_c=0.0, stream=None):
+        """n_cheb = 0 selects the adaptive series with ef_tol (synchronising);
+        bounds_mode 2/3 = Fixman's dilute / semidilute estimates (fixman_c = C)."""
         o = BdStepOpts(m=int(m), n_cheb=int(n_cheb), lanczos_iters=int(lanczos_iters),
                        bound_safety=float(bound_safety), dmin_fraction=float(dmin_fraction),
                        seed=int(seed), step_index=int(step_index), bounds_mode=int(bounds_mode),
-                       flags=int(flags))
+                       flags=int(flags), ef_tol=float(ef_tol), fixman_c=float(fixman_c))
         _check(load().bd_step(self._h, _p(R), _p(D), _p(dW), ctypes.byref(o), _p(DF), _p(dS),
                               _p(stats), _stream(stream)))
 

@@ -129,6 +129,8 @@ bd_status bd_batch_step(bd_batch *b, double *R, void *D, const bd_step_opts *opt
                         bd_step_stats *stats, bd_stream stream)
 {
     if (!b || !R || !D || !opts) return set_error(BD_ERR_INVALID, "NULL argument");
+    if (opts->n_cheb == 0)
+        return set_error(BD_ERR_INVALID, "adaptive N_Ch synchronises and cannot run in a batch");
     if (((uintptr_t)D & 255) != 0) return set_error(BD_ERR_INVALID, "D must be 256-byte aligned");
     cudaStream_t s = stream;
     if (b->calls == 0) {

@@ -10,6 +10,7 @@
 #include "tc_gemm.cuh"
 #include "adjoint.cuh"
 #include "recip_tc.cuh"
+#include "adaptive.cuh"
 
 struct bd_plan {
     bd::Plan P;
@@ -75,9 +76,10 @@ static void free_plan(Plan &P)
                     P.d_coef, P.d_wdw, P.d_red, P.d_redpart, P.d_bounds, P.d_status, P.d_lq[0], P.d_lq[1],
                     P.d_lq[2], P.d_lab, P.d_x16, P.d_xscale, P.d_part, P.d_counters,
                     P.d_stats_scratch, P.d_y32, P.d_lag_bounds, P.d_step_ctr, P.d_vhist, P.d_xhist, P.d_ubuf[0], P.d_ubuf[1],
-                    P.d_ubuf[2], P.d_ubuf[3], P.d_Uh, P.d_Ul, P.d_rtiles};
+                    P.d_ubuf[2], P.d_ubuf[3], P.d_Uh, P.d_Ul, P.d_rtiles, P.d_lanpart, P.d_mom};
     for (void *p : ptrs)
         if (p) cudaFree(p);
+    if (P.h_est) cudaFreeHost(P.h_est);
 }
 
 static bd_status validate(const bd_params *p)
@@ -187,8 +189,8 @@ bd_status bd_plan_create(const bd_params *params, bd_plan **out_plan)
     TRY(dmalloc(P, &P.d_DF, n3));
     TRY(dmalloc(P, &P.d_Rnew, n3));
     for (int i = 0; i < 3; i++) TRY(dmalloc(P, &P.d_V[i], n3 * R));
-    TRY(dmalloc(P, &P.d_X0, n3 * (R + 2)));
-    TRY(dmalloc(P, &P.d_Y0, n3 * (R + 2)));
+    TRY(dmalloc(P, &P.d_X0, n3 * (R + 3)));
+    TRY(dmalloc(P, &P.d_Y0, n3 * (R + 3)));
     TRY(dmalloc(P, &P.d_lag_bounds, 2));
     TRY(dmalloc(P, &P.d_step_ctr, 1));
     TRY(dmalloc(P, &P.d_dS, n3 * R));
@@ -307,6 +309,17 @@ static bd_status apply_core(Plan &P, const void *D, const double *X, int m, doub
     return BD_OK;
 }
 
+}  // extern "C"
+
+namespace bd {
+bd_status apply_dense(Plan &P, const void *D, const double *X, int m, double *Y, cudaStream_t s)
+{
+    return apply_core(P, D, X, m, Y, 0, s);
+}
+}  // namespace bd
+
+extern "C" {
+
 bd_status bd_apply_D(bd_plan *plan, const void *D, const double *X, int32_t m, double *Y,
                      int32_t flags, bd_stream stream)
 {
@@ -363,11 +376,9 @@ static bd_status cheb_core(Plan &P, const void *D, const double *bounds, int nch
             float *D32;
             void *D16;
             split_mixed(P, (void *)D, &D32, &D16);
-            const bool lan = lanczos_from >= 0;
-            bd_status st = tc_cheb(P, D16, m, P.d_coef, bounds, p, prev2, prev1, dS, s,
-                                   lan ? P.d_lq[1] : nullptr, lan ? P.d_lq[2] : nullptr);
+            const int lan_step = lanczos_from >= 0 ? lanczos_from + (p - 1) : -1;
+            bd_status st = tc_cheb(P, D16, m, P.d_coef, bounds, p, prev2, prev1, dS, s, lan_step);
             if (st != BD_OK) return st;
-            if (lan) launch_lanczos_update(P, lanczos_from + (p - 1), s);
         }
         double *t = prev2;   // prev2 now holds V_p
         prev2 = prev1;
@@ -389,6 +400,27 @@ bd_status bd_chebyshev_sqrt(bd_plan *plan, const void *D, const double *bounds, 
     bd_status st = apply_core(P, D, dW, m, P.d_V[2], 0, stream);
     if (st != BD_OK) return st;
     return cheb_core(P, D, bounds, n_cheb, dW, P.d_V[2], m, dS, Ef, nullptr, stream);
+}
+
+bd_status bd_chebyshev_sqrt_adaptive(bd_plan *plan, const void *D, const double *bounds,
+                                     double ef_tol, const double *dW, int32_t m, double *dS,
+                                     double *Ef, int32_t *n_used, bd_stream stream)
+{
+    if (!plan || !D || !bounds || !dW || !dS) return set_error(BD_ERR_INVALID, "NULL argument");
+    Plan &P = plan->P;
+    if (m < 1 || m > P.p.max_rhs) return set_error(BD_ERR_INVALID, "m=%d outside [1, max_rhs=%d]", m, P.p.max_rhs);
+    if (!(ef_tol > 0.0)) return set_error(BD_ERR_INVALID, "ef_tol must be > 0");
+    if (P.p.max_cheb < 2) return set_error(BD_ERR_INVALID, "plan max_cheb < 2");
+    bd_status st = apply_core(P, D, dW, m, P.d_V[2], 0, stream);
+    if (st != BD_OK) return st;
+    int N = 0, conv = 0;
+    st = cheb_adaptive_core(P, D, bounds, ef_tol, dW, P.d_V[2], m, dS, Ef, nullptr, stream, &N,
+                            &conv);
+    if (n_used) *n_used = N;
+    if (st != BD_OK) return st;
+    if (!conv)
+        return set_error(BD_ERR_CHEB_NOCONV, "E_f >= %g with max_cheb = %d terms", ef_tol, N);
+    return BD_OK;
 }
 
 bd_status bd_product_timing(bd_plan *plan, int32_t enable, float *total_ms, int32_t *launches)
@@ -469,8 +501,17 @@ bd_status bd_step(bd_plan *plan, double *R, void *D, const double *dW, const bd_
     Plan &P = plan->P;
     const int m = o->m;
     if (m < 1 || m > P.p.max_rhs) return set_error(BD_ERR_INVALID, "m=%d outside [1, max_rhs=%d]", m, P.p.max_rhs);
-    if (o->n_cheb < 2 || o->n_cheb > P.p.max_cheb)
-        return set_error(BD_ERR_INVALID, "n_cheb outside [2, max_cheb]");
+    const bool adaptive = o->n_cheb == 0;
+    if (!adaptive && (o->n_cheb < 2 || o->n_cheb > P.p.max_cheb))
+        return set_error(BD_ERR_INVALID, "n_cheb outside [2, max_cheb] (0: adaptive)");
+    if (adaptive && !(o->ef_tol > 0.0))
+        return set_error(BD_ERR_INVALID, "adaptive N_Ch (n_cheb = 0) needs ef_tol > 0");
+    const int fix = (o->bounds_mode == BD_BOUNDS_FIXMAN_DILUTE ||
+                     o->bounds_mode == BD_BOUNDS_FIXMAN_SEMIDILUTE) ? o->bounds_mode : 0;
+    if (o->bounds_mode < 0 || o->bounds_mode > BD_BOUNDS_FIXMAN_SEMIDILUTE)
+        return set_error(BD_ERR_INVALID, "unknown bounds_mode %d", o->bounds_mode);
+    if (fix == BD_BOUNDS_FIXMAN_SEMIDILUTE && !(o->fixman_c > 0.0))
+        return set_error(BD_ERR_INVALID, "BD_BOUNDS_FIXMAN_SEMIDILUTE needs fixman_c > 0");
     if (o->lanczos_iters < 1 || o->lanczos_iters > kMaxLanczos)
         return set_error(BD_ERR_INVALID, "lanczos_iters outside [1, %d]", kMaxLanczos);
     if (!(o->bound_safety >= 0.0) || !(o->dmin_fraction > 0.0) || !(o->dmin_fraction <= 1.0))
@@ -493,9 +534,11 @@ bd_status bd_step(bd_plan *plan, double *R, void *D, const double *dW, const bd_
     if (st != BD_OK) return st;
     PHASE(2);
     // (a6) bounds: fresh Lanczos, or the previous step's lagged recurrence
-    const bool lag = o->bounds_mode == BD_BOUNDS_LAGGED && is_mixed(P) && o->n_cheb >= 8 &&
+    const bool lag = !adaptive && o->bounds_mode == BD_BOUNDS_LAGGED && is_mixed(P) && o->n_cheb >= 8 &&
                      o->n_cheb - 1 <= kMaxLanczos && m + 2 <= kMaxRhs;
-    if (lag && P.lag_valid) {
+    if (fix) {
+        // Fixman's estimates come from the first product below
+    } else if (lag && P.lag_valid) {
         cudaMemcpyAsync(P.d_bounds, P.d_lag_bounds, 2 * sizeof(double), cudaMemcpyDeviceToDevice, s);
         launch_check_bounds(P.d_bounds, P.d_status + 3, s);
     } else {
@@ -503,7 +546,7 @@ bd_status bd_step(bd_plan *plan, double *R, void *D, const double *dW, const bd_
                              P.d_bounds, P.d_status + 3, s);
         if (st != BD_OK) return st;
     }
-    launch_stats_bounds(st_dev, P.d_bounds, P.d_status + 3, s);
+    if (!fix) launch_stats_bounds(st_dev, P.d_bounds, P.d_status + 3, s);
     PHASE(3);
     // Wiener increments
     const double *w = dW;
@@ -516,7 +559,8 @@ bd_status bd_step(bd_plan *plan, double *R, void *D, const double *dW, const bd_
     }
     // (a5) first product D [F, dW]  (one pass over D)
     double *Wcols;
-    if (m + 1 <= kMaxRhs && m + 1 <= P.p.max_rhs + 1) {
+    const int fcols = fix ? 2 : 0;         // Fixman's U+, U- ride along
+    if (m + 1 + fcols <= kMaxRhs) {
         const int extra = lag ? 1 : 0;     // the Lanczos start vector q_1
         cudaMemcpyAsync(P.d_X0, P.d_F, n3 * sizeof(double), cudaMemcpyDeviceToDevice, s);
         cudaMemcpyAsync(P.d_X0 + n3, w, n3 * m * sizeof(double), cudaMemcpyDeviceToDevice, s);
@@ -525,9 +569,13 @@ bd_status bd_step(bd_plan *plan, double *R, void *D, const double *dW, const bd_
             cudaMemcpyAsync(P.d_X0 + n3 * (m + 1), P.d_lq[1], n3 * sizeof(double),
                             cudaMemcpyDeviceToDevice, s);
         }
-        st = apply_core(P, D, P.d_X0, m + 1 + extra, P.d_Y0, 0, s);
+        if (fix) launch_fixman_fill(P.d_X0 + n3 * (m + 1), n3, s);
+        st = apply_core(P, D, P.d_X0, m + 1 + extra + fcols, P.d_Y0, 0, s);
         if (st != BD_OK) return st;
         Wcols = P.d_Y0 + n3;
+        if (fix)
+            launch_fixman_bounds(P, P.d_X0 + n3 * (m + 1), P.d_Y0 + n3 * (m + 1), fix,
+                                 o->fixman_c, P.d_bounds, P.d_status + 3, s);
         if (is_mixed(P)) {   // refine the drift column only
             launch_refine_f32(P, (const float *)D, P.d_F, 1, P.d_Y0, s);
         }
@@ -542,13 +590,27 @@ bd_status bd_step(bd_plan *plan, double *R, void *D, const double *dW, const bd_
         st = apply_core(P, D, w, m, P.d_Y0 + n3, 0, s);
         if (st != BD_OK) return st;
         Wcols = P.d_Y0 + n3;
+        if (fix) {
+            double *X2 = P.d_X0 + n3 * (m + 1), *Y2 = P.d_Y0 + n3 * (m + 1);
+            launch_fixman_fill(X2, n3, s);
+            st = apply_core(P, D, X2, 2, Y2, 0, s);
+            if (st != BD_OK) return st;
+            launch_fixman_bounds(P, X2, Y2, fix, o->fixman_c, P.d_bounds, P.d_status + 3, s);
+        }
     }
+    if (fix) launch_stats_bounds(st_dev, P.d_bounds, P.d_status + 3, s);
     const double *DFd = P.d_Y0;
     PHASE(4);
     // (a7) Chebyshev
     double *dSd = dS ? dS : P.d_dS;
-    st = cheb_core(P, D, P.d_bounds, o->n_cheb, w, Wcols, m, dSd, nullptr, st_dev, s,
-                   lag ? 0 : -1);
+    if (adaptive) {
+        int N = 0, conv = 0;
+        st = cheb_adaptive_core(P, D, P.d_bounds, o->ef_tol, w, Wcols, m, dSd, nullptr, st_dev, s,
+                                &N, &conv);
+    } else {
+        st = cheb_core(P, D, P.d_bounds, o->n_cheb, w, Wcols, m, dSd, nullptr, st_dev, s,
+                       lag ? 0 : -1);
+    }
     if (st != BD_OK) return st;
     if (lag) {               // N_Ch - 1 Lanczos steps -> bounds of the next step
         launch_lanczos_finish(P, o->n_cheb - 1, o->bound_safety, o->dmin_fraction,
@@ -566,12 +628,14 @@ bd_status bd_step(bd_plan *plan, double *R, void *D, const double *dW, const bd_
 
 static bd_status ensure_backward_scratch(Plan &P)
 {
-    if (P.d_vhist) return BD_OK;
+    // d_vhist may already exist (the adaptive Chebyshev series allocates it)
     size_t blk = (size_t)P.n3 * P.p.max_rhs;
     size_t hist = (size_t)(P.p.max_cheb - 1) * blk;
-    bd_status st = dmalloc(P, &P.d_vhist, hist);
-    if (st == BD_OK) st = dmalloc(P, &P.d_xhist, hist);
-    for (int i = 0; i < 4 && st == BD_OK; i++) st = dmalloc(P, &P.d_ubuf[i], blk);
+    bd_status st = BD_OK;
+    if (!P.d_vhist) st = dmalloc(P, &P.d_vhist, hist);
+    if (st == BD_OK && !P.d_xhist) st = dmalloc(P, &P.d_xhist, hist);
+    for (int i = 0; i < 4 && st == BD_OK; i++)
+        if (!P.d_ubuf[i]) st = dmalloc(P, &P.d_ubuf[i], blk);
     return st;
 }
 

@@ -82,7 +82,7 @@ struct Plan {
     double *d_F, *d_DF;                // forces and drift (3N)
     double *d_Rnew;                    // proposed positions (3N)
     double *d_V[3];                    // Chebyshev recurrence buffers (3N x max_rhs)
-    double *d_X0, *d_Y0;               // first product [F, dW] and its image (3N x (max_rhs+1))
+    double *d_X0, *d_Y0;               // first product [F, dW, extra] and its image (3N x (max_rhs+3))
     double *d_dS;                      // noise when the caller passes no dS
     double *d_dW;                      // Wiener block when generated on device
     double *d_coef;                    // Chebyshev coefficients [kMaxCheb]
@@ -98,9 +98,12 @@ struct Plan {
     void *d_x16;
     float *d_xscale;                   // per-column power-of-two scale
     float *d_part;                     // split-K partial sums
-    int32_t *d_counters;               // split-K arrival counters
+    int32_t *d_counters;               // stream-K arrival counters (per row block)
+    double *d_lanpart;                 // Lanczos dot partials per row block [3 * blocks]
     int ldx;                           // leading dimension of d_x16 (elements)
-    int tc_split;                      // K-splits of the tensor-core product (0: heuristic)
+    int tc_split;                      // resident CTAs per SM of the tensor-core product (0: 2)
+    int tc_maxslots;                   // partial slots per row block (stream-K schedule)
+    int num_sms;                       // SM count of the plan's device
     int64_t scratch_bytes;
     bd_step_stats *d_stats_scratch;
     cudaEvent_t phase_ev[BD_PHASE_EVENTS];
@@ -116,6 +119,9 @@ struct Plan {
     double *d_vhist;                   // V_0..V_{N_Ch-2}, [max_cheb-1][max_rhs][3N]
     double *d_xhist;                   // scaled adjoints X_q, same shape
     double *d_ubuf[4];                 // rolling adjoint vectors and D U products
+    // adaptive N_Ch (allocated by the first adaptive call)
+    double *d_mom;                     // moments, dot partials, estimates, D V scratch
+    double *h_est;                     // pinned host words read back per candidate N
     // reciprocal sum as a tensor-core product (mixed plans, recip_tc.cu)
     int recip_tc;                      // 1: D32's upper tiles are filled by U U^T first
     int recip_kp;                      // columns of U (4 per k-vector, padded to 32)
@@ -172,6 +178,10 @@ void launch_lanczos_finish(Plan &P, int k, double safety_max, double dmin_fracti
                            double *bounds, int32_t *status, cudaStream_t s);
 void launch_stats_begin(bd_step_stats *st, int nch, cudaStream_t s);
 void launch_check_bounds(const double *bounds, int32_t *status, cudaStream_t s);
+// Fixman estimates: U+, U- into two columns of X; bounds from X2 . Y2 (Y2 = D X2)
+void launch_fixman_fill(double *X, int n3, cudaStream_t s);
+void launch_fixman_bounds(Plan &P, const double *X2, const double *Y2, int mode, double C,
+                          double *bounds, int32_t *status, cudaStream_t s);
 void launch_stats_bounds(bd_step_stats *st, const double *bounds, const int32_t *bstatus,
                          cudaStream_t s);
 void launch_euler(Plan &P, double *R, const double *DF, const double *dS, bd_step_stats *stats,

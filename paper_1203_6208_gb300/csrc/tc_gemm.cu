@@ -6,7 +6,7 @@
 // pipe.  The kernel is a TMA -> shared memory -> tcgen05.mma -> TMEM stream:
 //   * a CTA owns a 128-row block of D and one K-split; warp 0 issues TMA
 //     loads of 128 x 64 tiles of D16 (128-byte swizzle) and 64 x BN tiles of
-//     the scaled 16-bit operand X^T into a STAGES-deep ring; warp 1 issues
+//     the scaled 16-bit operand X^T into a ST-deep ring; warp 1 issues
 //     tcgen05.mma (M = 128, N = BN, K = 16, FP32 accumulator in TMEM);
 //     warps 2-5 drain TMEM and write an FP32 partial;
 //   * the last CTA of a row block to finish (arrival counter) sums the
@@ -30,11 +30,18 @@ namespace tc {
 
 constexpr int BM = 128;          // rows of D per CTA (TMEM lanes)
 constexpr int BK = 64;           // K elements per stage (128 bytes of 16-bit)
-constexpr int STAGES = 5;
+// ring depth: as many stages as fit the CTA's share of shared memory (two
+// CTAs per SM, or one CTA per SM with a ring twice as deep); a stage is
+// released only when its MMAs have completed, so the bytes in flight per SM,
+// not the MMA rate, set the streaming rate
+template <int BN> constexpr int stages_for(int ctas_per_sm)
+{
+    return (ctas_per_sm == 1 ? 224 * 1024 : 110 * 1024) / (BM * BK * 2 + BN * BK * 2);
+}
 constexpr int THREADS = 192;     // warp 0 TMA, warp 1 MMA, warps 2-5 epilogue
 constexpr int A_BYTES = BM * BK * 2;
 constexpr uint32_t kWaitLimit = 1u << 22;
-constexpr int kMaxSplit = 16;
+constexpr int kMaxCtasPerSm = 2;
 
 __device__ __forceinline__ uint32_t smem_u32(const void *p)
 {
@@ -157,42 +164,70 @@ struct Epi {
     void *X16next;              // next operand (mode 1), [BN][ldx]
     int ldx;
     int is_bf16;
-    int lan_col;                // mode 1: column carrying an extra vector (-1: none)
-    double *lan_w;              // its product, FP64
+    int lan_col;                // mode 1: column carrying the Lanczos vector (-1: none)
+    double *lan_w;              // its product w = D q_j, FP64
+    const double *lan_q, *lan_qp;  // q_j and q_{j-1}
+    double *lan_part;           // per row block: q_j.w, q_{j-1}.w, w.w (FP64)
 };
 
 // -- kernel begin: k_tc_gemm
-template <int BN>
-__global__ void __launch_bounds__(THREADS, 2)
+// Stream-K schedule: the product is cut into units (row block mb, K tile kt),
+// u = mb * ktiles + kt, and CTA c of the G resident CTAs owns the contiguous
+// range [c U / G, (c + 1) U / G) of the U units.  A CTA's range crosses row
+// blocks; each run of units inside one row block (a segment) accumulates in
+// one of two TMEM buffers, so the MMA warp starts the next segment while the
+// epilogue warps drain the previous one.  A segment's FP32 partial goes to
+// slot (c - first CTA of mb) of its row block; the CTA that completes a row
+// block (arrival counter) sums the slots in slot order in FP64
+// (deterministic for a given G) and runs the epilogue, then resets the
+// counter for the next launch.  No CTA ever waits on another.
+__device__ __forceinline__ int cta_of_unit(long u, long U, int G)
+{
+    return (int)(((u + 1) * (long)G + U - 1) / U) - 1;
+}
+
+__device__ __forceinline__ void mbar_arrive(uint32_t bar)
+{
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
+}
+
+template <int BN, int ST>
+__global__ void __launch_bounds__(THREADS, (ST > 8 ? 1 : 2))
 k_tc_gemm(const __grid_constant__ CUtensorMap mapD, const __grid_constant__ CUtensorMap mapX,
-          int n3, int ktiles, int nsplit, float *__restrict__ part, int32_t *__restrict__ counters,
-          int32_t *__restrict__ err, Epi e)
+          int n3, int ktiles, int mblk, int maxslots, float *__restrict__ part,
+          int32_t *__restrict__ counters, int32_t *__restrict__ err, Epi e)
 {
     constexpr int B_BYTES = BN * BK * 2;
     constexpr int STAGE = A_BYTES + B_BYTES;          // multiple of 1024
     static_assert(STAGE % 1024 == 0, "stage alignment");
     constexpr uint32_t IDESC_F16 = idesc_f16(BN, 0), IDESC_BF16 = idesc_f16(BN, 1);
+    constexpr uint32_t TMEM_COLS = 2 * BN < 32 ? 32 : 2 * BN;
 
     extern __shared__ __align__(1024) uint8_t smem_raw[];
     uint8_t *smem = (uint8_t *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
-    __shared__ __align__(8) uint64_t full_bar[STAGES], empty_bar[STAGES], accum_bar, drain_bar;
+    __shared__ __align__(8) uint64_t full_bar[ST], empty_bar[ST];
+    __shared__ __align__(8) uint64_t acc_full[2], acc_empty[2], drain_bar;
     __shared__ uint32_t tmem_base_sh;
     __shared__ volatile int abort_flag;
     __shared__ int is_last_sh;
+    __shared__ double lan_red[4][3];
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int mb = blockIdx.x, split = blockIdx.y;
-    const int kt0 = (int)((long)ktiles * split / nsplit);
-    const int kt1 = (int)((long)ktiles * (split + 1) / nsplit);
-    const int nkt = kt1 - kt0;
+    const int G = gridDim.x, c = blockIdx.x;
+    const long U = (long)mblk * ktiles;
+    const long u0 = (long)c * U / G, u1 = (long)(c + 1) * U / G;
+    const int nunits = (int)(u1 - u0);
 
     if (threadIdx.x == 0) {
         abort_flag = 0;
-        for (int s = 0; s < STAGES; s++) {
+        for (int s = 0; s < ST; s++) {
             mbar_init(smem_u32(&full_bar[s]), 1);
             mbar_init(smem_u32(&empty_bar[s]), 1);
         }
-        mbar_init(smem_u32(&accum_bar), 1);
+        for (int b = 0; b < 2; b++) {
+            mbar_init(smem_u32(&acc_full[b]), 1);
+            mbar_init(smem_u32(&acc_empty[b]), 128);
+        }
         mbar_init(smem_u32(&drain_bar), 1);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
@@ -200,7 +235,7 @@ k_tc_gemm(const __grid_constant__ CUtensorMap mapD, const __grid_constant__ CUte
     if (warp == 1) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
                          smem_u32(&tmem_base_sh)),
-                     "r"(32)
+                     "r"(TMEM_COLS)
                      : "memory");
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
     }
@@ -210,35 +245,51 @@ k_tc_gemm(const __grid_constant__ CUtensorMap mapD, const __grid_constant__ CUte
     const uint32_t tmem = tmem_base_sh;
 
     if (warp == 0 && lane == 0) {
-        // ---- TMA producer
+        // ---- TMA producer: every unit of the range, in order
         int issued = 0;
-        for (int i = 0; i < nkt; i++) {
-            int s = i % STAGES;
-            uint32_t ph = (uint32_t)(i / STAGES) & 1u;
+        for (int i = 0; i < nunits; i++) {
+            const long u = u0 + i;
+            const int mb = (int)(u / ktiles), kt = (int)(u % ktiles);
+            int s = i % ST;
+            uint32_t ph = (uint32_t)(i / ST) & 1u;
             if (!mbar_wait(smem_u32(&empty_bar[s]), ph ^ 1u, &abort_flag)) break;
             uint32_t a = smem_u32(smem + s * STAGE), b = a + A_BYTES;
             uint32_t fb = smem_u32(&full_bar[s]);
             mbar_expect_tx(fb, STAGE);
-            int kx = (kt0 + i) * BK;
-            tma_load_2d(a, &mapD, kx, mb * BM, fb);
-            tma_load_2d(b, &mapX, kx, 0, fb);
+            tma_load_2d(a, &mapD, kt * BK, mb * BM, fb);
+            tma_load_2d(b, &mapX, kt * BK, 0, fb);
             issued = i + 1;
         }
         if (abort_flag) {
             // let every load issued land before the CTA can exit
-            for (int i = (issued > STAGES ? issued - STAGES : 0); i < issued; i++) {
-                int s = i % STAGES;
-                uint32_t ph = (uint32_t)(i / STAGES) & 1u;
+            for (int i = (issued > ST ? issued - ST : 0); i < issued; i++) {
+                int s = i % ST;
+                uint32_t ph = (uint32_t)(i / ST) & 1u;
                 for (uint32_t t = 0; t < kWaitLimit && !mbar_try(smem_u32(&full_bar[s]), ph); t++) {}
             }
         }
     } else if (warp == 1 && lane == 0) {
-        // ---- MMA issuer
+        // ---- MMA issuer: segment j accumulates in TMEM buffer j & 1
         const uint32_t idesc = e.is_bf16 ? IDESC_BF16 : IDESC_F16;
         bool ok = true;
-        for (int i = 0; i < nkt && ok; i++) {
-            int s = i % STAGES;
-            uint32_t ph = (uint32_t)(i / STAGES) & 1u;
+        int j = -1, cur_mb = -1;
+        for (int i = 0; i < nunits && ok; i++) {
+            const long u = u0 + i;
+            const int mb = (int)(u / ktiles);
+            const bool first = (mb != cur_mb);
+            if (first) {
+                cur_mb = mb;
+                j++;
+                if (j >= 2 &&
+                    !mbar_wait(smem_u32(&acc_empty[j & 1]), (uint32_t)((j >> 1) - 1) & 1u, &abort_flag)) {
+                    ok = false;
+                    break;
+                }
+                asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            }
+            const uint32_t acc = tmem + (uint32_t)((j & 1) * BN);
+            int s = i % ST;
+            uint32_t ph = (uint32_t)(i / ST) & 1u;
             if (!mbar_wait(smem_u32(&full_bar[s]), ph, &abort_flag)) { ok = false; break; }
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
             uint32_t a = smem_u32(smem + s * STAGE), b = a + A_BYTES;
@@ -246,81 +297,110 @@ k_tc_gemm(const __grid_constant__ CUtensorMap mapD, const __grid_constant__ CUte
 #pragma unroll
             for (int k = 0; k < BK / 16; k++) {
                 // advance 16 elements (32 bytes) along K inside the swizzled rows
-                mma_f16(tmem, da + (uint64_t)(2 * k), db + (uint64_t)(2 * k), idesc,
-                        (i > 0 || k > 0) ? 1u : 0u);
+                mma_f16(acc, da + (uint64_t)(2 * k), db + (uint64_t)(2 * k), idesc,
+                        (!first || k > 0) ? 1u : 0u);
             }
             mma_commit(smem_u32(&empty_bar[s]));
+            const bool last = (i + 1 == nunits) || ((u + 1) / ktiles != mb);
+            if (last) mma_commit(smem_u32(&acc_full[j & 1]));
         }
-        mma_commit(smem_u32(&accum_bar));
         if (!ok) {
             mma_commit(smem_u32(&drain_bar));
             for (uint32_t t = 0; t < kWaitLimit && !mbar_try(smem_u32(&drain_bar), 0); t++) {}
         }
     } else if (warp >= 2) {
-        // ---- epilogue: TMEM -> FP32 partial
+        // ---- epilogue warps: each segment in order
         const int q = warp & 3;                      // TMEM lane quadrant of this warp
         const int r = q * 32 + lane;                 // row within the block
-        const long row = (long)mb * BM + r;
-        float acc[BN];
-        bool ok = (nkt == 0) || mbar_wait(smem_u32(&accum_bar), 0, &abort_flag);
-        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-        if (ok && nkt > 0) {
+        long u = u0;
+        for (int j = 0; u < u1; j++) {
+            const int mb = (int)(u / ktiles);
+            const long ue = ((long)(mb + 1) * ktiles < u1) ? (long)(mb + 1) * ktiles : u1;
+            u = ue;
+            float acc[BN];
+            if (!mbar_wait(smem_u32(&acc_full[j & 1]), (uint32_t)(j >> 1) & 1u, &abort_flag)) break;
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
 #pragma unroll
-            for (int c = 0; c < BN; c += 16) tmem_ld16(tmem + ((uint32_t)(q * 32) << 16) + c, acc + c);
-        } else {
+            for (int cc = 0; cc < BN; cc += 16)
+                tmem_ld16(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)((j & 1) * BN + cc), acc + cc);
+            asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+            mbar_arrive(smem_u32(&acc_empty[j & 1]));
+            const int c0 = cta_of_unit((long)mb * ktiles, U, G);
+            const int c1 = cta_of_unit((long)mb * ktiles + ktiles - 1, U, G);
+            const int nslots = c1 - c0 + 1;
+            float4 *dst = (float4 *)(part + (((size_t)mb * maxslots + (c - c0)) * BM + r) * BN);
 #pragma unroll
-            for (int c = 0; c < BN; c++) acc[c] = 0.f;
-        }
-        float4 *dst = (float4 *)(part + ((size_t)split * gridDim.x * BM + (size_t)mb * BM + r) * BN);
-#pragma unroll
-        for (int c = 0; c < BN / 4; c++)
-            dst[c] = make_float4(acc[4 * c], acc[4 * c + 1], acc[4 * c + 2], acc[4 * c + 3]);
-        __threadfence();
-        asm volatile("bar.sync 1, 128;" ::: "memory");
-        if (threadIdx.x == 64) {
-            int old = atomicAdd(&counters[mb], 1);
-            is_last_sh = (old == nsplit - 1);
-        }
-        asm volatile("bar.sync 1, 128;" ::: "memory");
-        if (is_last_sh) {
+            for (int cc = 0; cc < BN / 4; cc++)
+                dst[cc] = make_float4(acc[4 * cc], acc[4 * cc + 1], acc[4 * cc + 2], acc[4 * cc + 3]);
             __threadfence();
+            asm volatile("bar.sync 1, 128;" ::: "memory");
+            if (threadIdx.x == 64) {
+                int old = atomicAdd(&counters[mb], 1);
+                is_last_sh = (old == nslots - 1);
+                if (old == nslots - 1) counters[mb] = 0;   // every slot is in: ready for the next launch
+            }
+            asm volatile("bar.sync 1, 128;" ::: "memory");
+            if (!is_last_sh) continue;
+            __threadfence();
+            const long row = (long)mb * BM + r;
             double y[BN];
 #pragma unroll
-            for (int c = 0; c < BN; c++) y[c] = 0.0;
-            for (int sp = 0; sp < nsplit; sp++) {
+            for (int cc = 0; cc < BN; cc++) y[cc] = 0.0;
+            for (int sp = 0; sp < nslots; sp++) {
                 const float4 *src =
-                    (const float4 *)(part + ((size_t)sp * gridDim.x * BM + (size_t)mb * BM + r) * BN);
+                    (const float4 *)(part + (((size_t)mb * maxslots + sp) * BM + r) * BN);
 #pragma unroll
-                for (int c = 0; c < BN / 4; c++) {
-                    float4 v = __ldcg(src + c);
-                    y[4 * c] += v.x; y[4 * c + 1] += v.y; y[4 * c + 2] += v.z; y[4 * c + 3] += v.w;
+                for (int cc = 0; cc < BN / 4; cc++) {
+                    float4 v = __ldcg(src + cc);
+                    y[4 * cc] += v.x; y[4 * cc + 1] += v.y; y[4 * cc + 2] += v.z; y[4 * cc + 3] += v.w;
                 }
             }
+            double lw = 0.0;                          // this row of D q_j (Lanczos column)
             if (row < n3) {
                 if (e.mode == 0) {
 #pragma unroll
-                    for (int c = 0; c < BN; c++)
-                        if (c < e.m) e.Y[(long)c * n3 + row] = y[c] * (double)e.inv_scale[c];
+                    for (int cc = 0; cc < BN; cc++)
+                        if (cc < e.m) e.Y[(long)cc * n3 + row] = y[cc] * (double)e.inv_scale[cc];
                 } else {
                     const double dmin = e.bounds[0], dmax = e.bounds[1];
                     const double ys = 2.0 / (dmax - dmin), yt = (dmax + dmin) / (dmax - dmin);
                     const double cp = e.coef[e.p];
 #pragma unroll
-                    for (int c = 0; c < BN; c++) {
-                        if (c == e.lan_col) e.lan_w[row] = y[c] * (double)e.inv_scale[c];
-                        if (c < e.m) {
-                            long o = (long)c * n3 + row;
-                            double w = y[c] * (double)e.inv_scale[c];
+                    for (int cc = 0; cc < BN; cc++) {
+                        if (cc == e.lan_col) {
+                            lw = y[cc] * (double)e.inv_scale[cc];
+                            e.lan_w[row] = lw;
+                        }
+                        if (cc < e.m) {
+                            long o = (long)cc * n3 + row;
+                            double w = y[cc] * (double)e.inv_scale[cc];
                             double v = 2.0 * (ys * w - yt * e.Vprev1[o]) - e.Vprev2[o];
                             e.Vprev2[o] = v;
                             e.dS[o] += cp * v;
-                            float sv = (float)(v * (double)e.scale[c]);
-                            size_t xo = (size_t)c * e.ldx + row;
+                            float sv = (float)(v * (double)e.scale[cc]);
+                            size_t xo = (size_t)cc * e.ldx + row;
                             if (e.is_bf16) ((__nv_bfloat16 *)e.X16next)[xo] = __float2bfloat16_rn(sv);
                             else ((__half *)e.X16next)[xo] = __float2half_rn(sv);
                         }
                     }
                 }
+            }
+            if (e.mode == 1 && e.lan_col >= 0) {
+                // this row block's share of q_j.w, q_{j-1}.w and w.w, reduced in
+                // a fixed order (deterministic)
+                double t[3] = {row < n3 ? e.lan_q[row] * lw : 0.0,
+                               row < n3 ? e.lan_qp[row] * lw : 0.0, lw * lw};
+#pragma unroll
+                for (int k = 0; k < 3; k++)
+#pragma unroll
+                    for (int o = 16; o > 0; o >>= 1) t[k] += __shfl_xor_sync(0xffffffffu, t[k], o);
+                if (lane == 0)
+                    for (int k = 0; k < 3; k++) lan_red[q][k] = t[k];
+                asm volatile("bar.sync 1, 128;" ::: "memory");
+                if (r == 0)
+                    for (int k = 0; k < 3; k++)
+                        e.lan_part[3 * mb + k] =
+                            ((lan_red[0][k] + lan_red[1][k]) + lan_red[2][k]) + lan_red[3][k];
             }
         }
     }
@@ -330,17 +410,17 @@ k_tc_gemm(const __grid_constant__ CUtensorMap mapD, const __grid_constant__ CUte
     __syncthreads();
     if (warp == 1) {
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(32)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TMEM_COLS)
                      : "memory");
     }
 }
 
 // -- kernel end: k_tc_gemm
 
-template <int BN>
+template <int BN, int ST>
 constexpr int smem_bytes()
 {
-    return STAGES * (A_BYTES + BN * BK * 2) + 1024;
+    return ST * (A_BYTES + BN * BK * 2) + 1024;
 }
 
 }  // namespace tc
@@ -425,52 +505,86 @@ static bd_status make_map(CUtensorMap *map, const void *base, int is_bf16, uint6
     return BD_OK;
 }
 
+// ring depths of the four launch shapes (BN x resident CTAs per SM)
+constexpr int S16_2 = tc::stages_for<16>(2), S32_2 = tc::stages_for<32>(2);
+constexpr int S16_1 = tc::stages_for<16>(1), S32_1 = tc::stages_for<32>(1);
+static_assert(S16_2 >= 4 && S32_2 >= 4, "ring too shallow");
+static_assert(tc::smem_bytes<16, S16_1>() <= 227 * 1024 && tc::smem_bytes<32, S32_1>() <= 227 * 1024,
+              "one-CTA ring exceeds shared memory");
+static_assert(2 * (tc::smem_bytes<16, S16_2>() + 2048) <= 228 * 1024 &&
+              2 * (tc::smem_bytes<32, S32_2>() + 2048) <= 228 * 1024,
+              "two CTAs per SM do not fit");
+
 static int mblocks(const Plan &P) { return (P.n3 + tc::BM - 1) / tc::BM; }
+static int ktiles_of(const Plan &P) { return (P.n3 + tc::BK - 1) / tc::BK; }
+
+// resident CTAs of the stream-K product: ctas_per_sm per SM, at most one per unit
+static int sk_grid(const Plan &P, int ctas_per_sm)
+{
+    long U = (long)mblocks(P) * ktiles_of(P);
+    long g = (long)ctas_per_sm * P.num_sms;
+    return (int)(g < U ? g : U);
+}
+
+// most CTAs sharing one row block for grid G (partial slots per row block)
+static int sk_maxslots(const Plan &P, int G)
+{
+    const long KT = ktiles_of(P), MB = mblocks(P), U = MB * KT;
+    auto cta_of = [&](long u) { return (int)(((u + 1) * G + U - 1) / U) - 1; };
+    int mx = 1;
+    for (long mb = 0; mb < MB; mb++) {
+        int ns = cta_of(mb * KT + KT - 1) - cta_of(mb * KT) + 1;
+        if (ns > mx) mx = ns;
+    }
+    return mx;
+}
 
 bd_status tc_plan_init(Plan &P)
 {
     bd_status st = get_encoder();
     if (st != BD_OK) return st;
+    if (cudaDeviceGetAttribute(&P.num_sms, cudaDevAttrMultiProcessorCount, P.device) != cudaSuccess ||
+        P.num_sms < 1)
+        return set_error(BD_ERR_CUDA, "SM count unavailable");
     P.ldx = (P.n3 + kLdAlign - 1) / kLdAlign * kLdAlign;
     size_t x16 = (size_t)2 * kMaxRhs * P.ldx * 2;               // two operand buffers
     size_t mbk = (size_t)mblocks(P);
+    P.tc_maxslots = 1;
+    for (int cps = 1; cps <= tc::kMaxCtasPerSm; cps++) {
+        int ms = sk_maxslots(P, sk_grid(P, cps));
+        if (ms > P.tc_maxslots) P.tc_maxslots = ms;
+    }
+    const size_t part = (size_t)P.tc_maxslots * mbk * tc::BM * kMaxRhs * sizeof(float);
     cudaError_t e = cudaMalloc(&P.d_x16, x16);
     if (e == cudaSuccess) e = cudaMalloc(&P.d_xscale, 4 * kMaxRhs * sizeof(float));
-    if (e == cudaSuccess)
-        e = cudaMalloc(&P.d_part, (size_t)tc::kMaxSplit * mbk * tc::BM * kMaxRhs * sizeof(float));
+    if (e == cudaSuccess) e = cudaMalloc(&P.d_part, part);
     if (e == cudaSuccess) e = cudaMalloc(&P.d_counters, (mbk + 64) * sizeof(int32_t));
+    if (e == cudaSuccess) e = cudaMalloc(&P.d_lanpart, 3 * mbk * sizeof(double));
     if (e != cudaSuccess) {
         cudaGetLastError();
         return set_error(BD_ERR_OOM, "mixed-precision scratch: %s", cudaGetErrorString(e));
     }
-    P.scratch_bytes += (int64_t)(x16 + 4 * kMaxRhs * sizeof(float) +
-                                 (size_t)tc::kMaxSplit * mbk * tc::BM * kMaxRhs * sizeof(float) +
-                                 (mbk + 64) * sizeof(int32_t));
+    P.scratch_bytes += (int64_t)(x16 + 4 * kMaxRhs * sizeof(float) + part +
+                                 (mbk + 64) * sizeof(int32_t) + 3 * mbk * sizeof(double));
     cudaMemset(P.d_x16, 0, x16);
-    for (int bn : {16, 32}) {
-        int sm = bn == 16 ? tc::smem_bytes<16>() : tc::smem_bytes<32>();
-        cudaError_t a = bn == 16
-            ? cudaFuncSetAttribute(tc::k_tc_gemm<16>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm)
-            : cudaFuncSetAttribute(tc::k_tc_gemm<32>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
-        if (a != cudaSuccess) return set_error(BD_ERR_CUDA, "smem attribute: %s", cudaGetErrorString(a));
-    }
+    cudaMemset(P.d_counters, 0, (mbk + 64) * sizeof(int32_t));
+    cudaError_t a[4] = {
+        cudaFuncSetAttribute(tc::k_tc_gemm<16, S16_2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             tc::smem_bytes<16, S16_2>()),
+        cudaFuncSetAttribute(tc::k_tc_gemm<32, S32_2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             tc::smem_bytes<32, S32_2>()),
+        cudaFuncSetAttribute(tc::k_tc_gemm<16, S16_1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             tc::smem_bytes<16, S16_1>()),
+        cudaFuncSetAttribute(tc::k_tc_gemm<32, S32_1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             tc::smem_bytes<32, S32_1>())};
+    for (cudaError_t x : a)
+        if (x != cudaSuccess) return set_error(BD_ERR_CUDA, "smem attribute: %s", cudaGetErrorString(x));
     return BD_OK;
 }
 
 static void *x16_buf(Plan &P, int which)
 {
     return (char *)P.d_x16 + (size_t)which * kMaxRhs * P.ldx * 2;
-}
-
-static int n_split(const Plan &P, int ktiles)
-{
-    // enough CTAs for ~5 waves of two CTAs per SM on 152 SMs, unless the
-    // autotuner measured a better split for this plan
-    int mbk = mblocks(P);
-    int s = P.tc_split > 0 ? P.tc_split : (5 * 2 * 152 + mbk - 1) / mbk;
-    if (s > tc::kMaxSplit) s = tc::kMaxSplit;
-    if (s > ktiles) s = ktiles;
-    return s < 1 ? 1 : s;
 }
 
 // column scales of X (rows 0..m-1 of the (m, 3N) block) and the 16-bit copy
@@ -487,36 +601,6 @@ static void prepare_operand(Plan &P, const double *X, int m, int bn, void *X16, 
     count_launches(1);
 }
 
-// one extra column: scale from its own max and the 16-bit copy in row `col`
-__global__ void k_scale_one(const unsigned long long *bits, float *scale, float *inv_scale)
-{
-    float sc = 1.f;
-    double mx = __longlong_as_double((long long)*bits);
-    if (mx > 0.0 && isfinite(mx)) {
-        int e;
-        frexp(mx, &e);
-        sc = ldexpf(1.f, -e);
-    }
-    *scale = sc;
-    *inv_scale = 1.f / sc;
-}
-
-static void prepare_column(Plan &P, const double *x, int col, void *X16, cudaStream_t s)
-{
-    unsigned long long *bits = (unsigned long long *)(P.d_xscale + 2 * kMaxRhs) + col;
-    cudaMemsetAsync(bits, 0, sizeof(unsigned long long), s);
-    k_col_absmax<<<dim3(64, 1), 256, 0, s>>>(x, P.n3, 1, bits);
-    count_launches(1);
-    k_scale_one<<<1, 1, 0, s>>>(bits, P.d_xscale + col, P.d_xscale + kMaxRhs + col);
-    count_launches(1);
-    // k_to16 converts column 0 of x into row 0 of the buffer it is given: offset
-    // the destination to row `col` and the scale to entry `col`
-    k_to16<<<dim3((P.n3 + 255) / 256, 1), 256, 0, s>>>(
-        x, P.n3, 1, 1, P.d_xscale + col, (char *)X16 + (size_t)col * P.ldx * 2, P.ldx,
-        P.p.precision == BD_MIXED_BF16);
-    count_launches(1);
-}
-
 static bd_status launch_tc(Plan &P, const void *D16, const void *X16, int bn, const tc::Epi &e,
                            cudaStream_t s)
 {
@@ -526,18 +610,25 @@ static bd_status launch_tc(Plan &P, const void *D16, const void *X16, int bn, co
     if (st != BD_OK) return st;
     st = make_map(&mapX, X16, is_bf16, P.n3, bn, (uint64_t)P.ldx * 2, tc::BK, bn);
     if (st != BD_OK) return st;
-    int ktiles = (P.n3 + tc::BK - 1) / tc::BK;
-    int ns = n_split(P, ktiles);
-    dim3 grid(mblocks(P), ns);
-    cudaMemsetAsync(P.d_counters, 0, sizeof(int32_t) * mblocks(P), s);
+    const int ktiles = ktiles_of(P), mbk = mblocks(P);
+    const int G = sk_grid(P, P.tc_split > 0 ? P.tc_split : tc::kMaxCtasPerSm);
+    // the arrival counters reset themselves; a plain product (the first of
+    // every step) also clears them in case an earlier launch gave up
+    if (e.mode == 0) cudaMemsetAsync(P.d_counters, 0, sizeof(int32_t) * mbk, s);
     int32_t *err = P.d_status + 6;
     if (e.mode == 1) prod_mark(P, 0, s);
-    if (bn == 16)
-        tc::k_tc_gemm<16><<<grid, tc::THREADS, tc::smem_bytes<16>(), s>>>(
-            mapD, mapX, P.n3, ktiles, ns, P.d_part, P.d_counters, err, e);
-    else
-        tc::k_tc_gemm<32><<<grid, tc::THREADS, tc::smem_bytes<32>(), s>>>(
-            mapD, mapX, P.n3, ktiles, ns, P.d_part, P.d_counters, err, e);
+    const bool two = (P.tc_split > 0 ? P.tc_split : tc::kMaxCtasPerSm) == 2;
+#define TC_LAUNCH(BNV, STV)                                                                   \
+    tc::k_tc_gemm<BNV, STV><<<G, tc::THREADS, tc::smem_bytes<BNV, STV>(), s>>>(              \
+        mapD, mapX, P.n3, ktiles, mbk, P.tc_maxslots, P.d_part, P.d_counters, err, e)
+    if (bn == 16) {
+        if (two) TC_LAUNCH(16, S16_2);
+        else TC_LAUNCH(16, S16_1);
+    } else {
+        if (two) TC_LAUNCH(32, S32_2);
+        else TC_LAUNCH(32, S32_1);
+    }
+#undef TC_LAUNCH
     count_launches(1);
     if (e.mode == 1) prod_mark(P, 1, s);
     return check_launch("tc_gemm");
@@ -558,24 +649,23 @@ bd_status tc_apply(Plan &P, const void *D16, const double *X, int m, double *Y, 
     return launch_tc(P, D16, X16, bn, e, s);
 }
 
-// Autotuner of the product's tile decomposition: time Y = D16 X (m = the
-// plan's max_rhs, up to 16 columns) for K-split counts 1, 2, 4, 8, 16 on this
-// plan's own matrix and keep the fastest.  Synchronous.
+// Autotuner of the product's launch shape: time Y = D16 X with the column
+// count of a lagged Chebyshev product (max_rhs + 1, the Lanczos vector riding
+// along) with 2 resident CTAs per SM (shallower ring) and 1 (ring twice as
+// deep) on this plan's own matrix and keep the faster.  Synchronous.
 bd_status tc_autotune(Plan &P, const void *D16, cudaStream_t s, int *best_out, float *ms_out)
 {
-    const int m = P.p.max_rhs < 16 ? P.p.max_rhs : 16;
-    double *X = P.d_V[0], *Y = P.d_V[1];
+    const int m = P.p.max_rhs + 1 < kMaxRhs ? P.p.max_rhs + 1 : kMaxRhs;
+    double *X = P.d_X0, *Y = P.d_Y0;
     cudaMemsetAsync(X, 0, sizeof(double) * (size_t)P.n3 * m, s);
-    const int ktiles = (P.n3 + tc::BK - 1) / tc::BK;
     cudaEvent_t e0, e1;
     cudaEventCreate(&e0);
     cudaEventCreate(&e1);
     int best = 0;
     float best_ms = 1e30f;
     const int saved = P.tc_split;
-    for (int sp : {1, 2, 4, 8, 16}) {
-        if (sp > ktiles) break;
-        P.tc_split = sp;
+    for (int cps = 1; cps <= tc::kMaxCtasPerSm; cps++) {
+        P.tc_split = cps;
         bd_status st = tc_apply(P, D16, X, m, Y, s);      // warm-up
         if (st != BD_OK) { P.tc_split = saved; cudaEventDestroy(e0); cudaEventDestroy(e1); return st; }
         cudaEventRecord(e0, s);
@@ -584,7 +674,7 @@ bd_status tc_autotune(Plan &P, const void *D16, cudaStream_t s, int *best_out, f
         cudaEventSynchronize(e1);
         float ms = 0.f;
         cudaEventElapsedTime(&ms, e0, e1);
-        if (ms < best_ms) { best_ms = ms; best = sp; }
+        if (ms < best_ms) { best_ms = ms; best = cps; }
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
@@ -594,19 +684,86 @@ bd_status tc_autotune(Plan &P, const void *D16, cudaStream_t s, int *best_out, f
     return check_launch("tc_autotune");
 }
 
-bd_status tc_cheb(Plan &P, const void *D16, int m, const double *coef, const double *bounds, int p,
-                  double *Vprev2, const double *Vprev1, double *dS, cudaStream_t s,
-                  const double *lan_q, double *lan_w)
+// Lanczos vector as an extra operand column: fixed scale 64 (|q_i| <= 1 for a
+// unit vector, so the 16-bit copy cannot overflow)
+constexpr float kLanScale = 64.f;
+
+__global__ void k_lan_column(const double *q, int n3, float *scale, float *inv_scale, void *X16col,
+                             int is_bf16)
 {
-    const int cols = m + (lan_q ? 1 : 0);
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i == 0) {
+        *scale = kLanScale;
+        *inv_scale = 1.f / kLanScale;
+    }
+    if (i >= n3) return;
+    float v = (float)(q[i] * (double)kLanScale);
+    if (is_bf16) ((__nv_bfloat16 *)X16col)[i] = __float2bfloat16_rn(v);
+    else ((__half *)X16col)[i] = __float2half_rn(v);
+}
+
+// One Lanczos step after a product that carried q_j: from the row-block
+// partials of q_j.w, q_{j-1}.w and w.w (every block sums them in the same
+// order, so all blocks agree bit for bit)
+//   alpha_j = q_j.w,  |w'|^2 = w.w - alpha_j^2 - 2 beta_{j-1} (q_{j-1}.w) + beta_{j-1}^2,
+//   w' = w - alpha_j q_j - beta_{j-1} q_{j-1},  beta_j = |w'|,  q_{j+1} = w' / beta_j
+// (the expansion takes q_j, q_{j-1} orthonormal), then q_{j-1} <- q_j,
+// q_j <- q_{j+1} and the 16-bit copy of q_{j+1} into the next operand.
+__global__ void k_lanczos_step(double *qprev, double *q, const double *w, int n3,
+                               const double *part, int nparts, double *lab, int j, void *X16col,
+                               int is_bf16)
+{
+    __shared__ double sh[3];
+    if (threadIdx.x < 32) {
+        double t[3] = {0.0, 0.0, 0.0};
+        for (int i = threadIdx.x; i < nparts; i += 32)
+            for (int k = 0; k < 3; k++) t[k] += part[3 * i + k];
+#pragma unroll
+        for (int k = 0; k < 3; k++)
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) t[k] += __shfl_xor_sync(0xffffffffu, t[k], o);
+        if (threadIdx.x == 0)
+            for (int k = 0; k < 3; k++) sh[k] = t[k];
+    }
+    __syncthreads();
+    const double alpha = sh[0];
+    const double bprev = j > 0 ? lab[kMaxLanczos + j - 1] : 0.0;
+    const double n2 = sh[2] - alpha * alpha - 2.0 * bprev * sh[1] + bprev * bprev;
+    const double beta = n2 > 0.0 ? sqrt(n2) : 0.0;
+    long i = (long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i == 0) {
+        lab[j] = alpha;
+        lab[kMaxLanczos + j] = beta;
+    }
+    if (i >= n3) return;
+    double x = w[i] - alpha * q[i] - bprev * qprev[i];
+    double qn = beta > 0.0 ? x / beta : 0.0;
+    qprev[i] = q[i];
+    q[i] = qn;
+    float v = (float)(qn * (double)kLanScale);
+    if (is_bf16) ((__nv_bfloat16 *)X16col)[i] = __float2bfloat16_rn(v);
+    else ((__half *)X16col)[i] = __float2half_rn(v);
+}
+
+bd_status tc_cheb(Plan &P, const void *D16, int m, const double *coef, const double *bounds, int p,
+                  double *Vprev2, const double *Vprev1, double *dS, cudaStream_t s, int lan_step)
+{
+    const bool lan = lan_step >= 0;
+    const int cols = m + (lan ? 1 : 0);
     const int bn = cols <= 16 ? 16 : 32;
+    const int is_bf16 = P.p.precision == BD_MIXED_BF16;
     // operand of V_{p-1}: buffer (p & 1); the epilogue writes V_p into the other
     void *cur = x16_buf(P, p & 1), *nxt = x16_buf(P, (p + 1) & 1);
     if (p == 2) {
         // scales from V_1's block (kept for the whole recurrence); 16-bit V_1
         prepare_operand(P, Vprev1, m, bn, cur, s);
+        if (lan) {
+            k_lan_column<<<(P.n3 + 255) / 256, 256, 0, s>>>(
+                P.d_lq[1], P.n3, P.d_xscale + m, P.d_xscale + kMaxRhs + m,
+                (char *)cur + (size_t)m * P.ldx * 2, is_bf16);
+            count_launches(1);
+        }
     }
-    if (lan_q) prepare_column(P, lan_q, m, cur, s);
     tc::Epi e{};
     e.mode = 1;
     e.m = m;
@@ -620,10 +777,19 @@ bd_status tc_cheb(Plan &P, const void *D16, int m, const double *coef, const dou
     e.dS = dS;
     e.X16next = nxt;
     e.ldx = P.ldx;
-    e.is_bf16 = P.p.precision == BD_MIXED_BF16;
-    e.lan_col = lan_q ? m : -1;
-    e.lan_w = lan_w;
-    return launch_tc(P, D16, cur, bn, e, s);
+    e.is_bf16 = is_bf16;
+    e.lan_col = lan ? m : -1;
+    e.lan_w = P.d_lq[2];
+    e.lan_q = P.d_lq[1];
+    e.lan_qp = P.d_lq[0];
+    e.lan_part = P.d_lanpart;
+    bd_status st = launch_tc(P, D16, cur, bn, e, s);
+    if (st != BD_OK || !lan) return st;
+    k_lanczos_step<<<(P.n3 + 255) / 256, 256, 0, s>>>(
+        P.d_lq[0], P.d_lq[1], P.d_lq[2], P.n3, P.d_lanpart, mblocks(P), P.d_lab, lan_step,
+        (char *)nxt + (size_t)m * P.ldx * 2, is_bf16);
+    count_launches(1);
+    return check_launch("lanczos step");
 }
 
 // One FP64-residual refinement step y += (D32 x - y) for one column.  The

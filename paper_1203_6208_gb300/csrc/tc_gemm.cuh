@@ -5,19 +5,20 @@
 
 namespace bd {
 
-// allocate the 16-bit operand scratch and split-K workspace of a mixed plan
+// allocate the 16-bit operand scratch and stream-K workspace of a mixed plan
 bd_status tc_plan_init(Plan &P);
 // Y = D16 X (FP32 accumulation, FP64 output)
 bd_status tc_apply(Plan &P, const void *D16, const double *X, int m, double *Y, cudaStream_t s);
-// measure the fastest K-split of the product for this plan (synchronous)
+// measure the faster launch shape (1 or 2 CTAs per SM) of the product (synchronous)
 bd_status tc_autotune(Plan &P, const void *D16, cudaStream_t s, int *best, float *ms);
 // one Chebyshev term: V_p = 2 (s D16 V_{p-1} - t V_{p-1}) - V_{p-2} (in place
 // over V_{p-2}), dS += c_p V_p
-// lan_q (optional): a vector carried as column m of the operand; its product
-// D16 lan_q is written (FP64) to lan_w
+// lan_step >= 0: the Lanczos vector q_j (P.d_lq[1]) rides as column m of the
+// operand; the product's epilogue writes w = D16 q_j and its row-block dot
+// partials, and one kernel then takes Lanczos step j (alpha_j, beta_j, q_{j+1})
 bd_status tc_cheb(Plan &P, const void *D16, int m, const double *coef, const double *bounds, int p,
                   double *Vprev2, const double *Vprev1, double *dS, cudaStream_t s,
-                  const double *lan_q = nullptr, double *lan_w = nullptr);
+                  int lan_step = -1);
 // one step of FP64-residual refinement: Y += (D32 X - Y), with the residual
 // accumulated in FP64 from the FP32 matrix
 void launch_refine_f32(Plan &P, const float *D32, const double *X, int m, double *Y,

@@ -363,60 +363,89 @@ void launch_lanczos_update(Plan &P, int j, cudaStream_t s)
     count_launches(1);
 }
 
-// number of eigenvalues of the k x k tridiagonal (alpha, beta) below x
+// number of eigenvalues of the k x k tridiagonal (alpha, beta) below x: sign
+// changes of the Sturm sequence p_0 = 1, p_i = (alpha_i - x) p_{i-1} -
+// beta_{i-1}^2 p_{i-2} (leading principal minors of T - x I).  No division:
+// the pair (p_{i-1}, p_i) is rescaled by a power of two when it grows or
+// shrinks too far, which changes no sign.  A zero p_i keeps the sign of
+// p_{i-1}.
 __device__ int sturm_count(const double *al, const double *be, int k, double x)
 {
-    int cnt = 0;
-    double q = al[0] - x;
-    if (q < 0) cnt++;
+    double pm = 1.0, p = al[0] - x;
+    bool neg_prev = false;
+    bool neg = p < 0.0 || (p == 0.0 && neg_prev);
+    int cnt = neg ? 1 : 0;
     for (int i = 1; i < k; i++) {
-        double b2 = be[i - 1] * be[i - 1];
-        if (q == 0.0) q = 1e-300;
-        q = al[i] - x - b2 / q;
-        if (q < 0) cnt++;
+        double pn = (al[i] - x) * p - (be[i - 1] * be[i - 1]) * pm;
+        bool nn = pn < 0.0 || (pn == 0.0 && neg);
+        cnt += (nn != neg) ? 1 : 0;
+        neg = nn;
+        pm = p;
+        p = pn;
+        double mx = fmax(fabs(p), fabs(pm));
+        if (mx > 0x1p+500 || (mx < 0x1p-500 && mx > 0.0)) {
+            int e;
+            frexp(mx, &e);
+            p = ldexp(p, -e);
+            pm = ldexp(pm, -e);
+        }
     }
     return cnt;
 }
 
-// Extreme Ritz values of the k x k tridiagonal matrix by warp-parallel
-// multisection on Sturm counts: each round the 32 lanes test 32 points of
-// the current bracket (Gershgorin at the start), which shrinks it 33-fold.
-// Then the widened bounds {d_min, d_max} and a status word.
+// Extreme Ritz values of the k x k tridiagonal matrix by multisection on
+// Sturm counts: 128 threads per end test 128 interior points of the current
+// bracket (Gershgorin at the start), which shrinks it 129-fold per round.
+// Then the widened bounds {d_min, d_max} and a status word.  Launched with
+// 256 threads.
 __global__ void k_lanczos_finish(const double *lab, int k, double smax, double fmin_,
                                  double *bounds, int32_t *status)
 {
-    const int lane = threadIdx.x;
+    __shared__ double br[2][2];
+    __shared__ int first[2];
+    __shared__ int kk;
+    const int g = threadIdx.x >> 7, t = threadIdx.x & 127;
     const double *al = lab, *be = lab + kMaxLanczos;
-    // stop at a breakdown (beta ~ 0: the Krylov space became invariant)
-    double scale = 0.0;
-    for (int i = 0; i < k; i++) scale = fmax(scale, fabs(al[i]));
-    for (int i = 0; i + 1 < k; i++)
-        if (!(fabs(be[i]) > 1e-13 * scale)) { k = i + 1; break; }
-    double lo = 1e300, hi = -1e300;
-    for (int i = 0; i < k; i++) {
-        double rad = (i > 0 ? fabs(be[i - 1]) : 0.0) + (i + 1 < k ? fabs(be[i]) : 0.0);
-        lo = fmin(lo, al[i] - rad);
-        hi = fmax(hi, al[i] + rad);
-    }
-    double th[2];
-    for (int w = 0; w < 2; w++) {
-        const int target = (w == 0) ? 1 : k;        // smallest x with count(x) >= target
-        double a = lo, b = hi;
-        for (int it = 0; it < 16 && b - a > 1e-15 * fmax(fabs(a), fabs(b)); it++) {
-            double x = a + (b - a) * (lane + 1) / 33.0;
-            bool ge = sturm_count(al, be, k, x) >= target;
-            unsigned mask = __ballot_sync(0xffffffffu, ge);
-            // first lane whose point already holds >= target eigenvalues
-            int f = mask ? __ffs(mask) - 1 : 32;
-            double na = f == 0 ? a : a + (b - a) * f / 33.0;
-            double nb = f == 32 ? b : a + (b - a) * (f + 1) / 33.0;
-            a = na;
-            b = nb;
+    if (threadIdx.x == 0) {
+        // stop at a breakdown (beta ~ 0: the Krylov space became invariant)
+        double scale = 0.0;
+        for (int i = 0; i < k; i++) scale = fmax(scale, fabs(al[i]));
+        int kt = k;
+        for (int i = 0; i + 1 < k; i++)
+            if (!(fabs(be[i]) > 1e-13 * scale)) { kt = i + 1; break; }
+        double lo = 1e300, hi = -1e300;
+        for (int i = 0; i < kt; i++) {
+            double rad = (i > 0 ? fabs(be[i - 1]) : 0.0) + (i + 1 < kt ? fabs(be[i]) : 0.0);
+            lo = fmin(lo, al[i] - rad);
+            hi = fmax(hi, al[i] + rad);
         }
-        th[w] = 0.5 * (a + b);
+        kk = kt;
+        br[0][0] = br[1][0] = lo;
+        br[0][1] = br[1][1] = hi;
     }
-    if (lane == 0) {
-        double dmin = fmin_ * th[0], dmax = (1.0 + smax) * th[1];
+    __syncthreads();
+    const int kt = kk;
+    const int target = (g == 0) ? 1 : kt;        // smallest x with count(x) >= target
+    for (int it = 0; it < 10; it++) {
+        const double a = br[g][0], b = br[g][1];
+        const bool done = !(b - a > 1e-15 * fmax(fabs(a), fabs(b)));
+        if (t == 0) first[g] = 128;
+        __syncthreads();
+        if (!done) {
+            double x = a + (b - a) * (t + 1) / 129.0;
+            if (sturm_count(al, be, kt, x) >= target) atomicMin(&first[g], t);
+        }
+        __syncthreads();
+        if (t == 0 && !done) {
+            const int f = first[g];
+            br[g][0] = f == 0 ? a : a + (b - a) * f / 129.0;
+            br[g][1] = f == 128 ? b : a + (b - a) * (f + 1) / 129.0;
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        const double th0 = 0.5 * (br[0][0] + br[0][1]), th1 = 0.5 * (br[1][0] + br[1][1]);
+        double dmin = fmin_ * th0, dmax = (1.0 + smax) * th1;
         bounds[0] = dmin;
         bounds[1] = dmax;
         if (status) *status = (dmin > 0.0 && dmax > dmin) ? BD_OK : BD_ERR_NOT_PD;
@@ -426,7 +455,53 @@ __global__ void k_lanczos_finish(const double *lab, int k, double smax, double f
 void launch_lanczos_finish(Plan &P, int k, double safety_max, double dmin_fraction,
                            double *bounds, int32_t *status, cudaStream_t s)
 {
-    k_lanczos_finish<<<1, 32, 0, s>>>(P.d_lab, k, safety_max, dmin_fraction, bounds, status);
+    k_lanczos_finish<<<1, 256, 0, s>>>(P.d_lab, k, safety_max, dmin_fraction, bounds, status);
+    count_launches(1);
+}
+
+// Fixman's estimates (Sec. IV): U+ (all ones) and U- (alternating +1, -1)
+// as two columns of the first product
+__global__ void k_fixman_fill(double *X, int n3)
+{
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n3) return;
+    X[i] = 1.0;
+    X[n3 + i] = (i & 1) ? -1.0 : 1.0;
+}
+
+// q = {U+.D.U+, U-.D.U-}; lambda^F = q / 3N (Eq. lmax-lmin-dilute), then the
+// dilute bounds (2 lambda^F_max, lambda^F_min / 2) or the semidilute ones of
+// Eqs. (fmax), (fmin): lambda_max = 0.35 N^0.6 lambda^F_max,
+// lambda_min = lambda_max / (C N^0.6)
+__global__ void k_fixman_bounds(const double *q, int n3, int nbeads, int mode, double C,
+                                double *bounds, int32_t *status)
+{
+    const double lmaxF = q[0] / n3, lminF = q[1] / n3;
+    double dmin, dmax;
+    if (mode == BD_BOUNDS_FIXMAN_DILUTE) {
+        dmax = 2.0 * lmaxF;
+        dmin = 0.5 * lminF;
+    } else {
+        const double n06 = pow((double)nbeads, 0.6);
+        dmax = 0.35 * n06 * lmaxF;
+        dmin = dmax / (C * n06);
+    }
+    bounds[0] = dmin;
+    bounds[1] = dmax;
+    if (status) *status = (dmin > 0.0 && dmax > dmin) ? BD_OK : BD_ERR_NOT_PD;
+}
+
+void launch_fixman_fill(double *X, int n3, cudaStream_t s)
+{
+    k_fixman_fill<<<(n3 + 255) / 256, 256, 0, s>>>(X, n3);
+    count_launches(1);
+}
+
+void launch_fixman_bounds(Plan &P, const double *X2, const double *Y2, int mode, double C,
+                          double *bounds, int32_t *status, cudaStream_t s)
+{
+    launch_dot_cols(X2, Y2, P.n3, 2, P.d_red + 2 * kMaxRhs, P.d_redpart, s);
+    k_fixman_bounds<<<1, 1, 0, s>>>(P.d_red + 2 * kMaxRhs, P.n3, P.n, mode, C, bounds, status);
     count_launches(1);
 }
 

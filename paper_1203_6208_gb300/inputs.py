@@ -142,3 +142,26 @@ def batch_systems(count: int = 64, seed: int = 1003, n_min: int = 200, n_max: in
         c = float(rng.uniform(1.0, 4.0))
         out.append(SystemConfig(n_chains=nc, nb=nb, c_over_cstar=c, seed=seed * 1000 + i))
     return out
+
+
+# theta-solution validation (Sec. VI): Hookean chains, a = 0.5, dt = 0.01,
+# N_c = 20, concentrations from 3e-4 c* to 3 c* (box size varied)
+THETA_CONCENTRATIONS = (3e-4, 3e-3, 3e-2, 0.3, 3.0)
+
+
+def theta_systems(nb: int = 20, n_chains: int = 20, concentrations=THETA_CONCENTRATIONS,
+                  replicas: int = 8, seed: int = 2000, alpha_factor: float = 1.5):
+    """Replica systems of the theta validation workload: for each c/c*,
+    `replicas` independent boxes of n_chains Hookean chains of nb beads
+    (EV off, overlap-corrected RPY, a = 0.5), seeded seed * 1000 + index.
+    The chains start from the exact theta equilibrium (Gaussian bonds of
+    unit variance per component)."""
+    out = []
+    i = 0
+    for c in concentrations:
+        for _ in range(replicas):
+            out.append(SystemConfig(n_chains=n_chains, nb=nb, c_over_cstar=float(c),
+                                    hstar=0.5 / SQRT_PI, dt=0.01, ev_on=0, spring=0,
+                                    alpha_factor=alpha_factor, seed=seed * 1000 + i))
+            i += 1
+    return out

@@ -1,0 +1,65 @@
+"""Theta-solution statics (Sec. VI, Eqs. Re2 and Rg2) from trajectories of
+the batched GPU step: Hookean chains of N_b = 20 beads, N_c = 20 chains per
+box, a = 0.5, dt = 0.01, three concentrations from 3e-3 c* to 3 c*.
+
+The chains start from the exact theta equilibrium, so a correct step keeps
+<Q^2> = 3 per bond, <R_e^2> = 3 (N_b - 1) and <R_g^2> = (N_b^2 - 1)/(2 N_b)
+at every concentration (chains cross freely in a theta solvent).  The bond
+statistic relaxes within a few time units, so a wrong noise amplitude or
+drift factor shows in it after the 1500 steps here; the Euler bias at
+dt = 0.01 is below 1 %.  Bars: <Q^2> within 3 %, <R_e^2> and <R_g^2>
+within 10 % (standard errors from replica-to-replica scatter are ~2-4 %).
+"""
+import numpy as np
+import pytest
+
+from paper_1203_6208_gb300 import inputs
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+def chain_stats(R, b, cfgs):
+    """Per replica: mean bond Q^2, R_e^2 and R_g^2 over its chains."""
+    out = []
+    for i, c in enumerate(cfgs):
+        r = R[b.r_off[i]:b.r_off[i] + b.n3[i]].view(c.n_chains, c.nb, 3)
+        q2 = ((r[:, 1:] - r[:, :-1]) ** 2).sum(-1).mean()
+        re2 = ((r[:, -1] - r[:, 0]) ** 2).sum(-1).mean()
+        rg2 = ((r - r.mean(1, keepdim=True)) ** 2).sum(-1).mean()
+        out.append(torch.stack([q2, re2, rg2]))
+    return torch.stack(out)
+
+
+def test_theta_statics_batched():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1203_6208_gb300 import binding as bnd, build
+    build.build()
+    bnd.load()
+    nb = 20
+    cfgs = inputs.theta_systems(nb=nb, concentrations=(3e-3, 0.3, 3.0), replicas=12)
+    b = bnd.Batch([c.params() for c in cfgs], "mixed_f16", max_rhs=1, max_cheb=20)
+    R = torch.tensor(np.concatenate([inputs.make_chains(c).reshape(-1) for c in cfgs]),
+                     device="cuda")
+    D = b.alloc_D()
+    stats = torch.zeros(b.count * bnd.STATS_BYTES, dtype=torch.uint8, device="cuda")
+    acc = torch.zeros(b.count, 3, dtype=torch.float64, device="cuda")
+    nsamp = 0
+    for k in range(1500):
+        b.step(R, D, m=1, n_cheb=20, seed=31, stats=stats, bounds_mode=1)
+        if k >= 300 and k % 20 == 0:
+            acc += chain_stats(R, b, cfgs)
+            nsamp += 1
+    torch.cuda.synchronize()
+    per_rep = (acc / nsamp).cpu().numpy()
+    st = [bnd.BdStepStats.from_buffer_copy(bytes(stats[i * bnd.STATS_BYTES:(i + 1) * bnd.STATS_BYTES]
+                                                 .cpu().numpy().tobytes())) for i in range(b.count)]
+    assert all(x.status == 0 and x.accepted == 1 for x in st)
+    ref = np.array([3.0, 3.0 * (nb - 1), (nb * nb - 1) / (2.0 * nb)])
+    for ci in range(3):
+        blk = per_rep[12 * ci:12 * (ci + 1)]
+        mean = blk.mean(0)
+        assert abs(mean[0] / ref[0] - 1) < 0.03, (ci, mean)
+        assert abs(mean[1] / ref[1] - 1) < 0.10, (ci, mean)
+        assert abs(mean[2] / ref[2] - 1) < 0.10, (ci, mean)

@@ -356,6 +356,56 @@ def test_cheb_converges_to_eigen_root_and_SS_equals_D():
     assert np.max(np.abs(S - S.T)) < 1e-12
 
 
+def test_fixman_estimates_closed_form():
+    """Eq. (lmax-lmin-dilute) on D = a I + b 1 1^T (n even): U+ is an
+    eigenvector with eigenvalue a + b n, U- sums to zero so U-.D.U- / n = a;
+    then the dilute factors (2, 1/2) and Eqs. (fmax), (fmin)."""
+    n, a, b = 12, 0.7, 0.05
+    D = a * np.eye(n) + b * np.ones((n, n))
+    dmin, dmax, lF, sF = oracle.fixman_bounds(D, 4, "dilute")
+    assert abs(lF - (a + b * n)) < 1e-14 and abs(sF - a) < 1e-14
+    assert abs(dmax - 2 * (a + b * n)) < 1e-14 and abs(dmin - a / 2) < 1e-14
+    nb, C = 4, 8.0
+    dmin, dmax, _, _ = oracle.fixman_bounds(D, nb, "semidilute", C)
+    lmax = 0.35 * nb ** 0.6 * (a + b * n)
+    assert abs(dmax - lmax) < 1e-14 and abs(dmin - lmax / (C * nb ** 0.6)) < 1e-14
+    # D = d I: both estimates are d
+    _, _, lF, sF = oracle.fixman_bounds(2.5 * np.eye(9), 3, "dilute")
+    assert abs(lF - 2.5) < 1e-14 and abs(sF - 2.5) < 1e-14
+
+
+def test_nch_initial_eq_nint():
+    """Eq. (nint): nint(sqrt(ratio)) + 1, halves rounded up."""
+    assert oracle.nch_initial(1.0, 100.0) == 11
+    assert oracle.nch_initial(1.0, 6.25) == 4          # sqrt = 2.5 -> 3
+    assert oracle.nch_initial(2.0, 2.0) == 2
+    assert oracle.nch_initial(1.0, 6700.0) == 83       # the N = 8000 spectrum
+
+
+def test_cheb_adaptive_loop():
+    """Sec. IV's adaptive N_Ch: the result is the first N >= N_0 with
+    E_f < tol; a loose tol stops at N_0; an unreachable one stops at the cap
+    unconverged; a tight tol reproduces the eigen-decomposition root."""
+    cfg = inputs.SystemConfig(n_chains=3, nb=8, c_over_cstar=2.0, seed=12)
+    p = cfg.params()
+    R = inputs.make_chains(cfg)
+    D = oracle.build_D(p, R)
+    lmin, lmax = oracle.exact_eigs(D)
+    dmin, dmax = 0.9 * lmin, 1.1 * lmax
+    dW = inputs.make_wiener(D.shape[0], 3, 1e-3, 13)
+    n0 = oracle.nch_initial(dmin, dmax)
+    _, _, n, ok = oracle.cheb_sqrt_adaptive(D, dmin, dmax, dW, 10.0, 200)
+    assert ok and n == n0
+    _, _, n, ok = oracle.cheb_sqrt_adaptive(D, dmin, dmax, dW, 1e-300, n0 + 3)
+    assert not ok and n == n0 + 3
+    dS, Ef, n, ok = oracle.cheb_sqrt_adaptive(D, dmin, dmax, dW, 1e-6, 200)
+    assert ok and n > n0 and np.max(Ef) < 1e-6
+    _, Ef_prev = oracle.cheb_sqrt(D, dmin, dmax, n - 1, dW)
+    assert np.max(Ef_prev) >= 1e-6
+    ref = (oracle.sqrt_eig(D) @ dW.T).T
+    assert np.max(np.abs(dS - ref)) / np.max(np.abs(ref)) < 1e-5
+
+
 def test_ef_definition():
     """E_f (Sec. IV) from the oracle equals the definition evaluated with
     the Cholesky factor: dW.D.dW = |L^T dW|^2."""
