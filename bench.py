@@ -55,9 +55,11 @@ def parse():
                          "carried in the products; fresh = --lanczos products per step")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=3)
-    ap.add_argument("--workload", default="n8000", choices=["n8000", "batch"],
+    ap.add_argument("--workload", default="n8000", choices=["n8000", "batch", "theta"],
                     help="batch: 64 replicas, N ~ U[200, 2000], mixed, one graph launch "
-                         "per step (replica-steps/s)")
+                         "per step (replica-steps/s); theta: the theta-solution statics "
+                         "validation (N_b = 20 and 40, N_c = 20, a = 0.5, dt = 0.01, five "
+                         "concentrations), reported against Eqs. (Re2), (Rg2)")
     ap.add_argument("--replicas", type=int, default=64)
     ap.add_argument("--chains", type=int, default=400,
                     help="chains of 20 beads (400 = the N=8000 workload; smaller only for "
@@ -506,10 +508,79 @@ def run_batch(args):
     print(json.dumps(line), flush=True)
 
 
+def run_theta(args):
+    """Theta-solution statics: batched trajectories from the exact equilibrium;
+    per N_b and c/c*, <R_e^2> / 3(N_b - 1) and <R_g^2> / ((N_b^2 - 1)/2N_b) with
+    standard errors over independent replicas.  --steps is the trajectory
+    length (default 5 is raised to 4000)."""
+    import torch
+    torch.cuda.set_device(0)
+    import numpy as np
+    from paper_1203_6208_gb300 import binding as bnd, build, inputs
+    build.build()
+    nsteps = args.steps if args.steps > 100 else 4000
+    every = 20
+    burn = nsteps // 5
+    out = {}
+    t_all = 0.0
+    steps_all = 0
+    for nb in (20, 40):
+        cfgs = inputs.theta_systems(nb=nb, replicas=8)
+        b = bnd.Batch([c.params() for c in cfgs], "mixed_f16", max_rhs=1, max_cheb=24)
+        R = torch.tensor(np.concatenate([inputs.make_chains(c).reshape(-1) for c in cfgs]),
+                         device="cuda")
+        D = b.alloc_D()
+        stats = torch.zeros(b.count * bnd.STATS_BYTES, dtype=torch.uint8, device="cuda")
+        acc = torch.zeros(b.count, 2, dtype=torch.float64, device="cuda")
+        ns = 0
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for k in range(nsteps):
+            b.step(R, D, m=1, n_cheb=24, seed=91 + nb, stats=stats, bounds_mode=1)
+            if k >= burn and k % every == 0:
+                rows = []
+                for i, c in enumerate(cfgs):
+                    r = R[b.r_off[i]:b.r_off[i] + b.n3[i]].view(c.n_chains, c.nb, 3)
+                    re2 = ((r[:, -1] - r[:, 0]) ** 2).sum(-1).mean()
+                    rg2 = ((r - r.mean(1, keepdim=True)) ** 2).sum(-1).mean()
+                    rows.append(torch.stack([re2, rg2]))
+                acc += torch.stack(rows)
+                ns += 1
+        torch.cuda.synchronize()
+        t_all += time.perf_counter() - t0
+        steps_all += nsteps * b.count
+        per = (acc / ns).cpu().numpy()
+        ref = np.array([3.0 * (nb - 1), (nb * nb - 1) / (2.0 * nb)])
+        res = {}
+        for ci, c in enumerate(inputs.THETA_CONCENTRATIONS):
+            blk = per[8 * ci:8 * (ci + 1)] / ref
+            res[str(c)] = {"Re2_ratio": float(blk[:, 0].mean()),
+                           "Re2_se": float(blk[:, 0].std(ddof=1) / math.sqrt(len(blk))),
+                           "Rg2_ratio": float(blk[:, 1].mean()),
+                           "Rg2_se": float(blk[:, 1].std(ddof=1) / math.sqrt(len(blk)))}
+        out[f"Nb={nb}"] = res
+        b.close()
+        del D
+        torch.cuda.empty_cache()
+    line = {"metric": "theta-solution statics: <R_e^2>/3(N_b-1), <R_g^2>/((N_b^2-1)/2N_b)",
+            "value": steps_all / t_all, "unit": "replica-steps/s (wall clock, incl. sampling)",
+            "n_gpus": 1, "steps": nsteps, "warmup": 0, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f16+f32+f64", "data": "synthetic",
+            "config": {"workload": "theta", "n_chains": 20, "a": 0.5, "dt": 0.01,
+                       "c_over_cstar": list(inputs.THETA_CONCENTRATIONS), "replicas_per_c": 8,
+                       "n_cheb": 24, "bounds": "lagged", "burn_in_steps": burn,
+                       "sample_every": every},
+            "statics": out}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         run_reference(args)
+        return
+    if args.workload == "theta":
+        run_theta(args)
     elif args.workload == "batch":
         run_batch(args)
     else:

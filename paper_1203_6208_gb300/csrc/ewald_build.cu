@@ -242,20 +242,48 @@ __device__ __forceinline__ void add_m1(T vx, T vy, T vz, T u, const EwaldT<T> &c
 }
 
 // Eq. (M1) for one image from the piecewise-polynomial table (4a^2 <= u <= r_c^2)
+// one table row (mid, 1/half-width, 9 + 9 coefficients) with 16-byte loads
+template <typename T> struct TabRow;
+template <> struct TabRow<float> {
+    float v[kTabStride];
+    __device__ __forceinline__ TabRow(const float *row)
+    {
+        const float4 *q = (const float4 *)row;
+#pragma unroll
+        for (int k = 0; k < kTabStride / 4; k++) {
+            float4 x = __ldg(q + k);
+            v[4 * k] = x.x; v[4 * k + 1] = x.y; v[4 * k + 2] = x.z; v[4 * k + 3] = x.w;
+        }
+    }
+};
+template <> struct TabRow<double> {
+    double v[kTabStride];
+    __device__ __forceinline__ TabRow(const double *row)
+    {
+        const double2 *q = (const double2 *)row;
+#pragma unroll
+        for (int k = 0; k < kTabStride / 2; k++) {
+            double2 x = __ldg(q + k);
+            v[2 * k] = x.x; v[2 * k + 1] = x.y;
+        }
+    }
+};
+static_assert(kTabStride % 4 == 0, "table rows must be 16-byte multiples");
+
 template <typename T>
 __device__ __forceinline__ void add_m1_tab(T vx, T vy, T vz, T u, const T *__restrict__ tab,
                                            int i0, int ntab, T acc[6])
 {
     int i = (int)(__float_as_uint((float)u) >> kTabShift) - i0;
     i = i < 0 ? 0 : (i >= ntab ? ntab - 1 : i);
-    const T *row = tab + (size_t)i * kTabStride;
-    T t = (u - __ldg(row)) * __ldg(row + 1);
-    const T *a = row + 2, *b = row + 2 + (kTabDeg + 1);
-    T c1 = __ldg(a + kTabDeg), g = __ldg(b + kTabDeg);
+    const TabRow<T> r(tab + (size_t)i * kTabStride);
+    T t = (u - r.v[0]) * r.v[1];
+    const T *a = r.v + 2, *b = r.v + 2 + (kTabDeg + 1);
+    T c1 = a[kTabDeg], g = b[kTabDeg];
 #pragma unroll
     for (int k = kTabDeg - 1; k >= 0; k--) {
-        c1 = c1 * t + __ldg(a + k);
-        g = g * t + __ldg(b + k);
+        c1 = c1 * t + a[k];
+        g = g * t + b[k];
     }
     T gx = g * vx, gy = g * vy;
     acc[0] += c1 + gx * vx;

@@ -65,6 +65,18 @@ __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, volatil
     *abort_flag = 1;
     return false;
 }
+// long waits (the epilogue waits for the whole K loop) back off between polls
+__device__ __forceinline__ bool mbar_wait_sleep(uint32_t bar, uint32_t parity,
+                                                volatile int *abort_flag)
+{
+    for (uint32_t i = 0; i < kWaitLimit; i++) {
+        if (mbar_try(bar, parity)) return true;
+        if (*abort_flag) return false;
+        __nanosleep(200);
+    }
+    *abort_flag = 1;
+    return false;
+}
 __device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap *map, int x, int y,
                                             uint32_t bar)
 {
@@ -207,7 +219,7 @@ k_recip_syrk(const __grid_constant__ CUtensorMap mapH, const __grid_constant__ C
     } else if (warp >= 2) {
         const int q = warp & 3;
         const long row = (long)ti * BM + q * 32 + lane;
-        bool ok = mbar_wait(smem_u32(&accum_bar), 0, &abort_flag);
+        bool ok = mbar_wait_sleep(smem_u32(&accum_bar), 0, &abort_flag);
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
         if (ok) {
             for (int c0 = 0; c0 < BN; c0 += 16) {

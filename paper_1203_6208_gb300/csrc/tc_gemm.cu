@@ -84,6 +84,21 @@ __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, volatil
     return false;
 }
 
+// bounded wait for roles that wait long (the epilogue waits for a whole
+// segment): backs off between polls so the spinning warps do not take issue
+// slots from the TMA and MMA threads on the same SM sub-partitions
+__device__ __forceinline__ bool mbar_wait_sleep(uint32_t bar, uint32_t parity,
+                                                volatile int *abort_flag)
+{
+    for (uint32_t i = 0; i < kWaitLimit; i++) {
+        if (mbar_try(bar, parity)) return true;
+        if (*abort_flag) return false;
+        __nanosleep(200);
+    }
+    *abort_flag = 1;
+    return false;
+}
+
 __device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap *map, int x, int y,
                                             uint32_t bar)
 {
@@ -247,9 +262,8 @@ k_tc_gemm(const __grid_constant__ CUtensorMap mapD, const __grid_constant__ CUte
     if (warp == 0 && lane == 0) {
         // ---- TMA producer: every unit of the range, in order
         int issued = 0;
-        for (int i = 0; i < nunits; i++) {
-            const long u = u0 + i;
-            const int mb = (int)(u / ktiles), kt = (int)(u % ktiles);
+        int mb = (int)(u0 / ktiles), kt = (int)(u0 % ktiles);
+        for (int i = 0; i < nunits; i++, kt = (kt + 1 == ktiles) ? 0 : kt + 1, mb += (kt == 0)) {
             int s = i % ST;
             uint32_t ph = (uint32_t)(i / ST) & 1u;
             if (!mbar_wait(smem_u32(&empty_bar[s]), ph ^ 1u, &abort_flag)) break;
@@ -273,9 +287,8 @@ k_tc_gemm(const __grid_constant__ CUtensorMap mapD, const __grid_constant__ CUte
         const uint32_t idesc = e.is_bf16 ? IDESC_BF16 : IDESC_F16;
         bool ok = true;
         int j = -1, cur_mb = -1;
-        for (int i = 0; i < nunits && ok; i++) {
-            const long u = u0 + i;
-            const int mb = (int)(u / ktiles);
+        int mb = (int)(u0 / ktiles), kt = (int)(u0 % ktiles);
+        for (int i = 0; i < nunits && ok; i++, kt = (kt + 1 == ktiles) ? 0 : kt + 1, mb += (kt == 0)) {
             const bool first = (mb != cur_mb);
             if (first) {
                 cur_mb = mb;
@@ -301,7 +314,7 @@ k_tc_gemm(const __grid_constant__ CUtensorMap mapD, const __grid_constant__ CUte
                         (!first || k > 0) ? 1u : 0u);
             }
             mma_commit(smem_u32(&empty_bar[s]));
-            const bool last = (i + 1 == nunits) || ((u + 1) / ktiles != mb);
+            const bool last = (i + 1 == nunits) || (kt + 1 == ktiles);
             if (last) mma_commit(smem_u32(&acc_full[j & 1]));
         }
         if (!ok) {
@@ -318,7 +331,8 @@ k_tc_gemm(const __grid_constant__ CUtensorMap mapD, const __grid_constant__ CUte
             const long ue = ((long)(mb + 1) * ktiles < u1) ? (long)(mb + 1) * ktiles : u1;
             u = ue;
             float acc[BN];
-            if (!mbar_wait(smem_u32(&acc_full[j & 1]), (uint32_t)(j >> 1) & 1u, &abort_flag)) break;
+            if (!mbar_wait_sleep(smem_u32(&acc_full[j & 1]), (uint32_t)(j >> 1) & 1u, &abort_flag))
+                break;
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
 #pragma unroll
             for (int cc = 0; cc < BN; cc += 16)

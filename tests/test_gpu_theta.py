@@ -7,8 +7,11 @@ The chains start from the exact theta equilibrium, so a correct step keeps
 at every concentration (chains cross freely in a theta solvent).  The bond
 statistic relaxes within a few time units, so a wrong noise amplitude or
 drift factor shows in it after the 1500 steps here; the Euler bias at
-dt = 0.01 is below 1 %.  Bars: <Q^2> within 3 %, <R_e^2> and <R_g^2>
-within 10 % (standard errors from replica-to-replica scatter are ~2-4 %).
+dt = 0.01 is below 1 %.  R_e^2 and R_g^2 follow the slowest Rouse modes
+(relaxation times of order 100 time units, against the 15 simulated), so
+their averages stay close to those of the seeded initial ensemble, whose
+sampling error is ~5 %.  Bars: <Q^2> within 3 %; <R_e^2> and <R_g^2>
+within 4 standard errors (replica-to-replica scatter) and within 20 %.
 """
 import numpy as np
 import pytest
@@ -60,6 +63,8 @@ def test_theta_statics_batched():
     for ci in range(3):
         blk = per_rep[12 * ci:12 * (ci + 1)]
         mean = blk.mean(0)
+        se = blk.std(0, ddof=1) / np.sqrt(len(blk))
         assert abs(mean[0] / ref[0] - 1) < 0.03, (ci, mean)
-        assert abs(mean[1] / ref[1] - 1) < 0.10, (ci, mean)
-        assert abs(mean[2] / ref[2] - 1) < 0.10, (ci, mean)
+        for k in (1, 2):
+            assert abs(mean[k] - ref[k]) < 4.0 * se[k], (ci, k, mean, se)
+            assert abs(mean[k] / ref[k] - 1) < 0.20, (ci, k, mean)
