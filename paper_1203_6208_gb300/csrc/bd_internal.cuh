@@ -69,6 +69,8 @@ struct Plan {
     EwaldCoef *d_ewc;                  // Eq. (M1) coefficients, device
     EwaldT<double> *d_ew64;            // the same per working precision
     EwaldT<float> *d_ew32;
+    EwaldT<double> h_ew64;             // host copies (passed to the pair kernels by value)
+    EwaldT<float> h_ew32;
     double *d_pw64;                    // positions wrapped into [0, L), FP64 [3N]
     float *d_pw32;                     // the same as FP32 hi/lo words [2][3N]
     double *d_tab;                     // M1 table [ntab][kTabStride] (FP64)

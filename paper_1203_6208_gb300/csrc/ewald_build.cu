@@ -393,9 +393,9 @@ template <> struct Sep<float> {
 constexpr int KC = 64;                 // k-vectors per shared-memory chunk
 
 template <typename T>
-__global__ void __launch_bounds__(TB *TB)
+__global__ void __launch_bounds__(TB *TB, 4)
 k_build_D(const double *__restrict__ pw, const float *__restrict__ pw32, int n,
-          const EwaldT<T> *__restrict__ ewt, const EwaldCoef *__restrict__ ewc,
+          const __grid_constant__ EwaldT<T> c, const EwaldCoef *__restrict__ ewc,
           const T *__restrict__ tab, int tab_i0, int ntab, const T *__restrict__ km, int nk,
           const T *__restrict__ cs, const T *__restrict__ sn, int overlap_corr, float rc,
           T *__restrict__ D, void *__restrict__ D16, int is_bf16, long ld, int recip_in_D)
@@ -410,7 +410,6 @@ k_build_D(const double *__restrict__ pw, const float *__restrict__ pw32, int n,
     while ((long)J * (J + 1) / 2 > idx) J--;
     while ((long)(J + 1) * (J + 2) / 2 <= idx) J++;
     int I = (int)(idx - (long)J * (J + 1) / 2);
-    const EwaldT<T> c = *ewt;
     (void)ewc;
     int ty = threadIdx.x / TB, tx = threadIdx.x % TB;
     int nu = I * TB + ty, mu = J * TB + tx;
@@ -436,7 +435,7 @@ k_build_D(const double *__restrict__ pw, const float *__restrict__ pw32, int n,
             T vx = d[0] + (T)cur.nx * c.L, vy = d[1] + (T)cur.ny * c.L,
               vz = d[2] + (T)cur.nz * c.L;
             T u = vx * vx + vy * vy + vz * vz;
-            bool zero_image = same && cur.nx == 0 && cur.ny == 0 && cur.nz == 0;
+            bool zero_image = same && cur.at_origin();
             if (u <= c.rc2 && !zero_image) {
                 if (u >= c.four_a2) add_m1_tab<T>(vx, vy, vz, u, tab, tab_i0, ntab, acc);
                 else if (!same && overlap_corr) add_overlap<T>(vx, vy, vz, u, c, acc);
@@ -534,6 +533,10 @@ void launch_kvec_table(Plan &P, cudaStream_t s)
     count_launches(1);
     k_ewald_typed<<<1, 1, 0, s>>>(P.d_ewc, P.d_ew64, P.d_ew32);
     count_launches(1);
+    cudaMemcpyAsync(&P.h_ew64, P.d_ew64, sizeof(EwaldT<double>), cudaMemcpyDeviceToHost, s);
+    if (P.d_ew32)
+        cudaMemcpyAsync(&P.h_ew32, P.d_ew32, sizeof(EwaldT<float>), cudaMemcpyDeviceToHost, s);
+    cudaStreamSynchronize(s);
     if (P.ntab > 0) {
         k_m1_table<<<(2 * P.ntab + 63) / 64, 64, 0, s>>>(P.d_ewc, P.tab_i0, P.ntab, P.d_tab,
                                                         P.d_tab32);
@@ -581,7 +584,7 @@ void launch_build_D_f64(Plan &P, const double *R, double *D, cudaStream_t s)
     launch_wrap(P, R, s);
     long nb = tile_pairs(P.n);
     k_build_D<double><<<(unsigned)nb, TB * TB, 0, s>>>(
-        P.d_pw64, P.d_pw32, P.n, P.d_ew64, P.d_ewc, P.d_tab, P.tab_i0, P.ntab, P.d_km64, P.nk,
+        P.d_pw64, P.d_pw32, P.n, P.h_ew64, P.d_ewc, P.d_tab, P.tab_i0, P.ntab, P.d_km64, P.nk,
         P.d_cos, P.d_sin, P.p.overlap_corr,
         (float)P.p.r_c, D, nullptr, 0, P.ld, 0);
     count_launches(1);
@@ -600,7 +603,7 @@ bd_status launch_build_D_f32(Plan &P, const double *R, float *D32, void *D16, in
     }
     long nb = tile_pairs(P.n);
     k_build_D<float><<<(unsigned)nb, TB * TB, 0, s>>>(
-        P.d_pw64, P.d_pw32, P.n, P.d_ew32, P.d_ewc, P.d_tab32, P.tab_i0, P.ntab, P.d_km32, nk,
+        P.d_pw64, P.d_pw32, P.n, P.h_ew32, P.d_ewc, P.d_tab32, P.tab_i0, P.ntab, P.d_km32, nk,
         P.d_cos32, P.d_sin32, P.p.overlap_corr,
         (float)P.p.r_c, D32, D16, is_bf16, P.ld, P.recip_tc);
     count_launches(1);

@@ -363,31 +363,32 @@ void launch_lanczos_update(Plan &P, int j, cudaStream_t s)
     count_launches(1);
 }
 
-// number of eigenvalues of the k x k tridiagonal (alpha, beta) below x: sign
+// number of eigenvalues of the k x k tridiagonal (alpha, beta^2) below x: sign
 // changes of the Sturm sequence p_0 = 1, p_i = (alpha_i - x) p_{i-1} -
-// beta_{i-1}^2 p_{i-2} (leading principal minors of T - x I).  No division:
-// the pair (p_{i-1}, p_i) is rescaled by a power of two when it grows or
-// shrinks too far, which changes no sign.  A zero p_i keeps the sign of
-// p_{i-1}.
-__device__ int sturm_count(const double *al, const double *be, int k, double x)
+// beta_{i-1}^2 p_{i-2} (leading principal minors of T - x I).  FP32 (the FP64
+// pipe of this GPU issues 2 operations per clock per SM; the bounds need a
+// few digits, and FP32 resolves the Ritz values to ~1e-6 of |T|).  No
+// division: the pair (p_{i-1}, p_i) is rescaled by a power of two when it
+// grows or shrinks too far, which changes no sign.  A zero p_i keeps the
+// sign of p_{i-1}.
+__device__ int sturm_count(const float *al, const float *b2, int k, float x)
 {
-    double pm = 1.0, p = al[0] - x;
-    bool neg_prev = false;
-    bool neg = p < 0.0 || (p == 0.0 && neg_prev);
+    float pm = 1.f, p = al[0] - x;
+    bool neg = p < 0.f;
     int cnt = neg ? 1 : 0;
     for (int i = 1; i < k; i++) {
-        double pn = (al[i] - x) * p - (be[i - 1] * be[i - 1]) * pm;
-        bool nn = pn < 0.0 || (pn == 0.0 && neg);
+        float pn = (al[i] - x) * p - b2[i - 1] * pm;
+        bool nn = pn < 0.f || (pn == 0.f && neg);
         cnt += (nn != neg) ? 1 : 0;
         neg = nn;
         pm = p;
         p = pn;
-        double mx = fmax(fabs(p), fabs(pm));
-        if (mx > 0x1p+500 || (mx < 0x1p-500 && mx > 0.0)) {
+        float mx = fmaxf(fabsf(p), fabsf(pm));
+        if (mx > 0x1p+60f || (mx < 0x1p-60f && mx > 0.f)) {
             int e;
-            frexp(mx, &e);
-            p = ldexp(p, -e);
-            pm = ldexp(pm, -e);
+            frexpf(mx, &e);
+            p = ldexpf(p, -e);
+            pm = ldexpf(pm, -e);
         }
     }
     return cnt;
@@ -395,7 +396,8 @@ __device__ int sturm_count(const double *al, const double *be, int k, double x)
 
 // Extreme Ritz values of the k x k tridiagonal matrix by multisection on
 // Sturm counts: 128 threads per end test 128 interior points of the current
-// bracket (Gershgorin at the start), which shrinks it 129-fold per round.
+// bracket (Gershgorin at the start), which shrinks it 129-fold per round,
+// until it is 1e-6 of the value wide (at most 6 rounds).
 // Then the widened bounds {d_min, d_max} and a status word.  Launched with
 // 256 threads.
 __global__ void k_lanczos_finish(const double *lab, int k, double smax, double fmin_,
@@ -404,8 +406,13 @@ __global__ void k_lanczos_finish(const double *lab, int k, double smax, double f
     __shared__ double br[2][2];
     __shared__ int first[2];
     __shared__ int kk;
+    __shared__ float alf[kMaxLanczos], b2f[kMaxLanczos];
     const int g = threadIdx.x >> 7, t = threadIdx.x & 127;
     const double *al = lab, *be = lab + kMaxLanczos;
+    for (int i = threadIdx.x; i < k; i += blockDim.x) {
+        alf[i] = (float)al[i];
+        b2f[i] = (float)(be[i] * be[i]);
+    }
     if (threadIdx.x == 0) {
         // stop at a breakdown (beta ~ 0: the Krylov space became invariant)
         double scale = 0.0;
@@ -426,14 +433,14 @@ __global__ void k_lanczos_finish(const double *lab, int k, double smax, double f
     __syncthreads();
     const int kt = kk;
     const int target = (g == 0) ? 1 : kt;        // smallest x with count(x) >= target
-    for (int it = 0; it < 10; it++) {
+    for (int it = 0; it < 6; it++) {
         const double a = br[g][0], b = br[g][1];
-        const bool done = !(b - a > 1e-15 * fmax(fabs(a), fabs(b)));
+        const bool done = !(b - a > 1e-6 * fmax(fabs(a), fabs(b)));
         if (t == 0) first[g] = 128;
         __syncthreads();
         if (!done) {
             double x = a + (b - a) * (t + 1) / 129.0;
-            if (sturm_count(al, be, kt, x) >= target) atomicMin(&first[g], t);
+            if (sturm_count(alf, b2f, kt, (float)x) >= target) atomicMin(&first[g], t);
         }
         __syncthreads();
         if (t == 0 && !done) {
