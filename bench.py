@@ -55,11 +55,12 @@ def parse():
                          "carried in the products; fresh = --lanczos products per step")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=3)
-    ap.add_argument("--workload", default="n8000", choices=["n8000", "batch", "theta"],
+    ap.add_argument("--workload", default="n8000", choices=["n8000", "batch", "theta", "lma"],
                     help="batch: 64 replicas, N ~ U[200, 2000], mixed, one graph launch "
                          "per step (replica-steps/s); theta: the theta-solution statics "
                          "validation (N_b = 20 and 40, N_c = 20, a = 0.5, dt = 0.01, five "
-                         "concentrations), reported against Eqs. (Re2), (Rg2)")
+                         "concentrations), reported against Eqs. (Re2), (Rg2); lma: dense D "
+                         "(HMA) against matrix-free products (LMA) at N = 8000 and larger N")
     ap.add_argument("--replicas", type=int, default=64)
     ap.add_argument("--chains", type=int, default=400,
                     help="chains of 20 beads (400 = the N=8000 workload; smaller only for "
@@ -574,6 +575,59 @@ def run_theta(args):
     print(json.dumps(line), flush=True)
 
 
+def run_lma(args):
+    """Dense-D steps (HMA, D assembled once per step) against matrix-free
+    steps (LMA, D(R) X recomputed in every product) on the theta workload of
+    the headline (c/c* = 4, 20-bead chains, m = 16, N_Ch = 40, mixed), at
+    N = 8000 and at larger N; dense runs only where D fits in device memory."""
+    import torch
+    torch.cuda.set_device(0)
+    from paper_1203_6208_gb300 import binding as bnd, build, inputs
+    build.build()
+    free, _ = torch.cuda.mem_get_info()
+    res = {}
+    for chains in (400, 1600, 5000):
+        cfg, _ = inputs.preset("c4", alpha_factor=1.75, n_chains=chains)
+        p = cfg.params()
+        R0 = inputs.make_chains(cfg)
+        row = {}
+        for mode in ("dense", "matfree"):
+            plan = bnd.Plan(p, "mixed_f16", max_rhs=args.m, max_cheb=args.nch)
+            if mode == "dense" and plan.info.d_bytes > 0.8 * free:
+                row[mode] = {"skipped": "D needs %.0f GB" % (plan.info.d_bytes / 1e9)}
+                plan.close()
+                continue
+            D = plan.alloc_D() if mode == "dense" else None
+            R = torch.tensor(R0.reshape(-1), device="cuda")
+            flags = bnd.BD_STEP_MATRIX_FREE if mode == "matfree" else 0
+            kw = dict(m=args.m, n_cheb=args.nch, bounds_mode=3, fixman_c=8.0, flags=flags,
+                      seed=7)
+            reps = 1 if (mode == "matfree" and chains > 400) else 2
+            plan.step(R, D, None, step_index=0, **kw)
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            for k in range(reps):
+                plan.step(R, D, None, step_index=1 + k, **kw)
+            e1.record()
+            torch.cuda.synchronize()
+            ms = e0.elapsed_time(e1) / reps
+            row[mode] = {"ms_per_step": ms, "steps_per_s": 1e3 / ms, "timed_steps": reps}
+            del D
+            plan.close()
+            torch.cuda.empty_cache()
+        res[f"N={cfg.n}"] = row
+    head = res["N=8000"]
+    line = {"metric": "steps/sec, dense D (HMA) vs matrix-free (LMA), mixed",
+            "value": head["matfree"]["steps_per_s"], "unit": "steps/s (matrix-free, N=8000)",
+            "n_gpus": 1, "steps": args.steps, "warmup": 1, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
+            "config": {"workload": "lma", "m": args.m, "n_cheb": args.nch,
+                       "bounds": "fixman semidilute (C = 8)", "alpha_factor": 1.75},
+            "results": res}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -581,6 +635,8 @@ def main():
         return
     if args.workload == "theta":
         run_theta(args)
+    elif args.workload == "lma":
+        run_lma(args)
     elif args.workload == "batch":
         run_batch(args)
     else:

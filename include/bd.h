@@ -124,11 +124,14 @@ typedef struct {
     uint64_t step_index;      /* Philox counter high word when dW == NULL          */
     int32_t bounds_mode;      /* BD_BOUNDS_FRESH, _LAGGED, _FIXMAN_DILUTE or
                                  _FIXMAN_SEMIDILUTE (see bd_step)                  */
-    int32_t flags;            /* BD_STEP_DEVICE_COUNTER or 0                        */
+    int32_t flags;            /* BD_STEP_DEVICE_COUNTER | BD_STEP_MATRIX_FREE or 0  */
     double  ef_tol;           /* n_cheb == 0: adaptive N_Ch until E_f < ef_tol      */
     double  fixman_c;         /* BD_BOUNDS_FIXMAN_SEMIDILUTE: C of Eq. (fmin)       */
 } bd_step_opts;
 
+#define BD_STEP_MATRIX_FREE 2 /* never store D: every product recomputes D(R) X from R
+                                 (bd_apply_D_matfree); D may be NULL.  Bounds come from
+                                 fresh Lanczos or Fixman's estimates (not lagged)     */
 #define BD_STEP_DEVICE_COUNTER 1  /* with dW == NULL: the Philox counter high word is
                                      the plan's device step counter (set by
                                      bd_plan_set_step_counter) and the step advances
@@ -251,6 +254,19 @@ bd_status bd_chebyshev_sqrt(bd_plan *plan, const void *D, const double *bounds, 
 bd_status bd_chebyshev_sqrt_adaptive(bd_plan *plan, const void *D, const double *bounds,
                                      double ef_tol, const double *dW, int32_t m, double *dS,
                                      double *Ef, int32_t *n_used, bd_stream stream);
+
+/* bd_apply_D_matfree -- Y = D(R) X without storing D (the paper's LMA,
+ * Sec. V): real-space images, overlap branch and self term are evaluated
+ * per bead pair inside the product (every unordered pair twice, once per
+ * row, so each row is summed in a fixed order), the reciprocal sum through
+ * structure factors S_k = sum_mu (cos, sin)(k.r_mu) X_mu per half-space k.
+ * Same D as bd_build_D (to rounding): FP64 arithmetic on FP64 plans, FP32
+ * with FP64 output on mixed plans (no 16-bit rounding).  Cost O(N^2 images)
+ * per call, memory O(N): the path for N whose D does not fit.
+ *   R     dev, 3N positions
+ *   X, Y  dev, 3N x m column-major doubles, 1 <= m <= max_rhs + 3      */
+bd_status bd_apply_D_matfree(bd_plan *plan, const double *R, const double *X, int32_t m,
+                             double *Y, bd_stream stream);
 
 /* ---------------------------------------------------------------------------
  * bd_step -- one Euler step of Eq. (sde) with kappa = 0:

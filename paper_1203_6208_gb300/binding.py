@@ -25,6 +25,7 @@ STATUS_NAMES = {0: "BD_OK", 1: "BD_ERR_INVALID", 2: "BD_ERR_OOM", 3: "BD_ERR_CUD
 PRECISIONS = {"fp64": 0, "mixed_f16": 1, "mixed_bf16": 2}
 BD_APPLY_REFINE = 1
 BD_STEP_DEVICE_COUNTER = 1
+BD_STEP_MATRIX_FREE = 2
 BOUNDS_MODES = {"fresh": 0, "lagged": 1, "fixman_dilute": 2, "fixman_semidilute": 3}
 
 EXPORTS = ["bd_plan_create", "bd_plan_destroy", "bd_plan_query", "bd_forces", "bd_build_D",
@@ -32,7 +33,7 @@ EXPORTS = ["bd_plan_create", "bd_plan_destroy", "bd_plan_query", "bd_forces", "b
            "bd_set_phase_events", "bd_kernel_launches", "bd_eig_bounds_noalloc",
            "bd_apply_D_backward", "bd_chebyshev_backward", "bd_plan_autotune", "bd_product_timing",
            "bd_plan_set_step_counter", "bd_batch_create", "bd_batch_destroy", "bd_batch_query",
-           "bd_batch_step", "bd_chebyshev_sqrt_adaptive",
+           "bd_batch_step", "bd_chebyshev_sqrt_adaptive", "bd_apply_D_matfree",
            "bd_last_error", "bd_version"]
 PHASES = ["forces", "build_D", "bounds", "first_product", "chebyshev", "update"]
 
@@ -111,6 +112,7 @@ def load(path: str = LIB_PATH):
                                  ctypes.POINTER(i64), ctypes.POINTER(i64), ctypes.POINTER(i64)]
     L.bd_batch_step.argtypes = [_vp, _vp, _vp, ctypes.POINTER(BdStepOpts), _vp, _vp]
     L.bd_chebyshev_backward.argtypes = [_vp, _vp, _vp, _vp, i32, _vp, i32, _vp, _vp, _vp, _vp]
+    L.bd_apply_D_matfree.argtypes = [_vp, _vp, _vp, i32, _vp, _vp]
     L.bd_chebyshev_sqrt_adaptive.argtypes = [_vp, _vp, _vp, f64, _vp, i32, _vp, _vp,
                                              ctypes.POINTER(i32), _vp]
     L.bd_eig_bounds_noalloc.argtypes = [_vp, i32, i32, i32, f64, f64, _vp, _vp, _vp]
@@ -218,6 +220,11 @@ class Plan:
         m = dW.shape[0] if dW.dim() == 2 else 1
         _check(load().bd_chebyshev_sqrt(self._h, _p(D), _p(bounds), int(n_cheb), _p(dW), m,
                                         _p(dS), _p(Ef), _stream(stream)))
+
+    def apply_matfree(self, R, X, Y, stream=None):
+        """Y = D(R) X without storing D (matrix-free product)."""
+        m = X.shape[0] if X.dim() == 2 else 1
+        _check(load().bd_apply_D_matfree(self._h, _p(R), _p(X), m, _p(Y), _stream(stream)))
 
     def chebyshev_adaptive(self, D, bounds, ef_tol, dW, dS, Ef=None, stream=None):
         """Adaptive N_Ch (synchronising); returns (n_used, converged)."""

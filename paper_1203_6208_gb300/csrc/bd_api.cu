@@ -46,7 +46,6 @@ bd_status check_launch(const char *what)
     return BD_OK;
 }
 
-static bool is_mixed(const Plan &P) { return P.p.precision != BD_FP64; }
 
 template <typename T>
 static bd_status dmalloc(Plan &P, T **ptr, size_t count)
@@ -76,7 +75,7 @@ static void free_plan(Plan &P)
                     P.d_coef, P.d_wdw, P.d_red, P.d_redpart, P.d_bounds, P.d_status, P.d_lq[0], P.d_lq[1],
                     P.d_lq[2], P.d_lab, P.d_x16, P.d_xscale, P.d_part, P.d_counters,
                     P.d_stats_scratch, P.d_y32, P.d_lag_bounds, P.d_step_ctr, P.d_vhist, P.d_xhist, P.d_ubuf[0], P.d_ubuf[1],
-                    P.d_ubuf[2], P.d_ubuf[3], P.d_Uh, P.d_Ul, P.d_rtiles, P.d_lanpart, P.d_mom};
+                    P.d_ubuf[2], P.d_ubuf[3], P.d_Uh, P.d_Ul, P.d_rtiles, P.d_lanpart, P.d_mom, P.d_sfac, P.d_mfW};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     if (P.h_est) cudaFreeHost(P.h_est);
@@ -293,6 +292,11 @@ bd_status bd_build_D(bd_plan *plan, const double *R, void *D, bd_stream stream)
 static bd_status apply_core(Plan &P, const void *D, const double *X, int m, double *Y,
                             int flags, cudaStream_t s)
 {
+    if (P.matfree_R) {        // inside a matrix-free step: recompute D(R) X (FP32 or FP64)
+        (void)D;
+        (void)flags;
+        return launch_apply_matfree(P, X, m, Y, s);
+    }
     if (!is_mixed(P)) {
         launch_gemm_f64(P, (const double *)D, X, m, Y, s);
         return check_launch("gemm_f64");
@@ -369,7 +373,11 @@ static bd_status cheb_core(Plan &P, const void *D, const double *bounds, int nch
     launch_cheb_first(P, bounds, dW, W, m, A, B, dS, s);   // A = V0, B = V1
     double *prev2 = A, *prev1 = B;
     for (int p = 2; p < nch; p++) {
-        if (!is_mixed(P)) {
+        if (P.matfree_R) {
+            bd_status st = launch_apply_matfree(P, prev1, m, P.d_mfW, s);
+            if (st != BD_OK) return st;
+            launch_cheb_term(P, P.d_mfW, prev1, prev2, m, bounds, p, dS, s);
+        } else if (!is_mixed(P)) {
             ChebEpi e{P.d_coef, bounds, p, prev2, prev1, dS};
             launch_gemm_f64_cheb(P, (const double *)D, m, e, s);
         } else {
@@ -421,6 +429,20 @@ bd_status bd_chebyshev_sqrt_adaptive(bd_plan *plan, const void *D, const double 
     if (!conv)
         return set_error(BD_ERR_CHEB_NOCONV, "E_f >= %g with max_cheb = %d terms", ef_tol, N);
     return BD_OK;
+}
+
+bd_status bd_apply_D_matfree(bd_plan *plan, const double *R, const double *X, int32_t m,
+                             double *Y, bd_stream stream)
+{
+    if (!plan || !R || !X || !Y) return set_error(BD_ERR_INVALID, "NULL argument");
+    Plan &P = plan->P;
+    if (m < 1 || m > P.p.max_rhs + 3)
+        return set_error(BD_ERR_INVALID, "m=%d outside [1, max_rhs + 3 = %d]", m, P.p.max_rhs + 3);
+    const char *xb = (const char *)X, *yb = (const char *)Y;
+    const size_t bytes = (size_t)P.n3 * m * sizeof(double);
+    if (xb < yb + bytes && yb < xb + bytes) return set_error(BD_ERR_INVALID, "X and Y overlap");
+    launch_matfree_tables(P, R, stream);
+    return launch_apply_matfree(P, X, m, Y, stream);
 }
 
 bd_status bd_product_timing(bd_plan *plan, int32_t enable, float *total_ms, int32_t *launches)
@@ -497,8 +519,10 @@ bd_status bd_wiener(bd_plan *plan, uint64_t seed, uint64_t step_index, int64_t c
 bd_status bd_step(bd_plan *plan, double *R, void *D, const double *dW, const bd_step_opts *o,
                   double *DF, double *dS, bd_step_stats *stats, bd_stream stream)
 {
-    if (!plan || !R || !D || !o) return set_error(BD_ERR_INVALID, "NULL argument");
+    if (!plan || !R || !o) return set_error(BD_ERR_INVALID, "NULL argument");
     Plan &P = plan->P;
+    const bool matfree = (o->flags & BD_STEP_MATRIX_FREE) != 0;
+    if (!D && !matfree) return set_error(BD_ERR_INVALID, "NULL D (needs BD_STEP_MATRIX_FREE)");
     const int m = o->m;
     if (m < 1 || m > P.p.max_rhs) return set_error(BD_ERR_INVALID, "m=%d outside [1, max_rhs=%d]", m, P.p.max_rhs);
     const bool adaptive = o->n_cheb == 0;
@@ -516,9 +540,21 @@ bd_status bd_step(bd_plan *plan, double *R, void *D, const double *dW, const bd_
         return set_error(BD_ERR_INVALID, "lanczos_iters outside [1, %d]", kMaxLanczos);
     if (!(o->bound_safety >= 0.0) || !(o->dmin_fraction > 0.0) || !(o->dmin_fraction <= 1.0))
         return set_error(BD_ERR_INVALID, "need bound_safety >= 0, 0 < dmin_fraction <= 1");
-    if (((uintptr_t)D & 255) != 0) return set_error(BD_ERR_INVALID, "D must be 256-byte aligned");
+    if (!matfree && ((uintptr_t)D & 255) != 0)
+        return set_error(BD_ERR_INVALID, "D must be 256-byte aligned");
     cudaStream_t s = stream;
     bd_step_stats *st_dev = stats ? stats : P.d_stats_scratch;
+    if (matfree) {
+        bd_status mst = matfree_init(P);
+        if (mst != BD_OK) return mst;
+    }
+    // every product of a matrix-free step recomputes D(R) from the positions
+    // at the start of the step (R changes only in the final update)
+    struct MatfreeScope {
+        Plan &P;
+        MatfreeScope(Plan &p, const double *R, bool on) : P(p) { P.matfree_R = on ? R : nullptr; }
+        ~MatfreeScope() { P.matfree_R = nullptr; }
+    } mf_scope(P, R, matfree);
     const size_t n3 = P.n3;
     bd_status st;
 #define PHASE(i) \
@@ -529,12 +565,17 @@ bd_status bd_step(bd_plan *plan, double *R, void *D, const double *dW, const bd_
     // (a1) forces; input over-stretch count in status word 2
     launch_forces(P, R, P.d_F, P.d_status + 2, s);
     PHASE(1);
-    // (a2-a4) D(R)
-    st = bd_build_D(plan, R, D, s);
-    if (st != BD_OK) return st;
+    // (a2-a4) D(R), or the tables of the matrix-free products
+    if (matfree) {
+        launch_matfree_tables(P, R, s);
+    } else {
+        st = bd_build_D(plan, R, D, s);
+        if (st != BD_OK) return st;
+    }
     PHASE(2);
     // (a6) bounds: fresh Lanczos, or the previous step's lagged recurrence
-    const bool lag = !adaptive && o->bounds_mode == BD_BOUNDS_LAGGED && is_mixed(P) && o->n_cheb >= 8 &&
+    const bool lag = !adaptive && !matfree && o->bounds_mode == BD_BOUNDS_LAGGED && is_mixed(P) &&
+                     o->n_cheb >= 8 &&
                      o->n_cheb - 1 <= kMaxLanczos && m + 2 <= kMaxRhs;
     if (fix) {
         // Fixman's estimates come from the first product below
@@ -576,7 +617,7 @@ bd_status bd_step(bd_plan *plan, double *R, void *D, const double *dW, const bd_
         if (fix)
             launch_fixman_bounds(P, P.d_X0 + n3 * (m + 1), P.d_Y0 + n3 * (m + 1), fix,
                                  o->fixman_c, P.d_bounds, P.d_status + 3, s);
-        if (is_mixed(P)) {   // refine the drift column only
+        if (is_mixed(P) && !matfree) {   // refine the drift column only
             launch_refine_f32(P, (const float *)D, P.d_F, 1, P.d_Y0, s);
         }
         if (lag) {           // Lanczos step 0 from the product's last column

@@ -121,6 +121,10 @@ struct Plan {
     double *d_vhist;                   // V_0..V_{N_Ch-2}, [max_cheb-1][max_rhs][3N]
     double *d_xhist;                   // scaled adjoints X_q, same shape
     double *d_ubuf[4];                 // rolling adjoint vectors and D U products
+    // matrix-free products (allocated by the first one)
+    void *d_sfac;                      // structure factors [nk][max_rhs + 3][6] (working precision)
+    double *d_mfW;                     // product scratch of matrix-free Chebyshev terms (3N x max_rhs)
+    const double *matfree_R;           // set inside a matrix-free step: products recompute D(R)
     // adaptive N_Ch (allocated by the first adaptive call)
     double *d_mom;                     // moments, dot partials, estimates, D V scratch
     double *h_est;                     // pinned host words read back per candidate N
@@ -131,6 +135,8 @@ struct Plan {
     float *d_Uh, *d_Ul;                // U as TF32 hi/lo words [3N][recip_kp]
     int2 *d_rtiles;                    // tile list
 };
+
+inline bool is_mixed(const Plan &P) { return P.p.precision != BD_FP64; }
 
 // host-side count of kernel launches (bd_kernel_launches)
 void count_launches(int k);
@@ -149,6 +155,11 @@ void launch_trig_tables(Plan &P, const double *R, cudaStream_t s);
 void launch_build_D_f64(Plan &P, const double *R, double *D, cudaStream_t s);
 bd_status launch_build_D_f32(Plan &P, const double *R, float *D32, void *D16, int is_bf16,
                         cudaStream_t s);
+
+// matrix-free Y = D(R) X (ewald_build.cu); the tables of R must be current
+void launch_matfree_tables(Plan &P, const double *R, cudaStream_t s);
+bd_status matfree_init(Plan &P);
+bd_status launch_apply_matfree(Plan &P, const double *X, int m, double *Y, cudaStream_t s);
 
 // dense_f64.cu : Y = D X (FP64), epilogue variants
 struct ChebEpi {
@@ -169,6 +180,8 @@ void launch_forces(Plan &P, const double *R, double *F, int32_t *n_bad, cudaStre
 void launch_cheb_coeffs(Plan &P, const double *bounds, int nch, cudaStream_t s);
 void launch_cheb_first(Plan &P, const double *bounds, const double *dW, const double *DW, int m,
                        double *V0, double *V1, double *dS, cudaStream_t s);
+void launch_cheb_term(Plan &P, const double *W, const double *V1, double *V2, int m,
+                      const double *bounds, int p, double *dS, cudaStream_t s);
 void launch_ef(Plan &P, const double *dW, const double *DW, const double *dS, int m,
                double *Ef, bd_step_stats *stats, cudaStream_t s);
 void launch_wiener(Plan &P, uint64_t seed, uint64_t step, int64_t count, double *out,

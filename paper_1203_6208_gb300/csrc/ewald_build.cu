@@ -390,6 +390,36 @@ template <> struct Sep<float> {
     }
 };
 
+// real-space images, overlap branch and self term of the block D_{nu mu}
+// (Eqs. DF, M1, DFmodified): the six components xx, xy, xz, yy, yz, zz are
+// added to acc
+template <typename T>
+__device__ __forceinline__ void pair_real(const double *__restrict__ pw,
+                                          const float *__restrict__ pw32, long n3, int nu, int mu,
+                                          const EwaldT<T> &c, const T *__restrict__ tab, int tab_i0,
+                                          int ntab, int overlap_corr, float rc, T acc[6])
+{
+    T d[3];
+    Sep<T>::get(pw, pw32, n3, nu, mu, c, d);
+    const bool same = (nu == mu);
+    ImageCursor cur;
+    cur.start((float)d[0], (float)d[1], (float)d[2], c.Lf, c.invLf, rc);
+    while (!cur.done) {
+        T vx = d[0] + (T)cur.nx * c.L, vy = d[1] + (T)cur.ny * c.L, vz = d[2] + (T)cur.nz * c.L;
+        T u = vx * vx + vy * vy + vz * vz;
+        bool zero_image = same && cur.at_origin();
+        if (u <= c.rc2 && !zero_image) {
+            if (u >= c.four_a2) add_m1_tab<T>(vx, vy, vz, u, tab, tab_i0, ntab, acc);
+            else if (!same && overlap_corr) add_overlap<T>(vx, vy, vz, u, c, acc);
+            else add_m1<T>(vx, vy, vz, u, c, acc);
+        }
+        cur.advance();
+    }
+    if (same) {
+        acc[0] += c.self; acc[3] += c.self; acc[5] += c.self;
+    }
+}
+
 constexpr int KC = 64;                 // k-vectors per shared-memory chunk
 
 template <typename T>
@@ -425,28 +455,7 @@ k_build_D(const double *__restrict__ pw, const float *__restrict__ pw32, int n,
         acc[0] = b[0]; acc[1] = b[1]; acc[2] = b[2];
         acc[3] = b[ld + 1]; acc[4] = b[ld + 2]; acc[5] = b[2 * ld + 2];
     }
-    if (active) {
-        T d[3];
-        Sep<T>::get(pw, pw32, n3, nu, mu, c, d);
-        const bool same = (nu == mu);
-        ImageCursor cur;
-        cur.start((float)d[0], (float)d[1], (float)d[2], c.Lf, c.invLf, rc);
-        while (!cur.done) {
-            T vx = d[0] + (T)cur.nx * c.L, vy = d[1] + (T)cur.ny * c.L,
-              vz = d[2] + (T)cur.nz * c.L;
-            T u = vx * vx + vy * vy + vz * vz;
-            bool zero_image = same && cur.at_origin();
-            if (u <= c.rc2 && !zero_image) {
-                if (u >= c.four_a2) add_m1_tab<T>(vx, vy, vz, u, tab, tab_i0, ntab, acc);
-                else if (!same && overlap_corr) add_overlap<T>(vx, vy, vz, u, c, acc);
-                else add_m1<T>(vx, vy, vz, u, c, acc);
-            }
-            cur.advance();
-        }
-        if (same) {
-            acc[0] += c.self; acc[3] += c.self; acc[5] += c.self;
-        }
-    }
+    if (active) pair_real<T>(pw, pw32, n3, nu, mu, c, tab, tab_i0, ntab, overlap_corr, rc, acc);
     // reciprocal sum over half-space k (each folded with -k), staged per chunk
     for (int t0 = 0; t0 < nk; t0 += KC) {
         const int kc = min(KC, nk - t0);
@@ -608,6 +617,192 @@ bd_status launch_build_D_f32(Plan &P, const double *R, float *D32, void *D16, in
         (float)P.p.r_c, D32, D16, is_bf16, P.ld, P.recip_tc);
     count_launches(1);
     return BD_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Matrix-free product Y = D(R) X (the paper's LMA: D is never stored).
+//
+// Real space: one thread per row bead nu; a block of kMfRows threads walks all
+// beads mu in tiles, evaluates the block B_{nu mu} with the same pair code as
+// the assembly (images, overlap branch, self term) and accumulates
+// y_nu += B_{nu mu} x_mu for every column in shared memory (per-thread
+// slots, written back once: deterministic, no atomics).  Every unordered
+// pair is evaluated twice (once per row), which keeps the sum per row in a
+// fixed order.
+// Reciprocal space: structure factors S_k = sum_mu (cos, sin)(k.r_mu) x_mu
+// per half-space k and column, then y_nu += sum_k m_k (cos_nu S^c_k +
+// sin_nu S^s_k) with the folded tensors m_k = 2 f(k)(I - khat khat).
+constexpr int kMfRows = 128;
+
+template <typename T>
+__global__ void __launch_bounds__(kMfRows)
+k_pair_apply(const double *__restrict__ pw, const float *__restrict__ pw32, int n,
+             const __grid_constant__ EwaldT<T> c, const T *__restrict__ tab, int tab_i0, int ntab,
+             int overlap_corr, float rc, const double *__restrict__ X, int m,
+             double *__restrict__ Y)
+{
+    extern __shared__ __align__(16) unsigned char mf_smem[];
+    T *ys = (T *)mf_smem;                          // [3m][kMfRows]
+    T *xs = ys + (size_t)3 * m * kMfRows;          // [kMfRows][3m]
+    const int tid = threadIdx.x;
+    const int nu = blockIdx.x * kMfRows + tid;
+    const long n3 = 3L * n;
+    const int w = 3 * m;
+    for (int i = tid; i < w * kMfRows; i += kMfRows) ys[i] = (T)0;
+    for (int j0 = 0; j0 < n; j0 += kMfRows) {
+        __syncthreads();
+        for (int e = tid; e < kMfRows * w; e += kMfRows) {
+            const int j = e / w, r = e % w, col = r / 3, b = r % 3, mu = j0 + j;
+            xs[e] = mu < n ? (T)X[(long)col * n3 + 3L * mu + b] : (T)0;
+        }
+        __syncthreads();
+        if (nu < n) {
+            const int jn = min(kMfRows, n - j0);
+            for (int j = 0; j < jn; j++) {
+                T acc[6] = {0, 0, 0, 0, 0, 0};
+                pair_real<T>(pw, pw32, n3, nu, j0 + j, c, tab, tab_i0, ntab, overlap_corr, rc, acc);
+                const T *x = xs + (size_t)j * w;
+                for (int col = 0; col < m; col++) {
+                    const T x0 = x[3 * col], x1 = x[3 * col + 1], x2 = x[3 * col + 2];
+                    T *y = ys + (size_t)(3 * col) * kMfRows + tid;
+                    y[0] += acc[0] * x0 + acc[1] * x1 + acc[2] * x2;
+                    y[kMfRows] += acc[1] * x0 + acc[3] * x1 + acc[4] * x2;
+                    y[2 * kMfRows] += acc[2] * x0 + acc[4] * x1 + acc[5] * x2;
+                }
+            }
+        }
+    }
+    if (nu < n)
+        for (int col = 0; col < m; col++)
+            for (int a = 0; a < 3; a++)
+                Y[(long)col * n3 + 3L * nu + a] = (double)ys[(size_t)(3 * col + a) * kMfRows + tid];
+}
+
+// S[(t m + col) 6 + {0,1,2}] = sum_mu cos_t(mu) x_mu[b], {3,4,5}: the sine sums;
+// one block per (k, column), fixed-order block reduction
+template <typename T>
+__global__ void k_struct_factor(const T *__restrict__ cs, const T *__restrict__ sn, int n,
+                                const double *__restrict__ X, int m, T *__restrict__ S)
+{
+    __shared__ T red[6][8];
+    const int t = blockIdx.x, col = blockIdx.y;
+    const long n3 = 3L * n;
+    T v[6] = {0, 0, 0, 0, 0, 0};
+    for (int mu = threadIdx.x; mu < n; mu += blockDim.x) {
+        const T cm = cs[(size_t)t * n + mu], sm = sn[(size_t)t * n + mu];
+#pragma unroll
+        for (int b = 0; b < 3; b++) {
+            const T x = (T)X[(long)col * n3 + 3L * mu + b];
+            v[b] += cm * x;
+            v[3 + b] += sm * x;
+        }
+    }
+    const int lane = threadIdx.x & 31, wp = threadIdx.x >> 5;
+#pragma unroll
+    for (int q = 0; q < 6; q++) {
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) v[q] += __shfl_xor_sync(0xffffffffu, v[q], o);
+        if (lane == 0) red[q][wp] = v[q];
+    }
+    __syncthreads();
+    if (threadIdx.x < 6) {
+        T a = (T)0;
+        for (int i = 0; i < (int)(blockDim.x >> 5); i++) a += red[threadIdx.x][i];
+        S[((size_t)t * m + col) * 6 + threadIdx.x] = a;
+    }
+}
+
+// Y[col][3 nu + a] += sum_k sum_b m_k[ab] (cos_nu S^c_k[col][b] + sin_nu S^s_k[col][b])
+template <typename T>
+__global__ void k_recip_apply(const T *__restrict__ cs, const T *__restrict__ sn,
+                              const T *__restrict__ km, int nk, const T *__restrict__ S, int m,
+                              int n, double *__restrict__ Y)
+{
+    const int nu = blockIdx.x * blockDim.x + threadIdx.x, col = blockIdx.y;
+    if (nu >= n) return;
+    T y0 = 0, y1 = 0, y2 = 0;
+    for (int t = 0; t < nk; t++) {
+        const T cn = cs[(size_t)t * n + nu], sv = sn[(size_t)t * n + nu];
+        const T *sf = S + ((size_t)t * m + col) * 6;
+        const T q0 = cn * sf[0] + sv * sf[3], q1 = cn * sf[1] + sv * sf[4],
+                q2 = cn * sf[2] + sv * sf[5];
+        const T *mk = km + 12 * (size_t)t;
+        y0 += mk[0] * q0 + mk[1] * q1 + mk[2] * q2;
+        y1 += mk[1] * q0 + mk[3] * q1 + mk[4] * q2;
+        y2 += mk[2] * q0 + mk[4] * q1 + mk[5] * q2;
+    }
+    const long n3 = 3L * n;
+    double *out = Y + (long)col * n3 + 3L * nu;
+    out[0] += (double)y0;
+    out[1] += (double)y1;
+    out[2] += (double)y2;
+}
+
+size_t matfree_smem(const Plan &P, int m)
+{
+    return (size_t)6 * m * kMfRows * (is_mixed(P) ? sizeof(float) : sizeof(double));
+}
+
+bd_status matfree_init(Plan &P)
+{
+    if (P.d_sfac) return BD_OK;
+    size_t cnt = (size_t)(P.nk > 0 ? P.nk : 1) * (P.p.max_rhs + 3) * 6 + 8;
+    size_t wn = (size_t)P.n3 * P.p.max_rhs;
+    cudaError_t e = cudaMalloc(&P.d_sfac, cnt * sizeof(double));
+    if (e == cudaSuccess) e = cudaMalloc(&P.d_mfW, wn * sizeof(double));
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return set_error(BD_ERR_OOM, "matrix-free scratch: %s", cudaGetErrorString(e));
+    }
+    P.scratch_bytes += (int64_t)((cnt + wn) * sizeof(double));
+    cudaFuncSetAttribute(k_pair_apply<double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         227 * 1024);
+    cudaFuncSetAttribute(k_pair_apply<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         227 * 1024);
+    return check_launch("matrix-free init");
+}
+
+void launch_matfree_tables(Plan &P, const double *R, cudaStream_t s)
+{
+    launch_trig_tables(P, R, s);
+    launch_wrap(P, R, s);
+}
+
+bd_status launch_apply_matfree(Plan &P, const double *X, int m, double *Y, cudaStream_t s)
+{
+    bd_status st = matfree_init(P);
+    if (st != BD_OK) return st;
+    const size_t sm = matfree_smem(P, m);
+    if (sm > 227 * 1024)
+        return set_error(BD_ERR_UNSUPPORTED, "matrix-free product: m = %d columns need %zu bytes "
+                         "of shared memory", m, sm);
+    const unsigned nb = (unsigned)((P.n + kMfRows - 1) / kMfRows);
+    if (!is_mixed(P)) {
+        k_pair_apply<double><<<nb, kMfRows, sm, s>>>(P.d_pw64, P.d_pw32, P.n, P.h_ew64, P.d_tab,
+                                                     P.tab_i0, P.ntab, P.p.overlap_corr,
+                                                     (float)P.p.r_c, X, m, Y);
+        count_launches(1);
+        if (P.nk > 0) {
+            double *S = (double *)P.d_sfac;
+            k_struct_factor<double><<<dim3(P.nk, m), 256, 0, s>>>(P.d_cos, P.d_sin, P.n, X, m, S);
+            k_recip_apply<double><<<dim3((P.n + 127) / 128, m), 128, 0, s>>>(
+                P.d_cos, P.d_sin, P.d_km64, P.nk, S, m, P.n, Y);
+            count_launches(2);
+        }
+    } else {
+        k_pair_apply<float><<<nb, kMfRows, sm, s>>>(P.d_pw64, P.d_pw32, P.n, P.h_ew32, P.d_tab32,
+                                                    P.tab_i0, P.ntab, P.p.overlap_corr,
+                                                    (float)P.p.r_c, X, m, Y);
+        count_launches(1);
+        if (P.nk > 0) {
+            float *S = (float *)P.d_sfac;
+            k_struct_factor<float><<<dim3(P.nk, m), 256, 0, s>>>(P.d_cos32, P.d_sin32, P.n, X, m, S);
+            k_recip_apply<float><<<dim3((P.n + 127) / 128, m), 128, 0, s>>>(
+                P.d_cos32, P.d_sin32, P.d_km32, P.nk, S, m, P.n, Y);
+            count_launches(2);
+        }
+    }
+    return check_launch("matrix-free product");
 }
 
 }  // namespace bd

@@ -360,13 +360,21 @@ k_tc_gemm(const __grid_constant__ CUtensorMap mapD, const __grid_constant__ CUte
             double y[BN];
 #pragma unroll
             for (int cc = 0; cc < BN; cc++) y[cc] = 0.0;
-            for (int sp = 0; sp < nslots; sp++) {
-                const float4 *src =
-                    (const float4 *)(part + (((size_t)mb * maxslots + sp) * BM + r) * BN);
+            for (int sp0 = 0; sp0 < nslots; sp0 += 2) {
+                // two slots per round, all loads of a round issued together
 #pragma unroll
-                for (int cc = 0; cc < BN / 4; cc++) {
-                    float4 v = __ldcg(src + cc);
-                    y[4 * cc] += v.x; y[4 * cc + 1] += v.y; y[4 * cc + 2] += v.z; y[4 * cc + 3] += v.w;
+                for (int h = 0; h < 2; h++) {
+                    const int sp = sp0 + h;
+                    if (sp < nslots) {
+                        const float4 *src =
+                            (const float4 *)(part + (((size_t)mb * maxslots + sp) * BM + r) * BN);
+#pragma unroll
+                        for (int cc = 0; cc < BN / 4; cc++) {
+                            float4 v = __ldcg(src + cc);
+                            y[4 * cc] += v.x; y[4 * cc + 1] += v.y;
+                            y[4 * cc + 2] += v.z; y[4 * cc + 3] += v.w;
+                        }
+                    }
                 }
             }
             double lw = 0.0;                          // this row of D q_j (Lanczos column)
@@ -379,26 +387,46 @@ k_tc_gemm(const __grid_constant__ CUtensorMap mapD, const __grid_constant__ CUte
                     const double dmin = e.bounds[0], dmax = e.bounds[1];
                     const double ys = 2.0 / (dmax - dmin), yt = (dmax + dmin) / (dmax - dmin);
                     const double cp = e.coef[e.p];
+                    // columns in chunks of 8: every load of a chunk is issued
+                    // before its stores (the vectors may alias as far as the
+                    // compiler knows, so loads do not move above earlier stores)
+                    constexpr int CH = 8;
 #pragma unroll
-                    for (int cc = 0; cc < BN; cc++) {
-                        if (cc == e.lan_col) {
-                            lw = y[cc] * (double)e.inv_scale[cc];
-                            e.lan_w[row] = lw;
+                    for (int c0 = 0; c0 < BN; c0 += CH) {
+                        double p1[CH], p2[CH], d0[CH];
+#pragma unroll
+                        for (int q = 0; q < CH; q++) {
+                            const int cc = c0 + q;
+                            if (cc < e.m) {
+                                const long o = (long)cc * n3 + row;
+                                p1[q] = __ldcg(e.Vprev1 + o);
+                                p2[q] = __ldcg(e.Vprev2 + o);
+                                d0[q] = __ldcg(e.dS + o);
+                            }
                         }
-                        if (cc < e.m) {
-                            long o = (long)cc * n3 + row;
-                            double w = y[cc] * (double)e.inv_scale[cc];
-                            double v = 2.0 * (ys * w - yt * e.Vprev1[o]) - e.Vprev2[o];
-                            e.Vprev2[o] = v;
-                            e.dS[o] += cp * v;
-                            float sv = (float)(v * (double)e.scale[cc]);
-                            size_t xo = (size_t)cc * e.ldx + row;
-                            if (e.is_bf16) ((__nv_bfloat16 *)e.X16next)[xo] = __float2bfloat16_rn(sv);
-                            else ((__half *)e.X16next)[xo] = __float2half_rn(sv);
+#pragma unroll
+                        for (int q = 0; q < CH; q++) {
+                            const int cc = c0 + q;
+                            // a select, not a branch: a branch on cc == lan_col
+                            // becomes y[lan_col] and sends y to local memory
+                            const double yv = y[cc];
+                            lw = (cc == e.lan_col) ? yv * (double)e.inv_scale[cc] : lw;
+                            if (cc < e.m) {
+                                const long o = (long)cc * n3 + row;
+                                const double w = y[cc] * (double)e.inv_scale[cc];
+                                const double v = 2.0 * (ys * w - yt * p1[q]) - p2[q];
+                                e.Vprev2[o] = v;
+                                e.dS[o] = d0[q] + cp * v;
+                                float sv = (float)(v * (double)e.scale[cc]);
+                                size_t xo = (size_t)cc * e.ldx + row;
+                                if (e.is_bf16) ((__nv_bfloat16 *)e.X16next)[xo] = __float2bfloat16_rn(sv);
+                                else ((__half *)e.X16next)[xo] = __float2half_rn(sv);
+                            }
                         }
                     }
                 }
             }
+            if (e.mode == 1 && e.lan_col >= 0 && row < n3) e.lan_w[row] = lw;
             if (e.mode == 1 && e.lan_col >= 0) {
                 // this row block's share of q_j.w, q_{j-1}.w and w.w, reduced in
                 // a fixed order (deterministic)

@@ -181,6 +181,29 @@ void launch_cheb_first(Plan &P, const double *bounds, const double *dW, const do
     count_launches(1);
 }
 
+// one Chebyshev term from a plain product W = D V_{p-1} (matrix-free steps):
+// V_p = 2 (s W - t V_{p-1}) - V_{p-2} over V_{p-2}, dS += c_p V_p
+__global__ void k_cheb_term(const double *W, const double *V1, double *V2, long len,
+                            const double *bounds, const double *coef, int p, double *dS)
+{
+    long i = (long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= len) return;
+    double dmin = bounds[0], dmax = bounds[1];
+    double ys = 2.0 / (dmax - dmin), yt = (dmax + dmin) / (dmax - dmin);
+    double v = 2.0 * (ys * W[i] - yt * V1[i]) - V2[i];
+    V2[i] = v;
+    dS[i] += coef[p] * v;
+}
+
+void launch_cheb_term(Plan &P, const double *W, const double *V1, double *V2, int m,
+                      const double *bounds, int p, double *dS, cudaStream_t s)
+{
+    long len = (long)P.n3 * m;
+    k_cheb_term<<<(unsigned)((len + 255) / 256), 256, 0, s>>>(W, V1, V2, len, bounds, P.d_coef, p,
+                                                              dS);
+    count_launches(1);
+}
+
 // Deterministic column dot products: block b writes its partial sum of
 // column j to part[j * kRedBlocks + b]; one warp per column then adds the
 // partials in block order.  No atomics, so every run gives the same bits.
