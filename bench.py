@@ -352,9 +352,17 @@ def measure(args, precision, p, R0, rank, ws):
                 "algorithmic_per_launch": f"2*(3N)^2*m = {flops:.3e} flop",
                 "launch_ms": cheb_launch_ms, "launches_timed": prod_n}
     else:
-        bytes_ = n3 * n3 * 2.0 + n3 * args.m * (2 + 2 + 8 * 5)
+        lag = args.bounds == "lagged"
+        cols = args.m + (1 if lag else 0)
+        bn = 16 if cols <= 16 else 32
+        cps = (shape or {}).get("ctas_per_sm") or 2
+        st = (224 * 1024 if cps == 1 else 110 * 1024) // (128 * 64 * 2 + bn * 64 * 2)
+        # 16-bit D once, the 16-bit operand in and out, V_{p-1}, V_{p-2}, dS
+        # read and V_p, dS written (FP64), the Lanczos column's q_j, q_{j-1}
+        # read and w written
+        bytes_ = n3 * n3 * 2.0 + n3 * args.m * (2 + 2 + 8 * 5) + (n3 * (2 + 8 * 3) if lag else 0)
         achieved = bytes_ / (cheb_launch_ms * 1e-3) / 1e9
-        roof = {"bound": "hbm", "kernel": "k_tc_gemm<16> (Chebyshev epilogue)",
+        roof = {"bound": "hbm", "kernel": f"k_tc_gemm<{bn},{st}> (stream-K, Chebyshev epilogue)",
                 "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
                 "frac": achieved / peaks["hbm_gbs"],
                 "peak_source": f"hbm_gbs ({peak_src} copy bandwidth)",

@@ -124,6 +124,8 @@ struct Plan {
     // matrix-free products (allocated by the first one)
     void *d_sfac;                      // structure factors [nk][max_rhs + 3][6] (working precision)
     double *d_mfW;                     // product scratch of matrix-free Chebyshev terms (3N x max_rhs)
+    double *d_mfpart;                  // per-chunk partial products [chunks][3N x (max_rhs + 3)]
+    int mf_chunks;                     // chunks of the bead loop in one matrix-free product
     const double *matfree_R;           // set inside a matrix-free step: products recompute D(R)
     // adaptive N_Ch (allocated by the first adaptive call)
     double *d_mom;                     // moments, dot partials, estimates, D V scratch

@@ -639,7 +639,7 @@ __global__ void __launch_bounds__(kMfRows)
 k_pair_apply(const double *__restrict__ pw, const float *__restrict__ pw32, int n,
              const __grid_constant__ EwaldT<T> c, const T *__restrict__ tab, int tab_i0, int ntab,
              int overlap_corr, float rc, const double *__restrict__ X, int m,
-             double *__restrict__ Y)
+             double *__restrict__ Y, int nchunk, double *__restrict__ part)
 {
     extern __shared__ __align__(16) unsigned char mf_smem[];
     T *ys = (T *)mf_smem;                          // [3m][kMfRows]
@@ -648,16 +648,18 @@ k_pair_apply(const double *__restrict__ pw, const float *__restrict__ pw32, int 
     const int nu = blockIdx.x * kMfRows + tid;
     const long n3 = 3L * n;
     const int w = 3 * m;
+    // this block's share of the beads mu (chunk blockIdx.y of nchunk)
+    const int mlo = (int)((long)n * blockIdx.y / nchunk), mhi = (int)((long)n * (blockIdx.y + 1) / nchunk);
     for (int i = tid; i < w * kMfRows; i += kMfRows) ys[i] = (T)0;
-    for (int j0 = 0; j0 < n; j0 += kMfRows) {
+    for (int j0 = mlo; j0 < mhi; j0 += kMfRows) {
         __syncthreads();
         for (int e = tid; e < kMfRows * w; e += kMfRows) {
             const int j = e / w, r = e % w, col = r / 3, b = r % 3, mu = j0 + j;
-            xs[e] = mu < n ? (T)X[(long)col * n3 + 3L * mu + b] : (T)0;
+            xs[e] = mu < mhi ? (T)X[(long)col * n3 + 3L * mu + b] : (T)0;
         }
         __syncthreads();
         if (nu < n) {
-            const int jn = min(kMfRows, n - j0);
+            const int jn = min(kMfRows, mhi - j0);
             for (int j = 0; j < jn; j++) {
                 T acc[6] = {0, 0, 0, 0, 0, 0};
                 pair_real<T>(pw, pw32, n3, nu, j0 + j, c, tab, tab_i0, ntab, overlap_corr, rc, acc);
@@ -672,10 +674,22 @@ k_pair_apply(const double *__restrict__ pw, const float *__restrict__ pw32, int 
             }
         }
     }
+    double *out = nchunk > 1 ? part + (size_t)blockIdx.y * n3 * m : Y;
     if (nu < n)
         for (int col = 0; col < m; col++)
             for (int a = 0; a < 3; a++)
-                Y[(long)col * n3 + 3L * nu + a] = (double)ys[(size_t)(3 * col + a) * kMfRows + tid];
+                out[(long)col * n3 + 3L * nu + a] = (double)ys[(size_t)(3 * col + a) * kMfRows + tid];
+}
+
+// Y = sum over chunks of the partial products, in chunk order (deterministic)
+__global__ void k_sum_chunks(const double *__restrict__ part, int nchunk, long len,
+                             double *__restrict__ Y)
+{
+    long i = (long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= len) return;
+    double v = 0.0;
+    for (int c = 0; c < nchunk; c++) v += part[(size_t)c * len + i];
+    Y[i] = v;
 }
 
 // S[(t m + col) 6 + {0,1,2}] = sum_mu cos_t(mu) x_mu[b], {3,4,5}: the sine sums;
@@ -743,9 +757,31 @@ size_t matfree_smem(const Plan &P, int m)
     return (size_t)6 * m * kMfRows * (is_mixed(P) ? sizeof(float) : sizeof(double));
 }
 
+// mu chunks of the matrix-free product: enough blocks for ~4 per SM
+static int matfree_chunks(const Plan &P)
+{
+    const int rows = (P.n + kMfRows - 1) / kMfRows;
+    int c = (4 * (P.num_sms > 0 ? P.num_sms : 152) + rows - 1) / rows;
+    const int cap = P.n / kMfRows;               // at least one row tile of beads per chunk
+    if (c > cap) c = cap;
+    if (c > 32) c = 32;
+    return c < 1 ? 1 : c;
+}
+
 bd_status matfree_init(Plan &P)
 {
     if (P.d_sfac) return BD_OK;
+    if (P.num_sms <= 0) cudaDeviceGetAttribute(&P.num_sms, cudaDevAttrMultiProcessorCount, P.device);
+    P.mf_chunks = matfree_chunks(P);
+    if (P.mf_chunks > 1) {
+        size_t pc = (size_t)P.mf_chunks * P.n3 * (P.p.max_rhs + 3);
+        cudaError_t e = cudaMalloc(&P.d_mfpart, pc * sizeof(double));
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            return set_error(BD_ERR_OOM, "matrix-free partials: %s", cudaGetErrorString(e));
+        }
+        P.scratch_bytes += (int64_t)(pc * sizeof(double));
+    }
     size_t cnt = (size_t)(P.nk > 0 ? P.nk : 1) * (P.p.max_rhs + 3) * 6 + 8;
     size_t wn = (size_t)P.n3 * P.p.max_rhs;
     cudaError_t e = cudaMalloc(&P.d_sfac, cnt * sizeof(double));
@@ -776,12 +812,18 @@ bd_status launch_apply_matfree(Plan &P, const double *X, int m, double *Y, cudaS
     if (sm > 227 * 1024)
         return set_error(BD_ERR_UNSUPPORTED, "matrix-free product: m = %d columns need %zu bytes "
                          "of shared memory", m, sm);
-    const unsigned nb = (unsigned)((P.n + kMfRows - 1) / kMfRows);
+    const dim3 nb((unsigned)((P.n + kMfRows - 1) / kMfRows), (unsigned)P.mf_chunks);
+    const long len = (long)P.n3 * m;
     if (!is_mixed(P)) {
         k_pair_apply<double><<<nb, kMfRows, sm, s>>>(P.d_pw64, P.d_pw32, P.n, P.h_ew64, P.d_tab,
                                                      P.tab_i0, P.ntab, P.p.overlap_corr,
-                                                     (float)P.p.r_c, X, m, Y);
+                                                     (float)P.p.r_c, X, m, Y, P.mf_chunks,
+                                                     P.d_mfpart);
         count_launches(1);
+        if (P.mf_chunks > 1) {
+            k_sum_chunks<<<(unsigned)((len + 255) / 256), 256, 0, s>>>(P.d_mfpart, P.mf_chunks, len, Y);
+            count_launches(1);
+        }
         if (P.nk > 0) {
             double *S = (double *)P.d_sfac;
             k_struct_factor<double><<<dim3(P.nk, m), 256, 0, s>>>(P.d_cos, P.d_sin, P.n, X, m, S);
@@ -792,8 +834,13 @@ bd_status launch_apply_matfree(Plan &P, const double *X, int m, double *Y, cudaS
     } else {
         k_pair_apply<float><<<nb, kMfRows, sm, s>>>(P.d_pw64, P.d_pw32, P.n, P.h_ew32, P.d_tab32,
                                                     P.tab_i0, P.ntab, P.p.overlap_corr,
-                                                    (float)P.p.r_c, X, m, Y);
+                                                    (float)P.p.r_c, X, m, Y, P.mf_chunks,
+                                                    P.d_mfpart);
         count_launches(1);
+        if (P.mf_chunks > 1) {
+            k_sum_chunks<<<(unsigned)((len + 255) / 256), 256, 0, s>>>(P.d_mfpart, P.mf_chunks, len, Y);
+            count_launches(1);
+        }
         if (P.nk > 0) {
             float *S = (float *)P.d_sfac;
             k_struct_factor<float><<<dim3(P.nk, m), 256, 0, s>>>(P.d_cos32, P.d_sin32, P.n, X, m, S);
