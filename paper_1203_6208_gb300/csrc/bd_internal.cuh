@@ -132,9 +132,9 @@ struct Plan {
     double *h_est;                     // pinned host words read back per candidate N
     // reciprocal sum as a tensor-core product (mixed plans, recip_tc.cu)
     int recip_tc;                      // 1: D32's upper tiles are filled by U U^T first
-    int recip_kp;                      // columns of U (4 per k-vector, padded to 32)
+    int recip_kp;                      // columns of U (4 per k-vector, padded to 64)
     int recip_ntiles;                  // 128 x 128 tiles on and above the diagonal
-    float *d_Uh, *d_Ul;                // U as TF32 hi/lo words [3N][recip_kp]
+    __half *d_Uh, *d_Ul;               // U as hi/lo words, half(word 2^8) [3N][recip_kp]
     int2 *d_rtiles;                    // tile list
 };
 

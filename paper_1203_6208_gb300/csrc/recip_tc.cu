@@ -7,10 +7,14 @@
 // is one symmetric product D_rec = U U^T,
 //   U[3 nu + a][4 t + 2 (c-1) + s] = sqrt(2 f_t) u_c^a(k_t) {cos, sin}(k_t . r_nu),
 // a rank-4 N_k contraction over all bead pairs -- dense work for the tensor
-// cores.  U is split into TF32 words U = Uh + Ul (each exactly representable
-// in TF32) and D_rec = Uh Uh^T + Uh Ul^T + Ul Uh^T is accumulated in FP32 in
-// TMEM (kind::tf32, M = N = 128, K = 8 per MMA): about 2^-21 relative per
-// term, below the FP32 assembly's own rounding.  The product fills the
+// cores.  U is split into two words U = Uh + Ul of 11 significant bits each
+// (Uh the TF32 rounding of U, Ul that of the remainder), stored as IEEE half
+// scaled by 2^8 (both words are exact in half over the range of U, which is
+// below 1; words under 2^-14 / 2^8 lose bits as subnormals, an absolute error
+// ~1e-10), and D_rec = Uh Uh^T + Uh Ul^T + Ul Uh^T is accumulated in FP32 in
+// TMEM (kind::f16, M = N = 128, K = 16 per MMA -- twice the TF32 rate) and
+// scaled by 2^-16 on the way out: about 2^-21 relative per term, below the
+// FP32 assembly's own rounding.  The product fills the
 // 128 x 128 tiles of D32 on and above the diagonal; the pair kernel reads the
 // six components (a <= b) of each 3 x 3 block it owns there (always row <=
 // column), adds the real-space, self and overlap terms and writes the final
@@ -25,10 +29,12 @@ namespace bd {
 
 namespace rt {
 
-constexpr int BM = 128, BN = 128, BK = 32;     // BK in TF32 elements (128 bytes)
+constexpr int BM = 128, BN = 128, BK = 64;     // BK in half elements (128 bytes)
 constexpr int STAGES = 3;
 constexpr int THREADS = 192;
-constexpr int TILE_BYTES = BM * BK * 4;        // 16 KB per operand tile
+constexpr int TILE_BYTES = BM * BK * 2;        // 16 KB per operand tile
+constexpr float kUScale = 256.f;               // U words stored as half(U 2^8)
+constexpr float kDUnscale = 1.f / (256.f * 256.f);
 constexpr uint32_t kWaitLimit = 1u << 22;
 
 __device__ __forceinline__ uint32_t smem_u32(const void *p)
@@ -96,17 +102,16 @@ __device__ __forceinline__ uint64_t sw128_desc(uint32_t addr)
     d |= (uint64_t)2 << 61;
     return d;
 }
-// kind::tf32: F32 accumulator, TF32 A and B, K-major, M = N = 128
-constexpr uint32_t kIdesc = (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(BN >> 3) << 17) |
-                            ((uint32_t)(BM >> 4) << 24);
+// kind::f16: F32 accumulator, F16 A and B, K-major, M = N = 128
+constexpr uint32_t kIdesc = (1u << 4) | ((uint32_t)(BN >> 3) << 17) | ((uint32_t)(BM >> 4) << 24);
 
-__device__ __forceinline__ void mma_tf32(uint32_t tmem_d, uint64_t da, uint64_t db,
-                                         uint32_t accumulate)
+__device__ __forceinline__ void mma_f16(uint32_t tmem_d, uint64_t da, uint64_t db,
+                                        uint32_t accumulate)
 {
     asm volatile(
         "{\n\t.reg .pred p;\n\t"
         "setp.ne.b32 p, %4, 0;\n\t"
-        "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem_d),
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem_d),
         "l"(da), "l"(db), "r"(kIdesc), "r"(accumulate)
         : "memory");
 }
@@ -206,8 +211,8 @@ k_recip_syrk(const __grid_constant__ CUtensorMap mapH, const __grid_constant__ C
             uint32_t a = smem_u32(smem + s * STAGE), b = a + TILE_BYTES;
             uint64_t da = sw128_desc(a), db = sw128_desc(b);
 #pragma unroll
-            for (int k = 0; k < BK / 8; k++)      // 8 TF32 = 32 bytes per MMA along K
-                mma_tf32(tmem, da + (uint64_t)(2 * k), db + (uint64_t)(2 * k),
+            for (int k = 0; k < BK / 16; k++)     // 16 halves = 32 bytes per MMA along K
+                mma_f16(tmem, da + (uint64_t)(2 * k), db + (uint64_t)(2 * k),
                          (i > 0 || k > 0) ? 1u : 0u);
             mma_commit(smem_u32(&empty_bar[s]));
         }
@@ -225,6 +230,8 @@ k_recip_syrk(const __grid_constant__ CUtensorMap mapH, const __grid_constant__ C
             for (int c0 = 0; c0 < BN; c0 += 16) {
                 float v[16];
                 tmem_ld16(tmem + ((uint32_t)(q * 32) << 16) + c0, v);
+#pragma unroll
+                for (int c = 0; c < 16; c++) v[c] *= kDUnscale;     // undo the 2^8 word scales
                 const long col = (long)tj * BN + c0;
                 if (row < n3) {
                     float *dst = D32 + row * ld + col;
@@ -254,8 +261,9 @@ k_recip_syrk(const __grid_constant__ CUtensorMap mapH, const __grid_constant__ C
 }  // namespace rt
 
 // U = Uh + Ul for one bead and one half-space k: the columns (c, s) of Eq. DF
-// written as a product; u1, u2 from the k vector (FP64), each word rounded to
-// TF32 (cvt.rna) so that the tensor cores use it exactly.
+// written as a product; u1, u2 from the k vector (FP64).  Uh is U rounded to
+// 11 significant bits (TF32 rounding, cvt.rna) and Ul the same rounding of
+// U - Uh; both are stored as half(word 2^8), exact in the normal range.
 __device__ __forceinline__ float to_tf32(float x)
 {
     uint32_t r;
@@ -264,8 +272,8 @@ __device__ __forceinline__ float to_tf32(float x)
 }
 
 __global__ void k_build_U(const double *__restrict__ cs, const double *__restrict__ sn,
-                          const KVec *__restrict__ kv, int n, int nk, int Kp, float *__restrict__ Uh,
-                          float *__restrict__ Ul)
+                          const KVec *__restrict__ kv, int n, int nk, int Kp, __half *__restrict__ Uh,
+                          __half *__restrict__ Ul)
 {
     const int nu = blockIdx.x * blockDim.x + threadIdx.x;
     const int t = blockIdx.y;
@@ -274,7 +282,7 @@ __global__ void k_build_U(const double *__restrict__ cs, const double *__restric
         for (int a = 0; a < 3; a++)
             for (int j = 0; j < 4; j++) {
                 size_t o = (size_t)(3 * nu + a) * Kp + 4 * t + j;
-                if (4 * t + j < Kp) { Uh[o] = 0.f; Ul[o] = 0.f; }
+                if (4 * t + j < Kp) { Uh[o] = __float2half_rn(0.f); Ul[o] = __float2half_rn(0.f); }
             }
         return;
     }
@@ -301,8 +309,8 @@ __global__ void k_build_U(const double *__restrict__ cs, const double *__restric
             float h = to_tf32((float)vals[j]);
             float l = to_tf32((float)(vals[j] - (double)h));
             size_t o = (size_t)(3 * nu + a) * Kp + 4 * t + j;
-            Uh[o] = h;
-            Ul[o] = l;
+            Uh[o] = __float2half_rn(h * rt::kUScale);
+            Ul[o] = __float2half_rn(l * rt::kUScale);
         }
     }
 }
@@ -342,7 +350,7 @@ bd_status recip_tc_init(Plan &P)
     const int T = (P.n3 + rt::BM - 1) / rt::BM;
     std::vector<int2> tiles;
     P.recip_ntiles = upper_tiles(T, &tiles);
-    size_t ub = (size_t)P.n3 * P.recip_kp * sizeof(float);
+    size_t ub = (size_t)P.n3 * P.recip_kp * sizeof(__half);
     cudaError_t e = cudaMalloc(&P.d_Uh, ub);
     if (e == cudaSuccess) e = cudaMalloc(&P.d_Ul, ub);
     if (e == cudaSuccess) e = cudaMalloc(&P.d_rtiles, tiles.size() * sizeof(int2));
@@ -360,13 +368,13 @@ bd_status recip_tc_init(Plan &P)
     return BD_OK;
 }
 
-static bd_status map_U(CUtensorMap *m, const float *base, int Kp, int n3)
+static bd_status map_U(CUtensorMap *m, const __half *base, int Kp, int n3)
 {
     cuuint64_t dims[2] = {(cuuint64_t)Kp, (cuuint64_t)n3};
-    cuuint64_t strides[1] = {(cuuint64_t)Kp * 4};
+    cuuint64_t strides[1] = {(cuuint64_t)Kp * 2};
     cuuint32_t box[2] = {rt::BK, rt::BM};
     cuuint32_t es[2] = {1, 1};
-    CUresult r = g_enc(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<float *>(base), dims,
+    CUresult r = g_enc(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT16, 2, const_cast<__half *>(base), dims,
                        strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
                        CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     if (r != CUDA_SUCCESS) return set_error(BD_ERR_CUDA, "tensor map for U (%d)", (int)r);
