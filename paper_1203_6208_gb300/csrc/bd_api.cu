@@ -75,7 +75,7 @@ static void free_plan(Plan &P)
                     P.d_coef, P.d_wdw, P.d_red, P.d_redpart, P.d_bounds, P.d_status, P.d_lq[0], P.d_lq[1],
                     P.d_lq[2], P.d_lab, P.d_x16, P.d_xscale, P.d_part, P.d_counters,
                     P.d_stats_scratch, P.d_y32, P.d_lag_bounds, P.d_step_ctr, P.d_vhist, P.d_xhist, P.d_ubuf[0], P.d_ubuf[1],
-                    P.d_ubuf[2], P.d_ubuf[3], P.d_Uh, P.d_Ul, P.d_rtiles, P.d_lanpart, P.d_mom, P.d_sfac, P.d_mfW, P.d_mfpart};
+                    P.d_ubuf[2], P.d_ubuf[3], P.d_Uh, P.d_Ul, P.d_rtiles, P.d_kbasis, P.d_lanpart, P.d_mom, P.d_sfac, P.d_mfW, P.d_mfpart};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     if (P.h_est) cudaFreeHost(P.h_est);

@@ -136,6 +136,7 @@ struct Plan {
     int recip_ntiles;                  // 128 x 128 tiles on and above the diagonal
     __half *d_Uh, *d_Ul;               // U as hi/lo words, half(word 2^8) [3N][recip_kp]
     int2 *d_rtiles;                    // tile list
+    float *d_kbasis;                   // per k: w u1, w u2 (FP32) [nk][8]
 };
 
 inline bool is_mixed(const Plan &P) { return P.p.precision != BD_FP64; }

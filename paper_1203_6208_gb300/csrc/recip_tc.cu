@@ -271,21 +271,13 @@ __device__ __forceinline__ float to_tf32(float x)
     return __uint_as_float(r);
 }
 
-__global__ void k_build_U(const double *__restrict__ cs, const double *__restrict__ sn,
-                          const KVec *__restrict__ kv, int n, int nk, int Kp, __half *__restrict__ Uh,
-                          __half *__restrict__ Ul)
+// per half-space k: w u1 and w u2 (w = sqrt(2 f), u1, u2 orthonormal and
+// perpendicular to k), computed once per plan in FP64 and kept in FP32:
+// basis[8 t + a] = w u1_a, basis[8 t + 3 + a] = w u2_a
+__global__ void k_kbasis(const KVec *__restrict__ kv, int nk, float *__restrict__ basis)
 {
-    const int nu = blockIdx.x * blockDim.x + threadIdx.x;
-    const int t = blockIdx.y;
-    if (nu >= n) return;
-    if (t >= nk) {                       // zero padding columns of this k group
-        for (int a = 0; a < 3; a++)
-            for (int j = 0; j < 4; j++) {
-                size_t o = (size_t)(3 * nu + a) * Kp + 4 * t + j;
-                if (4 * t + j < Kp) { Uh[o] = __float2half_rn(0.f); Ul[o] = __float2half_rn(0.f); }
-            }
-        return;
-    }
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= nk) return;
     const KVec &K = kv[t];
     double k2 = K.k[0] * K.k[0] + K.k[1] * K.k[1] + K.k[2] * K.k[2];
     double kn = sqrt(k2);
@@ -302,16 +294,52 @@ __global__ void k_build_U(const double *__restrict__ cs, const double *__restric
     double n1 = sqrt(u1[0] * u1[0] + u1[1] * u1[1] + u1[2] * u1[2]);
     for (int i = 0; i < 3; i++) u1[i] /= n1;
     double u2[3] = {kh[1] * u1[2] - kh[2] * u1[1], kh[2] * u1[0] - kh[0] * u1[2], kh[0] * u1[1] - kh[1] * u1[0]};
-    double c = cs[(size_t)t * n + nu], s = sn[(size_t)t * n + nu];
-    for (int a = 0; a < 3; a++) {
-        double vals[4] = {w * u1[a] * c, w * u1[a] * s, w * u2[a] * c, w * u2[a] * s};
-        for (int j = 0; j < 4; j++) {
-            float h = to_tf32((float)vals[j]);
-            float l = to_tf32((float)(vals[j] - (double)h));
-            size_t o = (size_t)(3 * nu + a) * Kp + 4 * t + j;
-            Uh[o] = __float2half_rn(h * rt::kUScale);
-            Ul[o] = __float2half_rn(l * rt::kUScale);
+    for (int i = 0; i < 3; i++) {
+        basis[8 * t + i] = (float)(w * u1[i]);
+        basis[8 * t + 3 + i] = (float)(w * u2[i]);
+    }
+    basis[8 * t + 6] = 0.f;
+    basis[8 * t + 7] = 0.f;
+}
+
+// U rows of one bead for one k group (4 columns): all FP32 -- the split keeps
+// 22 bits of U, within FP32's 24
+__device__ __forceinline__ uint2 pack4(float a, float b, float c, float d)
+{
+    __half2 x = __floats2half2_rn(a * rt::kUScale, b * rt::kUScale);
+    __half2 y = __floats2half2_rn(c * rt::kUScale, d * rt::kUScale);
+    return make_uint2(*(uint32_t *)&x, *(uint32_t *)&y);
+}
+
+__global__ void k_build_U(const float *__restrict__ cs, const float *__restrict__ sn,
+                          const float *__restrict__ basis, int n, int nk, int Kp,
+                          __half *__restrict__ Uh, __half *__restrict__ Ul)
+{
+    const int nu = blockIdx.x * blockDim.x + threadIdx.x;
+    const int t = blockIdx.y;
+    if (nu >= n) return;
+    if (t >= nk) {                       // zero padding columns of this k group
+        for (int a = 0; a < 3; a++) {
+            size_t o = (size_t)(3 * nu + a) * Kp + 4 * t;
+            *(uint2 *)(Uh + o) = make_uint2(0u, 0u);
+            *(uint2 *)(Ul + o) = make_uint2(0u, 0u);
         }
+        return;
+    }
+    const float c = cs[(size_t)t * n + nu], s = sn[(size_t)t * n + nu];
+    const float *b = basis + 8 * t;
+#pragma unroll
+    for (int a = 0; a < 3; a++) {
+        const float v[4] = {b[a] * c, b[a] * s, b[3 + a] * c, b[3 + a] * s};
+        float h[4], l[4];
+#pragma unroll
+        for (int j = 0; j < 4; j++) {
+            h[j] = to_tf32(v[j]);
+            l[j] = to_tf32(v[j] - h[j]);            // exact difference
+        }
+        size_t o = (size_t)(3 * nu + a) * Kp + 4 * t;
+        *(uint2 *)(Uh + o) = pack4(h[0], h[1], h[2], h[3]);
+        *(uint2 *)(Ul + o) = pack4(l[0], l[1], l[2], l[3]);
     }
 }
 
@@ -353,12 +381,15 @@ bd_status recip_tc_init(Plan &P)
     size_t ub = (size_t)P.n3 * P.recip_kp * sizeof(__half);
     cudaError_t e = cudaMalloc(&P.d_Uh, ub);
     if (e == cudaSuccess) e = cudaMalloc(&P.d_Ul, ub);
+    if (e == cudaSuccess) e = cudaMalloc(&P.d_kbasis, (size_t)8 * P.nk * sizeof(float));
     if (e == cudaSuccess) e = cudaMalloc(&P.d_rtiles, tiles.size() * sizeof(int2));
     if (e != cudaSuccess) {
         cudaGetLastError();
         return set_error(BD_ERR_OOM, "reciprocal product scratch: %s", cudaGetErrorString(e));
     }
-    P.scratch_bytes += (int64_t)(2 * ub + tiles.size() * sizeof(int2));
+    P.scratch_bytes += (int64_t)(2 * ub + tiles.size() * sizeof(int2) + 8 * P.nk * sizeof(float));
+    k_kbasis<<<(P.nk + 127) / 128, 128>>>(P.d_kvec, P.nk, P.d_kbasis);
+    count_launches(1);
     cudaMemcpy(P.d_rtiles, tiles.data(), tiles.size() * sizeof(int2), cudaMemcpyHostToDevice);
     const int sm = rt::STAGES * 2 * rt::TILE_BYTES + 1024;
     if (cudaFuncSetAttribute(rt::k_recip_syrk, cudaFuncAttributeMaxDynamicSharedMemorySize, sm) !=
@@ -386,7 +417,8 @@ bd_status launch_recip_tc(Plan &P, float *D32, cudaStream_t s)
 {
     const int nkgroups = P.recip_kp / 4;             // >= nk, the rest zero
     dim3 gu((P.n + 127) / 128, nkgroups);
-    k_build_U<<<gu, 128, 0, s>>>(P.d_cos, P.d_sin, P.d_kvec, P.n, P.nk, P.recip_kp, P.d_Uh, P.d_Ul);
+    k_build_U<<<gu, 128, 0, s>>>(P.d_cos32, P.d_sin32, P.d_kbasis, P.n, P.nk, P.recip_kp, P.d_Uh,
+                                 P.d_Ul);
     count_launches(1);
     CUtensorMap mh, ml;
     bd_status st = map_U(&mh, P.d_Uh, P.recip_kp, P.n3);

@@ -868,32 +868,43 @@ k_refine(const float *__restrict__ D32, long ld, int n3, const float *__restrict
     const float *d = D32 + (long)row * ld;
     const float *xh = xs, *xl = xs + n3;
     float s = 0.f, c = 0.f;
-    // n3 is a multiple of 3, rows start 256-byte aligned (ld multiple of 64)
-    int k = lane * 4;
-    for (; k + 3 < n3; k += 128) {
-        float4 dv = __ldg((const float4 *)(d + k));
-        float dd[4] = {dv.x, dv.y, dv.z, dv.w};
-#pragma unroll
-        for (int q = 0; q < 4; q++) {
-            float h = __ldg(xh + k + q), l = __ldg(xl + k + q);
-            float p = dd[q] * h;
-            float pe = fmaf(dd[q], h, -p);
-            pe = fmaf(dd[q], l, pe);
-            float t, e;
-            two_sum(s, p, t, e);
-            s = t;
-            c += e + pe;
-        }
-    }
-    for (; k < n3; k++) {             // tail (at most 3 elements per lane)
-        float p = d[k] * xh[k];
-        float pe = fmaf(d[k], xh[k], -p);
-        pe = fmaf(d[k], xl[k], pe);
+    auto term = [&](float dq, float h, float l) {
+        float p = dq * h;
+        float pe = fmaf(dq, h, -p);
+        pe = fmaf(dq, l, pe);
         float t, e;
         two_sum(s, p, t, e);
         s = t;
         c += e + pe;
+    };
+    // rows start 256-byte aligned (ld multiple of 64) and n3 is a multiple of
+    // 3; x is split in two arrays of n3 floats, read as float4 where n3 % 4 == 0
+    int k = lane * 4;
+    if ((n3 & 3) == 0) {
+        const float4 *xh4 = (const float4 *)xh, *xl4 = (const float4 *)xl;
+        // two float4 of D per lane in flight
+        for (; k + 128 + 3 < n3; k += 256) {
+            float4 d0 = __ldcs((const float4 *)(d + k)), d1 = __ldcs((const float4 *)(d + k + 128));
+            float4 h0 = __ldg(xh4 + (k >> 2)), l0 = __ldg(xl4 + (k >> 2));
+            float4 h1 = __ldg(xh4 + ((k + 128) >> 2)), l1 = __ldg(xl4 + ((k + 128) >> 2));
+            term(d0.x, h0.x, l0.x); term(d0.y, h0.y, l0.y); term(d0.z, h0.z, l0.z); term(d0.w, h0.w, l0.w);
+            term(d1.x, h1.x, l1.x); term(d1.y, h1.y, l1.y); term(d1.z, h1.z, l1.z); term(d1.w, h1.w, l1.w);
+        }
+        for (; k + 3 < n3; k += 128) {
+            float4 d0 = __ldcs((const float4 *)(d + k));
+            float4 h0 = __ldg(xh4 + (k >> 2)), l0 = __ldg(xl4 + (k >> 2));
+            term(d0.x, h0.x, l0.x); term(d0.y, h0.y, l0.y); term(d0.z, h0.z, l0.z); term(d0.w, h0.w, l0.w);
+        }
+    } else {
+        for (; k + 3 < n3; k += 128) {
+            float4 dv = __ldcs((const float4 *)(d + k));
+            term(dv.x, __ldg(xh + k), __ldg(xl + k));
+            term(dv.y, __ldg(xh + k + 1), __ldg(xl + k + 1));
+            term(dv.z, __ldg(xh + k + 2), __ldg(xl + k + 2));
+            term(dv.w, __ldg(xh + k + 3), __ldg(xl + k + 3));
+        }
     }
+    for (; k < n3; k++) term(d[k], xh[k], xl[k]);   // tail (at most 3 elements per lane)
     double acc = (double)s + (double)c;
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
