@@ -583,34 +583,62 @@ def run_theta(args):
     print(json.dumps(line), flush=True)
 
 
+def spectral_params(cfg, r_c=6.0, order=8):
+    """Spectral-path parameters for a system: r_c = 6 l_H (alpha = M/r_c), the
+    k-sphere of the same accuracy target, order-8 B-splines on a mesh of
+    3.5 L points per edge (rounded up to 8; the mesh error then sits at the
+    FP32 floor, ~1e-6, by the measured (m_eff/K)^p convergence with
+    m_eff ~ M L/(pi r_c))."""
+    from paper_1203_6208_gb300 import inputs
+    L = cfg.params()["L"]
+    f = cfg.M / r_c * L / inputs.SQRT_PI
+    q = replace_cfg(cfg, alpha_factor=f).params()
+    kmax = math.sqrt(q["n2max"])
+    K = int(math.ceil(3.5 * L / 8.0)) * 8
+    K = max(K, 2 * int(math.ceil(kmax)) + 2)
+    q.update(pme_grid=K + (K % 2), pme_order=order)
+    return q
+
+
+def replace_cfg(cfg, **kw):
+    from dataclasses import replace
+    return replace(cfg, **kw)
+
+
 def run_lma(args):
     """Dense-D steps (HMA, D assembled once per step) against matrix-free
-    steps (LMA, D(R) X recomputed in every product) on the theta workload of
-    the headline (c/c* = 4, 20-bead chains, m = 16, N_Ch = 40, mixed), at
-    N = 8000 and at larger N; dense runs only where D fits in device memory."""
+    steps (LMA, D(R) X recomputed in every product) and spectral matrix-free
+    steps (real space over cell lists, reciprocal sum on a mesh) on the theta
+    workload of the headline (c/c* = 4, 20-bead chains, m = 16, N_Ch = 40,
+    mixed), at N = 8000 and larger N; dense runs only where D fits in device
+    memory, the pair-sum LMA only up to N = 100 000."""
     import torch
     torch.cuda.set_device(0)
     from paper_1203_6208_gb300 import binding as bnd, build, inputs
     build.build()
     free, _ = torch.cuda.mem_get_info()
     res = {}
-    for chains in (400, 1600, 5000):
+    for chains in (400, 1600, 5000, 15000):
         cfg, _ = inputs.preset("c4", alpha_factor=1.75, n_chains=chains)
         p = cfg.params()
         R0 = inputs.make_chains(cfg)
         row = {}
-        for mode in ("dense", "matfree"):
-            plan = bnd.Plan(p, "mixed_f16", max_rhs=args.m, max_cheb=args.nch)
+        for mode in ("dense", "matfree", "spectral"):
+            q = spectral_params(cfg) if mode == "spectral" else p
+            if mode == "matfree" and chains > 5000:
+                row[mode] = {"skipped": "pair-sum LMA too slow at this N"}
+                continue
+            plan = bnd.Plan(q, "mixed_f16", max_rhs=args.m, max_cheb=args.nch)
             if mode == "dense" and plan.info.d_bytes > 0.8 * free:
                 row[mode] = {"skipped": "D needs %.0f GB" % (plan.info.d_bytes / 1e9)}
                 plan.close()
                 continue
             D = plan.alloc_D() if mode == "dense" else None
             R = torch.tensor(R0.reshape(-1), device="cuda")
-            flags = bnd.BD_STEP_MATRIX_FREE if mode == "matfree" else 0
+            flags = 0 if mode == "dense" else bnd.BD_STEP_MATRIX_FREE
             kw = dict(m=args.m, n_cheb=args.nch, bounds_mode=3, fixman_c=8.0, flags=flags,
                       seed=7)
-            reps = 1 if (mode == "matfree" and chains > 400) else 2
+            reps = 1 if (mode != "dense" and chains > 400) else 2
             plan.step(R, D, None, step_index=0, **kw)
             torch.cuda.synchronize()
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -621,13 +649,16 @@ def run_lma(args):
             torch.cuda.synchronize()
             ms = e0.elapsed_time(e1) / reps
             row[mode] = {"ms_per_step": ms, "steps_per_s": 1e3 / ms, "timed_steps": reps}
+            if mode == "spectral":
+                row[mode].update(r_c=q["rc"], n2max=q["n2max"], mesh=q["pme_grid"],
+                                 order=q["pme_order"])
             del D
             plan.close()
             torch.cuda.empty_cache()
         res[f"N={cfg.n}"] = row
     head = res["N=8000"]
-    line = {"metric": "steps/sec, dense D (HMA) vs matrix-free (LMA), mixed",
-            "value": head["matfree"]["steps_per_s"], "unit": "steps/s (matrix-free, N=8000)",
+    line = {"metric": "steps/sec, dense D (HMA) vs matrix-free (LMA) vs spectral, mixed",
+            "value": head["spectral"]["steps_per_s"], "unit": "steps/s (spectral, N=8000)",
             "n_gpus": 1, "steps": args.steps, "warmup": 1, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
             "config": {"workload": "lma", "m": args.m, "n_cheb": args.nch,

@@ -89,6 +89,11 @@ typedef struct {
     int32_t precision;        /* bd_precision                                     */
     int32_t max_rhs;          /* largest m (Wiener columns) any call will use, 1..32 */
     int32_t max_cheb;         /* largest number of Chebyshev terms N_Ch, 2..256   */
+    int32_t pme_grid;         /* > 0: matrix-free products use the spectral path:
+                                 real space over cell lists (needs r_c < L/2) and the
+                                 reciprocal sum on a pme_grid^3 mesh (even, >= 2
+                                 ceil(sqrt(n2max)) + 2, <= 512); 0: off            */
+    int32_t pme_order;        /* B-spline order of the mesh, 4..10 (pme_grid > 0)  */
 } bd_params;
 
 typedef struct bd_plan bd_plan;

@@ -47,7 +47,8 @@ class BdParams(ctypes.Structure):
                 ("ev_on", ctypes.c_int32), ("z_star", ctypes.c_double),
                 ("d_star", ctypes.c_double), ("r_ev", ctypes.c_double),
                 ("dt", ctypes.c_double), ("precision", ctypes.c_int32),
-                ("max_rhs", ctypes.c_int32), ("max_cheb", ctypes.c_int32)]
+                ("max_rhs", ctypes.c_int32), ("max_cheb", ctypes.c_int32),
+                ("pme_grid", ctypes.c_int32), ("pme_order", ctypes.c_int32)]
 
 
 class BdPlanInfo(ctypes.Structure):
@@ -156,7 +157,8 @@ def make_params(p: dict, precision: str = "fp64", max_rhs: int = 16,
                     ev_on=int(p.get("ev_on", 0)), z_star=float(p.get("z_star", 0.0)),
                     d_star=float(p.get("d_star", 1.0)), r_ev=float(p.get("r_ev", 0.0)),
                     dt=float(p.get("dt", 0.0)), precision=PRECISIONS[precision],
-                    max_rhs=int(max_rhs), max_cheb=int(max_cheb))
+                    max_rhs=int(max_rhs), max_cheb=int(max_cheb),
+                    pme_grid=int(p.get("pme_grid", 0)), pme_order=int(p.get("pme_order", 0)))
 
 
 class Plan:

@@ -11,6 +11,7 @@
 #include "adjoint.cuh"
 #include "recip_tc.cuh"
 #include "adaptive.cuh"
+#include "spectral.cuh"
 
 struct bd_plan {
     bd::Plan P;
@@ -79,6 +80,7 @@ static void free_plan(Plan &P)
     for (void *p : ptrs)
         if (p) cudaFree(p);
     if (P.h_est) cudaFreeHost(P.h_est);
+    spectral_free(P);
 }
 
 static bd_status validate(const bd_params *p)
@@ -96,8 +98,22 @@ static bd_status validate(const bd_params *p)
     if (!(p->alpha > 0.0)) return set_error(BD_ERR_INVALID, "alpha must be > 0");
     if (!(p->r_c > 0.0) || p->r_c / p->box_L > 64.0)
         return set_error(BD_ERR_INVALID, "r_c must satisfy 0 < r_c <= 64 L");
-    if (p->n2max < 0 || p->n2max > 4096)
-        return set_error(BD_ERR_INVALID, "n2max must be in [0, 4096]");
+    if (p->n2max < 0 || p->n2max > (p->pme_grid > 0 ? (1 << 22) : 4096))
+        return set_error(BD_ERR_INVALID, "n2max must be in [0, 4096] (2^22 with a mesh)");
+    if (p->pme_grid < 0) return set_error(BD_ERR_INVALID, "pme_grid must be >= 0");
+    if (p->pme_grid > 0) {
+        int kmax = 0;
+        while ((long)(kmax + 1) * (kmax + 1) <= p->n2max) kmax++;
+        if (p->pme_grid % 2 != 0 || p->pme_grid < 8 || p->pme_grid > 512 ||
+            p->pme_grid < 2 * kmax + 2)
+            return set_error(BD_ERR_INVALID, "pme_grid must be even, in [8, 512] and >= 2 "
+                             "sqrt(n2max) + 2 = %d", 2 * kmax + 2);
+        if (p->pme_order < 4 || p->pme_order > 10)
+            return set_error(BD_ERR_INVALID, "pme_order must be in [4, 10]");
+        if (!(p->r_c < 0.5 * p->box_L))
+            return set_error(BD_ERR_INVALID, "the spectral path needs r_c < L/2 (r_c=%g, L=%g)",
+                             p->r_c, p->box_L);
+    }
     if (p->spring != 0 && p->spring != 1)
         return set_error(BD_ERR_INVALID, "spring must be 0 (Hookean) or 1 (FENE)");
     if (p->spring == 1 && !(p->fene_b > 0.0))
@@ -206,6 +222,10 @@ bd_status bd_plan_create(const bd_params *params, bd_plan **out_plan)
     {
         cudaStream_t s = 0;
         launch_kvec_table(P, s);
+        if (P.nk > kMaxKvec && P.p.pme_grid > 0) {
+            P.nk = 0;            // mesh plan with a k-sphere too large for the dense tables:
+            P.dense_off = 1;     // only matrix-free (spectral) products
+        }
         if (P.nk > kMaxKvec) {
             st = set_error(BD_ERR_UNSUPPORTED, "%d half-space k-vectors exceed the limit %d",
                            P.nk, kMaxKvec);
@@ -221,6 +241,7 @@ bd_status bd_plan_create(const bd_params *params, bd_plan **out_plan)
             TRY(tc_plan_init(P));
             TRY(recip_tc_init(P));
         }
+        if (P.p.pme_grid > 0) TRY(spectral_init(P));
         cudaMemset(P.d_step_ctr, 0, sizeof(unsigned long long));
         if (cudaDeviceSynchronize() != cudaSuccess) {
             st = check_launch("plan creation");
@@ -275,6 +296,9 @@ bd_status bd_build_D(bd_plan *plan, const double *R, void *D, bd_stream stream)
 {
     if (!plan || !R || !D) return set_error(BD_ERR_INVALID, "NULL argument");
     Plan &P = plan->P;
+    if (P.dense_off)
+        return set_error(BD_ERR_UNSUPPORTED, "this mesh plan's k-sphere exceeds the dense tables; "
+                         "use matrix-free products");
     if (((uintptr_t)D & 255) != 0) return set_error(BD_ERR_INVALID, "D must be 256-byte aligned");
     if (!is_mixed(P)) {
         launch_build_D_f64(P, R, (double *)D, stream);
@@ -295,7 +319,7 @@ static bd_status apply_core(Plan &P, const void *D, const double *X, int m, doub
     if (P.matfree_R) {        // inside a matrix-free step: recompute D(R) X (FP32 or FP64)
         (void)D;
         (void)flags;
-        return launch_apply_matfree(P, X, m, Y, s);
+        return matfree_product(P, X, m, Y, s);
     }
     if (!is_mixed(P)) {
         launch_gemm_f64(P, (const double *)D, X, m, Y, s);
@@ -374,7 +398,7 @@ static bd_status cheb_core(Plan &P, const void *D, const double *bounds, int nch
     double *prev2 = A, *prev1 = B;
     for (int p = 2; p < nch; p++) {
         if (P.matfree_R) {
-            bd_status st = launch_apply_matfree(P, prev1, m, P.d_mfW, s);
+            bd_status st = matfree_product(P, prev1, m, P.d_mfW, s);
             if (st != BD_OK) return st;
             launch_cheb_term(P, P.d_mfW, prev1, prev2, m, bounds, p, dS, s);
         } else if (!is_mixed(P)) {
@@ -441,8 +465,10 @@ bd_status bd_apply_D_matfree(bd_plan *plan, const double *R, const double *X, in
     const char *xb = (const char *)X, *yb = (const char *)Y;
     const size_t bytes = (size_t)P.n3 * m * sizeof(double);
     if (xb < yb + bytes && yb < xb + bytes) return set_error(BD_ERR_INVALID, "X and Y overlap");
+    bd_status st = matfree_init(P);
+    if (st != BD_OK) return st;
     launch_matfree_tables(P, R, stream);
-    return launch_apply_matfree(P, X, m, Y, stream);
+    return matfree_product(P, X, m, Y, stream);
 }
 
 bd_status bd_product_timing(bd_plan *plan, int32_t enable, float *total_ms, int32_t *launches)

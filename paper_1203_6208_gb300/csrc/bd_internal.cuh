@@ -57,6 +57,8 @@ constexpr int kMaxCheb = 256;         // Chebyshev terms
 constexpr int kMaxLanczos = 128;      // Lanczos steps
 constexpr int kLdAlign = 64;          // D leading dimension multiple (elements)
 
+struct PmeState;
+
 struct Plan {
     bd_params p;
     int device;
@@ -127,6 +129,8 @@ struct Plan {
     double *d_mfpart;                  // per-chunk partial products [chunks][3N x (max_rhs + 3)]
     int mf_chunks;                     // chunks of the bead loop in one matrix-free product
     const double *matfree_R;           // set inside a matrix-free step: products recompute D(R)
+    PmeState *pme;                     // spectral product state (pme_grid > 0)
+    int dense_off;                     // 1: no dense D (k-sphere beyond the dense tables)
     // adaptive N_Ch (allocated by the first adaptive call)
     double *d_mom;                     // moments, dot partials, estimates, D V scratch
     double *h_est;                     // pinned host words read back per candidate N
@@ -163,6 +167,8 @@ bd_status launch_build_D_f32(Plan &P, const double *R, float *D32, void *D16, in
 void launch_matfree_tables(Plan &P, const double *R, cudaStream_t s);
 bd_status matfree_init(Plan &P);
 bd_status launch_apply_matfree(Plan &P, const double *X, int m, double *Y, cudaStream_t s);
+// the matrix-free product of the plan: spectral (pme_grid > 0) or pair sums
+bd_status matfree_product(Plan &P, const double *X, int m, double *Y, cudaStream_t s);
 
 // dense_f64.cu : Y = D X (FP64), epilogue variants
 struct ChebEpi {

@@ -17,6 +17,8 @@
 #include "bd_internal.cuh"
 #include "pair_common.cuh"
 #include "recip_tc.cuh"
+#include "kspace.cuh"
+#include "spectral.cuh"
 
 namespace bd {
 
@@ -93,22 +95,11 @@ __global__ void k_kvec(const int *nvec, int nk, double a, double alpha, double L
     int t = blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= nk) return;
     const double two_pi = 6.283185307179586476925;
-    double k[3];
-    for (int i = 0; i < 3; i++) k[i] = two_pi * nvec[3 * t + i] / L;
-    double k2 = k[0] * k[0] + k[1] * k[1] + k[2] * k[2];
-    double al2 = alpha * alpha;
-    double V = L * L * L;
-    double f = (a - a * a * a * k2 / 3.0) * (1.0 + k2 / (4.0 * al2) + k2 * k2 / (8.0 * al2 * al2))
-             * (6.0 * 3.14159265358979323846 / (k2 * V)) * exp(-k2 / (4.0 * al2));
-    f *= 2.0;
     KVec kv;
-    for (int i = 0; i < 3; i++) kv.k[i] = k[i];
-    kv.m[0] = f * (1.0 - k[0] * k[0] / k2);
-    kv.m[1] = f * (-k[0] * k[1] / k2);
-    kv.m[2] = f * (-k[0] * k[2] / k2);
-    kv.m[3] = f * (1.0 - k[1] * k[1] / k2);
-    kv.m[4] = f * (-k[1] * k[2] / k2);
-    kv.m[5] = f * (1.0 - k[2] * k[2] / k2);
+    for (int i = 0; i < 3; i++) kv.k[i] = two_pi * nvec[3 * t + i] / L;
+    double m[6];
+    m2_tensor(kv.k, a, alpha, L, m);
+    for (int i = 0; i < 6; i++) kv.m[i] = 2.0 * m[i];      // folded with -k
     out[t] = kv;
 }
 
@@ -800,8 +791,19 @@ bd_status matfree_init(Plan &P)
 
 void launch_matfree_tables(Plan &P, const double *R, cudaStream_t s)
 {
+    if (P.pme) {
+        launch_wrap(P, R, s);
+        spectral_tables(P, s);
+        return;
+    }
     launch_trig_tables(P, R, s);
     launch_wrap(P, R, s);
+}
+
+bd_status matfree_product(Plan &P, const double *X, int m, double *Y, cudaStream_t s)
+{
+    if (P.pme) return launch_apply_spectral(P, X, m, Y, s);
+    return launch_apply_matfree(P, X, m, Y, s);
 }
 
 bd_status launch_apply_matfree(Plan &P, const double *X, int m, double *Y, cudaStream_t s)
@@ -850,6 +852,92 @@ bd_status launch_apply_matfree(Plan &P, const double *X, int m, double *Y, cudaS
         }
     }
     return check_launch("matrix-free product");
+}
+
+// ---------------------------------------------------------------------------
+// Real-space part of the spectral product: r_c < L/2, so a pair has at most
+// its minimum image within r_c, and only beads of the 27 neighbouring cells
+// (cells of edge >= r_c; one cell when the box holds fewer than 3) can be
+// that close.  One thread per row bead, the neighbour cells in a fixed order
+// and the beads of a cell in ascending index, y accumulated in shared memory
+// per thread (deterministic).
+template <typename T>
+__global__ void __launch_bounds__(kMfRows)
+k_real_cells(const double *__restrict__ pw, const float *__restrict__ pw32, int n,
+             const __grid_constant__ EwaldT<T> c, const T *__restrict__ tab, int tab_i0, int ntab,
+             int overlap_corr, const int *__restrict__ cell_of, const int *__restrict__ cell_start,
+             const int *__restrict__ cell_beads, int nc, const double *__restrict__ X, int m,
+             double *__restrict__ Y)
+{
+    extern __shared__ __align__(16) unsigned char rc_smem[];
+    T *ys = (T *)rc_smem;                          // [3m][kMfRows]
+    const int tid = threadIdx.x;
+    const int nu = blockIdx.x * kMfRows + tid;
+    const long n3 = 3L * n;
+    const int w = 3 * m;
+    for (int i = 0; i < w; i++) ys[(size_t)i * kMfRows + tid] = (T)0;
+    if (nu < n) {
+        const int cell = cell_of[nu];
+        const int cx = cell / (nc * nc), cy = (cell / nc) % nc, cz = cell % nc;
+        const int span = nc >= 3 ? 1 : 0;
+        for (int dx = -span; dx <= span; dx++)
+            for (int dy = -span; dy <= span; dy++)
+                for (int dz = -span; dz <= span; dz++) {
+                    const int c2 = (((cx + dx + nc) % nc) * nc + (cy + dy + nc) % nc) * nc +
+                                   (cz + dz + nc) % nc;
+                    for (int i = cell_start[c2]; i < cell_start[c2 + 1]; i++) {
+                        const int mu = cell_beads[i];
+                        T acc[6] = {0, 0, 0, 0, 0, 0};
+                        if (mu == nu) {
+                            acc[0] = c.self; acc[3] = c.self; acc[5] = c.self;
+                        } else {
+                            T d[3];
+                            Sep<T>::get(pw, pw32, n3, nu, mu, c, d);
+                            const T u = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
+                            if (!(u <= c.rc2)) continue;
+                            if (u >= c.four_a2) add_m1_tab<T>(d[0], d[1], d[2], u, tab, tab_i0, ntab, acc);
+                            else if (overlap_corr) add_overlap<T>(d[0], d[1], d[2], u, c, acc);
+                            else add_m1<T>(d[0], d[1], d[2], u, c, acc);
+                        }
+                        for (int col = 0; col < m; col++) {
+                            const double *x = X + (long)col * n3 + 3L * mu;
+                            const T x0 = (T)x[0], x1 = (T)x[1], x2 = (T)x[2];
+                            T *y = ys + (size_t)(3 * col) * kMfRows + tid;
+                            y[0] += acc[0] * x0 + acc[1] * x1 + acc[2] * x2;
+                            y[kMfRows] += acc[1] * x0 + acc[3] * x1 + acc[4] * x2;
+                            y[2 * kMfRows] += acc[2] * x0 + acc[4] * x1 + acc[5] * x2;
+                        }
+                    }
+                }
+        for (int col = 0; col < m; col++)
+            for (int a = 0; a < 3; a++)
+                Y[(long)col * n3 + 3L * nu + a] = (double)ys[(size_t)(3 * col + a) * kMfRows + tid];
+    }
+}
+
+bd_status launch_real_cells(Plan &P, const double *X, int m, double *Y, cudaStream_t s)
+{
+    const PmeState *S = P.pme;
+    const size_t sm = (size_t)3 * m * kMfRows * (is_mixed(P) ? sizeof(float) : sizeof(double));
+    if (sm > 227 * 1024)
+        return set_error(BD_ERR_UNSUPPORTED, "spectral product: m = %d columns need %zu bytes of "
+                         "shared memory", m, sm);
+    const unsigned nb = (unsigned)((P.n + kMfRows - 1) / kMfRows);
+    if (!is_mixed(P)) {
+        cudaFuncSetAttribute(k_real_cells<double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             227 * 1024);
+        k_real_cells<double><<<nb, kMfRows, sm, s>>>(
+            P.d_pw64, P.d_pw32, P.n, P.h_ew64, P.d_tab, P.tab_i0, P.ntab, P.p.overlap_corr,
+            S->d_cell_of, S->d_cell_start, S->d_cell_beads, S->nc, X, m, Y);
+    } else {
+        cudaFuncSetAttribute(k_real_cells<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             227 * 1024);
+        k_real_cells<float><<<nb, kMfRows, sm, s>>>(
+            P.d_pw64, P.d_pw32, P.n, P.h_ew32, P.d_tab32, P.tab_i0, P.ntab, P.p.overlap_corr,
+            S->d_cell_of, S->d_cell_start, S->d_cell_beads, S->nc, X, m, Y);
+    }
+    count_launches(1);
+    return check_launch("real-space cells");
 }
 
 }  // namespace bd

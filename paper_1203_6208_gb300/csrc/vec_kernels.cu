@@ -136,24 +136,32 @@ void launch_forces(Plan &P, const double *R, double *F, int32_t *n_bad, cudaStre
 
 // c_p = (2/N) sum_j sqrt(h cos t_j + mid) cos(p t_j), t_j = pi (j + 1/2)/N:
 // the coefficients of the Chebyshev interpolant of sqrt on [d_min, d_max].
+// c_p = (2/N) sum_j f(cos t_j) cos(p t_j), t_j = pi (j + 1/2)/N: one block per
+// p, the terms summed in a fixed order (each thread a strided subset, then a
+// fixed tree)
 __global__ void k_cheb_coeffs(const double *bounds, int nch, double *c)
 {
-    int p = threadIdx.x;
-    double dmin = bounds[0], dmax = bounds[1];
-    double h = 0.5 * (dmax - dmin), mid = 0.5 * (dmax + dmin);
-    for (; p < nch; p += blockDim.x) {
-        double s = 0.0;
-        for (int j = 0; j < nch; j++) {
-            double t = kPi * (j + 0.5) / nch;
-            s += sqrt(h * cos(t) + mid) * cos(p * t);
-        }
-        c[p] = 2.0 * s / nch;
+    __shared__ double red[64];
+    const int p = blockIdx.x;
+    const double dmin = bounds[0], dmax = bounds[1];
+    const double h = 0.5 * (dmax - dmin), mid = 0.5 * (dmax + dmin);
+    double v = 0.0;
+    for (int j = threadIdx.x; j < nch; j += blockDim.x) {
+        double t = kPi * (j + 0.5) / nch;
+        v += sqrt(h * cos(t) + mid) * cos(p * t);
     }
+    red[threadIdx.x] = v;
+    __syncthreads();
+    for (int w = 32; w > 0; w >>= 1) {
+        if (threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) c[p] = 2.0 * red[0] / nch;
 }
 
 void launch_cheb_coeffs(Plan &P, const double *bounds, int nch, cudaStream_t s)
 {
-    k_cheb_coeffs<<<1, 256, 0, s>>>(bounds, nch, P.d_coef);
+    k_cheb_coeffs<<<nch, 64, 0, s>>>(bounds, nch, P.d_coef);
     count_launches(1);
 }
 
