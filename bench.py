@@ -268,7 +268,7 @@ def traffic_per_launch(kind):
         return None
 
 
-ALPHA_FACTORS = (1.0, 1.25, 1.5, 1.75, 2.0, 2.5)
+ALPHA_FACTORS = (1.0, 1.25, 1.5, 1.75, 2.0, 2.25, 2.5)
 
 
 def pick_alpha(args, p, R, precision):

@@ -856,87 +856,166 @@ bd_status launch_apply_matfree(Plan &P, const double *X, int m, double *Y, cudaS
 
 // ---------------------------------------------------------------------------
 // Real-space part of the spectral product: r_c < L/2, so a pair has at most
-// its minimum image within r_c, and only beads of the 27 neighbouring cells
-// (cells of edge >= r_c; one cell when the box holds fewer than 3) can be
-// that close.  One thread per row bead, the neighbour cells in a fixed order
-// and the beads of a cell in ascending index, y accumulated in shared memory
-// per thread (deterministic).
+// its minimum image within r_c, and only beads of the cells within `span`
+// cells of a bead's cell (cell edge >= r_c / span) can be that close.  One
+// block per cell: its beads are the rows (in chunks of kRcRows), each
+// neighbour cell's beads are staged in shared memory (positions and the
+// operand's rows) and every thread walks the same staged list in ascending
+// bead order; y is accumulated per thread in shared memory (deterministic).
+constexpr int kRcRows = 64;
+
+// minimum-image separation from split positions (hi + lo; lo = 0 for FP64)
 template <typename T>
-__global__ void __launch_bounds__(kMfRows)
+__device__ __forceinline__ void sep_split(const T *ah, const T *al, const T *bh, const T *bl,
+                                          const EwaldT<T> &c, T d[3])
+{
+#pragma unroll
+    for (int s = 0; s < 3; s++) {
+        T a = ah[s], b = -bh[s];
+        T hs = a + b;                                      // TwoSum(a, b)
+        T bb = hs - a;
+        T he = (a - (hs - bb)) + (b - bb);
+        he += al[s] - bl[s];
+        if (hs > c.halfL) { hs -= c.L; he -= c.Llo; }
+        else if (hs < -c.halfL) { hs += c.L; he += c.Llo; }
+        d[s] = hs + he;
+    }
+}
+
+template <typename T> struct PosSplit;
+template <> struct PosSplit<double> {
+    __device__ static void get(const double *pw, const float *, long, int i, double h[3], double l[3])
+    {
+        for (int s = 0; s < 3; s++) { h[s] = pw[3 * i + s]; l[s] = 0.0; }
+    }
+};
+template <> struct PosSplit<float> {
+    __device__ static void get(const double *, const float *pw32, long n3, int i, float h[3], float l[3])
+    {
+        for (int s = 0; s < 3; s++) { h[s] = pw32[3 * i + s]; l[s] = pw32[n3 + 3 * i + s]; }
+    }
+};
+
+template <typename T>
+__global__ void __launch_bounds__(kRcRows)
 k_real_cells(const double *__restrict__ pw, const float *__restrict__ pw32, int n,
              const __grid_constant__ EwaldT<T> c, const T *__restrict__ tab, int tab_i0, int ntab,
-             int overlap_corr, const int *__restrict__ cell_of, const int *__restrict__ cell_start,
-             const int *__restrict__ cell_beads, int nc, const double *__restrict__ X, int m,
-             double *__restrict__ Y)
+             int overlap_corr, const int *__restrict__ cell_start,
+             const int *__restrict__ cell_beads, int nc, int span, const double *__restrict__ X,
+             int m, double *__restrict__ Y, double *__restrict__ part)
 {
+    // blockIdx.y = one x-slab (dx) of the neighbour cells when part != NULL
+    // (its rows go to part[dx + span]); with part == NULL the block takes
+    // every slab and writes Y
     extern __shared__ __align__(16) unsigned char rc_smem[];
-    T *ys = (T *)rc_smem;                          // [3m][kMfRows]
-    const int tid = threadIdx.x;
-    const int nu = blockIdx.x * kMfRows + tid;
-    const long n3 = 3L * n;
     const int w = 3 * m;
-    for (int i = 0; i < w; i++) ys[(size_t)i * kMfRows + tid] = (T)0;
-    if (nu < n) {
-        const int cell = cell_of[nu];
-        const int cx = cell / (nc * nc), cy = (cell / nc) % nc, cz = cell % nc;
-        const int span = nc >= 3 ? 1 : 0;
-        for (int dx = -span; dx <= span; dx++)
+    T *ys = (T *)rc_smem;                            // [w][kRcRows] accumulators
+    T *xs = ys + (size_t)w * kRcRows;                // [kRcRows][w] staged operand rows
+    T *ps = xs + (size_t)w * kRcRows;                // [kRcRows][6] staged positions (hi, lo)
+    int *ids = (int *)(ps + 6 * kRcRows);            // [kRcRows] staged bead indices
+    const int tid = threadIdx.x;
+    const long n3 = 3L * n;
+    const int cell = blockIdx.x;
+    const int cx = cell / (nc * nc), cy = (cell / nc) % nc, cz = cell % nc;
+    const int lo = cell_start[cell], cnt = cell_start[cell + 1] - lo;
+    for (int r0 = 0; r0 < cnt; r0 += kRcRows) {
+        const bool row_ok = r0 + tid < cnt;
+        const int nu = row_ok ? cell_beads[lo + r0 + tid] : 0;
+        T mh[3], ml[3];
+        PosSplit<T>::get(pw, pw32, n3, nu, mh, ml);
+        for (int i = 0; i < w; i++) ys[(size_t)i * kRcRows + tid] = (T)0;
+        const int dx0 = part ? (int)blockIdx.y - span : -span, dx1 = part ? dx0 : span;
+        for (int dx = dx0; dx <= dx1; dx++)
             for (int dy = -span; dy <= span; dy++)
                 for (int dz = -span; dz <= span; dz++) {
                     const int c2 = (((cx + dx + nc) % nc) * nc + (cy + dy + nc) % nc) * nc +
                                    (cz + dz + nc) % nc;
-                    for (int i = cell_start[c2]; i < cell_start[c2 + 1]; i++) {
-                        const int mu = cell_beads[i];
-                        T acc[6] = {0, 0, 0, 0, 0, 0};
-                        if (mu == nu) {
-                            acc[0] = c.self; acc[3] = c.self; acc[5] = c.self;
-                        } else {
-                            T d[3];
-                            Sep<T>::get(pw, pw32, n3, nu, mu, c, d);
-                            const T u = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
-                            if (!(u <= c.rc2)) continue;
-                            if (u >= c.four_a2) add_m1_tab<T>(d[0], d[1], d[2], u, tab, tab_i0, ntab, acc);
-                            else if (overlap_corr) add_overlap<T>(d[0], d[1], d[2], u, c, acc);
-                            else add_m1<T>(d[0], d[1], d[2], u, c, acc);
+                    const int lo2 = cell_start[c2], cnt2 = cell_start[c2 + 1] - lo2;
+                    for (int j0 = 0; j0 < cnt2; j0 += kRcRows) {
+                        const int jn = min(kRcRows, cnt2 - j0);
+                        __syncthreads();
+                        if (tid < jn) {
+                            const int mu = cell_beads[lo2 + j0 + tid];
+                            ids[tid] = mu;
+                            T h[3], l[3];
+                            PosSplit<T>::get(pw, pw32, n3, mu, h, l);
+                            for (int q = 0; q < 3; q++) {
+                                ps[6 * tid + q] = h[q];
+                                ps[6 * tid + 3 + q] = l[q];
+                            }
+                            for (int col = 0; col < m; col++)
+                                for (int b = 0; b < 3; b++)
+                                    xs[(size_t)tid * w + 3 * col + b] = (T)X[(long)col * n3 + 3L * mu + b];
                         }
-                        for (int col = 0; col < m; col++) {
-                            const double *x = X + (long)col * n3 + 3L * mu;
-                            const T x0 = (T)x[0], x1 = (T)x[1], x2 = (T)x[2];
-                            T *y = ys + (size_t)(3 * col) * kMfRows + tid;
-                            y[0] += acc[0] * x0 + acc[1] * x1 + acc[2] * x2;
-                            y[kMfRows] += acc[1] * x0 + acc[3] * x1 + acc[4] * x2;
-                            y[2 * kMfRows] += acc[2] * x0 + acc[4] * x1 + acc[5] * x2;
+                        __syncthreads();
+                        if (!row_ok) continue;
+                        for (int j = 0; j < jn; j++) {
+                            const int mu = ids[j];
+                            T acc[6] = {0, 0, 0, 0, 0, 0};
+                            if (mu == nu) {
+                                acc[0] = c.self; acc[3] = c.self; acc[5] = c.self;
+                            } else {
+                                T d[3];
+                                sep_split<T>(mh, ml, ps + 6 * j, ps + 6 * j + 3, c, d);
+                                const T u = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
+                                if (!(u <= c.rc2)) continue;
+                                if (u >= c.four_a2) add_m1_tab<T>(d[0], d[1], d[2], u, tab, tab_i0, ntab, acc);
+                                else if (overlap_corr) add_overlap<T>(d[0], d[1], d[2], u, c, acc);
+                                else add_m1<T>(d[0], d[1], d[2], u, c, acc);
+                            }
+                            const T *x = xs + (size_t)j * w;
+                            for (int col = 0; col < m; col++) {
+                                const T x0 = x[3 * col], x1 = x[3 * col + 1], x2 = x[3 * col + 2];
+                                T *y = ys + (size_t)(3 * col) * kRcRows + tid;
+                                y[0] += acc[0] * x0 + acc[1] * x1 + acc[2] * x2;
+                                y[kRcRows] += acc[1] * x0 + acc[3] * x1 + acc[4] * x2;
+                                y[2 * kRcRows] += acc[2] * x0 + acc[4] * x1 + acc[5] * x2;
+                            }
                         }
                     }
                 }
-        for (int col = 0; col < m; col++)
-            for (int a = 0; a < 3; a++)
-                Y[(long)col * n3 + 3L * nu + a] = (double)ys[(size_t)(3 * col + a) * kMfRows + tid];
+        double *out = part ? part + (size_t)blockIdx.y * n3 * m : Y;
+        if (row_ok)
+            for (int col = 0; col < m; col++)
+                for (int a = 0; a < 3; a++)
+                    out[(long)col * n3 + 3L * nu + a] = (double)ys[(size_t)(3 * col + a) * kRcRows + tid];
+        __syncthreads();
     }
 }
 
 bd_status launch_real_cells(Plan &P, const double *X, int m, double *Y, cudaStream_t s)
 {
     const PmeState *S = P.pme;
-    const size_t sm = (size_t)3 * m * kMfRows * (is_mixed(P) ? sizeof(float) : sizeof(double));
+    const size_t ts = is_mixed(P) ? sizeof(float) : sizeof(double);
+    const size_t sm = ((size_t)2 * 3 * m * kRcRows + 6 * kRcRows) * ts + kRcRows * sizeof(int);
     if (sm > 227 * 1024)
         return set_error(BD_ERR_UNSUPPORTED, "spectral product: m = %d columns need %zu bytes of "
                          "shared memory", m, sm);
-    const unsigned nb = (unsigned)((P.n + kMfRows - 1) / kMfRows);
+    // one block per cell, and per x-slab of neighbour cells when that leaves
+    // too few warps for the GPU (partials summed in slab order)
+    const int slabs = 2 * S->span + 1;
+    const bool split = slabs > 1 && S->ncell < 16L * (P.num_sms > 0 ? P.num_sms : 152);
+    const dim3 nb((unsigned)S->ncell, split ? slabs : 1);
+    double *part = split ? S->d_rpart : nullptr;
     if (!is_mixed(P)) {
         cudaFuncSetAttribute(k_real_cells<double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              227 * 1024);
-        k_real_cells<double><<<nb, kMfRows, sm, s>>>(
+        k_real_cells<double><<<nb, kRcRows, sm, s>>>(
             P.d_pw64, P.d_pw32, P.n, P.h_ew64, P.d_tab, P.tab_i0, P.ntab, P.p.overlap_corr,
-            S->d_cell_of, S->d_cell_start, S->d_cell_beads, S->nc, X, m, Y);
+            S->d_cell_start, S->d_cell_beads, S->nc, S->span, X, m, Y, part);
     } else {
         cudaFuncSetAttribute(k_real_cells<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              227 * 1024);
-        k_real_cells<float><<<nb, kMfRows, sm, s>>>(
+        k_real_cells<float><<<nb, kRcRows, sm, s>>>(
             P.d_pw64, P.d_pw32, P.n, P.h_ew32, P.d_tab32, P.tab_i0, P.ntab, P.p.overlap_corr,
-            S->d_cell_of, S->d_cell_start, S->d_cell_beads, S->nc, X, m, Y);
+            S->d_cell_start, S->d_cell_beads, S->nc, S->span, X, m, Y, part);
     }
     count_launches(1);
+    if (split) {
+        const long len = (long)P.n3 * m;
+        k_sum_chunks<<<(unsigned)((len + 255) / 256), 256, 0, s>>>(part, slabs, len, Y);
+        count_launches(1);
+    }
     return check_launch("real-space cells");
 }
 

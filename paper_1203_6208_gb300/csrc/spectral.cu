@@ -4,7 +4,8 @@
 // sums: Verlet tables for the real-space part and fast Fourier transforms for
 // the Fourier part.  This file is that path for the matrix-free product:
 //   * real space with r_c < L/2 (every pair has at most one image within
-//     r_c, the minimum image) over a cell list of cells no smaller than r_c;
+//     r_c, the minimum image) over a cell list of cells no smaller than
+//     r_c / 2, searched two cells deep;
 //   * the reciprocal sum of the same truncated k-sphere as the dense D by
 //     smooth particle-mesh Ewald: the operand is spread onto a K^3 mesh with
 //     cardinal B-splines of order p, transformed (cuFFT, batched R2C), each
@@ -103,8 +104,11 @@ bd_status spectral_init(Plan &P)
     P.pme = S;
     S->K = p.pme_grid;
     S->p = p.pme_order;
-    const int nc = (int)floor(p.box_L / p.r_c);
-    S->nc = nc >= 3 ? nc : 1;
+    // cells of edge >= r_c / 2 searched two deep when the box holds 5 or more
+    // of them (5 distinct offsets -2..2), else the whole box as one cell
+    const int nc2 = (int)floor(2.0 * p.box_L / p.r_c);
+    if (nc2 >= 5) { S->nc = nc2; S->span = 2; }
+    else { S->nc = 1; S->span = 0; }
     S->ncell = (long)S->nc * S->nc * S->nc;
     S->K3 = (long)S->K * S->K * S->K;
     S->Kh = (long)S->K * S->K * (S->K / 2 + 1);
@@ -125,11 +129,13 @@ bd_status spectral_init(Plan &P)
     ALLOC(S->d_cell_count, sizeof(int) * S->ncell);
     ALLOC(S->d_cell_start, sizeof(int) * (S->ncell + 1));
     ALLOC(S->d_cell_beads, sizeof(int) * P.n);
+    ALLOC(S->d_cell_tmp, sizeof(int) * P.n);
+    ALLOC(S->d_rpart, sizeof(double) * (2 * S->span + 1) * P.n3 * S->mcap);
     ALLOC(S->d_infl, ts * 6 * S->Kh);
     ALLOC(S->d_qfix, sizeof(unsigned long long) * grids * S->K3);
     ALLOC(S->d_qreal, ts * grids * S->K3);
     ALLOC(S->d_qhat, 2 * ts * grids * S->Kh);
-    ALLOC(S->d_xmax, sizeof(unsigned long long) * 2);
+    ALLOC(S->d_xmax, sizeof(unsigned long long) * 4);
 #undef ALLOC
     if (e != cudaSuccess) return oom("mesh", e);
     P.scratch_bytes += (int64_t)bytes;
@@ -158,7 +164,8 @@ void spectral_free(Plan &P)
 {
     PmeState *S = P.pme;
     if (!S) return;
-    void *ptrs[] = {S->d_cell_of, S->d_cell_count, S->d_cell_start, S->d_cell_beads, S->d_infl,
+    void *ptrs[] = {S->d_cell_of, S->d_cell_count, S->d_cell_start, S->d_cell_beads, S->d_cell_tmp,
+                    S->d_rpart, S->d_infl,
                     S->d_qfix, S->d_qreal, S->d_qhat, S->d_xmax};
     for (void *q : ptrs)
         if (q) cudaFree(q);
@@ -228,20 +235,19 @@ __global__ void k_cell_scatter(const int *__restrict__ cell_of, int n, int *__re
     beads[pos] = nu;
 }
 
-// ascending bead order inside each cell (fixed summation order)
-__global__ void k_cell_sort(const int *__restrict__ start, long ncell, int *__restrict__ beads)
+// ascending bead order inside each cell (fixed summation order): one block per
+// cell, every bead's rank is the count of smaller indices in its cell
+__global__ void k_cell_sort(const int *__restrict__ start, long ncell, const int *__restrict__ in,
+                            int *__restrict__ out)
 {
-    const long c = (long)blockIdx.x * blockDim.x + threadIdx.x;
+    const long c = blockIdx.x;
     if (c >= ncell) return;
     const int lo = start[c], hi = start[c + 1];
-    for (int i = lo + 1; i < hi; i++) {
-        const int v = beads[i];
-        int j = i - 1;
-        while (j >= lo && beads[j] > v) {
-            beads[j + 1] = beads[j];
-            j--;
-        }
-        beads[j + 1] = v;
+    for (int i = lo + threadIdx.x; i < hi; i += blockDim.x) {
+        const int v = in[i];
+        int rank = 0;
+        for (int j = lo; j < hi; j++) rank += in[j] < v ? 1 : 0;
+        out[lo + rank] = v;
     }
 }
 
@@ -253,9 +259,9 @@ void spectral_tables(Plan &P, cudaStream_t s)
                                                    S->d_cell_count);
     k_cell_scan<<<1, 1024, 0, s>>>(S->d_cell_count, S->ncell, S->d_cell_start);
     k_cell_scatter<<<(P.n + 255) / 256, 256, 0, s>>>(S->d_cell_of, P.n, S->d_cell_count,
-                                                    S->d_cell_beads);
-    k_cell_sort<<<(unsigned)((S->ncell + 127) / 128), 128, 0, s>>>(S->d_cell_start, S->ncell,
-                                                                   S->d_cell_beads);
+                                                    S->d_cell_tmp);
+    k_cell_sort<<<(unsigned)S->ncell, 128, 0, s>>>(S->d_cell_start, S->ncell, S->d_cell_tmp,
+                                                   S->d_cell_beads);
     count_launches(4);
 }
 
@@ -273,15 +279,22 @@ __global__ void k_absmax_all(const double *__restrict__ X, long len, unsigned lo
     if ((threadIdx.x & 31) == 0) atomicMax(out, (unsigned long long)__double_as_longlong(v));
 }
 
-// fixed-point scale 2^E / max|x| with E such that n p^3 terms of magnitude
-// <= 2^E cannot overflow a signed 64-bit word
-__device__ __forceinline__ double fix_scale(const unsigned long long *xmax, int n)
+// fixed-point scale 2^E / max|x| with E such that n terms of magnitude
+// <= 2^E cannot overflow a signed 64-bit word; xmax[1], xmax[2] receive the
+// scale and its inverse (as double bits)
+__global__ void k_fix_scale(unsigned long long *xmax, int n)
 {
-    const double mx = __longlong_as_double((long long)*xmax);
+    const double mx = __longlong_as_double((long long)xmax[0]);
     int lg = 0;
     while ((1L << lg) <= (long)n) lg++;
-    const int E = 61 - lg;
-    return mx > 0.0 ? ldexp(1.0, E) / mx : 1.0;
+    const double sc = mx > 0.0 ? ldexp(1.0, 61 - lg) / mx : 1.0;
+    xmax[1] = (unsigned long long)__double_as_longlong(sc);
+    xmax[2] = (unsigned long long)__double_as_longlong(1.0 / sc);
+}
+
+__device__ __forceinline__ double fix_scale(const unsigned long long *xmax, int)
+{
+    return __longlong_as_double((long long)xmax[1]);
 }
 
 template <typename T>
@@ -328,7 +341,8 @@ __global__ void k_pme_unfix(const unsigned long long *__restrict__ qfix, long le
 {
     const long i = (long)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= len) return;
-    const double inv = 1.0 / fix_scale(xmax, n);
+    (void)n;
+    const double inv = __longlong_as_double((long long)xmax[2]);
     q[i] = (T)((double)(long long)qfix[i] * inv);
 }
 
@@ -431,6 +445,8 @@ bd_status launch_apply_spectral(Plan &P, const double *X, int m, double *Y, cuda
     const long grid_len = (long)3 * m * S->K3;
     cudaMemsetAsync(S->d_xmax, 0, sizeof(unsigned long long), s);
     k_absmax_all<<<256, 256, 0, s>>>(X, n3 * m, S->d_xmax);
+    k_fix_scale<<<1, 1, 0, s>>>(S->d_xmax, P.n);
+    count_launches(1);
     cudaMemsetAsync(S->d_qfix, 0, sizeof(unsigned long long) * grid_len, s);
     const unsigned nbm = (unsigned)(((long)P.n * m + 127) / 128);
     const unsigned ng = (unsigned)((grid_len + 255) / 256);

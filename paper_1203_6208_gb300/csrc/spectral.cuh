@@ -9,7 +9,8 @@ namespace bd {
 
 struct PmeState {
     int K, p;                     // mesh points per edge, B-spline order
-    int nc;                       // cells per edge of the real-space cell list (1 if < 3)
+    int nc;                       // cells per edge of the real-space cell list
+    int span;                     // neighbour cells searched on each side (0: one cell)
     long ncell;                   // nc^3
     long K3, Kh;                  // K^3 and K * K * (K/2 + 1)
     int mcap;                     // columns the grids hold (max_rhs + 3)
@@ -17,11 +18,13 @@ struct PmeState {
     int *d_cell_count;            // [ncell] beads per cell, then scatter cursors
     int *d_cell_start;            // [ncell + 1] exclusive prefix sums
     int *d_cell_beads;            // [n] bead indices grouped by cell, ascending in a cell
+    int *d_cell_tmp;              // [n] the same before the in-cell sort
+    double *d_rpart;              // [2 span + 1][3N x mcap] real-space partials per neighbour slab
     void *d_infl;                 // [Kh][6] influence function G(m)|b(m)|^2 (working precision)
     unsigned long long *d_qfix;   // [3 mcap][K3] spread in 64-bit fixed point
     void *d_qreal;                // [3 mcap][K3] real mesh (working precision)
     void *d_qhat;                 // [3 mcap][Kh] complex mesh
-    unsigned long long *d_xmax;   // [1] max |x| of the current operand (bits of a double)
+    unsigned long long *d_xmax;   // [4] max |x| of the operand, fixed-point scale, its inverse
     cufftHandle fwd, inv;         // batched R2C / C2R plans for plan_m columns
     int plan_m;                   // 0: no cuFFT plans yet
 };

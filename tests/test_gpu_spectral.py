@@ -78,7 +78,7 @@ def test_spectral_fp32(bnd, ref):
 def test_real_space_cells_exact(bnd, n_chains, f):
     """n2max = 0: only the real-space sum and the self term, against the
     oracle with no k-sum; alpha = f sqrt(pi)/L gives one cell (f = 6) or
-    3 cells per edge (f = 8 and 9)."""
+    6 and 7 cells per edge searched two deep (f = 8 and 9)."""
     cfg, p, R = system(n_chains=n_chains, f=f, c=4.0)
     p = dict(p, n2max=0)
     X = inputs.make_wiener(3 * cfg.n, 3, 1.0, 93)
