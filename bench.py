@@ -594,9 +594,8 @@ def spectral_params(cfg, r_c=6.0, order=8):
     f = cfg.M / r_c * L / inputs.SQRT_PI
     q = replace_cfg(cfg, alpha_factor=f).params()
     kmax = math.sqrt(q["n2max"])
-    K = int(math.ceil(3.5 * L / 8.0)) * 8
-    K = max(K, 2 * int(math.ceil(kmax)) + 2)
-    q.update(pme_grid=K + (K % 2), pme_order=order)
+    K = max(3.5 * L, 2 * math.ceil(kmax) + 2)
+    q.update(pme_grid=int(math.ceil(K / 8.0)) * 8, pme_order=order)
     return q
 
 

@@ -53,7 +53,8 @@ typedef struct CUstream_st *bd_stream; /* a cudaStream_t; NULL = legacy default 
 typedef enum {
     BD_OK = 0,
     BD_ERR_INVALID = 1,       /* bad argument or plan/argument mismatch            */
-    BD_ERR_OOM = 2,           /* device allocation failed (plan creation only)     */
+    BD_ERR_OOM = 2,           /* device allocation failed (plan creation; the
+                                 neighbour table of a spectral matrix-free call)  */
     BD_ERR_CUDA = 3,          /* a CUDA runtime/driver call failed                 */
     BD_ERR_NOT_PD = 4,        /* eigenvalue bound <= 0: D not positive definite    */
     BD_ERR_FENE_STRETCH = 5,  /* a FENE spring reached |Q|^2 >= b                  */
@@ -91,9 +92,9 @@ typedef struct {
     int32_t max_cheb;         /* largest number of Chebyshev terms N_Ch, 2..256   */
     int32_t pme_grid;         /* > 0: matrix-free products use the spectral path:
                                  real space over cell lists (needs r_c < L/2) and the
-                                 reciprocal sum on a pme_grid^3 mesh (even, >= 2
-                                 ceil(sqrt(n2max)) + 2, <= 512); 0: off            */
-    int32_t pme_order;        /* B-spline order of the mesh, 4..10 (pme_grid > 0)  */
+                                 reciprocal sum on a pme_grid^3 mesh (a multiple
+                                 of 8, >= 2 ceil(sqrt(n2max)) + 2, <= 512); 0: off */
+    int32_t pme_order;        /* B-spline order of the mesh, 4..10 and <= pme_grid */
 } bd_params;
 
 typedef struct bd_plan bd_plan;
@@ -268,6 +269,13 @@ bd_status bd_chebyshev_sqrt_adaptive(bd_plan *plan, const void *D, const double 
  * Same D as bd_build_D (to rounding): FP64 arithmetic on FP64 plans, FP32
  * with FP64 output on mixed plans (no 16-bit rounding).  Cost O(N^2 images)
  * per call, memory O(N): the path for N whose D does not fit.
+ * With pme_grid > 0 the product is the spectral one instead: the real-space
+ * part over a neighbour table of the pairs within r_c (built from a cell
+ * list on every call, and once per step in bd_step), the reciprocal sum on
+ * the B-spline mesh; cost O(N) real space + O(K^3 log K) mesh per product,
+ * memory O(N r_c^3 density) for the table.  This form synchronises the
+ * stream once (sizing the neighbour table) and may return BD_ERR_OOM when
+ * the table grows.
  *   R     dev, 3N positions
  *   X, Y  dev, 3N x m column-major doubles, 1 <= m <= max_rhs + 3      */
 bd_status bd_apply_D_matfree(bd_plan *plan, const double *R, const double *X, int32_t m,

@@ -104,12 +104,11 @@ static bd_status validate(const bd_params *p)
     if (p->pme_grid > 0) {
         int kmax = 0;
         while ((long)(kmax + 1) * (kmax + 1) <= p->n2max) kmax++;
-        if (p->pme_grid % 2 != 0 || p->pme_grid < 8 || p->pme_grid > 512 ||
-            p->pme_grid < 2 * kmax + 2)
-            return set_error(BD_ERR_INVALID, "pme_grid must be even, in [8, 512] and >= 2 "
+        if (p->pme_grid % 8 != 0 || p->pme_grid > 512 || p->pme_grid < 2 * kmax + 2)
+            return set_error(BD_ERR_INVALID, "pme_grid must be a multiple of 8, <= 512 and >= 2 "
                              "sqrt(n2max) + 2 = %d", 2 * kmax + 2);
-        if (p->pme_order < 4 || p->pme_order > 10)
-            return set_error(BD_ERR_INVALID, "pme_order must be in [4, 10]");
+        if (p->pme_order < 4 || p->pme_order > 10 || p->pme_order > p->pme_grid)
+            return set_error(BD_ERR_INVALID, "pme_order must be in [4, 10] and <= pme_grid");
         if (!(p->r_c < 0.5 * p->box_L))
             return set_error(BD_ERR_INVALID, "the spectral path needs r_c < L/2 (r_c=%g, L=%g)",
                              p->r_c, p->box_L);
@@ -467,7 +466,8 @@ bd_status bd_apply_D_matfree(bd_plan *plan, const double *R, const double *X, in
     if (xb < yb + bytes && yb < xb + bytes) return set_error(BD_ERR_INVALID, "X and Y overlap");
     bd_status st = matfree_init(P);
     if (st != BD_OK) return st;
-    launch_matfree_tables(P, R, stream);
+    st = launch_matfree_tables(P, R, stream);
+    if (st != BD_OK) return st;
     return matfree_product(P, X, m, Y, stream);
 }
 
@@ -593,7 +593,8 @@ bd_status bd_step(bd_plan *plan, double *R, void *D, const double *dW, const bd_
     PHASE(1);
     // (a2-a4) D(R), or the tables of the matrix-free products
     if (matfree) {
-        launch_matfree_tables(P, R, s);
+        st = launch_matfree_tables(P, R, s);
+        if (st != BD_OK) return st;
     } else {
         st = bd_build_D(plan, R, D, s);
         if (st != BD_OK) return st;

@@ -164,7 +164,7 @@ bd_status launch_build_D_f32(Plan &P, const double *R, float *D32, void *D16, in
                         cudaStream_t s);
 
 // matrix-free Y = D(R) X (ewald_build.cu); the tables of R must be current
-void launch_matfree_tables(Plan &P, const double *R, cudaStream_t s);
+bd_status launch_matfree_tables(Plan &P, const double *R, cudaStream_t s);
 bd_status matfree_init(Plan &P);
 bd_status launch_apply_matfree(Plan &P, const double *X, int m, double *Y, cudaStream_t s);
 // the matrix-free product of the plan: spectral (pme_grid > 0) or pair sums

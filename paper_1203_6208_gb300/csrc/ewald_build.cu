@@ -789,15 +789,15 @@ bd_status matfree_init(Plan &P)
     return check_launch("matrix-free init");
 }
 
-void launch_matfree_tables(Plan &P, const double *R, cudaStream_t s)
+bd_status launch_matfree_tables(Plan &P, const double *R, cudaStream_t s)
 {
     if (P.pme) {
         launch_wrap(P, R, s);
-        spectral_tables(P, s);
-        return;
+        return spectral_tables(P, s);
     }
     launch_trig_tables(P, R, s);
     launch_wrap(P, R, s);
+    return BD_OK;
 }
 
 bd_status matfree_product(Plan &P, const double *X, int m, double *Y, cudaStream_t s)
@@ -855,14 +855,16 @@ bd_status launch_apply_matfree(Plan &P, const double *X, int m, double *Y, cudaS
 }
 
 // ---------------------------------------------------------------------------
-// Real-space part of the spectral product: r_c < L/2, so a pair has at most
-// its minimum image within r_c, and only beads of the cells within `span`
-// cells of a bead's cell (cell edge >= r_c / span) can be that close.  One
-// block per cell: its beads are the rows (in chunks of kRcRows), each
-// neighbour cell's beads are staged in shared memory (positions and the
-// operand's rows) and every thread walks the same staged list in ascending
-// bead order; y is accumulated per thread in shared memory (deterministic).
-constexpr int kRcRows = 64;
+// Real-space part of the spectral product as a neighbour table (the Verlet
+// tables of the paper's outlook, Sec. VIII).  With r_c < L/2 a pair has at
+// most its minimum image within r_c, and only beads of the cells within
+// `span` cells of a bead's cell (cell edge >= r_c / span) can be that close.
+// The positions are fixed through a step, so for every row (bead in cell
+// order) the table holds the rows within r_c -- itself included, with the
+// self term -- and the six components of their block of Eqs. (M1) and
+// (DFmodified), built once per position set; each product is then a sparse
+// 3x3-block product over the table.  Entries are ordered by neighbour cell and
+// then by row, and a row's sum is reduced in a fixed order: deterministic.
 
 // minimum-image separation from split positions (hi + lo; lo = 0 for FP64)
 template <typename T>
@@ -896,127 +898,326 @@ template <> struct PosSplit<float> {
     }
 };
 
-template <typename T>
-__global__ void __launch_bounds__(kRcRows)
-k_real_cells(const double *__restrict__ pw, const float *__restrict__ pw32, int n,
-             const __grid_constant__ EwaldT<T> c, const T *__restrict__ tab, int tab_i0, int ntab,
-             int overlap_corr, const int *__restrict__ cell_start,
-             const int *__restrict__ cell_beads, int nc, int span, const double *__restrict__ X,
-             int m, double *__restrict__ Y, double *__restrict__ part)
+// one warp per row: the candidate rows of the row's (2 span + 1)^3 cells are
+// taken 32 at a time in a fixed order (cells in offset order, rows ascending
+// inside a cell).  FILL = false counts those within r_c (the row itself
+// included) into row_start[r]; FILL = true writes them, in that order, to nbr
+// (and the row to prow) from row_start[r] on.  The two passes take the same
+// decisions (u is formed with explicit fused operations); the fill still stops
+// at the next row's start and pads a short row (prow = -1: a zero block), so a
+// row never writes outside its own entries.
+constexpr int kMaxNbrCells = 125;
+constexpr int kPairWarps = 8;
+
+template <typename T, bool FILL>
+__global__ void __launch_bounds__(32 * kPairWarps)
+k_real_pairs(const double *__restrict__ pw, const float *__restrict__ pw32, int n,
+             const __grid_constant__ EwaldT<T> c, const int *__restrict__ cell_start,
+             const int *__restrict__ cell_beads, const int *__restrict__ cell_of, int nc, int span,
+             int *__restrict__ row_start, int *__restrict__ nbr, int *__restrict__ prow)
 {
-    // blockIdx.y = one x-slab (dx) of the neighbour cells when part != NULL
-    // (its rows go to part[dx + span]); with part == NULL the block takes
-    // every slab and writes Y
-    extern __shared__ __align__(16) unsigned char rc_smem[];
-    const int w = 3 * m;
-    T *ys = (T *)rc_smem;                            // [w][kRcRows] accumulators
-    T *xs = ys + (size_t)w * kRcRows;                // [kRcRows][w] staged operand rows
-    T *ps = xs + (size_t)w * kRcRows;                // [kRcRows][6] staged positions (hi, lo)
-    int *ids = (int *)(ps + 6 * kRcRows);            // [kRcRows] staged bead indices
-    const int tid = threadIdx.x;
+    __shared__ int s_lo[kPairWarps][kMaxNbrCells];       // first candidate row of each cell
+    __shared__ int s_pre[kPairWarps][kMaxNbrCells + 1];  // candidates before each cell
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    const int r = blockIdx.x * kPairWarps + wid;
+    if (r >= n) return;                                  // the whole warp
     const long n3 = 3L * n;
-    const int cell = blockIdx.x;
+    const int nu = cell_beads[r];
+    const int cell = cell_of[nu];
     const int cx = cell / (nc * nc), cy = (cell / nc) % nc, cz = cell % nc;
-    const int lo = cell_start[cell], cnt = cell_start[cell + 1] - lo;
-    for (int r0 = 0; r0 < cnt; r0 += kRcRows) {
-        const bool row_ok = r0 + tid < cnt;
-        const int nu = row_ok ? cell_beads[lo + r0 + tid] : 0;
-        T mh[3], ml[3];
-        PosSplit<T>::get(pw, pw32, n3, nu, mh, ml);
-        for (int i = 0; i < w; i++) ys[(size_t)i * kRcRows + tid] = (T)0;
-        const int dx0 = part ? (int)blockIdx.y - span : -span, dx1 = part ? dx0 : span;
-        for (int dx = dx0; dx <= dx1; dx++)
-            for (int dy = -span; dy <= span; dy++)
-                for (int dz = -span; dz <= span; dz++) {
-                    const int c2 = (((cx + dx + nc) % nc) * nc + (cy + dy + nc) % nc) * nc +
-                                   (cz + dz + nc) % nc;
-                    const int lo2 = cell_start[c2], cnt2 = cell_start[c2 + 1] - lo2;
-                    for (int j0 = 0; j0 < cnt2; j0 += kRcRows) {
-                        const int jn = min(kRcRows, cnt2 - j0);
-                        __syncthreads();
-                        if (tid < jn) {
-                            const int mu = cell_beads[lo2 + j0 + tid];
-                            ids[tid] = mu;
-                            T h[3], l[3];
-                            PosSplit<T>::get(pw, pw32, n3, mu, h, l);
-                            for (int q = 0; q < 3; q++) {
-                                ps[6 * tid + q] = h[q];
-                                ps[6 * tid + 3 + q] = l[q];
-                            }
-                            for (int col = 0; col < m; col++)
-                                for (int b = 0; b < 3; b++)
-                                    xs[(size_t)tid * w + 3 * col + b] = (T)X[(long)col * n3 + 3L * mu + b];
-                        }
-                        __syncthreads();
-                        if (!row_ok) continue;
-                        for (int j = 0; j < jn; j++) {
-                            const int mu = ids[j];
-                            T acc[6] = {0, 0, 0, 0, 0, 0};
-                            if (mu == nu) {
-                                acc[0] = c.self; acc[3] = c.self; acc[5] = c.self;
-                            } else {
-                                T d[3];
-                                sep_split<T>(mh, ml, ps + 6 * j, ps + 6 * j + 3, c, d);
-                                const T u = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
-                                if (!(u <= c.rc2)) continue;
-                                if (u >= c.four_a2) add_m1_tab<T>(d[0], d[1], d[2], u, tab, tab_i0, ntab, acc);
-                                else if (overlap_corr) add_overlap<T>(d[0], d[1], d[2], u, c, acc);
-                                else add_m1<T>(d[0], d[1], d[2], u, c, acc);
-                            }
-                            const T *x = xs + (size_t)j * w;
-                            for (int col = 0; col < m; col++) {
-                                const T x0 = x[3 * col], x1 = x[3 * col + 1], x2 = x[3 * col + 2];
-                                T *y = ys + (size_t)(3 * col) * kRcRows + tid;
-                                y[0] += acc[0] * x0 + acc[1] * x1 + acc[2] * x2;
-                                y[kRcRows] += acc[1] * x0 + acc[3] * x1 + acc[4] * x2;
-                                y[2 * kRcRows] += acc[2] * x0 + acc[4] * x1 + acc[5] * x2;
-                            }
-                        }
-                    }
+    const int w = 2 * span + 1, ncells = w * w * w;
+    int *lo = s_lo[wid], *pre = s_pre[wid];
+    for (int t = lane; t < ncells; t += 32) {
+        const int dx = t / (w * w) - span, dy = (t / w) % w - span, dz = t % w - span;
+        const int c2 = (((cx + dx + nc) % nc) * nc + (cy + dy + nc) % nc) * nc + (cz + dz + nc) % nc;
+        lo[t] = cell_start[c2];
+        pre[t + 1] = cell_start[c2 + 1] - cell_start[c2];
+    }
+    __syncwarp();
+    if (lane == 0) {
+        pre[0] = 0;
+        for (int t = 1; t <= ncells; t++) pre[t] += pre[t - 1];
+    }
+    __syncwarp();
+    const int total = pre[ncells];
+    T mh[3], ml[3];
+    PosSplit<T>::get(pw, pw32, n3, nu, mh, ml);
+    long k = FILL ? (long)row_start[r] : 0;
+    const long kend = FILL ? (long)row_start[r + 1] : 0;
+    int cnt = 0, cc = 0;
+    for (int t0 = 0; t0 < total; t0 += 32) {
+        const int t = t0 + lane;
+        bool in = false;
+        int j = 0;
+        if (t < total) {
+            while (pre[cc + 1] <= t) cc++;               // t grows: the cell cursor only advances
+            j = lo[cc] + (t - pre[cc]);
+            const int mu = cell_beads[j];
+            if (mu == nu) {
+                in = true;
+            } else {
+                T h[3], l[3], d[3];
+                PosSplit<T>::get(pw, pw32, n3, mu, h, l);
+                sep_split<T>(mh, ml, h, l, c, d);
+                const T u = fma(d[2], d[2], fma(d[1], d[1], d[0] * d[0]));
+                in = u <= c.rc2;
+            }
+        }
+        const unsigned bal = __ballot_sync(0xffffffffu, in);
+        if (FILL) {
+            if (in) {
+                const long kk = k + __popc(bal & ((1u << lane) - 1u));
+                if (kk < kend) {
+                    nbr[kk] = j;
+                    prow[kk] = r;
                 }
-        double *out = part ? part + (size_t)blockIdx.y * n3 * m : Y;
-        if (row_ok)
-            for (int col = 0; col < m; col++)
-                for (int a = 0; a < 3; a++)
-                    out[(long)col * n3 + 3L * nu + a] = (double)ys[(size_t)(3 * col + a) * kRcRows + tid];
-        __syncthreads();
+            }
+            k += __popc(bal);
+        } else {
+            cnt += __popc(bal);
+        }
+    }
+    if (FILL) {
+        for (long kk = k + lane; kk < kend; kk += 32) {
+            nbr[kk] = r;
+            prow[kk] = -1;
+        }
+    } else if (lane == 0) {
+        row_start[r] = cnt;
     }
 }
 
-bd_status launch_real_cells(Plan &P, const double *X, int m, double *Y, cudaStream_t s)
+// the 3x3 blocks of the table, one thread per entry: real-space image,
+// overlap branch or the self term (Eqs. M1, DFmodified, DF)
+template <typename T>
+__global__ void k_pair_blocks(const double *__restrict__ pw, const float *__restrict__ pw32, int n,
+                              const __grid_constant__ EwaldT<T> c, const T *__restrict__ tab,
+                              int tab_i0, int ntab, int overlap_corr,
+                              const int *__restrict__ cell_beads, const int *__restrict__ prow,
+                              const int *__restrict__ nbr, long np, T *__restrict__ tens, long cap)
 {
-    const PmeState *S = P.pme;
-    const size_t ts = is_mixed(P) ? sizeof(float) : sizeof(double);
-    const size_t sm = ((size_t)2 * 3 * m * kRcRows + 6 * kRcRows) * ts + kRcRows * sizeof(int);
-    if (sm > 227 * 1024)
-        return set_error(BD_ERR_UNSUPPORTED, "spectral product: m = %d columns need %zu bytes of "
-                         "shared memory", m, sm);
-    // one block per cell, and per x-slab of neighbour cells when that leaves
-    // too few warps for the GPU (partials summed in slab order)
-    const int slabs = 2 * S->span + 1;
-    const bool split = slabs > 1 && S->ncell < 16L * (P.num_sms > 0 ? P.num_sms : 152);
-    const dim3 nb((unsigned)S->ncell, split ? slabs : 1);
-    double *part = split ? S->d_rpart : nullptr;
-    if (!is_mixed(P)) {
-        cudaFuncSetAttribute(k_real_cells<double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             227 * 1024);
-        k_real_cells<double><<<nb, kRcRows, sm, s>>>(
-            P.d_pw64, P.d_pw32, P.n, P.h_ew64, P.d_tab, P.tab_i0, P.ntab, P.p.overlap_corr,
-            S->d_cell_start, S->d_cell_beads, S->nc, S->span, X, m, Y, part);
+    const long k = (long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= np) return;
+    const int r = prow[k];
+    T acc[6] = {0, 0, 0, 0, 0, 0};
+    if (r >= 0) {
+        const int j = nbr[k];
+        if (j == r) {
+            acc[0] = c.self; acc[3] = c.self; acc[5] = c.self;
+        } else {
+            const long n3 = 3L * n;
+            T mh[3], ml[3], h[3], l[3], d[3];
+            PosSplit<T>::get(pw, pw32, n3, cell_beads[r], mh, ml);
+            PosSplit<T>::get(pw, pw32, n3, cell_beads[j], h, l);
+            sep_split<T>(mh, ml, h, l, c, d);
+            const T u = fma(d[2], d[2], fma(d[1], d[1], d[0] * d[0]));
+            if (u >= c.four_a2) add_m1_tab<T>(d[0], d[1], d[2], u, tab, tab_i0, ntab, acc);
+            else if (overlap_corr) add_overlap<T>(d[0], d[1], d[2], u, c, acc);
+            else add_m1<T>(d[0], d[1], d[2], u, c, acc);
+        }
+    }
+#pragma unroll
+    for (int q = 0; q < 6; q++) tens[q * cap + k] = acc[q];
+}
+
+// operand rows in cell order, by column chunk: xr[(ch n + r) ldx + i] =
+// X[ch cw + i / 3][3 cell_beads[r] + i % 3] for i < 3 cw (zero padding up to
+// ldx and past the last column)
+template <typename T>
+__global__ void k_pack_rows(const double *__restrict__ X, int n, int m, int cw, int ldx,
+                            long len, const int *__restrict__ cell_beads, T *__restrict__ xr)
+{
+    const long idx = (long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= len) return;
+    const long per = (long)n * ldx;
+    const int ch = (int)(idx / per);
+    const long rem = idx - ch * per;
+    const int r = (int)(rem / ldx), i = (int)(rem - (long)r * ldx);
+    const int col = ch * cw + i / 3;
+    double v = 0.0;
+    if (i < 3 * cw && col < m) v = X[(long)col * 3 * n + 3L * cell_beads[r] + i % 3];
+    xr[idx] = (T)v;
+}
+
+// Y[col][3 nu + a] = sum over the row's entries of block(nu, mu) x_mu: one warp
+// per row, lanes over the entries, a butterfly sum over the lanes (every
+// lane ends with the same, order-fixed sum); CC columns per pass
+template <typename T, int CC>
+__global__ void __launch_bounds__(256)
+k_real_pairs_apply(int n, const int *__restrict__ cell_beads, const int *__restrict__ row_start,
+                   const int *__restrict__ nbr, const T *__restrict__ tens, long cap,
+                   const T *__restrict__ xr, int ldx, int m, int cw, double *__restrict__ Y)
+{
+    constexpr int VW = 16 / sizeof(T);
+    constexpr int NV = (3 * CC + VW - 1) / VW;
+    const int lane = threadIdx.x & 31;
+    const int r = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    if (r >= n) return;
+    const int k0 = row_start[r], k1 = row_start[r + 1];
+    const int nu = cell_beads[r];
+    const long n3 = 3L * n;
+    for (int c0 = 0, ch = 0; c0 < m; c0 += cw, ch++) {
+        const int nx = 3 * min(cw, m - c0);
+        const T *xc = xr + (size_t)ch * n * ldx;
+        T acc[3 * CC];
+#pragma unroll
+        for (int i = 0; i < 3 * CC; i++) acc[i] = (T)0;
+        for (int k = k0 + lane; k < k1; k += 32) {
+            const T t0 = tens[k], t1 = tens[cap + k], t2 = tens[2 * cap + k];
+            const T t3 = tens[3 * cap + k], t4 = tens[4 * cap + k], t5 = tens[5 * cap + k];
+            const T *xj = xc + (size_t)nbr[k] * ldx;
+            T xv[NV * VW];
+#pragma unroll
+            for (int v = 0; v < NV; v++) {
+                if (v * VW < ldx) {
+                    const uint4 u = *reinterpret_cast<const uint4 *>(xj + v * VW);
+                    memcpy(&xv[v * VW], &u, 16);
+                } else {
+#pragma unroll
+                    for (int e = 0; e < VW; e++) xv[v * VW + e] = (T)0;
+                }
+            }
+#pragma unroll
+            for (int q = 0; q < 3 * CC; q += 3) {
+                if (q < nx) {
+                    const T x0 = xv[q], x1 = xv[q + 1], x2 = xv[q + 2];
+                    acc[q] += t0 * x0 + t1 * x1 + t2 * x2;
+                    acc[q + 1] += t1 * x0 + t3 * x1 + t4 * x2;
+                    acc[q + 2] += t2 * x0 + t4 * x1 + t5 * x2;
+                }
+            }
+        }
+        T mine = (T)0;
+#pragma unroll
+        for (int i = 0; i < 3 * CC; i++) {
+            T v = acc[i];
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+            if (lane == i) mine = v;
+        }
+        if (lane < nx) Y[(long)(c0 + lane / 3) * n3 + 3L * nu + lane % 3] = (double)mine;
+    }
+}
+
+static void chunk_shape(int m, int cc, int vw, int *nchunk, int *cw, int *ldx)
+{
+    *nchunk = (m + cc - 1) / cc;
+    *cw = (m + *nchunk - 1) / *nchunk;
+    *ldx = (3 * *cw + vw - 1) / vw * vw;
+}
+
+static bd_status pairs_oom(const char *what, cudaError_t e)
+{
+    cudaGetLastError();
+    return set_error(BD_ERR_OOM, "spectral product %s: %s", what, cudaGetErrorString(e));
+}
+
+template <typename T>
+static void pairs_pass(Plan &P, const EwaldT<T> &c, bool fill, cudaStream_t s)
+{
+    PmeState *S = P.pme;
+    const unsigned nb = (unsigned)((P.n + kPairWarps - 1) / kPairWarps);
+    if (fill)
+        k_real_pairs<T, true><<<nb, 32 * kPairWarps, 0, s>>>(
+            P.d_pw64, P.d_pw32, P.n, c, S->d_cell_start, S->d_cell_beads, S->d_cell_of, S->nc,
+            S->span, S->d_row_start, S->d_nbr, S->d_prow);
+    else
+        k_real_pairs<T, false><<<nb, 32 * kPairWarps, 0, s>>>(
+            P.d_pw64, P.d_pw32, P.n, c, S->d_cell_start, S->d_cell_beads, S->d_cell_of, S->nc,
+            S->span, S->d_row_start, nullptr, nullptr);
+    count_launches(1);
+}
+
+bd_status build_real_pairs(Plan &P, cudaStream_t s)
+{
+    PmeState *S = P.pme;
+    if (S->span > 2) return set_error(BD_ERR_INVALID, "cell search span %d > 2", S->span);
+    const bool dbl = !is_mixed(P);
+    const size_t ts = dbl ? sizeof(double) : sizeof(float);
+    if (dbl) pairs_pass<double>(P, P.h_ew64, false, s);
+    else pairs_pass<float>(P, P.h_ew32, false, s);
+    // counts -> starts (the counts array doubles as the cursor array of the scan)
+    launch_scan_counts(S->d_row_start, P.n, S->d_row_start, s);
+    count_launches(1);
+    cudaMemcpyAsync(S->h_npair, S->d_row_start + P.n, sizeof(int), cudaMemcpyDeviceToHost, s);
+    cudaError_t e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return set_error(BD_ERR_CUDA, "neighbour count: %s", cudaGetErrorString(e));
+    const long np = (long)*(const int *)S->h_npair;
+    const size_t per = 2 * sizeof(int) + 6 * ts;
+    if (np > S->pair_cap) {
+        void *old[] = {S->d_nbr, S->d_prow, S->d_tens};
+        for (void *q : old)
+            if (q) cudaFree(q);
+        S->d_nbr = S->d_prow = nullptr;
+        S->d_tens = nullptr;
+        P.scratch_bytes -= (int64_t)(S->pair_cap * per);
+        const long cap = np + np / 8 + 1024;
+        e = cudaMalloc((void **)&S->d_nbr, sizeof(int) * cap);
+        if (e == cudaSuccess) e = cudaMalloc((void **)&S->d_prow, sizeof(int) * cap);
+        if (e == cudaSuccess) e = cudaMalloc(&S->d_tens, 6 * ts * cap);
+        if (e != cudaSuccess) {
+            S->pair_cap = 0;
+            return pairs_oom("neighbour table", e);
+        }
+        S->pair_cap = cap;
+        P.scratch_bytes += (int64_t)(cap * per);
+    }
+    S->npair = np;
+    const unsigned nbp = (unsigned)((np + 255) / 256);
+    if (dbl) {
+        pairs_pass<double>(P, P.h_ew64, true, s);
+        k_pair_blocks<double><<<nbp, 256, 0, s>>>(P.d_pw64, P.d_pw32, P.n, P.h_ew64, P.d_tab,
+                                                   P.tab_i0, P.ntab, P.p.overlap_corr,
+                                                   S->d_cell_beads, S->d_prow, S->d_nbr, np,
+                                                   (double *)S->d_tens, S->pair_cap);
     } else {
-        cudaFuncSetAttribute(k_real_cells<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             227 * 1024);
-        k_real_cells<float><<<nb, kRcRows, sm, s>>>(
-            P.d_pw64, P.d_pw32, P.n, P.h_ew32, P.d_tab32, P.tab_i0, P.ntab, P.p.overlap_corr,
-            S->d_cell_start, S->d_cell_beads, S->nc, S->span, X, m, Y, part);
+        pairs_pass<float>(P, P.h_ew32, true, s);
+        k_pair_blocks<float><<<nbp, 256, 0, s>>>(P.d_pw64, P.d_pw32, P.n, P.h_ew32, P.d_tab32,
+                                                  P.tab_i0, P.ntab, P.p.overlap_corr,
+                                                  S->d_cell_beads, S->d_prow, S->d_nbr, np,
+                                                  (float *)S->d_tens, S->pair_cap);
     }
     count_launches(1);
-    if (split) {
-        const long len = (long)P.n3 * m;
-        k_sum_chunks<<<(unsigned)((len + 255) / 256), 256, 0, s>>>(part, slabs, len, Y);
-        count_launches(1);
+    return check_launch("neighbour table");
+}
+
+template <typename T, int CC>
+static bd_status real_pairs_apply(Plan &P, const double *X, int m, double *Y, cudaStream_t s)
+{
+    PmeState *S = P.pme;
+    int nchunk, cw, ldx;
+    chunk_shape(m, CC, 16 / (int)sizeof(T), &nchunk, &cw, &ldx);
+    const long len = (long)nchunk * P.n * ldx;
+    if (len > S->xrows_len)
+        return set_error(BD_ERR_INVALID, "operand rows: %ld elements > %ld", len, S->xrows_len);
+    T *xr = (T *)S->d_xrows;
+    k_pack_rows<T><<<(unsigned)((len + 255) / 256), 256, 0, s>>>(X, P.n, m, cw, ldx, len,
+                                                                  S->d_cell_beads, xr);
+    k_real_pairs_apply<T, CC><<<(unsigned)((P.n + 7) / 8), 256, 0, s>>>(
+        P.n, S->d_cell_beads, S->d_row_start, S->d_nbr, (const T *)S->d_tens, S->pair_cap, xr, ldx,
+        m, cw, Y);
+    count_launches(2);
+    return check_launch("real-space pairs");
+}
+
+long real_pairs_rows_len(int n, int mcap, bool dbl)
+{
+    int nchunk, cw, ldx;
+    if (dbl) {
+        chunk_shape(mcap, kPairCols64, 2, &nchunk, &cw, &ldx);
+        ldx = (3 * kPairCols64 + 1) / 2 * 2;
+    } else {
+        chunk_shape(mcap, kPairCols32, 4, &nchunk, &cw, &ldx);
+        ldx = (3 * kPairCols32 + 3) / 4 * 4;
     }
-    return check_launch("real-space cells");
+    return (long)nchunk * n * ldx;
+}
+
+bd_status launch_real_pairs(Plan &P, const double *X, int m, double *Y, cudaStream_t s)
+{
+    if (!P.pme->d_nbr) return set_error(BD_ERR_INVALID, "spectral product without its tables");
+    if (!is_mixed(P)) return real_pairs_apply<double, kPairCols64>(P, X, m, Y, s);
+    return real_pairs_apply<float, kPairCols32>(P, X, m, Y, s);
 }
 
 }  // namespace bd

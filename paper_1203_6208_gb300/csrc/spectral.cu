@@ -14,10 +14,10 @@
 //     Euler exponential-spline factors, transformed back and interpolated
 //     with the same splines.
 // The mesh sum approximates the k-sum by spline interpolation; its error
-// falls as (k_max L / (2 pi K))^p.  Spreading accumulates in 64-bit fixed
-// point (integer atomics commute, so the mesh is the same on every run); the
-// cell lists are ordered by bead index inside each cell, so the real-space
-// sums are too.
+// falls as (k_max L / (2 pi K))^p.  Spreading is mesh-centric: each mesh
+// point sums its beads in a fixed order (no atomics), and the cell lists are
+// ordered by bead index inside each cell, so every product is the same on
+// every run.
 #include <math.h>
 
 #include <vector>
@@ -113,6 +113,8 @@ bd_status spectral_init(Plan &P)
     S->K3 = (long)S->K * S->K * S->K;
     S->Kh = (long)S->K * S->K * (S->K / 2 + 1);
     S->mcap = p.max_rhs + 3;
+    S->tpd = S->K / kMeshTile;
+    S->ntile = (long)S->tpd * S->tpd * S->tpd;
     const bool dbl = !is_mixed(P);
     const size_t ts = dbl ? sizeof(double) : sizeof(float);
     const size_t grids = (size_t)3 * S->mcap;
@@ -130,13 +132,20 @@ bd_status spectral_init(Plan &P)
     ALLOC(S->d_cell_start, sizeof(int) * (S->ncell + 1));
     ALLOC(S->d_cell_beads, sizeof(int) * P.n);
     ALLOC(S->d_cell_tmp, sizeof(int) * P.n);
-    ALLOC(S->d_rpart, sizeof(double) * (2 * S->span + 1) * P.n3 * S->mcap);
+    ALLOC(S->d_row_start, sizeof(int) * (P.n + 1));
+    S->xrows_len = real_pairs_rows_len(P.n, S->mcap, dbl);
+    ALLOC(S->d_xrows, ts * S->xrows_len);
     ALLOC(S->d_infl, ts * 6 * S->Kh);
-    ALLOC(S->d_qfix, sizeof(unsigned long long) * grids * S->K3);
+    ALLOC(S->d_tile_of, sizeof(int) * P.n);
+    ALLOC(S->d_tile_count, sizeof(int) * S->ntile);
+    ALLOC(S->d_tile_start, sizeof(int) * (S->ntile + 1));
+    ALLOC(S->d_tile_beads, sizeof(int) * P.n);
+    ALLOC(S->d_bfl, sizeof(int) * 3 * P.n);
+    ALLOC(S->d_bw, ts * 3 * S->p * P.n);
     ALLOC(S->d_qreal, ts * grids * S->K3);
     ALLOC(S->d_qhat, 2 * ts * grids * S->Kh);
-    ALLOC(S->d_xmax, sizeof(unsigned long long) * 4);
 #undef ALLOC
+    if (e == cudaSuccess) e = cudaMallocHost((void **)&S->h_npair, sizeof(long long));
     if (e != cudaSuccess) return oom("mesh", e);
     P.scratch_bytes += (int64_t)bytes;
     // influence function (plan constant)
@@ -165,10 +174,11 @@ void spectral_free(Plan &P)
     PmeState *S = P.pme;
     if (!S) return;
     void *ptrs[] = {S->d_cell_of, S->d_cell_count, S->d_cell_start, S->d_cell_beads, S->d_cell_tmp,
-                    S->d_rpart, S->d_infl,
-                    S->d_qfix, S->d_qreal, S->d_qhat, S->d_xmax};
+                    S->d_row_start, S->d_nbr, S->d_prow, S->d_tens, S->d_xrows, S->d_infl, S->d_tile_of, S->d_tile_count, S->d_tile_start,
+                    S->d_tile_beads, S->d_bfl, S->d_bw, S->d_qreal, S->d_qhat};
     for (void *q : ptrs)
         if (q) cudaFree(q);
+    if (S->h_npair) cudaFreeHost(S->h_npair);
     if (S->plan_m) {
         cufftDestroy(S->fwd);
         cufftDestroy(S->inv);
@@ -251,99 +261,168 @@ __global__ void k_cell_sort(const int *__restrict__ start, long ncell, const int
     }
 }
 
-void spectral_tables(Plan &P, cudaStream_t s)
+// spline base index floor(u_d) mod K and weights of every bead (u_d = K x_d / L
+// of the wrapped position), and the mesh tile holding the base index
+template <typename T>
+__global__ void k_tile_assign(const double *__restrict__ pw, int n, double L, int K, int p, int tpd,
+                              int *__restrict__ bfl, T *__restrict__ bw, int *__restrict__ tile_of,
+                              int *__restrict__ count)
+{
+    const int nu = blockIdx.x * blockDim.x + threadIdx.x;
+    if (nu >= n) return;
+    int ti[3];
+    for (int d = 0; d < 3; d++) {
+        const double u = pw[3 * nu + d] * K / L;
+        const double fl = floor(u);
+        T w[kMaxOrder];
+        bspline_weights<T>((T)(u - fl), p, w);
+        for (int j = 0; j < p; j++) bw[((size_t)nu * 3 + d) * p + j] = w[j];
+        int g = (int)fl;
+        g = g < 0 ? g + K : (g >= K ? g - K : g);
+        bfl[3 * nu + d] = g;
+        ti[d] = g / kMeshTile;
+    }
+    const int t = (ti[0] * tpd + ti[1]) * tpd + ti[2];
+    tile_of[nu] = t;
+    atomicAdd(&count[t], 1);
+}
+
+// beads grouped by bin, ascending inside a bin: count, scan, scatter, sort
+static void bin_sort(const int *bin_of, int n, int *count, long nbin, int *start, int *tmp,
+                     int *out, cudaStream_t s)
+{
+    k_cell_scan<<<1, 1024, 0, s>>>(count, nbin, start);
+    k_cell_scatter<<<(n + 255) / 256, 256, 0, s>>>(bin_of, n, count, tmp);
+    k_cell_sort<<<(unsigned)nbin, 128, 0, s>>>(start, nbin, tmp, out);
+    count_launches(3);
+}
+
+void launch_scan_counts(int *count, long len, int *start, cudaStream_t s)
+{
+    k_cell_scan<<<1, 1024, 0, s>>>(count, len, start);
+}
+
+bd_status spectral_tables(Plan &P, cudaStream_t s)
 {
     PmeState *S = P.pme;
+    const unsigned nb = (unsigned)((P.n + 255) / 256);
     cudaMemsetAsync(S->d_cell_count, 0, sizeof(int) * S->ncell, s);
-    k_cell_assign<<<(P.n + 255) / 256, 256, 0, s>>>(P.d_pw64, P.n, S->nc, P.p.box_L, S->d_cell_of,
-                                                   S->d_cell_count);
-    k_cell_scan<<<1, 1024, 0, s>>>(S->d_cell_count, S->ncell, S->d_cell_start);
-    k_cell_scatter<<<(P.n + 255) / 256, 256, 0, s>>>(S->d_cell_of, P.n, S->d_cell_count,
-                                                    S->d_cell_tmp);
-    k_cell_sort<<<(unsigned)S->ncell, 128, 0, s>>>(S->d_cell_start, S->ncell, S->d_cell_tmp,
-                                                   S->d_cell_beads);
-    count_launches(4);
+    k_cell_assign<<<nb, 256, 0, s>>>(P.d_pw64, P.n, S->nc, P.p.box_L, S->d_cell_of,
+                                     S->d_cell_count);
+    count_launches(1);
+    bin_sort(S->d_cell_of, P.n, S->d_cell_count, S->ncell, S->d_cell_start, S->d_cell_tmp,
+             S->d_cell_beads, s);
+    bd_status st = build_real_pairs(P, s);
+    if (st != BD_OK || P.p.n2max <= 0) return st;
+    cudaMemsetAsync(S->d_tile_count, 0, sizeof(int) * S->ntile, s);
+    if (is_mixed(P))
+        k_tile_assign<float><<<nb, 256, 0, s>>>(P.d_pw64, P.n, P.p.box_L, S->K, S->p, S->tpd,
+                                                S->d_bfl, (float *)S->d_bw, S->d_tile_of,
+                                                S->d_tile_count);
+    else
+        k_tile_assign<double><<<nb, 256, 0, s>>>(P.d_pw64, P.n, P.p.box_L, S->K, S->p, S->tpd,
+                                                 S->d_bfl, (double *)S->d_bw, S->d_tile_of,
+                                                 S->d_tile_count);
+    count_launches(1);
+    bin_sort(S->d_tile_of, P.n, S->d_tile_count, S->ntile, S->d_tile_start, S->d_cell_tmp,
+             S->d_tile_beads, s);
+    return check_launch("spectral tables");
 }
 
 // ---------------------------------------------------------------------------
 // mesh reciprocal sum
 
-__global__ void k_absmax_all(const double *__restrict__ X, long len, unsigned long long *out)
-{
-    double v = 0.0;
-    for (long i = (long)blockIdx.x * blockDim.x + threadIdx.x; i < len;
-         i += (long)gridDim.x * blockDim.x)
-        v = fmax(v, fabs(X[i]));
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
-    if ((threadIdx.x & 31) == 0) atomicMax(out, (unsigned long long)__double_as_longlong(v));
-}
+// Mesh-centric spreading, Q[3 col + b][g] = sum_nu W(u_nu - g) X[col][3 nu + b]:
+// one block per tile of kMeshTile^3 mesh points, one thread per point.  A
+// bead with base index f_d = floor(u_d) reaches the points f_d - j, j < p,
+// so the tile's beads are those binned in tiles t_d .. t_d + 1 + (p-2)/E per
+// dimension (mod tpd).  The block stages them (bins in a fixed order, beads
+// ascending inside a bin) with their base indices, weights and operand rows;
+// each thread adds w1[j1] w2[j2] w3[j3] x over the beads with
+// j_d = (f_d - g_d) mod K < p.  Every mesh point is written once and summed in
+// a fixed order: no atomics.  The columns go in balanced chunks of <= CC.
+constexpr int kStage = 64;
 
-// fixed-point scale 2^E / max|x| with E such that n terms of magnitude
-// <= 2^E cannot overflow a signed 64-bit word; xmax[1], xmax[2] receive the
-// scale and its inverse (as double bits)
-__global__ void k_fix_scale(unsigned long long *xmax, int n)
+template <typename T, int CC>
+__global__ void __launch_bounds__(kMeshTile *kMeshTile *kMeshTile)
+k_pme_spread(int n, int K, int p, int tpd, const int *__restrict__ tile_start,
+             const int *__restrict__ tile_beads, const int *__restrict__ bfl,
+             const T *__restrict__ bw, const double *__restrict__ X, int m, T *__restrict__ q)
 {
-    const double mx = __longlong_as_double((long long)xmax[0]);
-    int lg = 0;
-    while ((1L << lg) <= (long)n) lg++;
-    const double sc = mx > 0.0 ? ldexp(1.0, 61 - lg) / mx : 1.0;
-    xmax[1] = (unsigned long long)__double_as_longlong(sc);
-    xmax[2] = (unsigned long long)__double_as_longlong(1.0 / sc);
-}
-
-__device__ __forceinline__ double fix_scale(const unsigned long long *xmax, int)
-{
-    return __longlong_as_double((long long)xmax[1]);
-}
-
-template <typename T>
-__global__ void k_pme_spread(const double *__restrict__ pw, int n, double L, int K, int p,
-                             const double *__restrict__ X, int m,
-                             const unsigned long long *__restrict__ xmax,
-                             unsigned long long *__restrict__ qfix)
-{
-    const long tid = (long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (tid >= (long)n * m) return;
-    const int nu = (int)(tid % n), col = (int)(tid / n);
-    const long n3 = 3L * n, K3 = (long)K * K * K;
-    const double scale = fix_scale(xmax, n);
-    T w[3][kMaxOrder];
-    int g0[3];
-    for (int d = 0; d < 3; d++) {
-        const double u = pw[3 * nu + d] * K / L;
-        double fl = floor(u);
-        bspline_weights<T>((T)(u - fl), p, w[d]);
-        g0[d] = (int)fl;
+    constexpr int E = kMeshTile;
+    __shared__ int s_bin0[27], s_off[28];
+    __shared__ int s_mu[kStage];
+    __shared__ int s_fl[kStage][3];
+    __shared__ T s_w[kStage][3 * kMaxOrder];
+    __shared__ T s_x[kStage][3 * CC];
+    const int b = blockIdx.x, tid = threadIdx.x;
+    const int t[3] = {b / (tpd * tpd), (b / tpd) % tpd, b % tpd};
+    const int g[3] = {t[0] * E + tid / (E * E), t[1] * E + (tid / E) % E, t[2] * E + tid % E};
+    const int nbd = min(2 + (p - 2) / E, tpd);
+    const int nbins = nbd * nbd * nbd;
+    if (tid < nbins) {
+        const int i0 = tid / (nbd * nbd), i1 = (tid / nbd) % nbd, i2 = tid % nbd;
+        const int bin = (((t[0] + i0) % tpd) * tpd + (t[1] + i1) % tpd) * tpd + (t[2] + i2) % tpd;
+        s_bin0[tid] = tile_start[bin];
+        s_off[tid + 1] = tile_start[bin + 1] - tile_start[bin];
     }
-    const double x[3] = {X[(long)col * n3 + 3L * nu] * scale, X[(long)col * n3 + 3L * nu + 1] * scale,
-                         X[(long)col * n3 + 3L * nu + 2] * scale};
-    unsigned long long *q0 = qfix + (size_t)(3 * col) * K3;
-    for (int j1 = 0; j1 < p; j1++) {
-        const int a1 = ((g0[0] - j1) % K + K) % K;
-        for (int j2 = 0; j2 < p; j2++) {
-            const int a2 = ((g0[1] - j2) % K + K) % K;
-            const double w12 = (double)w[0][j1] * (double)w[1][j2];
-            for (int j3 = 0; j3 < p; j3++) {
-                const int a3 = ((g0[2] - j3) % K + K) % K;
-                const long g = ((long)a1 * K + a2) * K + a3;
-                const double ww = w12 * (double)w[2][j3];
-                for (int b = 0; b < 3; b++)
-                    atomicAdd(q0 + (size_t)b * K3 + g, (unsigned long long)llrint(ww * x[b]));
+    __syncthreads();
+    if (tid == 0) {
+        s_off[0] = 0;
+        for (int i = 1; i <= nbins; i++) s_off[i] += s_off[i - 1];
+    }
+    __syncthreads();
+    const int total = s_off[nbins];
+    const int w3 = 3 * p;
+    const long n3 = 3L * n, K3 = (long)K * K * K;
+    const long gi = ((long)g[0] * K + g[1]) * K + g[2];
+    const int nchunk = (m + CC - 1) / CC, cw = (m + nchunk - 1) / nchunk;
+    for (int c0 = 0; c0 < m; c0 += cw) {
+        const int ncol = min(cw, m - c0), nx = 3 * ncol;
+        T acc[3 * CC];
+#pragma unroll
+        for (int i = 0; i < 3 * CC; i++) acc[i] = (T)0;
+        for (int j0 = 0; j0 < total; j0 += kStage) {
+            const int jn = min(kStage, total - j0);
+            __syncthreads();
+            if (tid < jn) {
+                const int e = j0 + tid;
+                int k = 0;
+                while (s_off[k + 1] <= e) k++;
+                const int mu = tile_beads[s_bin0[k] + (e - s_off[k])];
+                s_mu[tid] = mu;
+                s_fl[tid][0] = bfl[3 * mu];
+                s_fl[tid][1] = bfl[3 * mu + 1];
+                s_fl[tid][2] = bfl[3 * mu + 2];
+            }
+            __syncthreads();
+            for (int e = tid; e < jn * w3; e += blockDim.x) {
+                const int i = e / w3, r = e - i * w3;
+                s_w[i][r] = bw[(size_t)s_mu[i] * w3 + r];
+            }
+            for (int e = tid; e < jn * nx; e += blockDim.x) {
+                const int i = e / nx, r = e - i * nx;
+                const int c = r / 3, bb = r - 3 * c;
+                s_x[i][r] = (T)X[(long)(c0 + c) * n3 + 3L * s_mu[i] + bb];
+            }
+            __syncthreads();
+            for (int j = 0; j < jn; j++) {
+                int v0 = s_fl[j][0] - g[0], v1 = s_fl[j][1] - g[1], v2 = s_fl[j][2] - g[2];
+                v0 += v0 < 0 ? K : 0;
+                v1 += v1 < 0 ? K : 0;
+                v2 += v2 < 0 ? K : 0;
+                if (v0 < p && v1 < p && v2 < p) {
+                    const T ww = s_w[j][v0] * s_w[j][p + v1] * s_w[j][2 * p + v2];
+#pragma unroll
+                    for (int i = 0; i < 3 * CC; i++)
+                        if (i < nx) acc[i] += ww * s_x[j][i];
+                }
             }
         }
+#pragma unroll
+        for (int i = 0; i < 3 * CC; i++)
+            if (i < nx) q[(size_t)(3 * c0 + i) * K3 + gi] = acc[i];
     }
-}
-
-template <typename T>
-__global__ void k_pme_unfix(const unsigned long long *__restrict__ qfix, long len,
-                            const unsigned long long *__restrict__ xmax, int n, T *__restrict__ q)
-{
-    const long i = (long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= len) return;
-    (void)n;
-    const double inv = __longlong_as_double((long long)xmax[2]);
-    q[i] = (T)((double)(long long)qfix[i] * inv);
 }
 
 // Yhat(m) = G(m) |b(m)|^2 Qhat(m) for every column (3 x 3 real symmetric
@@ -370,40 +449,80 @@ __global__ void k_pme_influence_apply(const T *__restrict__ infl, long Kh, int m
     q[2 * Kh] = r2;
 }
 
-// Y[col][3 nu + b] += sum_g W(u_nu - g) Ymesh[3 col + b][g]
-template <typename T>
-__global__ void k_pme_gather(const double *__restrict__ pw, int n, double L, int K, int p,
-                             const T *__restrict__ q, int m, double *__restrict__ Y)
+// Y[col][3 nu + b] += sum_g W(u_nu - g) Ymesh[3 col + b][g]: one warp per
+// bead (beads in mesh-tile order, so a block's warps read the same
+// neighbourhood of the mesh), the lanes over the P^2 (j2, j3) spline points
+// of a plane -- one load instruction reads a few contiguous mesh rows -- the
+// planes j1 in order, one column at a time (the block's working set is one
+// column's neighbourhood), then a butterfly sum over the lanes (every lane
+// ends with the same, order-fixed sum)
+template <typename T, int P>
+__global__ void __launch_bounds__(256)
+k_pme_gather(int n, int K, const int *__restrict__ tile_beads, const int *__restrict__ bfl,
+             const T *__restrict__ bw, const T *__restrict__ q, int m, double *__restrict__ Y)
 {
-    const long tid = (long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (tid >= (long)n * m) return;
-    const int nu = (int)(tid % n), col = (int)(tid / n);
-    const long n3 = 3L * n, K3 = (long)K * K * K;
-    T w[3][kMaxOrder];
-    int g0[3];
-    for (int d = 0; d < 3; d++) {
-        const double u = pw[3 * nu + d] * K / L;
-        double fl = floor(u);
-        bspline_weights<T>((T)(u - fl), p, w[d]);
-        g0[d] = (int)fl;
+    constexpr int NP = P * P, PER = (NP + 31) / 32;
+    const int lane = threadIdx.x & 31;
+    const int i = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    if (i >= n) return;
+    const int nu = tile_beads[i];
+    const T *wb = bw + (size_t)nu * 3 * P;
+    const int g0 = bfl[3 * nu], g1 = bfl[3 * nu + 1], g2 = bfl[3 * nu + 2];
+    const long K3 = (long)K * K * K, n3 = 3L * n;
+    int off[PER];
+    T w23[PER];
+#pragma unroll
+    for (int h = 0; h < PER; h++) {
+        const int c = lane + 32 * h;
+        const int j2 = c / P, j3 = c - (c / P) * P;
+        const bool ok = c < NP;
+        const int a2 = g1 - j2 < 0 ? g1 - j2 + K : g1 - j2;
+        const int a3 = g2 - j3 < 0 ? g2 - j3 + K : g2 - j3;
+        off[h] = ok ? a2 * K + a3 : 0;
+        w23[h] = ok ? wb[P + j2] * wb[2 * P + j3] : (T)0;
     }
-    const T *q0 = q + (size_t)(3 * col) * K3;
-    T y[3] = {0, 0, 0};
-    for (int j1 = 0; j1 < p; j1++) {
-        const int a1 = ((g0[0] - j1) % K + K) % K;
-        for (int j2 = 0; j2 < p; j2++) {
-            const int a2 = ((g0[1] - j2) % K + K) % K;
-            const T w12 = w[0][j1] * w[1][j2];
-            for (int j3 = 0; j3 < p; j3++) {
-                const int a3 = ((g0[2] - j3) % K + K) % K;
-                const long g = ((long)a1 * K + a2) * K + a3;
-                const T ww = w12 * w[2][j3];
-                for (int b = 0; b < 3; b++) y[b] += ww * q0[(size_t)b * K3 + g];
+    for (int col = 0; col < m; col++) {
+        const T *qc = q + (size_t)(3 * col) * K3;
+        T a0 = 0, a1 = 0, a2 = 0;
+#pragma unroll 2
+        for (int j1 = 0; j1 < P; j1++) {
+            const int r1 = g0 - j1 < 0 ? g0 - j1 + K : g0 - j1;
+            const T *pl = qc + (long)r1 * K * K;
+            const T w1 = wb[j1];
+#pragma unroll
+            for (int h = 0; h < PER; h++) {
+                if (lane + 32 * h < NP) {
+                    const T ww = w1 * w23[h];
+                    const T *pt = pl + off[h];
+                    a0 += ww * pt[0];
+                    a1 += ww * pt[K3];
+                    a2 += ww * pt[2 * K3];
+                }
             }
         }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            a0 += __shfl_xor_sync(0xffffffffu, a0, o);
+            a1 += __shfl_xor_sync(0xffffffffu, a1, o);
+            a2 += __shfl_xor_sync(0xffffffffu, a2, o);
+        }
+        if (lane < 3) Y[(long)col * n3 + 3L * nu + lane] += (double)(lane == 0 ? a0 : (lane == 1 ? a1 : a2));
     }
-    double *out = Y + (long)col * n3 + 3L * nu;
-    for (int b = 0; b < 3; b++) out[b] += (double)y[b];
+}
+
+template <typename T>
+static void launch_gather(const PmeState *S, int n, int m, double *Y, cudaStream_t s)
+{
+    const unsigned nb = (unsigned)((n + 7) / 8);
+    const T *bw = (const T *)S->d_bw, *q = (const T *)S->d_qreal;
+#define GATHER(PP)                                                                      \
+    case PP:                                                                            \
+        k_pme_gather<T, PP><<<nb, 256, 0, s>>>(n, S->K, S->d_tile_beads, S->d_bfl, bw, q, m, Y); \
+        break;
+    switch (S->p) {
+        GATHER(4) GATHER(5) GATHER(6) GATHER(7) GATHER(8) GATHER(9) GATHER(10)
+    }
+#undef GATHER
 }
 
 static bd_status cufft_plans(Plan &P, int m)
@@ -436,48 +555,37 @@ bd_status launch_apply_spectral(Plan &P, const double *X, int m, double *Y, cuda
     PmeState *S = P.pme;
     if (!S) return set_error(BD_ERR_INVALID, "plan has no mesh (pme_grid = 0)");
     if (m > S->mcap) return set_error(BD_ERR_INVALID, "m = %d exceeds the mesh capacity %d", m, S->mcap);
-    bd_status st = launch_real_cells(P, X, m, Y, s);
+    bd_status st = launch_real_pairs(P, X, m, Y, s);
     if (st != BD_OK) return st;
     if (P.p.n2max <= 0) return BD_OK;
     st = cufft_plans(P, m);
     if (st != BD_OK) return st;
-    const long n3 = (long)P.n3;
-    const long grid_len = (long)3 * m * S->K3;
-    cudaMemsetAsync(S->d_xmax, 0, sizeof(unsigned long long), s);
-    k_absmax_all<<<256, 256, 0, s>>>(X, n3 * m, S->d_xmax);
-    k_fix_scale<<<1, 1, 0, s>>>(S->d_xmax, P.n);
-    count_launches(1);
-    cudaMemsetAsync(S->d_qfix, 0, sizeof(unsigned long long) * grid_len, s);
-    const unsigned nbm = (unsigned)(((long)P.n * m + 127) / 128);
-    const unsigned ng = (unsigned)((grid_len + 255) / 256);
+    const unsigned ntiles = (unsigned)S->ntile;
     const unsigned nh = (unsigned)((S->Kh * m + 255) / 256);
+    constexpr int kTileThreads = kMeshTile * kMeshTile * kMeshTile;
     cufftSetStream(S->fwd, s);
     cufftSetStream(S->inv, s);
     cufftResult r1, r2;
     if (!is_mixed(P)) {
-        k_pme_spread<double><<<nbm, 128, 0, s>>>(P.d_pw64, P.n, P.p.box_L, S->K, S->p, X, m,
-                                                S->d_xmax, S->d_qfix);
-        k_pme_unfix<double><<<ng, 256, 0, s>>>(S->d_qfix, grid_len, S->d_xmax, P.n,
-                                              (double *)S->d_qreal);
+        k_pme_spread<double, 6><<<ntiles, kTileThreads, 0, s>>>(
+            P.n, S->K, S->p, S->tpd, S->d_tile_start, S->d_tile_beads, S->d_bfl,
+            (const double *)S->d_bw, X, m, (double *)S->d_qreal);
         r1 = cufftExecD2Z(S->fwd, (cufftDoubleReal *)S->d_qreal, (cufftDoubleComplex *)S->d_qhat);
         k_pme_influence_apply<double, cufftDoubleComplex><<<nh, 256, 0, s>>>(
             (const double *)S->d_infl, S->Kh, m, (cufftDoubleComplex *)S->d_qhat);
         r2 = cufftExecZ2D(S->inv, (cufftDoubleComplex *)S->d_qhat, (cufftDoubleReal *)S->d_qreal);
-        k_pme_gather<double><<<nbm, 128, 0, s>>>(P.d_pw64, P.n, P.p.box_L, S->K, S->p,
-                                                (const double *)S->d_qreal, m, Y);
+        launch_gather<double>(S, P.n, m, Y, s);
     } else {
-        k_pme_spread<float><<<nbm, 128, 0, s>>>(P.d_pw64, P.n, P.p.box_L, S->K, S->p, X, m,
-                                               S->d_xmax, S->d_qfix);
-        k_pme_unfix<float><<<ng, 256, 0, s>>>(S->d_qfix, grid_len, S->d_xmax, P.n,
-                                             (float *)S->d_qreal);
+        k_pme_spread<float, 12><<<ntiles, kTileThreads, 0, s>>>(
+            P.n, S->K, S->p, S->tpd, S->d_tile_start, S->d_tile_beads, S->d_bfl,
+            (const float *)S->d_bw, X, m, (float *)S->d_qreal);
         r1 = cufftExecR2C(S->fwd, (cufftReal *)S->d_qreal, (cufftComplex *)S->d_qhat);
         k_pme_influence_apply<float, cufftComplex><<<nh, 256, 0, s>>>(
             (const float *)S->d_infl, S->Kh, m, (cufftComplex *)S->d_qhat);
         r2 = cufftExecC2R(S->inv, (cufftComplex *)S->d_qhat, (cufftReal *)S->d_qreal);
-        k_pme_gather<float><<<nbm, 128, 0, s>>>(P.d_pw64, P.n, P.p.box_L, S->K, S->p,
-                                               (const float *)S->d_qreal, m, Y);
+        launch_gather<float>(S, P.n, m, Y, s);
     }
-    count_launches(6);
+    count_launches(3);
     if (r1 != CUFFT_SUCCESS || r2 != CUFFT_SUCCESS)
         return set_error(BD_ERR_CUDA, "cuFFT execution failed (%d, %d)", (int)r1, (int)r2);
     return check_launch("spectral product");
