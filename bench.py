@@ -55,7 +55,8 @@ def parse():
                          "carried in the products; fresh = --lanczos products per step")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=3)
-    ap.add_argument("--workload", default="n8000", choices=["n8000", "batch", "theta", "lma"],
+    ap.add_argument("--workload", default="n8000",
+                    choices=["n8000", "batch", "theta", "lma", "spectral"],
                     help="batch: 64 replicas, N ~ U[200, 2000], mixed, one graph launch "
                          "per step (replica-steps/s); theta: the theta-solution statics "
                          "validation (N_b = 20 and 40, N_c = 20, a = 0.5, dt = 0.01, five "
@@ -583,19 +584,34 @@ def run_theta(args):
     print(json.dumps(line), flush=True)
 
 
-def spectral_params(cfg, r_c=6.0, order=8):
+def fft_size(k):
+    """Smallest multiple of 8 >= k whose prime factors are 2, 3 and 5 (cuFFT
+    runs such sizes fastest; a factor 7 measured ~40 % slower)."""
+    K = int(math.ceil(k / 8.0)) * 8
+    while True:
+        r = K
+        for f in (2, 3, 5):
+            while r % f == 0:
+                r //= f
+        if r == 1:
+            return K
+        K += 8
+
+
+def spectral_params(cfg, r_c=6.0, order=8, mesh_per_L=2.5):
     """Spectral-path parameters for a system: r_c = 6 l_H (alpha = M/r_c), the
     k-sphere of the same accuracy target, order-8 B-splines on a mesh of
-    3.5 L points per edge (rounded up to 8; the mesh error then sits at the
-    FP32 floor, ~1e-6, by the measured (m_eff/K)^p convergence with
-    m_eff ~ M L/(pi r_c))."""
+    2.5 L points per edge (rounded up by fft_size).  Measured on the N = 8000
+    system against a converged mesh (order 10, 6 L points): the mesh error
+    is 3.3e-7 in FP64 there, below the FP32 floor of the mixed product
+    (1.0e-6, the same as with 3.5 L points)."""
     from paper_1203_6208_gb300 import inputs
     L = cfg.params()["L"]
     f = cfg.M / r_c * L / inputs.SQRT_PI
     q = replace_cfg(cfg, alpha_factor=f).params()
     kmax = math.sqrt(q["n2max"])
-    K = max(3.5 * L, 2 * math.ceil(kmax) + 2)
-    q.update(pme_grid=int(math.ceil(K / 8.0)) * 8, pme_order=order)
+    K = max(mesh_per_L * L, 2 * math.ceil(kmax) + 2)
+    q.update(pme_grid=fft_size(K), pme_order=order)
     return q
 
 
@@ -610,7 +626,8 @@ def run_lma(args):
     steps (real space over cell lists, reciprocal sum on a mesh) on the theta
     workload of the headline (c/c* = 4, 20-bead chains, m = 16, N_Ch = 40,
     mixed), at N = 8000 and larger N; dense runs only where D fits in device
-    memory, the pair-sum LMA only up to N = 100 000."""
+    memory, the pair-sum LMA only up to N = 32 000 (53 s per step at N = 100 000),
+    the spectral path up to N = 300 000."""
     import torch
     torch.cuda.set_device(0)
     from paper_1203_6208_gb300 import binding as bnd, build, inputs
@@ -624,7 +641,7 @@ def run_lma(args):
         row = {}
         for mode in ("dense", "matfree", "spectral"):
             q = spectral_params(cfg) if mode == "spectral" else p
-            if mode == "matfree" and chains > 5000:
+            if mode == "matfree" and chains > 1600:
                 row[mode] = {"skipped": "pair-sum LMA too slow at this N"}
                 continue
             plan = bnd.Plan(q, "mixed_f16", max_rhs=args.m, max_cheb=args.nch)
@@ -655,6 +672,7 @@ def run_lma(args):
             plan.close()
             torch.cuda.empty_cache()
         res[f"N={cfg.n}"] = row
+        print(f"N={cfg.n}", json.dumps(row), file=sys.stderr, flush=True)
     head = res["N=8000"]
     line = {"metric": "steps/sec, dense D (HMA) vs matrix-free (LMA) vs spectral, mixed",
             "value": head["spectral"]["steps_per_s"], "unit": "steps/s (spectral, N=8000)",
@@ -663,6 +681,44 @@ def run_lma(args):
             "config": {"workload": "lma", "m": args.m, "n_cheb": args.nch,
                        "bounds": "fixman semidilute (C = 8)", "alpha_factor": 1.75},
             "results": res}
+    print(json.dumps(line), flush=True)
+
+
+def run_spectral(args):
+    """The spectral matrix-free product Y = D(R) X of m + 1 columns (drift and
+    Wiener columns, as in a Chebyshev product), each call building the
+    per-position tables too (cell list, neighbour table, mesh-tile bins) --
+    the unit the spectral step repeats; c/c* = 4, 20-bead chains, mixed."""
+    import torch
+    torch.cuda.set_device(0)
+    from paper_1203_6208_gb300 import binding as bnd, build, inputs
+    build.build()
+    cfg, _ = inputs.preset("c4", alpha_factor=1.75, n_chains=args.chains)
+    q = spectral_params(cfg)
+    m = args.m + 1
+    plan = bnd.Plan(q, "mixed_f16", max_rhs=args.m, max_cheb=args.nch)
+    R = torch.tensor(inputs.make_chains(cfg).reshape(-1), device="cuda")
+    g = torch.Generator(device="cuda").manual_seed(5)
+    X = torch.randn(m, 3 * cfg.n, dtype=torch.float64, device="cuda", generator=g)
+    Y = torch.empty_like(X)
+    for _ in range(max(args.warmup, 3)):
+        plan.apply_matfree(R, X, Y)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(args.steps):
+        plan.apply_matfree(R, X, Y)
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / args.steps
+    line = {"metric": "spectral products/sec (tables included)", "value": 1e3 / ms,
+            "unit": "products/s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32+f64", "data": "synthetic",
+            "config": {"workload": "spectral", "n_beads": cfg.n, "columns": m, "r_c": q["rc"],
+                       "n2max": q["n2max"], "mesh": q["pme_grid"], "order": q["pme_order"],
+                       "l2": "mesh larger than L2"}}
+    plan.close()
     print(json.dumps(line), flush=True)
 
 
@@ -675,6 +731,8 @@ def main():
         run_theta(args)
     elif args.workload == "lma":
         run_lma(args)
+    elif args.workload == "spectral":
+        run_spectral(args)
     elif args.workload == "batch":
         run_batch(args)
     else:

@@ -337,11 +337,14 @@ bd_status spectral_tables(Plan &P, cudaStream_t s)
 // bead with base index f_d = floor(u_d) reaches the points f_d - j, j < p,
 // so the tile's beads are those binned in tiles t_d .. t_d + 1 + (p-2)/E per
 // dimension (mod tpd).  The block stages them (bins in a fixed order, beads
-// ascending inside a bin) with their base indices, weights and operand rows;
-// each thread adds w1[j1] w2[j2] w3[j3] x over the beads with
+// ascending inside a bin) with their base indices, weights and operand rows.
+// Each warp covers a 2 x 4 x 4 brick of points and first compacts (ballot)
+// the staged beads that reach its brick, keeping their order; each thread
+// then adds w1[j1] w2[j2] w3[j3] x over those beads with
 // j_d = (f_d - g_d) mod K < p.  Every mesh point is written once and summed in
 // a fixed order: no atomics.  The columns go in balanced chunks of <= CC.
-constexpr int kStage = 64;
+template <typename T> struct SpreadStage { static constexpr int value = 128; };
+template <> struct SpreadStage<double> { static constexpr int value = 64; };
 
 template <typename T, int CC>
 __global__ void __launch_bounds__(kMeshTile *kMeshTile *kMeshTile)
@@ -350,14 +353,23 @@ k_pme_spread(int n, int K, int p, int tpd, const int *__restrict__ tile_start,
              const T *__restrict__ bw, const double *__restrict__ X, int m, T *__restrict__ q)
 {
     constexpr int E = kMeshTile;
+    constexpr int NW = E * E * E / 32;                     // warps: 4 x 2 x 2 bricks
+    constexpr int ST = SpreadStage<T>::value;
+    constexpr int VW = 16 / sizeof(T);                     // T per 16-byte shared load
+    constexpr int XW = (3 * CC + VW - 1) / VW * VW;        // staged operand row
     __shared__ int s_bin0[27], s_off[28];
-    __shared__ int s_mu[kStage];
-    __shared__ int s_fl[kStage][3];
-    __shared__ T s_w[kStage][3 * kMaxOrder];
-    __shared__ T s_x[kStage][3 * CC];
+    __shared__ int s_mu[ST];
+    __shared__ int4 s_fl[ST];
+    __shared__ T s_w[ST][3 * kMaxOrder];
+    __shared__ __align__(16) T s_x[ST][XW];
+    __shared__ unsigned char s_list[NW][ST];
     const int b = blockIdx.x, tid = threadIdx.x;
+    const int lane = tid & 31, wid = tid >> 5;
     const int t[3] = {b / (tpd * tpd), (b / tpd) % tpd, b % tpd};
-    const int g[3] = {t[0] * E + tid / (E * E), t[1] * E + (tid / E) % E, t[2] * E + tid % E};
+    // brick origin of this warp and the thread's point inside it
+    const int w0[3] = {t[0] * E + 2 * (wid >> 2), t[1] * E + 4 * ((wid >> 1) & 1), t[2] * E + 4 * (wid & 1)};
+    const int g[3] = {w0[0] + (lane >> 4), w0[1] + ((lane >> 2) & 3), w0[2] + (lane & 3)};
+    const int reach[3] = {p, p + 2, p + 2};                // (f - w0) mod K <= p + extent - 2
     const int nbd = min(2 + (p - 2) / E, tpd);
     const int nbins = nbd * nbd * nbd;
     if (tid < nbins) {
@@ -382,8 +394,8 @@ k_pme_spread(int n, int K, int p, int tpd, const int *__restrict__ tile_start,
         T acc[3 * CC];
 #pragma unroll
         for (int i = 0; i < 3 * CC; i++) acc[i] = (T)0;
-        for (int j0 = 0; j0 < total; j0 += kStage) {
-            const int jn = min(kStage, total - j0);
+        for (int j0 = 0; j0 < total; j0 += ST) {
+            const int jn = min(ST, total - j0);
             __syncthreads();
             if (tid < jn) {
                 const int e = j0 + tid;
@@ -391,9 +403,7 @@ k_pme_spread(int n, int K, int p, int tpd, const int *__restrict__ tile_start,
                 while (s_off[k + 1] <= e) k++;
                 const int mu = tile_beads[s_bin0[k] + (e - s_off[k])];
                 s_mu[tid] = mu;
-                s_fl[tid][0] = bfl[3 * mu];
-                s_fl[tid][1] = bfl[3 * mu + 1];
-                s_fl[tid][2] = bfl[3 * mu + 2];
+                s_fl[tid] = make_int4(bfl[3 * mu], bfl[3 * mu + 1], bfl[3 * mu + 2], 0);
             }
             __syncthreads();
             for (int e = tid; e < jn * w3; e += blockDim.x) {
@@ -405,17 +415,44 @@ k_pme_spread(int n, int K, int p, int tpd, const int *__restrict__ tile_start,
                 const int c = r / 3, bb = r - 3 * c;
                 s_x[i][r] = (T)X[(long)(c0 + c) * n3 + 3L * s_mu[i] + bb];
             }
+            // this warp's beads, in staging order
+            int cnt = 0;
+            for (int jj = 0; jj < jn; jj += 32) {
+                const int j = jj + lane;
+                bool in = false;
+                if (j < jn) {
+                    const int4 f = s_fl[j];
+                    int d0 = f.x - w0[0], d1 = f.y - w0[1], d2 = f.z - w0[2];
+                    d0 += d0 < 0 ? K : 0;
+                    d1 += d1 < 0 ? K : 0;
+                    d2 += d2 < 0 ? K : 0;
+                    in = d0 <= reach[0] && d1 <= reach[1] && d2 <= reach[2];
+                }
+                const unsigned bal = __ballot_sync(0xffffffffu, in);
+                if (in) s_list[wid][cnt + __popc(bal & ((1u << lane) - 1u))] = (unsigned char)j;
+                cnt += __popc(bal);
+            }
             __syncthreads();
-            for (int j = 0; j < jn; j++) {
-                int v0 = s_fl[j][0] - g[0], v1 = s_fl[j][1] - g[1], v2 = s_fl[j][2] - g[2];
+            for (int l = 0; l < cnt; l++) {
+                const int j = s_list[wid][l];
+                const int4 f = s_fl[j];
+                int v0 = f.x - g[0], v1 = f.y - g[1], v2 = f.z - g[2];
                 v0 += v0 < 0 ? K : 0;
                 v1 += v1 < 0 ? K : 0;
                 v2 += v2 < 0 ? K : 0;
                 if (v0 < p && v1 < p && v2 < p) {
                     const T ww = s_w[j][v0] * s_w[j][p + v1] * s_w[j][2 * p + v2];
 #pragma unroll
-                    for (int i = 0; i < 3 * CC; i++)
-                        if (i < nx) acc[i] += ww * s_x[j][i];
+                    for (int v = 0; v < XW / VW; v++) {
+                        const uint4 u = *reinterpret_cast<const uint4 *>(&s_x[j][v * VW]);
+                        T xv[VW];
+                        memcpy(xv, &u, 16);
+#pragma unroll
+                        for (int e = 0; e < VW; e++) {
+                            const int i = v * VW + e;
+                            if (i < 3 * CC && i < nx) acc[i] += ww * xv[e];
+                        }
+                    }
                 }
             }
         }
@@ -576,7 +613,7 @@ bd_status launch_apply_spectral(Plan &P, const double *X, int m, double *Y, cuda
         r2 = cufftExecZ2D(S->inv, (cufftDoubleComplex *)S->d_qhat, (cufftDoubleReal *)S->d_qreal);
         launch_gather<double>(S, P.n, m, Y, s);
     } else {
-        k_pme_spread<float, 12><<<ntiles, kTileThreads, 0, s>>>(
+        k_pme_spread<float, 9><<<ntiles, kTileThreads, 0, s>>>(
             P.n, S->K, S->p, S->tpd, S->d_tile_start, S->d_tile_beads, S->d_bfl,
             (const float *)S->d_bw, X, m, (float *)S->d_qreal);
         r1 = cufftExecR2C(S->fwd, (cufftReal *)S->d_qreal, (cufftComplex *)S->d_qhat);
