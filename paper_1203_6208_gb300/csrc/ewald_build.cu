@@ -898,6 +898,47 @@ template <> struct PosSplit<float> {
     }
 };
 
+// positions in cell order (row r is bead cell_beads[r]): 32 bytes a row, the
+// working-precision split (hi, lo) of the wrapped position
+struct __align__(32) RowPos64 { double x, y, z, w; };
+
+template <typename T> struct RowPos;
+template <> struct RowPos<double> {
+    using V = RowPos64;
+    __device__ static void get(const V *rp, int r, double h[3], double l[3])
+    {
+        const RowPos64 v = rp[r];
+        h[0] = v.x; h[1] = v.y; h[2] = v.z;
+        l[0] = l[1] = l[2] = 0.0;
+    }
+};
+template <> struct RowPos<float> {
+    using V = float4;   // two per row: hi, lo
+    __device__ static void get(const float4 *rp, int r, float h[3], float l[3])
+    {
+        const float4 a = rp[2 * r], b = rp[2 * r + 1];
+        h[0] = a.x; h[1] = a.y; h[2] = a.z;
+        l[0] = b.x; l[1] = b.y; l[2] = b.z;
+    }
+};
+
+__global__ void k_row_positions(const double *__restrict__ pw, const float *__restrict__ pw32,
+                                int n, const int *__restrict__ cell_beads, int dbl,
+                                void *__restrict__ out)
+{
+    const int r = blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= n) return;
+    const int nu = cell_beads[r];
+    if (dbl) {
+        ((RowPos64 *)out)[r] = RowPos64{pw[3 * nu], pw[3 * nu + 1], pw[3 * nu + 2], 0.0};
+    } else {
+        const long n3 = 3L * n;
+        float4 *o = (float4 *)out;
+        o[2 * r] = make_float4(pw32[3 * nu], pw32[3 * nu + 1], pw32[3 * nu + 2], 0.f);
+        o[2 * r + 1] = make_float4(pw32[n3 + 3 * nu], pw32[n3 + 3 * nu + 1], pw32[n3 + 3 * nu + 2], 0.f);
+    }
+}
+
 // one warp per row: the candidate rows of the row's (2 span + 1)^3 cells are
 // taken 32 at a time in a fixed order (cells in offset order, rows ascending
 // inside a cell).  FILL = false counts those within r_c (the row itself
@@ -911,7 +952,7 @@ constexpr int kPairWarps = 8;
 
 template <typename T, bool FILL>
 __global__ void __launch_bounds__(32 * kPairWarps)
-k_real_pairs(const double *__restrict__ pw, const float *__restrict__ pw32, int n,
+k_real_pairs(const typename RowPos<T>::V *__restrict__ rp, int n,
              const __grid_constant__ EwaldT<T> c, const int *__restrict__ cell_start,
              const int *__restrict__ cell_beads, const int *__restrict__ cell_of, int nc, int span,
              int *__restrict__ row_start, int *__restrict__ nbr, int *__restrict__ prow)
@@ -921,9 +962,7 @@ k_real_pairs(const double *__restrict__ pw, const float *__restrict__ pw32, int 
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     const int r = blockIdx.x * kPairWarps + wid;
     if (r >= n) return;                                  // the whole warp
-    const long n3 = 3L * n;
-    const int nu = cell_beads[r];
-    const int cell = cell_of[nu];
+    const int cell = cell_of[cell_beads[r]];
     const int cx = cell / (nc * nc), cy = (cell / nc) % nc, cz = cell % nc;
     const int w = 2 * span + 1, ncells = w * w * w;
     int *lo = s_lo[wid], *pre = s_pre[wid];
@@ -941,7 +980,7 @@ k_real_pairs(const double *__restrict__ pw, const float *__restrict__ pw32, int 
     __syncwarp();
     const int total = pre[ncells];
     T mh[3], ml[3];
-    PosSplit<T>::get(pw, pw32, n3, nu, mh, ml);
+    RowPos<T>::get(rp, r, mh, ml);
     long k = FILL ? (long)row_start[r] : 0;
     const long kend = FILL ? (long)row_start[r + 1] : 0;
     int cnt = 0, cc = 0;
@@ -952,12 +991,11 @@ k_real_pairs(const double *__restrict__ pw, const float *__restrict__ pw32, int 
         if (t < total) {
             while (pre[cc + 1] <= t) cc++;               // t grows: the cell cursor only advances
             j = lo[cc] + (t - pre[cc]);
-            const int mu = cell_beads[j];
-            if (mu == nu) {
+            if (j == r) {
                 in = true;
             } else {
                 T h[3], l[3], d[3];
-                PosSplit<T>::get(pw, pw32, n3, mu, h, l);
+                RowPos<T>::get(rp, j, h, l);
                 sep_split<T>(mh, ml, h, l, c, d);
                 const T u = fma(d[2], d[2], fma(d[1], d[1], d[0] * d[0]));
                 in = u <= c.rc2;
@@ -990,10 +1028,9 @@ k_real_pairs(const double *__restrict__ pw, const float *__restrict__ pw32, int 
 // the 3x3 blocks of the table, one thread per entry: real-space image,
 // overlap branch or the self term (Eqs. M1, DFmodified, DF)
 template <typename T>
-__global__ void k_pair_blocks(const double *__restrict__ pw, const float *__restrict__ pw32, int n,
+__global__ void k_pair_blocks(const typename RowPos<T>::V *__restrict__ rp,
                               const __grid_constant__ EwaldT<T> c, const T *__restrict__ tab,
-                              int tab_i0, int ntab, int overlap_corr,
-                              const int *__restrict__ cell_beads, const int *__restrict__ prow,
+                              int tab_i0, int ntab, int overlap_corr, const int *__restrict__ prow,
                               const int *__restrict__ nbr, long np, T *__restrict__ tens, long cap)
 {
     const long k = (long)blockIdx.x * blockDim.x + threadIdx.x;
@@ -1005,10 +1042,9 @@ __global__ void k_pair_blocks(const double *__restrict__ pw, const float *__rest
         if (j == r) {
             acc[0] = c.self; acc[3] = c.self; acc[5] = c.self;
         } else {
-            const long n3 = 3L * n;
             T mh[3], ml[3], h[3], l[3], d[3];
-            PosSplit<T>::get(pw, pw32, n3, cell_beads[r], mh, ml);
-            PosSplit<T>::get(pw, pw32, n3, cell_beads[j], h, l);
+            RowPos<T>::get(rp, r, mh, ml);
+            RowPos<T>::get(rp, j, h, l);
             sep_split<T>(mh, ml, h, l, c, d);
             const T u = fma(d[2], d[2], fma(d[1], d[1], d[0] * d[0]));
             if (u >= c.four_a2) add_m1_tab<T>(d[0], d[1], d[2], u, tab, tab_i0, ntab, acc);
@@ -1117,14 +1153,15 @@ static void pairs_pass(Plan &P, const EwaldT<T> &c, bool fill, cudaStream_t s)
 {
     PmeState *S = P.pme;
     const unsigned nb = (unsigned)((P.n + kPairWarps - 1) / kPairWarps);
+    const auto *rp = (const typename RowPos<T>::V *)S->d_rowpos;
     if (fill)
         k_real_pairs<T, true><<<nb, 32 * kPairWarps, 0, s>>>(
-            P.d_pw64, P.d_pw32, P.n, c, S->d_cell_start, S->d_cell_beads, S->d_cell_of, S->nc,
-            S->span, S->d_row_start, S->d_nbr, S->d_prow);
+            rp, P.n, c, S->d_cell_start, S->d_cell_beads, S->d_cell_of, S->nc, S->span,
+            S->d_row_start, S->d_nbr, S->d_prow);
     else
         k_real_pairs<T, false><<<nb, 32 * kPairWarps, 0, s>>>(
-            P.d_pw64, P.d_pw32, P.n, c, S->d_cell_start, S->d_cell_beads, S->d_cell_of, S->nc,
-            S->span, S->d_row_start, nullptr, nullptr);
+            rp, P.n, c, S->d_cell_start, S->d_cell_beads, S->d_cell_of, S->nc, S->span,
+            S->d_row_start, nullptr, nullptr);
     count_launches(1);
 }
 
@@ -1134,6 +1171,9 @@ bd_status build_real_pairs(Plan &P, cudaStream_t s)
     if (S->span > 2) return set_error(BD_ERR_INVALID, "cell search span %d > 2", S->span);
     const bool dbl = !is_mixed(P);
     const size_t ts = dbl ? sizeof(double) : sizeof(float);
+    k_row_positions<<<(P.n + 255) / 256, 256, 0, s>>>(P.d_pw64, P.d_pw32, P.n, S->d_cell_beads,
+                                                      dbl ? 1 : 0, S->d_rowpos);
+    count_launches(1);
     if (dbl) pairs_pass<double>(P, P.h_ew64, false, s);
     else pairs_pass<float>(P, P.h_ew32, false, s);
     // counts -> starts (the counts array doubles as the cursor array of the scan)
@@ -1166,16 +1206,14 @@ bd_status build_real_pairs(Plan &P, cudaStream_t s)
     const unsigned nbp = (unsigned)((np + 255) / 256);
     if (dbl) {
         pairs_pass<double>(P, P.h_ew64, true, s);
-        k_pair_blocks<double><<<nbp, 256, 0, s>>>(P.d_pw64, P.d_pw32, P.n, P.h_ew64, P.d_tab,
-                                                   P.tab_i0, P.ntab, P.p.overlap_corr,
-                                                   S->d_cell_beads, S->d_prow, S->d_nbr, np,
-                                                   (double *)S->d_tens, S->pair_cap);
+        k_pair_blocks<double><<<nbp, 256, 0, s>>>((const RowPos64 *)S->d_rowpos, P.h_ew64, P.d_tab,
+                                                   P.tab_i0, P.ntab, P.p.overlap_corr, S->d_prow,
+                                                   S->d_nbr, np, (double *)S->d_tens, S->pair_cap);
     } else {
         pairs_pass<float>(P, P.h_ew32, true, s);
-        k_pair_blocks<float><<<nbp, 256, 0, s>>>(P.d_pw64, P.d_pw32, P.n, P.h_ew32, P.d_tab32,
-                                                  P.tab_i0, P.ntab, P.p.overlap_corr,
-                                                  S->d_cell_beads, S->d_prow, S->d_nbr, np,
-                                                  (float *)S->d_tens, S->pair_cap);
+        k_pair_blocks<float><<<nbp, 256, 0, s>>>((const float4 *)S->d_rowpos, P.h_ew32, P.d_tab32,
+                                                  P.tab_i0, P.ntab, P.p.overlap_corr, S->d_prow,
+                                                  S->d_nbr, np, (float *)S->d_tens, S->pair_cap);
     }
     count_launches(1);
     return check_launch("neighbour table");

@@ -133,6 +133,7 @@ bd_status spectral_init(Plan &P)
     ALLOC(S->d_cell_beads, sizeof(int) * P.n);
     ALLOC(S->d_cell_tmp, sizeof(int) * P.n);
     ALLOC(S->d_row_start, sizeof(int) * (P.n + 1));
+    ALLOC(S->d_rowpos, (size_t)32 * P.n);
     S->xrows_len = real_pairs_rows_len(P.n, S->mcap, dbl);
     ALLOC(S->d_xrows, ts * S->xrows_len);
     ALLOC(S->d_infl, ts * 6 * S->Kh);
@@ -174,7 +175,7 @@ void spectral_free(Plan &P)
     PmeState *S = P.pme;
     if (!S) return;
     void *ptrs[] = {S->d_cell_of, S->d_cell_count, S->d_cell_start, S->d_cell_beads, S->d_cell_tmp,
-                    S->d_row_start, S->d_nbr, S->d_prow, S->d_tens, S->d_xrows, S->d_infl, S->d_tile_of, S->d_tile_count, S->d_tile_start,
+                    S->d_row_start, S->d_rowpos, S->d_nbr, S->d_prow, S->d_tens, S->d_xrows, S->d_infl, S->d_tile_of, S->d_tile_count, S->d_tile_start,
                     S->d_tile_beads, S->d_bfl, S->d_bw, S->d_qreal, S->d_qhat};
     for (void *q : ptrs)
         if (q) cudaFree(q);

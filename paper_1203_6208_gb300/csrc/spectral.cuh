@@ -26,6 +26,7 @@ struct PmeState {
     // included) and the six components of their 3x3 block, stored by
     // component ([6][pair_cap])
     int *d_row_start;             // [n + 1] first entry of each row (counts before the scan)
+    void *d_rowpos;               // [n] positions in row order, 32 bytes a row
     int *d_nbr;                   // [pair_cap] neighbour rows
     int *d_prow;                  // [pair_cap] the entry's own row (-1: padding)
     void *d_tens;                 // [6][pair_cap] xx, xy, xz, yy, yz, zz (working precision)
