@@ -247,7 +247,8 @@ def kernel_source_hash(path, name):
 
 
 KERNELS = {"fp64": ("paper_1203_6208_gb300/csrc/dense_f64.cu", "k_gemm_f64"),
-           "mixed": ("paper_1203_6208_gb300/csrc/tc_gemm.cu", "k_tc_gemm")}
+           "mixed": ("paper_1203_6208_gb300/csrc/tc_gemm.cu", "k_tc_gemm"),
+           "sym": ("paper_1203_6208_gb300/csrc/sym_gemm.cu", "k_sym_gemm")}
 
 
 def traffic_per_launch(kind):
@@ -299,7 +300,10 @@ def measure(args, precision, p, R0, rank, ws):
         if w == 0 and precision != "fp64":
             # launch shape of the tensor-core product, timed on this D
             cps, pms = plan.autotune(D)
-            shape = {"ctas_per_sm": cps, "autotune_ms": round(pms, 4)}
+            shape = ({"kernel": "symmetric (upper triangle of D16)", "autotune_ms": round(pms, 4)}
+                     if cps == bnd.BD_SHAPE_SYMMETRIC else
+                     {"kernel": "stream-K (all of D16)", "ctas_per_sm": cps,
+                      "autotune_ms": round(pms, 4)})
     torch.cuda.synchronize()
     stream = torch.cuda.current_stream()
     evs = [[torch.cuda.Event(enable_timing=True) for _ in range(7)] for _ in range(args.steps)]
@@ -356,19 +360,32 @@ def measure(args, precision, p, R0, rank, ws):
         lag = args.bounds == "lagged"
         cols = args.m + (1 if lag else 0)
         bn = 16 if cols <= 16 else 32
-        cps = (shape or {}).get("ctas_per_sm") or 2
-        st = (224 * 1024 if cps == 1 else 110 * 1024) // (128 * 64 * 2 + bn * 64 * 2)
-        # 16-bit D once, the 16-bit operand in and out, V_{p-1}, V_{p-2}, dS
-        # read and V_p, dS written (FP64), the Lanczos column's q_j, q_{j-1}
-        # read and w written
-        bytes_ = n3 * n3 * 2.0 + n3 * args.m * (2 + 2 + 8 * 5) + (n3 * (2 + 8 * 3) if lag else 0)
+        sym = "ctas_per_sm" not in (shape or {"ctas_per_sm": 2})
+        # the 16-bit operand in and out, V_{p-1}, V_{p-2}, dS read and V_p, dS
+        # written (FP64), the Lanczos column's q_j, q_{j-1} read and w written
+        vec = n3 * args.m * (2 + 2 + 8 * 5) + (n3 * (2 + 8 * 3) if lag else 0)
+        if sym:
+            # the tiles on and above the diagonal of the 16-bit D (diagonal
+            # tiles whole): the unique half of a symmetric D
+            t = -(-n3 // 128)
+            tiles = t * (t + 1) // 2
+            dbytes = min(tiles * 128 * 128, n3 * (n3 + 128) // 2) * 2.0
+            kernel = f"k_sym_gemm<{bn}> + k_sym_reduce<{bn}> (upper triangle, Chebyshev epilogue)"
+            what = "upper-triangle 16-bit D + vectors"
+        else:
+            cps = shape["ctas_per_sm"] if shape else 2
+            st = (224 * 1024 if cps == 1 else 110 * 1024) // (128 * 64 * 2 + bn * 64 * 2)
+            dbytes = n3 * n3 * 2.0
+            kernel = f"k_tc_gemm<{bn},{st}> (stream-K, Chebyshev epilogue)"
+            what = "16-bit D + vectors"
+        bytes_ = dbytes + vec
         achieved = bytes_ / (cheb_launch_ms * 1e-3) / 1e9
-        roof = {"bound": "hbm", "kernel": f"k_tc_gemm<{bn},{st}> (stream-K, Chebyshev epilogue)",
+        roof = {"bound": "hbm", "kernel": kernel,
                 "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
                 "frac": achieved / peaks["hbm_gbs"],
                 "peak_source": f"hbm_gbs ({peak_src} copy bandwidth)",
-                "traffic": traffic_per_launch("mixed"),
-                "algorithmic_per_launch": f"16-bit D + vectors = {bytes_:.3e} B",
+                "traffic": traffic_per_launch("sym" if sym else "mixed"),
+                "algorithmic_per_launch": f"{what} = {bytes_:.3e} B",
                 "launch_ms": cheb_launch_ms, "launches_timed": prod_n}
 
     # end to end through the public API with host buffers

@@ -335,14 +335,28 @@ bd_status bd_chebyshev_backward(bd_plan *plan, const double *R, const void *D,
                                 int32_t m, const double *gS, double *gR, double *gdW,
                                 bd_stream stream);
 
+/* Launch shapes of the mixed plans' tensor-core product Y = D16 X:
+ *   1, 2  the stream-K kernel over all of D16 with 1 or 2 resident CTAs per
+ *         SM (0, the default of a new plan, means 2);
+ *   3     the symmetric kernel: only the 128 x 128 tiles on and above the
+ *         diagonal are read, each serving D_IJ X_J and D_IJ^T X_I (D is
+ *         symmetric, Eq. DF), with a second kernel summing the partials in a
+ *         fixed order and running the epilogue.
+ * All shapes give the same product up to FP32 summation order.            */
+#define BD_SHAPE_SYMMETRIC 3
+
 /* Autotuner: for a mixed plan, times the tensor-core product on D (its
- * contents do not matter) with 1 and 2 resident CTAs per SM (the product is a
- * persistent stream-K kernel with one grid of that many CTAs) and keeps the
- * faster for all later products of this plan; returns the choice in
- * *split_out and the time per product (ms).  Synchronous.  FP64 plans: no-op
- * (0).                                                                   */
+ * contents do not matter) in shapes 1, 2 and 3 and keeps the fastest for all
+ * later products of this plan; returns the choice in *split_out and the time
+ * per product (ms).  Synchronous.  FP64 plans: no-op (0).                 */
 bd_status bd_plan_autotune(bd_plan *plan, void *D, int32_t *split_out, float *ms_out,
                            bd_stream stream);
+
+/* Set the launch shape (0..3, above) of the plan's later products without
+ * timing.  Shape 3 allocates its schedule and partial buffers on first use
+ * (synchronous, BD_ERR_OOM if they do not fit).  BD_ERR_INVALID outside 0..3;
+ * FP64 plans accept and ignore it.                                        */
+bd_status bd_plan_set_shape(bd_plan *plan, int32_t shape);
 
 /* Set the plan's device step counter used by BD_STEP_DEVICE_COUNTER (stream-
  * ordered write of one uint64). */

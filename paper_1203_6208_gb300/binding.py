@@ -26,12 +26,13 @@ PRECISIONS = {"fp64": 0, "mixed_f16": 1, "mixed_bf16": 2}
 BD_APPLY_REFINE = 1
 BD_STEP_DEVICE_COUNTER = 1
 BD_STEP_MATRIX_FREE = 2
+BD_SHAPE_SYMMETRIC = 3
 BOUNDS_MODES = {"fresh": 0, "lagged": 1, "fixman_dilute": 2, "fixman_semidilute": 3}
 
 EXPORTS = ["bd_plan_create", "bd_plan_destroy", "bd_plan_query", "bd_forces", "bd_build_D",
            "bd_apply_D", "bd_eig_bounds", "bd_chebyshev_sqrt", "bd_step", "bd_wiener",
            "bd_set_phase_events", "bd_kernel_launches", "bd_eig_bounds_noalloc",
-           "bd_apply_D_backward", "bd_chebyshev_backward", "bd_plan_autotune", "bd_product_timing",
+           "bd_apply_D_backward", "bd_chebyshev_backward", "bd_plan_autotune", "bd_plan_set_shape", "bd_product_timing",
            "bd_plan_set_step_counter", "bd_batch_create", "bd_batch_destroy", "bd_batch_query",
            "bd_batch_step", "bd_chebyshev_sqrt_adaptive", "bd_apply_D_matfree",
            "bd_last_error", "bd_version"]
@@ -102,6 +103,8 @@ def load(path: str = LIB_PATH):
     L.bd_wiener.argtypes = [_vp, u64, u64, i64, _vp, _vp]
     L.bd_set_phase_events.argtypes = [_vp, ctypes.POINTER(_vp), i32]
     L.bd_apply_D_backward.argtypes = [_vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp]
+    L.bd_plan_set_shape.argtypes = [_vp, i32]
+    L.bd_plan_set_shape.restype = i32
     L.bd_plan_autotune.argtypes = [_vp, _vp, ctypes.POINTER(i32), ctypes.POINTER(ctypes.c_float),
                                    _vp]
     L.bd_plan_set_step_counter.argtypes = [_vp, u64, _vp]
@@ -271,6 +274,11 @@ class Plan:
 
     def set_step_counter(self, value, stream=None):
         _check(load().bd_plan_set_step_counter(self._h, int(value), _stream(stream)))
+
+    def set_shape(self, shape: int):
+        """Launch shape of the mixed product: 1/2 stream-K CTAs per SM, 3 the
+        symmetric kernel over the upper triangle (BD_SHAPE_SYMMETRIC)."""
+        _check(load().bd_plan_set_shape(self._h, int(shape)))
 
     def autotune(self, D, stream=None):
         sp = ctypes.c_int32()

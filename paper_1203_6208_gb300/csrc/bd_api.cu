@@ -7,6 +7,7 @@
 #include <new>
 
 #include "bd_internal.cuh"
+#include "sym_gemm.cuh"
 #include "tc_gemm.cuh"
 #include "adjoint.cuh"
 #include "recip_tc.cuh"
@@ -81,6 +82,7 @@ static void free_plan(Plan &P)
         if (p) cudaFree(p);
     if (P.h_est) cudaFreeHost(P.h_est);
     spectral_free(P);
+    sym_plan_free(P);
 }
 
 static bd_status validate(const bd_params *p)
@@ -521,6 +523,20 @@ bd_status bd_plan_autotune(bd_plan *plan, void *D, int32_t *split_out, float *ms
     if (split_out) *split_out = best;
     if (ms_out) *ms_out = ms;
     return st;
+}
+
+bd_status bd_plan_set_shape(bd_plan *plan, int32_t shape)
+{
+    if (!plan) return set_error(BD_ERR_INVALID, "NULL plan");
+    if (shape < 0 || shape > kSymShape) return set_error(BD_ERR_INVALID, "shape %d outside 0..3", shape);
+    Plan &P = plan->P;
+    if (!is_mixed(P)) return BD_OK;
+    if (shape == kSymShape) {
+        bd_status st = sym_plan_init(P);
+        if (st != BD_OK) return st;
+    }
+    P.tc_split = shape;
+    return BD_OK;
 }
 
 bd_status bd_plan_set_step_counter(bd_plan *plan, uint64_t value, bd_stream stream)

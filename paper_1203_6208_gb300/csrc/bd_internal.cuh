@@ -58,6 +58,7 @@ constexpr int kMaxLanczos = 128;      // Lanczos steps
 constexpr int kLdAlign = 64;          // D leading dimension multiple (elements)
 
 struct PmeState;
+struct SymState;
 
 struct Plan {
     bd_params p;
@@ -107,6 +108,7 @@ struct Plan {
     int ldx;                           // leading dimension of d_x16 (elements)
     int tc_split;                      // resident CTAs per SM of the tensor-core product (0: 2)
     int tc_maxslots;                   // partial slots per row block (stream-K schedule)
+    SymState *sym;                     // symmetric product schedule (mixed plans)
     int num_sms;                       // SM count of the plan's device
     int64_t scratch_bytes;
     bd_step_stats *d_stats_scratch;

@@ -1,0 +1,638 @@
+// sym_gemm.cu -- the mixed-precision product Y = D16 X from the tiles on and
+// above the diagonal of D16 only.
+//
+// D is symmetric (Eq. DF: the 3 x 3 block of (mu, nu) is the transpose of
+// that of (nu, mu); the 16-bit copy is written mirrored), so one 128 x 128
+// tile (I, J), I < J, serves both products Y_I += D_IJ X_J and
+// Y_J += D_IJ^T X_I, and the product streams half of D16 from HBM.  Both
+// products run on the 5th-generation tensor cores from the same staged tile:
+// the first with the tile as a K-major A operand, the second with the same
+// shared memory read as an MN-major A operand (its rows are the K dimension).
+//
+// Schedule.  The tile rows are grouped in bands of R; band b takes its tiles
+// with J outer (J = r0 .. T-1) and I inner (I = r0 .. min(J, r1 - 1)), and
+// the bands follow one another: a single sequence of U units that CTA c of
+// the G resident CTAs cuts at [c U / G, (c + 1) U / G) (stream-K).  A CTA
+// keeps one TMEM accumulator per band row (D_IJ X_J summed over its J) and
+// two for the columns (D_IJ^T X_I summed over the band's rows of one J,
+// double-buffered so the epilogue drains one while the next J accumulates).
+// The band's operand rows X_I stay in shared memory; each stage of the ring
+// holds one tile and X_J.  Partial sums leave the CTA as FP32 slots: one per
+// (band, CTA) for the rows and one per (J-step, CTA) for the columns.  A
+// second kernel sums, for each 128-row block, its row slots and then its
+// column slots, band by band, in a fixed order (double-float, deterministic), and
+// runs the epilogue of the product (plain store, or the Chebyshev term with
+// the Lanczos column).  Every mbarrier wait is bounded; a CTA that gives up
+// records BD_ERR_TIMEOUT, drains its copies in flight, frees its TMEM and
+// returns.
+#include <math.h>
+
+#include <vector>
+
+#include "sym_gemm.cuh"
+
+namespace bd {
+
+namespace sy {
+
+using tc::BK;
+using tc::BM;
+using tc::kWaitLimit;
+
+constexpr int R = 8;               // tile rows per band
+constexpr int THREADS = 192;       // warp 0 TMA, warp 1 MMA, warps 2-5 epilogue
+constexpr int A_TILE = 2 * BM * BK * 2;   // one 128 x 128 tile: two 64-column boxes
+template <int BN> __host__ __device__ constexpr int xbox() { return BN * BK * 2; }   // 64 operand rows
+template <int BN> __host__ __device__ constexpr int stage_bytes() { return A_TILE + 2 * xbox<BN>(); }
+template <int BN> __host__ __device__ constexpr int vband_bytes() { return R * 2 * xbox<BN>(); }
+template <int BN> __host__ __device__ constexpr int stages()
+{
+    return (226 * 1024 - vband_bytes<BN>() - 1024) / stage_bytes<BN>();
+}
+template <int BN> __host__ __device__ constexpr int smem_bytes()
+{
+    return stages<BN>() * stage_bytes<BN>() + vband_bytes<BN>() + 1024;
+}
+
+// schedule geometry, shared by the product and the reduction
+struct Geo {
+    int T;                 // 128-row tiles per side
+    int nb;                // bands
+    long U;                // units (tiles on and above the diagonal)
+    int G;                 // CTAs of the product
+    int rslots;            // row slots per band
+    int cslots;            // column slots per J-step
+    const long *boff;      // [nb + 1] first unit of each band
+    const int *jbase;      // [nb + 1] first J-step of each band
+    long colbase;          // first column slot in the partial pool (after the row slots)
+    const int *xstart;     // [T + 1] first entry of each 128-row block in xlist
+    const int *xlist;      // partial slots of each block, in summation order
+};
+
+__host__ __device__ inline int band_rows(int b, int T) { return T - b * R < R ? T - b * R : R; }
+
+// units of band b before its J-step J
+__host__ __device__ inline long jstep_off(int b, int J, int T)
+{
+    const int rb = band_rows(b, T), d = J - b * R;
+    if (d < rb) return (long)d * (d + 1) / 2;
+    return (long)rb * (rb + 1) / 2 + (long)(d - rb) * rb;
+}
+
+// CTA owning unit u: the c with c U / G <= u < (c + 1) U / G (integer division)
+__host__ __device__ inline int cta_of(long u, long U, int G)
+{
+    return (int)(((u + 1) * (long)G + U - 1) / U) - 1;
+}
+
+struct It {
+    int b, J, I;
+};
+
+__device__ inline void it_seek(It &t, long u, const long *boff, int nb, int T)
+{
+    int b = 0;
+    while (b + 1 < nb && boff[b + 1] <= u) b++;
+    long rem = u - boff[b];
+    const int r0 = b * R, rb = band_rows(b, T);
+    int d = 0;
+    while (d < rb && rem >= d + 1) {
+        rem -= d + 1;
+        d++;
+    }
+    t.b = b;
+    if (d < rb) {
+        t.J = r0 + d;
+        t.I = r0 + (int)rem;
+    } else {
+        t.J = r0 + rb + (int)(rem / rb);
+        t.I = r0 + (int)(rem % rb);
+    }
+}
+
+__device__ inline void it_next(It &t, int T)
+{
+    const int r0 = t.b * R, r1 = r0 + band_rows(t.b, T);
+    t.I++;
+    if (t.I > t.J || t.I >= r1) {
+        t.J++;
+        t.I = r0;
+        if (t.J >= T) {
+            t.b++;
+            t.J = t.b * R;
+            t.I = t.J;
+        }
+    }
+}
+
+__device__ __forceinline__ void mbar_arrive(uint32_t bar)
+{
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
+}
+
+// MN-major operand, 128-byte swizzle: 64-element chunks along M lbo bytes
+// apart, 8-row groups along K 1024 bytes apart (SBO), version 1
+__device__ __forceinline__ uint64_t sw128_desc_mn(uint32_t addr, uint32_t lbo)
+{
+    uint64_t d = 0;
+    d |= (uint64_t)((addr & 0x3FFFFu) >> 4);
+    d |= (uint64_t)((lbo >> 4) & 0x3FFFu) << 16;
+    d |= (uint64_t)(1024 >> 4) << 32;
+    d |= (uint64_t)1 << 46;
+    d |= (uint64_t)2 << 61;
+    return d;
+}
+
+// -- kernel begin: k_sym_gemm
+template <int BN>
+__global__ void __launch_bounds__(THREADS, 1)
+k_sym_gemm(const __grid_constant__ CUtensorMap mapD, const __grid_constant__ CUtensorMap mapX,
+           Geo g, int m, int is_bf16, float *__restrict__ part, int32_t *__restrict__ err)
+{
+    constexpr int ST = stages<BN>();
+    constexpr int XB = xbox<BN>();
+    constexpr int STAGE = stage_bytes<BN>();
+    constexpr uint32_t TMEM_COLS = 512;
+    static_assert((R + 2) * BN <= (int)TMEM_COLS, "accumulators exceed TMEM");
+    static_assert(STAGE % 1024 == 0 && XB % 1024 == 0, "stage alignment");
+    static_assert(ST >= 3, "ring too shallow");
+    const uint32_t idesc_k = tc::idesc_f16(BN, is_bf16);
+    const uint32_t idesc_mn = idesc_k | (1u << 15);          // A read MN-major
+
+    extern __shared__ __align__(1024) uint8_t smem_raw[];
+    uint8_t *smem = (uint8_t *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+    uint8_t *vband = smem + ST * STAGE;
+    __shared__ __align__(8) uint64_t full_bar[ST], empty_bar[ST];
+    __shared__ __align__(8) uint64_t vb_full, vb_empty, row_full, row_empty, col_full[2],
+        col_empty[2], drain_bar;
+    __shared__ uint32_t tmem_base_sh;
+    __shared__ volatile int abort_flag;
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int c = blockIdx.x;
+    const long u0 = (long)c * g.U / g.G, u1 = (long)(c + 1) * g.U / g.G;
+    const int nunits = (int)(u1 - u0);
+    const int T = g.T;
+
+    if (threadIdx.x == 0) {
+        abort_flag = 0;
+        for (int s = 0; s < ST; s++) {
+            tc::mbar_init(tc::smem_u32(&full_bar[s]), 1);
+            tc::mbar_init(tc::smem_u32(&empty_bar[s]), 1);
+        }
+        tc::mbar_init(tc::smem_u32(&vb_full), 1);
+        tc::mbar_init(tc::smem_u32(&vb_empty), 1);
+        tc::mbar_init(tc::smem_u32(&row_full), 1);
+        tc::mbar_init(tc::smem_u32(&row_empty), 128);
+        for (int q = 0; q < 2; q++) {
+            tc::mbar_init(tc::smem_u32(&col_full[q]), 1);
+            tc::mbar_init(tc::smem_u32(&col_empty[q]), 128);
+        }
+        tc::mbar_init(tc::smem_u32(&drain_bar), 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    }
+    if (warp == 1) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                         tc::smem_u32(&tmem_base_sh)),
+                     "r"(TMEM_COLS)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const uint32_t tmem = tmem_base_sh;
+
+    if (warp == 0 && lane == 0) {
+        // ---- TMA producer
+        It t;
+        it_seek(t, u0, g.boff, g.nb, T);
+        int issued = 0, seg = 0, pb = -1;
+        bool vb_pending = false;
+        for (int i = 0; i < nunits; i++) {
+            if (t.b != pb) {
+                // the band's operand rows X_I, once the previous band's MMAs are done
+                if (seg > 0 &&
+                    !tc::mbar_wait(tc::smem_u32(&vb_empty), (uint32_t)(seg - 1) & 1u, &abort_flag))
+                    break;
+                const int r0 = t.b * R, rb = band_rows(t.b, T);
+                const uint32_t vf = tc::smem_u32(&vb_full);
+                tc::mbar_expect_tx(vf, (uint32_t)(rb * 2 * XB));
+                for (int rr = 0; rr < rb; rr++)
+                    for (int h = 0; h < 2; h++)
+                        tc::tma_load_2d(tc::smem_u32(vband + (rr * 2 + h) * XB), &mapX,
+                                        (r0 + rr) * BM + h * BK, 0, vf);
+                vb_pending = true;
+                seg++;
+                pb = t.b;
+            }
+            const int s = i % ST;
+            const uint32_t ph = (uint32_t)(i / ST) & 1u;
+            if (!tc::mbar_wait(tc::smem_u32(&empty_bar[s]), ph ^ 1u, &abort_flag)) break;
+            const uint32_t a = tc::smem_u32(smem + s * STAGE);
+            const uint32_t fb = tc::smem_u32(&full_bar[s]);
+            tc::mbar_expect_tx(fb, STAGE);
+            tc::tma_load_2d(a, &mapD, t.J * BM, t.I * BM, fb);
+            tc::tma_load_2d(a + BM * BK * 2, &mapD, t.J * BM + BK, t.I * BM, fb);
+            tc::tma_load_2d(a + A_TILE, &mapX, t.J * BM, 0, fb);
+            tc::tma_load_2d(a + A_TILE + XB, &mapX, t.J * BM + BK, 0, fb);
+            issued = i + 1;
+            it_next(t, T);
+        }
+        if (abort_flag) {
+            // let every load issued land before the CTA can exit
+            for (int i = (issued > ST ? issued - ST : 0); i < issued; i++) {
+                const int s = i % ST;
+                const uint32_t ph = (uint32_t)(i / ST) & 1u;
+                for (uint32_t k = 0; k < kWaitLimit && !tc::mbar_try(tc::smem_u32(&full_bar[s]), ph); k++) {}
+            }
+            if (vb_pending)
+                for (uint32_t k = 0;
+                     k < kWaitLimit && !tc::mbar_try(tc::smem_u32(&vb_full), (uint32_t)(seg - 1) & 1u); k++) {}
+        }
+    } else if (warp == 1 && lane == 0) {
+        // ---- MMA issuer
+        It t;
+        it_seek(t, u0, g.boff, g.nb, T);
+        bool ok = true;
+        int seg = 0, jsteps = 0, pb = -1, pJ = -1;
+        uint32_t started = 0;
+        bool col_on = false;
+        for (int i = 0; i < nunits && ok; i++) {
+            It nx = t;
+            it_next(nx, T);
+            const bool first_band = (t.b != pb);
+            const bool last_band = (i + 1 == nunits) || (nx.b != t.b);
+            const bool first_j = first_band || (t.J != pJ);
+            const bool last_j = last_band || (nx.J != t.J);
+            if (first_band) {
+                if (seg > 0 &&
+                    !tc::mbar_wait(tc::smem_u32(&row_empty), (uint32_t)(seg - 1) & 1u, &abort_flag)) {
+                    ok = false;
+                    break;
+                }
+                if (!tc::mbar_wait(tc::smem_u32(&vb_full), (uint32_t)seg & 1u, &abort_flag)) {
+                    ok = false;
+                    break;
+                }
+                asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                started = 0;
+                seg++;
+            }
+            if (first_j) col_on = false;
+            const int s = i % ST;
+            const uint32_t ph = (uint32_t)(i / ST) & 1u;
+            if (!tc::mbar_wait(tc::smem_u32(&full_bar[s]), ph, &abort_flag)) { ok = false; break; }
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            const int rr = t.I - t.b * R;
+            const uint32_t a = tc::smem_u32(smem + s * STAGE);
+            const uint32_t xj = a + A_TILE;
+            // Y_I += D_IJ X_J: the tile K-major, K = the tile's columns
+            const uint32_t acc_r = tmem + (uint32_t)(rr * BN);
+            const bool racc = (started >> rr) & 1u;
+#pragma unroll
+            for (int k = 0; k < 8; k++) {
+                const uint64_t da = tc::sw128_desc(a + (k >> 2) * (BM * BK * 2)) + (uint64_t)(2 * (k & 3));
+                const uint64_t db = tc::sw128_desc(xj + (k >> 2) * XB) + (uint64_t)(2 * (k & 3));
+                tc::mma_f16(acc_r, da, db, idesc_k, (racc || k > 0) ? 1u : 0u);
+            }
+            started |= 1u << rr;
+            if (t.I != t.J) {
+                // Y_J += D_IJ^T X_I: the same tile MN-major, K = the tile's rows
+                if (!col_on && jsteps >= 2 &&
+                    !tc::mbar_wait(tc::smem_u32(&col_empty[jsteps & 1]),
+                                   (uint32_t)((jsteps >> 1) - 1) & 1u, &abort_flag)) {
+                    ok = false;
+                    break;
+                }
+                if (!col_on) asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                const uint32_t acc_c = tmem + (uint32_t)((R + (jsteps & 1)) * BN);
+                const uint32_t xi = tc::smem_u32(vband + rr * 2 * XB);
+#pragma unroll
+                for (int k = 0; k < 8; k++) {
+                    const uint64_t da = sw128_desc_mn(a + k * 2048, BM * BK * 2);
+                    const uint64_t db = tc::sw128_desc(xi + (k >> 2) * XB) + (uint64_t)(2 * (k & 3));
+                    tc::mma_f16(acc_c, da, db, idesc_mn, (col_on || k > 0) ? 1u : 0u);
+                }
+                col_on = true;
+            }
+            tc::mma_commit(tc::smem_u32(&empty_bar[s]));
+            if (last_j && col_on) {
+                tc::mma_commit(tc::smem_u32(&col_full[jsteps & 1]));
+                jsteps++;
+            }
+            if (last_band) {
+                tc::mma_commit(tc::smem_u32(&row_full));
+                tc::mma_commit(tc::smem_u32(&vb_empty));
+            }
+            pb = t.b;
+            pJ = t.J;
+            t = nx;
+        }
+        if (!ok) {
+            tc::mma_commit(tc::smem_u32(&drain_bar));
+            for (uint32_t k = 0; k < kWaitLimit && !tc::mbar_try(tc::smem_u32(&drain_bar), 0); k++) {}
+        }
+    } else if (warp >= 2) {
+        // ---- epilogue warps: TMEM lane quadrant q, row r of the tile
+        const int q = warp & 3;
+        const int r = q * 32 + lane;
+        const uint32_t lane_off = (uint32_t)(q * 32) << 16;
+        It t;
+        it_seek(t, u0, g.boff, g.nb, T);
+        int seg = 0, jsteps = 0, pb = -1, pJ = -1;
+        uint32_t started = 0;
+        bool col_on = false;
+        for (int i = 0; i < nunits; i++) {
+            It nx = t;
+            it_next(nx, T);
+            const bool first_band = (t.b != pb);
+            const bool last_band = (i + 1 == nunits) || (nx.b != t.b);
+            const bool first_j = first_band || (t.J != pJ);
+            const bool last_j = last_band || (nx.J != t.J);
+            if (first_band) started = 0;
+            if (first_j) col_on = false;
+            started |= 1u << (t.I - t.b * R);
+            if (t.I != t.J) col_on = true;
+            if (last_j && col_on) {
+                const int qb = jsteps & 1;
+                if (!tc::mbar_wait_sleep(tc::smem_u32(&col_full[qb]), (uint32_t)(jsteps >> 1) & 1u,
+                                         &abort_flag))
+                    break;
+                asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                float acc[BN];
+#pragma unroll
+                for (int cc = 0; cc < BN; cc += 16)
+                    tc::tmem_ld16(tmem + lane_off + (uint32_t)((R + qb) * BN + cc), acc + cc);
+                asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+                mbar_arrive(tc::smem_u32(&col_empty[qb]));
+                const long uf = g.boff[t.b] + jstep_off(t.b, t.J, T);
+                const int slot = c - cta_of(uf, g.U, g.G);
+                const long jid = (long)g.jbase[t.b] + (t.J - t.b * R);
+                float *dst = part + ((g.colbase + jid * g.cslots + slot) * BN) * BM + r;
+#pragma unroll
+                for (int cc = 0; cc < BN; cc++)
+                    if (cc < m) dst[(size_t)cc * BM] = acc[cc];
+                jsteps++;
+            }
+            if (last_band) {
+                if (!tc::mbar_wait_sleep(tc::smem_u32(&row_full), (uint32_t)seg & 1u, &abort_flag))
+                    break;
+                asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                const int rb = band_rows(t.b, T);
+                const int slot = c - cta_of(g.boff[t.b], g.U, g.G);
+                for (int rr = 0; rr < rb; rr++) {
+                    float acc[BN];
+                    if ((started >> rr) & 1u) {
+#pragma unroll
+                        for (int cc = 0; cc < BN; cc += 16)
+                            tc::tmem_ld16(tmem + lane_off + (uint32_t)(rr * BN + cc), acc + cc);
+                    } else {
+#pragma unroll
+                        for (int cc = 0; cc < BN; cc++) acc[cc] = 0.f;
+                    }
+                    float *dst = part + ((((long)t.b * g.rslots + slot) * R + rr) * BN) * BM + r;
+#pragma unroll
+                    for (int cc = 0; cc < BN; cc++)
+                        if (cc < m) dst[(size_t)cc * BM] = acc[cc];
+                }
+                asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+                mbar_arrive(tc::smem_u32(&row_empty));
+                seg++;
+            }
+            pb = t.b;
+            pJ = t.J;
+            t = nx;
+        }
+    }
+    // ---- teardown
+    if (threadIdx.x == 0 && abort_flag) atomicExch(err, (int32_t)BD_ERR_TIMEOUT);
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    if (warp == 1) {
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TMEM_COLS)
+                     : "memory");
+    }
+}
+// -- kernel end: k_sym_gemm
+
+// ---------------------------------------------------------------------------
+// For the 128-row block X (blockIdx.x) and one column (blockIdx.y): its row
+// slots (band bX, every CTA whose range met the band, in CTA order) and then
+// its column slots (bands b = 0 .. bX with rows above X, each J-step's CTAs
+// in order) -- the list the plan built for X -- summed in that order;
+// then that column's part of the product's epilogue (the Lanczos column also
+// reduces its row block's dot partials).
+template <int BN>
+__global__ void __launch_bounds__(128)
+k_sym_reduce(Geo g, const float *__restrict__ part, int n3, tc::Epi e)
+{
+    constexpr int kList = 256;
+    __shared__ double lan_red[4][3];
+    __shared__ int s_list[kList];
+    const int X = blockIdx.x, cc = blockIdx.y, r = threadIdx.x;
+    const int q = r >> 5, lane = r & 31;
+    const long row = (long)X * BM + r;
+    const float *base = part + (size_t)cc * BM + r;
+    const int i0 = g.xstart[X], i1 = g.xstart[X + 1];
+    // FP32 partials summed as a double-float (TwoSum: the running sum and its
+    // exact rounding errors), in list order: as exact as an FP64 sum of FP32
+    // values for these lengths, at FP32 issue rate (the FP64 pipe of this GPU
+    // runs at 1/64 of it)
+    float sh = 0.f, sl = 0.f;
+    auto add = [&](float v) {
+        const float t = sh + v, bp = t - sh;
+        sl += (sh - (t - bp)) + (v - bp);
+        sh = t;
+    };
+    for (int c0 = i0; c0 < i1; c0 += kList) {
+        const int cn = min(kList, i1 - c0);
+        __syncthreads();
+        for (int k = r; k < cn; k += 128) s_list[k] = g.xlist[c0 + k];
+        __syncthreads();
+        int k = 0;
+        for (; k + 8 <= cn; k += 8) {
+            float v[8];
+#pragma unroll
+            for (int h = 0; h < 8; h++) v[h] = __ldcg(base + (size_t)s_list[k + h] * (BN * BM));
+#pragma unroll
+            for (int h = 0; h < 8; h++) add(v[h]);
+        }
+        for (; k < cn; k++) add(__ldcg(base + (size_t)s_list[k] * (BN * BM)));
+    }
+    const double y = (double)sh + (double)sl;
+    if (e.mode == 0) {
+        if (row < n3) e.Y[(long)cc * n3 + row] = y * (double)e.inv_scale[cc];
+        return;
+    }
+    if (cc == e.lan_col) {
+        // the Lanczos column: w = D q_j and this row block's share of q_j.w,
+        // q_{j-1}.w and w.w, reduced in a fixed order (deterministic)
+        const double lw = y * (double)e.inv_scale[cc];
+        if (row < n3) e.lan_w[row] = lw;
+        double t[3] = {row < n3 ? e.lan_q[row] * lw : 0.0, row < n3 ? e.lan_qp[row] * lw : 0.0,
+                       row < n3 ? lw * lw : 0.0};
+#pragma unroll
+        for (int k = 0; k < 3; k++)
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) t[k] += __shfl_xor_sync(0xffffffffu, t[k], o);
+        if (lane == 0)
+            for (int k = 0; k < 3; k++) lan_red[q][k] = t[k];
+        __syncthreads();
+        if (r == 0)
+            for (int k = 0; k < 3; k++)
+                e.lan_part[3 * X + k] = ((lan_red[0][k] + lan_red[1][k]) + lan_red[2][k]) + lan_red[3][k];
+        return;
+    }
+    if (row >= n3) return;
+    // Chebyshev term of Eqs. (cheb2)/(cheb3): V_p = 2 (s W - t V_{p-1}) - V_{p-2},
+    // dS += c_p V_p, and the scaled 16-bit V_p as the next product's operand
+    const double dmin = e.bounds[0], dmax = e.bounds[1];
+    const double ys = 2.0 / (dmax - dmin), yt = (dmax + dmin) / (dmax - dmin);
+    const long o = (long)cc * n3 + row;
+    const double p1 = e.Vprev1[o], p2 = e.Vprev2[o], d0 = e.dS[o];
+    const double w = y * (double)e.inv_scale[cc];
+    const double v = 2.0 * (ys * w - yt * p1) - p2;
+    e.Vprev2[o] = v;
+    e.dS[o] = d0 + e.coef[e.p] * v;
+    const float sv = (float)(v * (double)e.scale[cc]);
+    const size_t xo = (size_t)cc * e.ldx + row;
+    if (e.is_bf16) ((__nv_bfloat16 *)e.X16next)[xo] = __float2bfloat16_rn(sv);
+    else ((__half *)e.X16next)[xo] = __float2half_rn(sv);
+}
+
+}  // namespace sy
+
+// ---------------------------------------------------------------------------
+// host side
+
+struct SymState {
+    sy::Geo geo;            // device pointers filled in
+    long *d_boff;
+    int *d_jbase;
+    int *d_xstart, *d_xlist;
+    float *d_part;
+};
+
+static bd_status sym_oom(cudaError_t e)
+{
+    cudaGetLastError();
+    return set_error(BD_ERR_OOM, "symmetric product scratch: %s", cudaGetErrorString(e));
+}
+
+bd_status sym_plan_init(Plan &P)
+{
+    if (P.sym) return BD_OK;
+    using namespace sy;
+    const int T = (P.n3 + BM - 1) / BM;
+    const int nb = (T + R - 1) / R;
+    std::vector<long> boff(nb + 1);
+    std::vector<int> jbase(nb + 1);
+    boff[0] = 0;
+    jbase[0] = 0;
+    for (int b = 0; b < nb; b++) {
+        const int rb = band_rows(b, T);
+        boff[b + 1] = boff[b] + (long)rb * (rb + 1) / 2 + (long)(T - b * R - rb) * rb;
+        jbase[b + 1] = jbase[b] + (T - b * R);
+    }
+    const long U = boff[nb];
+    const int G = (int)((long)P.num_sms < U ? P.num_sms : U);
+    // CTAs meeting each band (row slots) and each J-step's column units
+    // (column slots; none for the band's first J-step, its diagonal tile only)
+    std::vector<int> bsl(nb), jsl(jbase[nb], 0);
+    int rs = 1, cs = 1;
+    for (int b = 0; b < nb; b++) {
+        const int n = cta_of(boff[b + 1] - 1, U, G) - cta_of(boff[b], U, G) + 1;
+        bsl[b] = n;
+        rs = n > rs ? n : rs;
+        const int r0 = b * R, r1 = r0 + band_rows(b, T);
+        for (int J = r0 + 1; J < T; J++) {
+            const int ncol = (J < r1 ? J : r1) - r0;
+            const long uf = boff[b] + jstep_off(b, J, T);
+            const int k = cta_of(uf + ncol - 1, U, G) - cta_of(uf, U, G) + 1;
+            jsl[jbase[b] + (J - r0)] = k;
+            cs = k > cs ? k : cs;
+        }
+    }
+    // the summation list of each 128-row block: its band's row slots, then
+    // the column slots of its J-step in every band above it, in band order
+    const long colbase = (long)nb * rs * R;
+    std::vector<int> xstart(T + 1), xlist;
+    for (int X = 0; X < T; X++) {
+        xstart[X] = (int)xlist.size();
+        const int bX = X / R;
+        for (int sl = 0; sl < bsl[bX]; sl++)
+            xlist.push_back((int)(((long)bX * rs + sl) * R + (X - bX * R)));
+        for (int b = 0; b <= bX && b * R < X; b++) {
+            const long jid = (long)jbase[b] + (X - b * R);
+            for (int sl = 0; sl < jsl[jid]; sl++) xlist.push_back((int)(colbase + jid * cs + sl));
+        }
+    }
+    xstart[T] = (int)xlist.size();
+    SymState *S = new SymState();
+    memset(S, 0, sizeof(*S));
+    P.sym = S;
+    const size_t nslots = (size_t)colbase + (size_t)jbase[nb] * cs;
+    const size_t pool = nslots * kMaxRhs * BM;
+    cudaError_t e = cudaMalloc((void **)&S->d_boff, sizeof(long) * (nb + 1));
+    if (e == cudaSuccess) e = cudaMalloc((void **)&S->d_jbase, sizeof(int) * (nb + 1));
+    if (e == cudaSuccess) e = cudaMalloc((void **)&S->d_xstart, sizeof(int) * (T + 1));
+    if (e == cudaSuccess) e = cudaMalloc((void **)&S->d_xlist, sizeof(int) * (xlist.size() + 1));
+    if (e == cudaSuccess) e = cudaMalloc((void **)&S->d_part, sizeof(float) * pool);
+    if (e != cudaSuccess) return sym_oom(e);
+    P.scratch_bytes += (int64_t)(sizeof(long) * (nb + 1) + sizeof(int) * (nb + 1 + T + 1 + xlist.size()) +
+                                 sizeof(float) * pool);
+    cudaMemcpy(S->d_boff, boff.data(), sizeof(long) * (nb + 1), cudaMemcpyHostToDevice);
+    cudaMemcpy(S->d_jbase, jbase.data(), sizeof(int) * (nb + 1), cudaMemcpyHostToDevice);
+    cudaMemcpy(S->d_xstart, xstart.data(), sizeof(int) * (T + 1), cudaMemcpyHostToDevice);
+    if (!xlist.empty())
+        cudaMemcpy(S->d_xlist, xlist.data(), sizeof(int) * xlist.size(), cudaMemcpyHostToDevice);
+    S->geo = Geo{T, nb, U, G, rs, cs, S->d_boff, S->d_jbase, colbase, S->d_xstart, S->d_xlist};
+    cudaError_t a[2] = {
+        cudaFuncSetAttribute(k_sym_gemm<16>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             smem_bytes<16>()),
+        cudaFuncSetAttribute(k_sym_gemm<32>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             smem_bytes<32>())};
+    for (cudaError_t x : a)
+        if (x != cudaSuccess)
+            return set_error(BD_ERR_CUDA, "smem attribute (symmetric product): %s",
+                             cudaGetErrorString(x));
+    return check_launch("symmetric product init");
+}
+
+void sym_plan_free(Plan &P)
+{
+    SymState *S = P.sym;
+    if (!S) return;
+    void *ptrs[] = {S->d_boff, S->d_jbase, S->d_xstart, S->d_xlist, S->d_part};
+    for (void *q : ptrs)
+        if (q) cudaFree(q);
+    delete S;
+    P.sym = nullptr;
+}
+
+bd_status sym_launch(Plan &P, const CUtensorMap &mapD, const CUtensorMap &mapX, int bn,
+                     const tc::Epi &e, cudaStream_t s)
+{
+    bd_status st = sym_plan_init(P);
+    if (st != BD_OK) return st;
+    const SymState *S = P.sym;
+    const sy::Geo &g = S->geo;
+    const int cols = e.m + (e.lan_col >= 0 ? 1 : 0);
+    int32_t *err = P.d_status + 6;
+    if (bn == 16) {
+        sy::k_sym_gemm<16><<<g.G, sy::THREADS, sy::smem_bytes<16>(), s>>>(
+            mapD, mapX, g, cols, e.is_bf16, S->d_part, err);
+        sy::k_sym_reduce<16><<<dim3(g.T, cols), 128, 0, s>>>(g, S->d_part, P.n3, e);
+    } else {
+        sy::k_sym_gemm<32><<<g.G, sy::THREADS, sy::smem_bytes<32>(), s>>>(
+            mapD, mapX, g, cols, e.is_bf16, S->d_part, err);
+        sy::k_sym_reduce<32><<<dim3(g.T, cols), 128, 0, s>>>(g, S->d_part, P.n3, e);
+    }
+    count_launches(2);
+    return check_launch("symmetric product");
+}
+
+}  // namespace bd

@@ -9,7 +9,10 @@ namespace bd {
 bd_status tc_plan_init(Plan &P);
 // Y = D16 X (FP32 accumulation, FP64 output)
 bd_status tc_apply(Plan &P, const void *D16, const double *X, int m, double *Y, cudaStream_t s);
-// measure the faster launch shape (1 or 2 CTAs per SM) of the product (synchronous)
+// launch shape 3 of the product: the symmetric kernel over the upper triangle
+constexpr int kSymShape = 3;
+// measure the fastest launch shape of the product (1 or 2 CTAs per SM of the
+// stream-K kernel, or the symmetric kernel) (synchronous)
 bd_status tc_autotune(Plan &P, const void *D16, cudaStream_t s, int *best, float *ms);
 // one Chebyshev term: V_p = 2 (s D16 V_{p-1} - t V_{p-1}) - V_{p-2} (in place
 // over V_{p-2}), dS += c_p V_p

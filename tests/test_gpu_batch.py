@@ -95,7 +95,7 @@ def test_autotune_split(bnd):
     D = plan.alloc_D()
     plan.build_D(torch.tensor(R, device="cuda"), D)
     split, ms = plan.autotune(D)
-    assert split in (1, 2) and ms > 0
+    assert split in (1, 2, 3) and ms > 0
     X = inputs.make_wiener(3 * cfg.n, 16, 1.0, 6)
     Y = torch.empty(16, 3 * cfg.n, dtype=torch.float64, device="cuda")
     plan.apply(D, torch.tensor(X, device="cuda"), Y)
