@@ -127,15 +127,16 @@ k_pair_adjoint(const double *__restrict__ R, int n, const EwaldCoef *__restrict_
             if (u <= rc2 && u > (T)0) {
                 T f1p, f2, f2p;
                 if (u >= four_a2) {
-                    int i = (int)(__float_as_uint((float)u) >> kTabShift) - tab_i0;
+                    constexpr int DEG = TabFmt<T>::DEG;
+                    int i = (int)(__float_as_uint((float)u) >> TabFmt<T>::SHIFT) - tab_i0;
                     i = i < 0 ? 0 : (i >= ntab ? ntab - 1 : i);
-                    const T *row = tab + (size_t)i * kTabStride;
+                    const T *row = tab + (size_t)i * TabFmt<T>::STRIDE;
                     T ihw = __ldg(row + 1);
                     T t = (u - __ldg(row)) * ihw;
-                    const T *a1 = row + 2, *b1 = row + 2 + (kTabDeg + 1);
-                    T p1 = __ldg(a1 + kTabDeg), d1 = (T)0, p2 = __ldg(b1 + kTabDeg), d2 = (T)0;
+                    const T *a1 = row + 2, *b1 = row + 2 + (DEG + 1);
+                    T p1 = __ldg(a1 + DEG), d1 = (T)0, p2 = __ldg(b1 + DEG), d2 = (T)0;
 #pragma unroll
-                    for (int k = kTabDeg - 1; k >= 0; k--) {
+                    for (int k = DEG - 1; k >= 0; k--) {
                         d1 = d1 * t + p1;
                         p1 = p1 * t + __ldg(a1 + k);
                         d2 = d2 * t + p2;
@@ -234,7 +235,7 @@ void launch_pair_adjoint(Plan &P, const double *R, const double *X, const double
             P.p.overlap_corr, (float)P.p.r_c, X, Y, Q, P.n3, gR);
     } else {
         k_pair_adjoint<float><<<(unsigned)nb, ATB * ATB, 0, s>>>(
-            R, P.n, P.d_ewc, P.d_tab32, P.tab_i0, P.ntab, P.d_km32, P.nk, P.d_cos32, P.d_sin32,
+            R, P.n, P.d_ewc, P.d_tab32, P.tab32_i0, P.ntab32, P.d_km32, P.nk, P.d_cos32, P.d_sin32,
             P.p.overlap_corr, (float)P.p.r_c, X, Y, Q, P.n3, gR);
     }
     count_launches(1);

@@ -193,14 +193,16 @@ bd_status bd_plan_create(const bd_params *params, bd_plan **out_plan)
     if (mixed) TRY(dmalloc(P, &P.d_ew32, 1));
     TRY(dmalloc(P, &P.d_pw64, n3));
     if (mixed) TRY(dmalloc(P, &P.d_pw32, 2 * n3));
-    m1_table_range(P.p, &P.tab_i0, &P.ntab);
-    if (P.ntab > kTabMax) {
+    m1_table_range(P.p, TabFmt<double>::BITS, &P.tab_i0, &P.ntab);
+    m1_table_range(P.p, TabFmt<float>::BITS, &P.tab32_i0, &P.ntab32);
+    if (P.ntab > kTabMax || (mixed && P.ntab32 > kTabMax)) {
         st = set_error(BD_ERR_UNSUPPORTED, "r_c/a ratio needs %d table intervals (limit %d)",
-                       P.ntab, kTabMax);
+                       mixed ? P.ntab32 : P.ntab, kTabMax);
         goto fail;
     }
-    TRY(dmalloc(P, &P.d_tab, (size_t)(P.ntab > 0 ? P.ntab : 1) * kTabStride));
-    if (mixed) TRY(dmalloc(P, &P.d_tab32, (size_t)(P.ntab > 0 ? P.ntab : 1) * kTabStride));
+    TRY(dmalloc(P, &P.d_tab, (size_t)(P.ntab > 0 ? P.ntab : 1) * TabFmt<double>::STRIDE));
+    if (mixed)
+        TRY(dmalloc(P, &P.d_tab32, (size_t)(P.ntab32 > 0 ? P.ntab32 : 1) * TabFmt<float>::STRIDE));
     TRY(dmalloc(P, &P.d_F, n3));
     TRY(dmalloc(P, &P.d_DF, n3));
     TRY(dmalloc(P, &P.d_Rnew, n3));

@@ -32,14 +32,22 @@ struct EwaldCoef {
 
 // Piecewise-polynomial table of the Eq. (M1) coefficients for images with
 // 4a^2 <= u = |r|^2 <= r_c^2: interval i covers the u whose FP32 bit pattern
-// has (bits >> kTabShift) == i0 + i, i.e. 2^kTabBits intervals per octave of u.
-// Per interval: mid, 1/half-width, then kTabDeg+1 monomial coefficients in
-// t = (u - mid)/half-width of c1(u) and of c2(u)/u.
-constexpr int kTabBits = 4;
-constexpr int kTabShift = 23 - kTabBits;
-constexpr int kTabDeg = 8;
-constexpr int kTabStride = 2 + 2 * (kTabDeg + 1);  // doubles per interval
-constexpr int kTabMax = 512;
+// has (bits >> SHIFT) == i0 + i, i.e. 2^BITS intervals per octave of u.
+// Per interval: mid, 1/half-width, then DEG+1 monomial coefficients in
+// t = (u - mid)/half-width of c1(u) and of c2(u)/u.  The FP64 table (degree 8
+// on 16 intervals per octave) interpolates to ~1e-12 of the local value; the
+// FP32 table (degree 4 on 64 intervals per octave, 48-byte rows) to ~3e-9,
+// below FP32 rounding, with half the loads and FMAs per image.
+template <typename T> struct TabFmt;
+template <> struct TabFmt<double> {
+    static constexpr int BITS = 4, DEG = 8, SHIFT = 23 - BITS, STRIDE = 2 + 2 * (DEG + 1);
+};
+template <> struct TabFmt<float> {
+    static constexpr int BITS = 6, DEG = 4, SHIFT = 23 - BITS, STRIDE = 2 + 2 * (DEG + 1);
+};
+static_assert(TabFmt<double>::STRIDE % 2 == 0 && TabFmt<float>::STRIDE % 4 == 0,
+              "table rows must be 16-byte multiples");
+constexpr int kTabMax = 2048;
 
 // the Eq. (M1) coefficients and the box constants in the working precision of
 // a pair kernel (converted once per plan: on this GPU a double-to-float
@@ -76,9 +84,10 @@ struct Plan {
     EwaldT<float> h_ew32;
     double *d_pw64;                    // positions wrapped into [0, L), FP64 [3N]
     float *d_pw32;                     // the same as FP32 hi/lo words [2][3N]
-    double *d_tab;                     // M1 table [ntab][kTabStride] (FP64)
-    float *d_tab32;                    // the same table in FP32 (mixed plans)
-    int tab_i0, ntab;                  // first interval index, interval count
+    double *d_tab;                     // M1 table [ntab][TabFmt<double>::STRIDE] (FP64)
+    float *d_tab32;                    // FP32 table [ntab32][TabFmt<float>::STRIDE] (mixed plans)
+    int tab_i0, ntab;                  // first interval index, interval count (FP64 table)
+    int tab32_i0, ntab32;              // the same for the FP32 table (mixed plans)
     // per-bead trig tables for the reciprocal sum: cos/sin(k_t . r_nu),
     // stored [t][nu] (FP64) for the current R
     double *d_cos, *d_sin;
@@ -158,7 +167,7 @@ bd_status check_launch(const char *what);
 
 // ---- launchers (defined in the .cu files) ---------------------------------
 // ewald_build.cu
-void m1_table_range(const bd_params &p, int *i0, int *ntab);
+void m1_table_range(const bd_params &p, int bits, int *i0, int *ntab);
 void launch_kvec_table(Plan &P, cudaStream_t s);
 void launch_trig_tables(Plan &P, const double *R, cudaStream_t s);
 void launch_build_D_f64(Plan &P, const double *R, double *D, cudaStream_t s);

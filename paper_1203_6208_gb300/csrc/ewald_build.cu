@@ -114,20 +114,23 @@ __device__ void m1_pair(const EwaldCoef &c, double u, double *f1, double *f2)
     *f2 = c2 * uinv;
 }
 
-// One thread per (interval, function): interpolate at the kTabDeg+1
-// Chebyshev nodes of the interval and solve for the monomial coefficients in
-// t in [-1, 1] (Gaussian elimination with partial pivoting, FP64).
-__global__ void k_m1_table(const EwaldCoef *ewc, int i0, int ntab, double *tab, float *tab32)
+// One thread per (interval, function): interpolate at the DEG+1 Chebyshev
+// nodes of the interval and solve for the monomial coefficients in t in
+// [-1, 1] (Gaussian elimination with partial pivoting, FP64), stored in the
+// table's precision.
+template <typename T>
+__global__ void k_m1_table(const EwaldCoef *ewc, int i0, int ntab, T *tab)
 {
+    constexpr int DEG = TabFmt<T>::DEG, SHIFT = TabFmt<T>::SHIFT, STRIDE = TabFmt<T>::STRIDE;
     int id = blockIdx.x * blockDim.x + threadIdx.x;
     if (id >= 2 * ntab) return;
     const int i = id >> 1, which = id & 1;
-    const int N = kTabDeg + 1;
+    const int N = DEG + 1;
     const EwaldCoef &c = *ewc;
-    double lo = (double)__uint_as_float((unsigned)(i0 + i) << kTabShift);
-    double hi = (double)__uint_as_float((unsigned)(i0 + i + 1) << kTabShift);
+    double lo = (double)__uint_as_float((unsigned)(i0 + i) << SHIFT);
+    double hi = (double)__uint_as_float((unsigned)(i0 + i + 1) << SHIFT);
     double mid = 0.5 * (lo + hi), hw = 0.5 * (hi - lo);
-    double A[kTabDeg + 1][kTabDeg + 2];
+    double A[DEG + 1][DEG + 2];
     for (int j = 0; j < N; j++) {
         double t = cos(3.14159265358979323846 * (j + 0.5) / N);
         double f1, f2;
@@ -147,20 +150,15 @@ __global__ void k_m1_table(const EwaldCoef *ewc, int i0, int ntab, double *tab, 
             for (int k = col; k <= N; k++) A[r][k] -= f * A[col][k];
         }
     }
-    double x[kTabDeg + 1];
+    double x[DEG + 1];
     for (int r = N - 1; r >= 0; r--) {
         double acc = A[r][N];
         for (int k = r + 1; k < N; k++) acc -= A[r][k] * x[k];
         x[r] = acc / A[r][r];
     }
-    double *row = tab + (size_t)i * kTabStride;
-    if (which == 0) { row[0] = mid; row[1] = 1.0 / hw; }
-    for (int k = 0; k < N; k++) row[2 + which * N + k] = x[k];
-    if (tab32) {
-        float *r32 = tab32 + (size_t)i * kTabStride;
-        if (which == 0) { r32[0] = (float)mid; r32[1] = (float)(1.0 / hw); }
-        for (int k = 0; k < N; k++) r32[2 + which * N + k] = (float)x[k];
-    }
+    T *row = tab + (size_t)i * STRIDE;
+    if (which == 0) { row[0] = (T)mid; row[1] = (T)(1.0 / hw); }
+    for (int k = 0; k < N; k++) row[2 + which * N + k] = (T)x[k];
 }
 
 // per k in the working precision, [nk][12]: the six folded tensor components
@@ -236,43 +234,43 @@ __device__ __forceinline__ void add_m1(T vx, T vy, T vz, T u, const EwaldT<T> &c
 // one table row (mid, 1/half-width, 9 + 9 coefficients) with 16-byte loads
 template <typename T> struct TabRow;
 template <> struct TabRow<float> {
-    float v[kTabStride];
+    float v[TabFmt<float>::STRIDE];
     __device__ __forceinline__ TabRow(const float *row)
     {
         const float4 *q = (const float4 *)row;
 #pragma unroll
-        for (int k = 0; k < kTabStride / 4; k++) {
+        for (int k = 0; k < TabFmt<float>::STRIDE / 4; k++) {
             float4 x = __ldg(q + k);
             v[4 * k] = x.x; v[4 * k + 1] = x.y; v[4 * k + 2] = x.z; v[4 * k + 3] = x.w;
         }
     }
 };
 template <> struct TabRow<double> {
-    double v[kTabStride];
+    double v[TabFmt<double>::STRIDE];
     __device__ __forceinline__ TabRow(const double *row)
     {
         const double2 *q = (const double2 *)row;
 #pragma unroll
-        for (int k = 0; k < kTabStride / 2; k++) {
+        for (int k = 0; k < TabFmt<double>::STRIDE / 2; k++) {
             double2 x = __ldg(q + k);
             v[2 * k] = x.x; v[2 * k + 1] = x.y;
         }
     }
 };
-static_assert(kTabStride % 4 == 0, "table rows must be 16-byte multiples");
 
 template <typename T>
 __device__ __forceinline__ void add_m1_tab(T vx, T vy, T vz, T u, const T *__restrict__ tab,
                                            int i0, int ntab, T acc[6])
 {
-    int i = (int)(__float_as_uint((float)u) >> kTabShift) - i0;
+    constexpr int DEG = TabFmt<T>::DEG;
+    int i = (int)(__float_as_uint((float)u) >> TabFmt<T>::SHIFT) - i0;
     i = i < 0 ? 0 : (i >= ntab ? ntab - 1 : i);
-    const TabRow<T> r(tab + (size_t)i * kTabStride);
+    const TabRow<T> r(tab + (size_t)i * TabFmt<T>::STRIDE);
     T t = (u - r.v[0]) * r.v[1];
-    const T *a = r.v + 2, *b = r.v + 2 + (kTabDeg + 1);
-    T c1 = a[kTabDeg], g = b[kTabDeg];
+    const T *a = r.v + 2, *b = r.v + 2 + (DEG + 1);
+    T c1 = a[DEG], g = b[DEG];
 #pragma unroll
-    for (int k = kTabDeg - 1; k >= 0; k--) {
+    for (int k = DEG - 1; k >= 0; k--) {
         c1 = c1 * t + a[k];
         g = g * t + b[k];
     }
@@ -340,6 +338,13 @@ constexpr int TSP = TS + 1;            // padded smem row
 template <typename T> struct Store;
 template <> struct Store<double> {
     __device__ static void put(double *D, void *, size_t idx, double v, int) { D[idx] = v; }
+    // four consecutive elements, idx a multiple of 4 (32-byte aligned rows)
+    __device__ static void put4(double *D, void *, size_t idx, const double v[4], int)
+    {
+        double2 *d = (double2 *)(D + idx);
+        d[0] = make_double2(v[0], v[1]);
+        d[1] = make_double2(v[2], v[3]);
+    }
 };
 template <> struct Store<float> {
     __device__ static void put(float *D, void *D16, size_t idx, float v, int is_bf16)
@@ -347,6 +352,22 @@ template <> struct Store<float> {
         D[idx] = v;
         if (is_bf16) ((__nv_bfloat16 *)D16)[idx] = __float2bfloat16_rn(v);
         else ((__half *)D16)[idx] = __float2half_rn(v);
+    }
+    // four consecutive elements: one 16-byte FP32 store and one 8-byte 16-bit store
+    __device__ static void put4(float *D, void *D16, size_t idx, const float v[4], int is_bf16)
+    {
+        *(float4 *)(D + idx) = make_float4(v[0], v[1], v[2], v[3]);
+        uint2 h;
+        if (is_bf16) {
+            __nv_bfloat162 a = __floats2bfloat162_rn(v[0], v[1]), b = __floats2bfloat162_rn(v[2], v[3]);
+            h.x = *(const unsigned *)&a;
+            h.y = *(const unsigned *)&b;
+        } else {
+            __half2 a = __floats2half2_rn(v[0], v[1]), b = __floats2half2_rn(v[2], v[3]);
+            h.x = *(const unsigned *)&a;
+            h.y = *(const unsigned *)&b;
+        }
+        *(uint2 *)((__half *)D16 + idx) = h;
     }
 };
 
@@ -477,19 +498,38 @@ k_build_D(const double *__restrict__ pw, const float *__restrict__ pw32, int n,
         b[2 * TSP] = acc[2]; b[2 * TSP + 1] = acc[4]; b[2 * TSP + 2] = acc[5];
     }
     __syncthreads();
+    // four consecutive columns per thread and store (rows start 256-byte
+    // aligned, tile columns at multiples of 48 elements); a ragged last group
+    // of columns goes element by element
     const long r0 = 3L * TB * I, c0 = 3L * TB * J;
-    for (int e = threadIdx.x; e < TS * TS; e += TB * TB) {
-        int r = e / TS, cc = e % TS;
-        T v = (I == J && r / 3 > cc / 3) ? tile[cc * TSP + r] : tile[r * TSP + cc];
-        if (r0 + r < n3 && c0 + cc < n3)
-            Store<T>::put(D, D16, (size_t)((r0 + r) * ld + c0 + cc), v, is_bf16);
+    constexpr int NQ = TS / 4;
+    static_assert(TS % 4 == 0, "tile width");
+    for (int e = threadIdx.x; e < TS * NQ; e += TB * TB) {
+        const int r = e / NQ, cc = 4 * (e - (e / NQ) * NQ);
+        if (r0 + r >= n3) continue;
+        T v[4];
+#pragma unroll
+        for (int k = 0; k < 4; k++)
+            v[k] = (I == J && r / 3 > (cc + k) / 3) ? tile[(cc + k) * TSP + r] : tile[r * TSP + cc + k];
+        const size_t idx = (size_t)((r0 + r) * ld + c0 + cc);
+        if (c0 + cc + 4 <= n3) Store<T>::put4(D, D16, idx, v, is_bf16);
+        else
+            for (int k = 0; k < 4; k++)
+                if (c0 + cc + k < n3) Store<T>::put(D, D16, idx + k, v[k], is_bf16);
     }
     if (I != J) {
-        for (int e = threadIdx.x; e < TS * TS; e += TB * TB) {
-            int r = e / TS, cc = e % TS;   // mirror: row c0+r, col r0+cc = tile[cc][r]
-            if (c0 + r < n3 && r0 + cc < n3)
-                Store<T>::put(D, D16, (size_t)((c0 + r) * ld + r0 + cc), tile[cc * TSP + r],
-                              is_bf16);
+        for (int e = threadIdx.x; e < TS * NQ; e += TB * TB) {
+            // mirror: row c0 + r, columns r0 + cc .. r0 + cc + 3 = tile[cc + k][r]
+            const int r = e / NQ, cc = 4 * (e - (e / NQ) * NQ);
+            if (c0 + r >= n3) continue;
+            T v[4];
+#pragma unroll
+            for (int k = 0; k < 4; k++) v[k] = tile[(cc + k) * TSP + r];
+            const size_t idx = (size_t)((c0 + r) * ld + r0 + cc);
+            if (r0 + cc + 4 <= n3) Store<T>::put4(D, D16, idx, v, is_bf16);
+            else
+                for (int k = 0; k < 4; k++)
+                    if (r0 + cc + k < n3) Store<T>::put(D, D16, idx + k, v[k], is_bf16);
         }
     }
 }
@@ -498,15 +538,16 @@ k_build_D(const double *__restrict__ pw, const float *__restrict__ pw32, int n,
 // launchers
 
 // interval range of the M1 table for u in [4a^2, r_c^2] (integer bit patterns only)
-void m1_table_range(const bd_params &p, int *i0, int *ntab)
+void m1_table_range(const bd_params &p, int bits, int *i0, int *ntab)
 {
+    const int shift = 23 - bits;
     float lo = (float)(4.0 * p.a * p.a), hi = (float)(p.r_c * p.r_c * (1.0 + 1e-6));
     if (!(lo > 0.f) || !(hi > lo)) { *i0 = 0; *ntab = 0; return; }
     unsigned blo, bhi;
     memcpy(&blo, &lo, 4);
     memcpy(&bhi, &hi, 4);
-    *i0 = (int)(blo >> kTabShift);
-    *ntab = (int)(bhi >> kTabShift) - *i0 + 1;
+    *i0 = (int)(blo >> shift);
+    *ntab = (int)(bhi >> shift) - *i0 + 1;
 }
 
 void launch_kvec_table(Plan &P, cudaStream_t s)
@@ -538,8 +579,12 @@ void launch_kvec_table(Plan &P, cudaStream_t s)
         cudaMemcpyAsync(&P.h_ew32, P.d_ew32, sizeof(EwaldT<float>), cudaMemcpyDeviceToHost, s);
     cudaStreamSynchronize(s);
     if (P.ntab > 0) {
-        k_m1_table<<<(2 * P.ntab + 63) / 64, 64, 0, s>>>(P.d_ewc, P.tab_i0, P.ntab, P.d_tab,
-                                                        P.d_tab32);
+        k_m1_table<double><<<(2 * P.ntab + 63) / 64, 64, 0, s>>>(P.d_ewc, P.tab_i0, P.ntab, P.d_tab);
+        count_launches(1);
+    }
+    if (P.d_tab32 && P.ntab32 > 0) {
+        k_m1_table<float><<<(2 * P.ntab32 + 63) / 64, 64, 0, s>>>(P.d_ewc, P.tab32_i0, P.ntab32,
+                                                                 P.d_tab32);
         count_launches(1);
     }
     if (nk > kMaxKvec || nk == 0) {
@@ -603,7 +648,7 @@ bd_status launch_build_D_f32(Plan &P, const double *R, float *D32, void *D16, in
     }
     long nb = tile_pairs(P.n);
     k_build_D<float><<<(unsigned)nb, TB * TB, 0, s>>>(
-        P.d_pw64, P.d_pw32, P.n, P.h_ew32, P.d_ewc, P.d_tab32, P.tab_i0, P.ntab, P.d_km32, nk,
+        P.d_pw64, P.d_pw32, P.n, P.h_ew32, P.d_ewc, P.d_tab32, P.tab32_i0, P.ntab32, P.d_km32, nk,
         P.d_cos32, P.d_sin32, P.p.overlap_corr,
         (float)P.p.r_c, D32, D16, is_bf16, P.ld, P.recip_tc);
     count_launches(1);
@@ -835,7 +880,7 @@ bd_status launch_apply_matfree(Plan &P, const double *X, int m, double *Y, cudaS
         }
     } else {
         k_pair_apply<float><<<nb, kMfRows, sm, s>>>(P.d_pw64, P.d_pw32, P.n, P.h_ew32, P.d_tab32,
-                                                    P.tab_i0, P.ntab, P.p.overlap_corr,
+                                                    P.tab32_i0, P.ntab32, P.p.overlap_corr,
                                                     (float)P.p.r_c, X, m, Y, P.mf_chunks,
                                                     P.d_mfpart);
         count_launches(1);
@@ -1212,7 +1257,7 @@ bd_status build_real_pairs(Plan &P, cudaStream_t s)
     } else {
         pairs_pass<float>(P, P.h_ew32, true, s);
         k_pair_blocks<float><<<nbp, 256, 0, s>>>((const float4 *)S->d_rowpos, P.h_ew32, P.d_tab32,
-                                                  P.tab_i0, P.ntab, P.p.overlap_corr, S->d_prow,
+                                                  P.tab32_i0, P.ntab32, P.p.overlap_corr, S->d_prow,
                                                   S->d_nbr, np, (float *)S->d_tens, S->pair_cap);
     }
     count_launches(1);
