@@ -53,6 +53,11 @@ def parse():
     ap.add_argument("--bounds", default="lagged", choices=["lagged", "fresh"],
                     help="mixed plans: lagged = bounds from the previous step's Lanczos "
                          "carried in the products; fresh = --lanczos products per step")
+    ap.add_argument("--shape", default="auto", choices=["auto", "1", "2", "3"],
+                    help="launch shape of the mixed product: auto = autotuned on the first "
+                         "warm-up step; 1/2 = stream-K with 1/2 CTAs per SM; 3 = symmetric "
+                         "(upper triangle of D16).  Profiles fix it (a profiler distorts the "
+                         "autotuner's timings)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--workload", default="n8000",
@@ -298,12 +303,16 @@ def measure(args, precision, p, R0, rank, ws):
     for w in range(args.warmup):
         plan.step(R, D, None, step_index=w, **kw)
         if w == 0 and precision != "fp64":
-            # launch shape of the tensor-core product, timed on this D
-            cps, pms = plan.autotune(D)
-            shape = ({"kernel": "symmetric (upper triangle of D16)", "autotune_ms": round(pms, 4)}
+            # launch shape of the tensor-core product, timed on this D (or fixed)
+            if args.shape != "auto":
+                plan.set_shape(int(args.shape))
+                cps, pms = int(args.shape), float("nan")
+            else:
+                cps, pms = plan.autotune(D)
+            shape = ({"kernel": "symmetric (upper triangle of D16)"}
                      if cps == bnd.BD_SHAPE_SYMMETRIC else
-                     {"kernel": "stream-K (all of D16)", "ctas_per_sm": cps,
-                      "autotune_ms": round(pms, 4)})
+                     {"kernel": "stream-K (all of D16)", "ctas_per_sm": cps})
+            shape["autotune_ms"] = None if args.shape != "auto" else round(pms, 4)
     torch.cuda.synchronize()
     stream = torch.cuda.current_stream()
     evs = [[torch.cuda.Event(enable_timing=True) for _ in range(7)] for _ in range(args.steps)]
