@@ -462,15 +462,17 @@ k_sym_reduce(Geo g, const float *__restrict__ part, int n3, tc::Epi e)
         }
         for (; k < cn; k++) add(__ldcg(base + (size_t)s_list[k] * (BN * BM)));
     }
-    const double y = (double)sh + (double)sl;
+    // the operand's column scales are powers of two: undone exactly in FP32
+    const float isc = e.inv_scale[cc];
+    const double w = (double)(sh * isc) + (double)(sl * isc);
     if (e.mode == 0) {
-        if (row < n3) e.Y[(long)cc * n3 + row] = y * (double)e.inv_scale[cc];
+        if (row < n3) e.Y[(long)cc * n3 + row] = w;
         return;
     }
     if (cc == e.lan_col) {
         // the Lanczos column: w = D q_j and this row block's share of q_j.w,
         // q_{j-1}.w and w.w, reduced in a fixed order (deterministic)
-        const double lw = y * (double)e.inv_scale[cc];
+        const double lw = w;
         if (row < n3) e.lan_w[row] = lw;
         double t[3] = {row < n3 ? e.lan_q[row] * lw : 0.0, row < n3 ? e.lan_qp[row] * lw : 0.0,
                        row < n3 ? lw * lw : 0.0};
@@ -486,18 +488,26 @@ k_sym_reduce(Geo g, const float *__restrict__ part, int n3, tc::Epi e)
                 e.lan_part[3 * X + k] = ((lan_red[0][k] + lan_red[1][k]) + lan_red[2][k]) + lan_red[3][k];
         return;
     }
-    if (row >= n3) return;
     // Chebyshev term of Eqs. (cheb2)/(cheb3): V_p = 2 (s W - t V_{p-1}) - V_{p-2},
-    // dS += c_p V_p, and the scaled 16-bit V_p as the next product's operand
-    const double dmin = e.bounds[0], dmax = e.bounds[1];
-    const double ys = 2.0 / (dmax - dmin), yt = (dmax + dmin) / (dmax - dmin);
+    // dS += c_p V_p, and the scaled 16-bit V_p as the next product's operand.
+    // The interval map s, t is formed once per CTA (FP64 divisions run on
+    // this GPU's slow FP64 pipe).
+    __shared__ double s_map[2];
+    if (r == 0) {
+        const double dmin = e.bounds[0], dmax = e.bounds[1];
+        const double iw = 1.0 / (dmax - dmin);
+        s_map[0] = 2.0 * iw;
+        s_map[1] = (dmax + dmin) * iw;
+    }
+    __syncthreads();
+    if (row >= n3) return;
+    const double ys = s_map[0], yt = s_map[1];
     const long o = (long)cc * n3 + row;
     const double p1 = e.Vprev1[o], p2 = e.Vprev2[o], d0 = e.dS[o];
-    const double w = y * (double)e.inv_scale[cc];
     const double v = 2.0 * (ys * w - yt * p1) - p2;
     e.Vprev2[o] = v;
     e.dS[o] = d0 + e.coef[e.p] * v;
-    const float sv = (float)(v * (double)e.scale[cc]);
+    const float sv = (float)v * e.scale[cc];
     const size_t xo = (size_t)cc * e.ldx + row;
     if (e.is_bf16) ((__nv_bfloat16 *)e.X16next)[xo] = __float2bfloat16_rn(sv);
     else ((__half *)e.X16next)[xo] = __float2half_rn(sv);

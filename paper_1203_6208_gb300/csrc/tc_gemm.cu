@@ -630,11 +630,14 @@ __global__ void k_lanczos_step(double *qprev, double *q, const double *w, int n3
         lab[kMaxLanczos + j] = beta;
     }
     if (i >= n3) return;
+    // one reciprocal, not a division per element (FP64 divisions run on this
+    // GPU's slow FP64 pipe)
+    const double ib = beta > 0.0 ? 1.0 / beta : 0.0;
     double x = w[i] - alpha * q[i] - bprev * qprev[i];
-    double qn = beta > 0.0 ? x / beta : 0.0;
+    double qn = x * ib;
     qprev[i] = q[i];
     q[i] = qn;
-    float v = (float)(qn * (double)kLanScale);
+    float v = (float)qn * kLanScale;
     if (is_bf16) ((__nv_bfloat16 *)X16col)[i] = __float2bfloat16_rn(v);
     else ((__half *)X16col)[i] = __float2half_rn(v);
 }
