@@ -148,9 +148,9 @@ struct Plan {
     // reciprocal sum as a tensor-core product (mixed plans, recip_tc.cu)
     int recip_tc;                      // 1: D32's upper tiles are filled by U U^T first
     int recip_kp;                      // columns of U (4 per k-vector, padded to 64)
-    int recip_ntiles;                  // 128 x 128 tiles on and above the diagonal
+    int recip_ntiles;                  // 128 x 256 blocks reaching the diagonal
     __half *d_Uh, *d_Ul;               // U as hi/lo words, half(word 2^8) [3N][recip_kp]
-    int2 *d_rtiles;                    // tile list
+    int2 *d_rtiles;                    // block list (128-row tile, 256-column block)
     float *d_kbasis;                   // per k: w u1, w u2 (FP32) [nk][8]
 };
 

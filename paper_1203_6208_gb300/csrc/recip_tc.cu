@@ -12,10 +12,10 @@
 // scaled by 2^8 (both words are exact in half over the range of U, which is
 // below 1; words under 2^-14 / 2^8 lose bits as subnormals, an absolute error
 // ~1e-10), and D_rec = Uh Uh^T + Uh Ul^T + Ul Uh^T is accumulated in FP32 in
-// TMEM (kind::f16, M = N = 128, K = 16 per MMA -- twice the TF32 rate) and
+// TMEM (kind::f16, M = 128, N = 256, K = 16 per MMA -- twice the TF32 rate) and
 // scaled by 2^-16 on the way out: about 2^-21 relative per term, below the
-// FP32 assembly's own rounding.  The product fills the
-// 128 x 128 tiles of D32 on and above the diagonal; the pair kernel reads the
+// FP32 assembly's own rounding.  The product fills the 128 x 256 blocks of
+// D32 that reach the diagonal (128 x 128 tiles on and above it); the pair kernel reads the
 // six components (a <= b) of each 3 x 3 block it owns there (always row <=
 // column), adds the real-space, self and overlap terms and writes the final
 // D32 / D16 over them.
@@ -29,10 +29,13 @@ namespace bd {
 
 namespace rt {
 
-constexpr int BM = 128, BN = 128, BK = 64;     // BK in half elements (128 bytes)
-constexpr int STAGES = 3;
+constexpr int BM = 128, BN = 256, BK = 64;     // BK in half elements (128 bytes)
+constexpr int STAGES = 4;
 constexpr int THREADS = 192;
-constexpr int TILE_BYTES = BM * BK * 2;        // 16 KB per operand tile
+constexpr int A_BYTES = BM * BK * 2;           // 16 KB: 128 rows of U
+constexpr int B_BYTES = BN * BK * 2;           // 32 KB: 256 rows of U
+constexpr int STAGE_BYTES = A_BYTES + B_BYTES;
+constexpr uint32_t TMEM_COLS = 2 * BN;         // two accumulators
 constexpr float kUScale = 256.f;               // U words stored as half(U 2^8)
 constexpr float kDUnscale = 1.f / (256.f * 256.f);
 constexpr uint32_t kWaitLimit = 1u << 22;
@@ -102,7 +105,7 @@ __device__ __forceinline__ uint64_t sw128_desc(uint32_t addr)
     d |= (uint64_t)2 << 61;
     return d;
 }
-// kind::f16: F32 accumulator, F16 A and B, K-major, M = N = 128
+// kind::f16: F32 accumulator, F16 A and B, K-major, M = 128, N = 256
 constexpr uint32_t kIdesc = (1u << 4) | ((uint32_t)(BN >> 3) << 17) | ((uint32_t)(BM >> 4) << 24);
 
 __device__ __forceinline__ void mma_f16(uint32_t tmem_d, uint64_t da, uint64_t db,
@@ -137,31 +140,42 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float *v)
 }
 
 // -- kernel begin: k_recip_syrk
-// One CTA per 128 x 128 tile (ti, tj), ti <= tj; the K loop
-// runs over three segments (Uh.Uh, Uh.Ul, Ul.Uh) of nkt k-tiles each.
-__global__ void __launch_bounds__(THREADS, 2)
-k_recip_syrk(const __grid_constant__ CUtensorMap mapH, const __grid_constant__ CUtensorMap mapL,
-             const int2 *__restrict__ tiles, int n3, int nkt, float *__restrict__ D32, long ld,
-             int32_t *__restrict__ err)
+// Persistent: CTA c takes the blocks c, c + G, c + 2G, ... of the block list
+// (128 rows ti x 256 columns tj2, the column block reaching the diagonal).
+// Per block the K loop runs over three segments (Uh.Uh, Uh.Ul, Ul.Uh) of nkt
+// k-tiles each into one of two TMEM accumulators, so the epilogue warps drain
+// one block while the MMA warp fills the next.
+__device__ __forceinline__ void mbar_arrive_cta(uint32_t bar)
 {
-    constexpr int STAGE = 2 * TILE_BYTES;
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
+}
+
+__global__ void __launch_bounds__(THREADS, 1)
+k_recip_syrk(const __grid_constant__ CUtensorMap mapH, const __grid_constant__ CUtensorMap mapL,
+             const __grid_constant__ CUtensorMap mapHB, const __grid_constant__ CUtensorMap mapLB,
+             const int2 *__restrict__ blocks, int nblocks, int n3, int nkt, float *__restrict__ D32,
+             long ld, int32_t *__restrict__ err)
+{
     extern __shared__ __align__(1024) uint8_t smem_raw[];
     uint8_t *smem = (uint8_t *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
-    __shared__ __align__(8) uint64_t full_bar[STAGES], empty_bar[STAGES], accum_bar, drain_bar;
+    __shared__ __align__(8) uint64_t full_bar[STAGES], empty_bar[STAGES], acc_full[2], acc_empty[2],
+        drain_bar;
     __shared__ uint32_t tmem_base_sh;
     __shared__ volatile int abort_flag;
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int2 t2 = tiles[blockIdx.x];
-    const int ti = t2.x, tj = t2.y;
+    const int c = blockIdx.x, G = gridDim.x;
     const int nsteps = 3 * nkt;
     if (threadIdx.x == 0) {
         abort_flag = 0;
-        for (int s = 0; s < STAGES; s++) {
-            mbar_init(smem_u32(&full_bar[s]), 1);
-            mbar_init(smem_u32(&empty_bar[s]), 1);
+        for (int st = 0; st < STAGES; st++) {
+            mbar_init(smem_u32(&full_bar[st]), 1);
+            mbar_init(smem_u32(&empty_bar[st]), 1);
         }
-        mbar_init(smem_u32(&accum_bar), 1);
+        for (int b = 0; b < 2; b++) {
+            mbar_init(smem_u32(&acc_full[b]), 1);
+            mbar_init(smem_u32(&acc_empty[b]), 128);
+        }
         mbar_init(smem_u32(&drain_bar), 1);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
@@ -169,7 +183,7 @@ k_recip_syrk(const __grid_constant__ CUtensorMap mapH, const __grid_constant__ C
     if (warp == 1) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
                          smem_u32(&tmem_base_sh)),
-                     "r"(BN)
+                     "r"(TMEM_COLS)
                      : "memory");
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
     }
@@ -179,72 +193,98 @@ k_recip_syrk(const __grid_constant__ CUtensorMap mapH, const __grid_constant__ C
     const uint32_t tmem = tmem_base_sh;
 
     if (warp == 0 && lane == 0) {
-        int issued = 0;
-        for (int i = 0; i < nsteps; i++) {
-            int s = i % STAGES;
-            uint32_t ph = (uint32_t)(i / STAGES) & 1u;
-            if (!mbar_wait(smem_u32(&empty_bar[s]), ph ^ 1u, &abort_flag)) break;
-            const int seg = i / nkt, kk = i % nkt;
-            const CUtensorMap *ma = seg == 2 ? &mapL : &mapH;   // Ul.Uh in segment 2
-            const CUtensorMap *mb = seg == 1 ? &mapL : &mapH;   // Uh.Ul in segment 1
-            uint32_t a = smem_u32(smem + s * STAGE), b = a + TILE_BYTES;
-            uint32_t fb = smem_u32(&full_bar[s]);
-            mbar_expect_tx(fb, STAGE);
-            tma_load_2d(a, ma, kk * BK, ti * BM, fb);
-            tma_load_2d(b, mb, kk * BK, tj * BN, fb);
-            issued = i + 1;
+        // ---- TMA producer
+        int it = 0, issued = 0;
+        for (int bi = c; bi < nblocks && !abort_flag; bi += G) {
+            const int2 t2 = blocks[bi];
+            for (int i = 0; i < nsteps; i++, it++) {
+                const int st = it % STAGES;
+                const uint32_t ph = (uint32_t)(it / STAGES) & 1u;
+                if (!mbar_wait(smem_u32(&empty_bar[st]), ph ^ 1u, &abort_flag)) break;
+                const int seg = i / nkt, kk = i % nkt;
+                const CUtensorMap *ma = seg == 2 ? &mapL : &mapH;     // Ul.Uh in segment 2
+                const CUtensorMap *mb = seg == 1 ? &mapLB : &mapHB;   // Uh.Ul in segment 1
+                const uint32_t a = smem_u32(smem + st * STAGE_BYTES), b = a + A_BYTES;
+                const uint32_t fb = smem_u32(&full_bar[st]);
+                mbar_expect_tx(fb, STAGE_BYTES);
+                tma_load_2d(a, ma, kk * BK, t2.x * BM, fb);
+                tma_load_2d(b, mb, kk * BK, t2.y * BN, fb);
+                issued = it + 1;
+            }
         }
         if (abort_flag) {
             for (int i = (issued > STAGES ? issued - STAGES : 0); i < issued; i++) {
-                int s = i % STAGES;
-                uint32_t ph = (uint32_t)(i / STAGES) & 1u;
-                for (uint32_t t = 0; t < kWaitLimit && !mbar_try(smem_u32(&full_bar[s]), ph); t++) {}
+                const int st = i % STAGES;
+                const uint32_t ph = (uint32_t)(i / STAGES) & 1u;
+                for (uint32_t t = 0; t < kWaitLimit && !mbar_try(smem_u32(&full_bar[st]), ph); t++) {}
             }
         }
     } else if (warp == 1 && lane == 0) {
+        // ---- MMA issuer: block k accumulates in TMEM buffer k & 1
         bool ok = true;
-        for (int i = 0; i < nsteps && ok; i++) {
-            int s = i % STAGES;
-            uint32_t ph = (uint32_t)(i / STAGES) & 1u;
-            if (!mbar_wait(smem_u32(&full_bar[s]), ph, &abort_flag)) { ok = false; break; }
+        int it = 0, k = 0;
+        for (int bi = c; bi < nblocks && ok; bi += G, k++) {
+            const int buf = k & 1;
+            if (k >= 2 &&
+                !mbar_wait(smem_u32(&acc_empty[buf]), (uint32_t)((k >> 1) - 1) & 1u, &abort_flag)) {
+                ok = false;
+                break;
+            }
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-            uint32_t a = smem_u32(smem + s * STAGE), b = a + TILE_BYTES;
-            uint64_t da = sw128_desc(a), db = sw128_desc(b);
+            const uint32_t acc = tmem + (uint32_t)(buf * BN);
+            for (int i = 0; i < nsteps; i++, it++) {
+                const int st = it % STAGES;
+                const uint32_t ph = (uint32_t)(it / STAGES) & 1u;
+                if (!mbar_wait(smem_u32(&full_bar[st]), ph, &abort_flag)) { ok = false; break; }
+                asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                const uint32_t a = smem_u32(smem + st * STAGE_BYTES), b = a + A_BYTES;
+                const uint64_t da = sw128_desc(a), db = sw128_desc(b);
 #pragma unroll
-            for (int k = 0; k < BK / 16; k++)     // 16 halves = 32 bytes per MMA along K
-                mma_f16(tmem, da + (uint64_t)(2 * k), db + (uint64_t)(2 * k),
-                         (i > 0 || k > 0) ? 1u : 0u);
-            mma_commit(smem_u32(&empty_bar[s]));
+                for (int kq = 0; kq < BK / 16; kq++)      // 16 halves = 32 bytes per MMA along K
+                    mma_f16(acc, da + (uint64_t)(2 * kq), db + (uint64_t)(2 * kq),
+                            (i > 0 || kq > 0) ? 1u : 0u);
+                mma_commit(smem_u32(&empty_bar[st]));
+            }
+            if (ok) mma_commit(smem_u32(&acc_full[buf]));
         }
-        mma_commit(smem_u32(&accum_bar));
         if (!ok) {
             mma_commit(smem_u32(&drain_bar));
             for (uint32_t t = 0; t < kWaitLimit && !mbar_try(smem_u32(&drain_bar), 0); t++) {}
         }
     } else if (warp >= 2) {
+        // ---- epilogue warps: TMEM lane quadrant q, row r of the block
         const int q = warp & 3;
-        const long row = (long)ti * BM + q * 32 + lane;
-        bool ok = mbar_wait_sleep(smem_u32(&accum_bar), 0, &abort_flag);
-        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-        if (ok) {
-            for (int c0 = 0; c0 < BN; c0 += 16) {
+        const uint32_t lane_off = (uint32_t)(q * 32) << 16;
+        int k = 0;
+        for (int bi = c; bi < nblocks; bi += G, k++) {
+            const int buf = k & 1;
+            if (!mbar_wait_sleep(smem_u32(&acc_full[buf]), (uint32_t)(k >> 1) & 1u, &abort_flag))
+                break;
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            const int2 t2 = blocks[bi];
+            const long row = (long)t2.x * BM + q * 32 + lane;
+            // the first 128 columns lie below the diagonal when 2 tj2 < ti
+            const int cstart = (2 * t2.y < t2.x) ? BM : 0;
+            for (int c0 = cstart; c0 < BN; c0 += 16) {
                 float v[16];
-                tmem_ld16(tmem + ((uint32_t)(q * 32) << 16) + c0, v);
+                tmem_ld16(tmem + lane_off + (uint32_t)(buf * BN + c0), v);
 #pragma unroll
-                for (int c = 0; c < 16; c++) v[c] *= kDUnscale;     // undo the 2^8 word scales
-                const long col = (long)tj * BN + c0;
+                for (int cc = 0; cc < 16; cc++) v[cc] *= kDUnscale;     // undo the 2^8 word scales
+                const long col = (long)t2.y * BN + c0;
                 if (row < n3) {
                     float *dst = D32 + row * ld + col;
                     if (col + 16 <= n3) {
 #pragma unroll
-                        for (int c = 0; c < 16; c += 4)
-                            *(float4 *)(dst + c) = make_float4(v[c], v[c + 1], v[c + 2], v[c + 3]);
+                        for (int cc = 0; cc < 16; cc += 4)
+                            *(float4 *)(dst + cc) = make_float4(v[cc], v[cc + 1], v[cc + 2], v[cc + 3]);
                     } else {
-                        for (int c = 0; c < 16; c++)
-                            if (col + c < n3) dst[c] = v[c];
+                        for (int cc = 0; cc < 16; cc++)
+                            if (col + cc < n3) dst[cc] = v[cc];
                     }
                 }
             }
+            asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+            mbar_arrive_cta(smem_u32(&acc_empty[buf]));
         }
     }
     if (threadIdx.x == 0 && abort_flag) atomicExch(err, (int32_t)BD_ERR_TIMEOUT);
@@ -252,7 +292,7 @@ k_recip_syrk(const __grid_constant__ CUtensorMap mapH, const __grid_constant__ C
     __syncthreads();
     if (warp == 1) {
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(BN)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TMEM_COLS)
                      : "memory");
     }
 }
@@ -347,12 +387,16 @@ __global__ void k_build_U(const float *__restrict__ cs, const float *__restrict_
 
 static PFN_cuTensorMapEncodeTiled_v12000 g_enc = nullptr;
 
-static int upper_tiles(int T, std::vector<int2> *out)
+// blocks of 128 rows x 256 columns reaching the diagonal (column block j2
+// covers 128-row tiles 2 j2 and 2 j2 + 1), column-major so that the CTAs
+// running together share their column block of U in L2
+static int upper_blocks(int T, std::vector<int2> *out)
 {
     int cnt = 0;
-    for (int j = 0; j < T; j++)
-        for (int i = 0; i <= j; i++) {
-            if (out) out->push_back(make_int2(i, j));
+    const int T2 = (T + 1) / 2;
+    for (int j2 = 0; j2 < T2; j2++)
+        for (int i = 0; i <= 2 * j2 + 1 && i < T; i++) {
+            if (out) out->push_back(make_int2(i, j2));
             cnt++;
         }
     return cnt;
@@ -377,7 +421,7 @@ bd_status recip_tc_init(Plan &P)
     P.recip_kp = (4 * P.nk + rt::BK - 1) / rt::BK * rt::BK;
     const int T = (P.n3 + rt::BM - 1) / rt::BM;
     std::vector<int2> tiles;
-    P.recip_ntiles = upper_tiles(T, &tiles);
+    P.recip_ntiles = upper_blocks(T, &tiles);
     size_t ub = (size_t)P.n3 * P.recip_kp * sizeof(__half);
     cudaError_t e = cudaMalloc(&P.d_Uh, ub);
     if (e == cudaSuccess) e = cudaMalloc(&P.d_Ul, ub);
@@ -391,7 +435,7 @@ bd_status recip_tc_init(Plan &P)
     k_kbasis<<<(P.nk + 127) / 128, 128>>>(P.d_kvec, P.nk, P.d_kbasis);
     count_launches(1);
     cudaMemcpy(P.d_rtiles, tiles.data(), tiles.size() * sizeof(int2), cudaMemcpyHostToDevice);
-    const int sm = rt::STAGES * 2 * rt::TILE_BYTES + 1024;
+    const int sm = rt::STAGES * rt::STAGE_BYTES + 1024;
     if (cudaFuncSetAttribute(rt::k_recip_syrk, cudaFuncAttributeMaxDynamicSharedMemorySize, sm) !=
         cudaSuccess)
         return set_error(BD_ERR_CUDA, "smem attribute (reciprocal product)");
@@ -399,11 +443,11 @@ bd_status recip_tc_init(Plan &P)
     return BD_OK;
 }
 
-static bd_status map_U(CUtensorMap *m, const __half *base, int Kp, int n3)
+static bd_status map_U(CUtensorMap *m, const __half *base, int Kp, int n3, int rows)
 {
     cuuint64_t dims[2] = {(cuuint64_t)Kp, (cuuint64_t)n3};
     cuuint64_t strides[1] = {(cuuint64_t)Kp * 2};
-    cuuint32_t box[2] = {rt::BK, rt::BM};
+    cuuint32_t box[2] = {rt::BK, (cuuint32_t)rows};
     cuuint32_t es[2] = {1, 1};
     CUresult r = g_enc(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT16, 2, const_cast<__half *>(base), dims,
                        strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
@@ -420,15 +464,19 @@ bd_status launch_recip_tc(Plan &P, float *D32, cudaStream_t s)
     k_build_U<<<gu, 128, 0, s>>>(P.d_cos32, P.d_sin32, P.d_kbasis, P.n, P.nk, P.recip_kp, P.d_Uh,
                                  P.d_Ul);
     count_launches(1);
-    CUtensorMap mh, ml;
-    bd_status st = map_U(&mh, P.d_Uh, P.recip_kp, P.n3);
+    CUtensorMap mh, ml, mhb, mlb;
+    bd_status st = map_U(&mh, P.d_Uh, P.recip_kp, P.n3, rt::BM);
+    if (st == BD_OK) st = map_U(&ml, P.d_Ul, P.recip_kp, P.n3, rt::BM);
+    if (st == BD_OK) st = map_U(&mhb, P.d_Uh, P.recip_kp, P.n3, rt::BN);
+    if (st == BD_OK) st = map_U(&mlb, P.d_Ul, P.recip_kp, P.n3, rt::BN);
     if (st != BD_OK) return st;
-    st = map_U(&ml, P.d_Ul, P.recip_kp, P.n3);
-    if (st != BD_OK) return st;
-    const int sm = rt::STAGES * 2 * rt::TILE_BYTES + 1024;
-    rt::k_recip_syrk<<<P.recip_ntiles, rt::THREADS, sm, s>>>(mh, ml, P.d_rtiles, P.n3,
-                                                            P.recip_kp / rt::BK, D32, P.ld,
-                                                            P.d_status + 6);
+    const int sm = rt::STAGES * rt::STAGE_BYTES + 1024;
+    int nsm = P.num_sms;
+    if (nsm <= 0) cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, P.device);
+    const int G = P.recip_ntiles < nsm ? P.recip_ntiles : nsm;
+    rt::k_recip_syrk<<<G, rt::THREADS, sm, s>>>(mh, ml, mhb, mlb, P.d_rtiles, P.recip_ntiles,
+                                               P.n3, P.recip_kp / rt::BK, D32, P.ld,
+                                               P.d_status + 6);
     count_launches(1);
     return check_launch("reciprocal product");
 }
