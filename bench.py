@@ -61,7 +61,7 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--workload", default="n8000",
-                    choices=["n8000", "batch", "theta", "lma", "spectral"],
+                    choices=["n8000", "batch", "theta", "lma", "spectral", "lambda"],
                     help="batch: 64 replicas, N ~ U[200, 2000], mixed, one graph launch "
                          "per step (replica-steps/s); theta: the theta-solution statics "
                          "validation (N_b = 20 and 40, N_c = 20, a = 0.5, dt = 0.01, five "
@@ -748,6 +748,68 @@ def run_spectral(args):
     print(json.dumps(line), flush=True)
 
 
+def run_lambda(args):
+    """Sec. IV's eigenvalue study behind Eqs. (fmax) and (fmin): for N_b = 10
+    chains at c/c* = 4.44 and a = 0.5, N_c = 10 .. 300 (three conformations
+    each), Fixman's estimates lambda^F_max,min = U+-.D.U+- / 3N (Eq.
+    lmax-lmin-dilute, from the library's own FP64 products) against the exact
+    extreme eigenvalues of the FP64 D (a dense symmetric eigensolver, as the
+    paper's GSL routine) and the library's Lanczos bounds (60 steps).  Reports
+    lambda^exact_max / lambda^F_max beside 0.35 N^0.6, C = (lambda_max /
+    lambda_min) / N^0.6, and the fitted log-log slopes over N."""
+    import numpy as np
+    import torch
+    torch.cuda.set_device(0)
+    from paper_1203_6208_gb300 import binding as bnd, build, inputs
+    build.build()
+    rows = []
+    t0 = time.perf_counter()
+    for nc in (10, 20, 40, 80, 160, 300):
+        for k in range(3):
+            cfg = inputs.SystemConfig(n_chains=nc, nb=10, c_over_cstar=4.44,
+                                      hstar=0.5 / inputs.SQRT_PI, seed=5000 + 10 * nc + k)
+            p = cfg.params()
+            plan = bnd.Plan(p, "fp64", max_rhs=2, max_cheb=8)
+            R = torch.tensor(inputs.make_chains(cfg).reshape(-1), device="cuda")
+            D = plan.alloc_D()
+            plan.build_D(R, D)
+            n3 = 3 * cfg.n
+            U = torch.ones(2, n3, dtype=torch.float64, device="cuda")
+            U[1, 1::2] = -1.0
+            Y = torch.empty_like(U)
+            plan.apply(D, U, Y)
+            lF_max = float((U[0] * Y[0]).sum()) / n3
+            lF_min = float((U[1] * Y[1]).sum()) / n3
+            ev = torch.linalg.eigvalsh(plan.D_view(D))
+            lmin, lmax = float(ev[0]), float(ev[-1])
+            bounds = torch.empty(2, dtype=torch.float64, device="cuda")
+            plan.eig_bounds(D, 60, 0.0, 1.0, bounds)
+            th = bounds.cpu().numpy()
+            n06 = cfg.n ** 0.6
+            rows.append({"N": cfg.n, "lambdaF_max": lF_max, "lambdaF_min": lF_min,
+                         "lambda_max": lmax, "lambda_min": lmin,
+                         "lanczos_max": float(th[1]), "lanczos_min": float(th[0]),
+                         "ratio_max": lmax / lF_max, "eq_fmax": 0.35 * n06,
+                         "C": lmax / lmin / n06})
+            del D, ev
+            plan.close()
+            torch.cuda.empty_cache()
+    Ns = np.array([r["N"] for r in rows], dtype=np.float64)
+    slope = lambda key: float(np.polyfit(np.log(Ns), np.log([r[key] for r in rows]), 1)[0])
+    fits = {"lambda_max": slope("lambda_max"), "lambda_min": slope("lambda_min"),
+            "lambdaF_max": slope("lambdaF_max"), "ratio_max": slope("ratio_max"),
+            "kappa": float(np.polyfit(np.log(Ns), np.log([r["lambda_max"] / r["lambda_min"]
+                                                          for r in rows]), 1)[0])}
+    line = {"metric": "eigenvalue study (Sec. IV, Eqs. fmax, fmin): fitted exponents over N",
+            "value": fits["ratio_max"], "unit": "d log(lambda_max/lambda^F_max) / d log N",
+            "n_gpus": 1, "higher_is_better": None, "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "wall_s": round(time.perf_counter() - t0, 1),
+            "config": {"workload": "lambda", "nb": 10, "c_over_cstar": 4.44, "a": 0.5,
+                       "n_chains": [10, 20, 40, 80, 160, 300], "conformations": 3},
+            "fits": fits, "rows": rows}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -759,6 +821,8 @@ def main():
         run_lma(args)
     elif args.workload == "spectral":
         run_spectral(args)
+    elif args.workload == "lambda":
+        run_lambda(args)
     elif args.workload == "batch":
         run_batch(args)
     else:
