@@ -58,6 +58,10 @@ def parse():
                          "warm-up step; 1/2 = stream-K with 1/2 CTAs per SM; 3 = symmetric "
                          "(upper triangle of D16).  Profiles fix it (a profiler distorts the "
                          "autotuner's timings)")
+    ap.add_argument("--no-graph", action="store_true",
+                    help="mixed plans: time direct bd_step calls only (default: the step "
+                         "captured once with bd_step_capture and replayed with "
+                         "bd_step_replay, the direct steps reported beside it)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--workload", default="n8000",
@@ -337,11 +341,33 @@ def measure(args, precision, p, R0, rank, ws):
     torch.cuda.synchronize()
     prod_ms, prod_n = plan.product_timing(False)
     launches = bnd.kernel_launches() - l0
+    plan.set_phase_events(None)
+    ms = e0.elapsed_time(e1)
+    direct_ms = ms
+    graph = precision != "fp64" and not args.no_graph
+    if graph:
+        # the same step recorded once as a CUDA graph (noise from the device
+        # step counter) and replayed: no host launch gaps between its kernels
+        kwg = {k: v for k, v in kw.items()}
+        plan.set_step_counter(7_000_000)
+        l1 = bnd.kernel_launches()
+        plan.step_capture(R, D, flags=bnd.BD_STEP_DEVICE_COUNTER, **kwg)
+        launches = (bnd.kernel_launches() - l1) * args.steps     # kernels of the replays
+        for _ in range(3):
+            plan.step_replay()
+        torch.cuda.synchronize()
+        if ws > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize()
+        e0.record(stream)
+        for k in range(args.steps):
+            plan.step_replay()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1)
     if ws > 1:
         torch.distributed.barrier()
     clk = clocks.stop()
-    plan.set_phase_events(None)
-    ms = e0.elapsed_time(e1)
     if ws > 1:
         t = torch.tensor([ms], device="cuda")
         torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
@@ -406,16 +432,23 @@ def measure(args, precision, p, R0, rank, ws):
         t0 = time.perf_counter()
         for k in range(args.e2e_steps):
             R.copy_(Rh, non_blocking=True)
-            plan.step(R, D, None, step_index=10_000 + k, **kw)
+            if graph:
+                plan.step_replay()
+            else:
+                plan.step(R, D, None, step_index=10_000 + k, **kw)
             Rh.copy_(R, non_blocking=True)
             sh.copy_(stats, non_blocking=True)
             stream.synchronize()
         e2e_s = (time.perf_counter() - t0) / args.e2e_steps
         e2e = {"value": ws / e2e_s, "unit": "steps/s", "h2d_bytes_per_step": 8 * n3,
                "d2h_bytes_per_step": 8 * n3 + bnd.STATS_BYTES,
-               "note": "per step: positions H2D from pinned memory, bd_step, positions + "
-                       "stats D2H, stream sync (wall clock)"}
+               "note": "per step: positions H2D from pinned memory, the step (bd_step_replay "
+                       "of the captured step on mixed plans, else bd_step), positions + stats "
+                       "D2H, stream sync (wall clock)"}
     out = {"value": ws * args.steps / (ms * 1e-3), "ms_per_step": ms / args.steps,
+           "launch": "CUDA graph replay (bd_step_capture / bd_step_replay)" if graph
+                     else "direct bd_step calls",
+           "direct_ms_per_step": direct_ms / args.steps,
            "phases_ms": phases, "step_stats": st, "roofline": roof, "gpu_launches": launches,
            "clocks": clk, "e2e": e2e, "n_kvec_half": plan.info.n_kvec,
            "d_gb": plan.info.d_bytes / 1e9, "product_shape": shape}
@@ -469,7 +502,8 @@ def run_ours(args):
                        "bounds": args.bounds if head != "fp64" else "fresh",
                        "l2": "inputs larger than L2 (D alone is %.2f GB)" % r["d_gb"],
                        "parallelism": "replicas" if ws > 1 else "single",
-                       "product_shape": r["product_shape"]},
+                       "product_shape": r["product_shape"], "launch": r["launch"]},
+            "direct_ms_per_step": r["direct_ms_per_step"],
             "phases_ms": r["phases_ms"], "step_stats": r["step_stats"], "roofline": r["roofline"],
             "gpu_launches": r["gpu_launches"], "clocks": r["clocks"], "e2e": r["e2e"]}
     if "fp64" in results and head != "fp64":

@@ -309,6 +309,25 @@ bd_status bd_apply_D_matfree(bd_plan *plan, const double *R, const double *X, in
 bd_status bd_step(bd_plan *plan, double *R, void *D, const double *dW, const bd_step_opts *opts,
                   double *DF, double *dS, bd_step_stats *stats, bd_stream stream);
 
+/* bd_step_capture / bd_step_replay -- the same step as one CUDA graph.
+ * bd_step_capture records the launches of bd_step(plan, R, D, NULL, opts,
+ * DF, dS, stats) by stream capture on a private stream (nothing runs; `stream`
+ * is not used, the legacy default stream cannot be captured) with the Wiener
+ * increments drawn from the plan's device step counter (BD_STEP_DEVICE_COUNTER
+ * is added to opts->flags), instantiates the graph and keeps it in the plan,
+ * replacing an earlier one; every bd_step_replay then launches that step on
+ * `stream` -- new noise per replay, the pointers and options of the capture.
+ * Steps that synchronise the host cannot be captured: adaptive N_Ch
+ * (n_cheb == 0) and BD_STEP_MATRIX_FREE return BD_ERR_INVALID.  A lagged-bounds
+ * step should be captured after one bd_step has run with the same options
+ * (else the captured step recomputes fresh Lanczos bounds on every replay).
+ * The plan's phase events and product timing are not recorded in the graph.
+ * Errors: BD_ERR_INVALID as above, BD_ERR_CUDA if capture or instantiation
+ * fails; bd_step_replay: BD_ERR_INVALID without a captured step.          */
+bd_status bd_step_capture(bd_plan *plan, double *R, void *D, const bd_step_opts *opts,
+                          double *DF, double *dS, bd_step_stats *stats, bd_stream stream);
+bd_status bd_step_replay(bd_plan *plan, bd_stream stream);
+
 /* ---------------------------------------------------------------------------
  * Reverse mode.  D(R) enters the step through D_{nu mu} = B(r_nu - r_mu)
  * (Eq. DFmodified); the derivative of each block is recomputed per pair from

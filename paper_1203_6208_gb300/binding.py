@@ -32,7 +32,7 @@ BOUNDS_MODES = {"fresh": 0, "lagged": 1, "fixman_dilute": 2, "fixman_semidilute"
 EXPORTS = ["bd_plan_create", "bd_plan_destroy", "bd_plan_query", "bd_forces", "bd_build_D",
            "bd_apply_D", "bd_eig_bounds", "bd_chebyshev_sqrt", "bd_step", "bd_wiener",
            "bd_set_phase_events", "bd_kernel_launches", "bd_eig_bounds_noalloc",
-           "bd_apply_D_backward", "bd_chebyshev_backward", "bd_plan_autotune", "bd_plan_set_shape", "bd_product_timing",
+           "bd_apply_D_backward", "bd_chebyshev_backward", "bd_plan_autotune", "bd_plan_set_shape", "bd_step_capture", "bd_step_replay", "bd_product_timing",
            "bd_plan_set_step_counter", "bd_batch_create", "bd_batch_destroy", "bd_batch_query",
            "bd_batch_step", "bd_chebyshev_sqrt_adaptive", "bd_apply_D_matfree",
            "bd_last_error", "bd_version"]
@@ -100,6 +100,8 @@ def load(path: str = LIB_PATH):
     L.bd_eig_bounds.argtypes = [_vp, _vp, i32, f64, f64, _vp, _vp, _vp]
     L.bd_chebyshev_sqrt.argtypes = [_vp, _vp, _vp, i32, _vp, i32, _vp, _vp, _vp]
     L.bd_step.argtypes = [_vp, _vp, _vp, _vp, ctypes.POINTER(BdStepOpts), _vp, _vp, _vp, _vp]
+    L.bd_step_capture.argtypes = [_vp, _vp, _vp, ctypes.POINTER(BdStepOpts), _vp, _vp, _vp, _vp]
+    L.bd_step_replay.argtypes = [_vp, _vp]
     L.bd_wiener.argtypes = [_vp, u64, u64, i64, _vp, _vp]
     L.bd_set_phase_events.argtypes = [_vp, ctypes.POINTER(_vp), i32]
     L.bd_apply_D_backward.argtypes = [_vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp]
@@ -254,6 +256,21 @@ class Plan:
                        flags=int(flags), ef_tol=float(ef_tol), fixman_c=float(fixman_c))
         _check(load().bd_step(self._h, _p(R), _p(D), _p(dW), ctypes.byref(o), _p(DF), _p(dS),
                               _p(stats), _stream(stream)))
+
+    def step_capture(self, R, D, *, m=1, n_cheb=20, lanczos_iters=30, bound_safety=0.05,
+                     dmin_fraction=0.5, seed=0, DF=None, dS=None, stats=None, bounds_mode=0,
+                     flags=0, fixman_c=0.0, stream=None):
+        """bd_step_capture: record one step (noise from the device step counter)
+        as a CUDA graph kept by the plan; replay it with step_replay."""
+        o = BdStepOpts(m=int(m), n_cheb=int(n_cheb), lanczos_iters=int(lanczos_iters),
+                       bound_safety=float(bound_safety), dmin_fraction=float(dmin_fraction),
+                       seed=int(seed), step_index=0, bounds_mode=int(bounds_mode),
+                       flags=int(flags), ef_tol=0.0, fixman_c=float(fixman_c))
+        _check(load().bd_step_capture(self._h, _p(R), _p(D), ctypes.byref(o), _p(DF), _p(dS),
+                                      _p(stats), _stream(stream)))
+
+    def step_replay(self, stream=None):
+        _check(load().bd_step_replay(self._h, _stream(stream)))
 
     def apply_backward(self, R, D, F, gY, gR, gF=None, stream=None):
         _check(load().bd_apply_D_backward(self._h, _p(R), _p(D), _p(F), _p(gY), _p(gR), _p(gF),

@@ -83,6 +83,10 @@ static void free_plan(Plan &P)
     if (P.h_est) cudaFreeHost(P.h_est);
     spectral_free(P);
     sym_plan_free(P);
+    if (P.step_exec) cudaGraphExecDestroy(P.step_exec);
+    if (P.step_graph) cudaGraphDestroy(P.step_graph);
+    P.step_exec = nullptr;
+    P.step_graph = nullptr;
 }
 
 static bd_status validate(const bd_params *p)
@@ -538,6 +542,71 @@ bd_status bd_plan_set_shape(bd_plan *plan, int32_t shape)
         if (st != BD_OK) return st;
     }
     P.tc_split = shape;
+    return BD_OK;
+}
+
+bd_status bd_step_capture(bd_plan *plan, double *R, void *D, const bd_step_opts *opts,
+                          double *DF, double *dS, bd_step_stats *stats, bd_stream stream)
+{
+    if (!plan || !opts) return set_error(BD_ERR_INVALID, "NULL argument");
+    if (opts->n_cheb == 0)
+        return set_error(BD_ERR_INVALID, "adaptive N_Ch synchronises the host: not capturable");
+    if (opts->flags & BD_STEP_MATRIX_FREE)
+        return set_error(BD_ERR_INVALID, "matrix-free steps synchronise the host: not capturable");
+    Plan &P = plan->P;
+    if (P.step_exec) cudaGraphExecDestroy(P.step_exec);
+    if (P.step_graph) cudaGraphDestroy(P.step_graph);
+    P.step_exec = nullptr;
+    P.step_graph = nullptr;
+    bd_step_opts o = *opts;
+    o.flags |= BD_STEP_DEVICE_COUNTER;
+    const int phase_on = P.phase_on, prod_on = P.prod_on;
+    P.phase_on = 0;
+    P.prod_on = 0;
+    (void)stream;
+    // recorded on a private stream (the legacy default stream cannot be
+    // captured; nothing runs during a capture)
+    cudaStream_t s = nullptr;
+    cudaError_t e = cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess) {
+        P.phase_on = phase_on;
+        P.prod_on = prod_on;
+        if (s) cudaStreamDestroy(s);
+        cudaGetLastError();
+        return set_error(BD_ERR_CUDA, "stream capture: %s", cudaGetErrorString(e));
+    }
+    bd_status st = bd_step(plan, R, D, nullptr, &o, DF, dS, stats, (bd_stream)s);
+    cudaGraph_t g = nullptr;
+    e = cudaStreamEndCapture(s, &g);
+    cudaStreamDestroy(s);
+    P.phase_on = phase_on;
+    P.prod_on = prod_on;
+    if (st != BD_OK || e != cudaSuccess || !g) {
+        if (g) cudaGraphDestroy(g);
+        cudaGetLastError();
+        if (st != BD_OK) return st;
+        return set_error(BD_ERR_CUDA, "stream capture of the step: %s", cudaGetErrorString(e));
+    }
+    cudaGraphExec_t x = nullptr;
+    e = cudaGraphInstantiate(&x, g, 0);
+    if (e != cudaSuccess) {
+        cudaGraphDestroy(g);
+        cudaGetLastError();
+        return set_error(BD_ERR_CUDA, "graph instantiation: %s", cudaGetErrorString(e));
+    }
+    P.step_graph = g;
+    P.step_exec = x;
+    return BD_OK;
+}
+
+bd_status bd_step_replay(bd_plan *plan, bd_stream stream)
+{
+    if (!plan) return set_error(BD_ERR_INVALID, "NULL plan");
+    Plan &P = plan->P;
+    if (!P.step_exec) return set_error(BD_ERR_INVALID, "no captured step (bd_step_capture)");
+    cudaError_t e = cudaGraphLaunch(P.step_exec, (cudaStream_t)stream);
+    if (e != cudaSuccess) return set_error(BD_ERR_CUDA, "graph launch: %s", cudaGetErrorString(e));
     return BD_OK;
 }
 

@@ -118,6 +118,8 @@ struct Plan {
     int tc_split;                      // resident CTAs per SM of the tensor-core product (0: 2)
     int tc_maxslots;                   // partial slots per row block (stream-K schedule)
     SymState *sym;                     // symmetric product schedule (mixed plans)
+    cudaGraph_t step_graph;            // a captured bd_step (bd_step_capture)
+    cudaGraphExec_t step_exec;
     int num_sms;                       // SM count of the plan's device
     int64_t scratch_bytes;
     bd_step_stats *d_stats_scratch;

@@ -174,3 +174,42 @@ def test_symmetric_n8000_sampled_rows(bnd):
     for b in (0, 2345, 4095, 7999):
         rows = oracle.build_D_rows(p, R, b, b + 1)
         assert np.max(np.abs(Y3[:, 3 * b:3 * b + 3].T - rows @ X.T)) <= 2e-3 * scale
+
+
+def test_step_capture_replay_matches_direct(bnd):
+    """bd_step_capture / bd_step_replay: one lagged mixed step recorded as a
+    CUDA graph replays the same kernels in the same order as bd_step with the
+    device step counter, so three replays after one direct step land on the
+    same positions, bit for bit, as four direct steps; adaptive N_Ch and an
+    empty replay are refused."""
+    cfg, _ = inputs.preset("c1")
+    p = cfg.params()
+    R0 = inputs.make_chains(cfg)
+    kw = dict(m=4, n_cheb=30, lanczos_iters=40, bounds_mode=1, flags=bnd.BD_STEP_DEVICE_COUNTER)
+    out = []
+    for graph in (False, True):
+        plan = bnd.Plan(p, "mixed_f16", max_rhs=4, max_cheb=64)
+        plan.set_shape(bnd.BD_SHAPE_SYMMETRIC)
+        R = torch.tensor(R0.reshape(-1), device="cuda")
+        D = plan.alloc_D()
+        stats = bnd.new_stats()
+        plan.set_step_counter(100)
+        plan.step(R, D, None, stats=stats, **kw)
+        if graph:
+            with pytest.raises(bnd.BDError):
+                plan.step_replay()
+            with pytest.raises(bnd.BDError):
+                plan.step_capture(R, D, m=4, n_cheb=0, bounds_mode=1, stats=stats)
+            plan.step_capture(R, D, stats=stats, **kw)
+            for _ in range(3):
+                plan.step_replay()
+        else:
+            for _ in range(3):
+                plan.step(R, D, None, stats=stats, **kw)
+        torch.cuda.synchronize()
+        st = bnd.read_stats(stats)
+        assert st["status"] == 0 and st["accepted"] == 1
+        out.append(R.cpu().numpy())
+        plan.close()
+    assert np.array_equal(out[0], out[1])
+    assert np.max(np.abs(out[0] - R0.reshape(-1))) > 0
