@@ -360,7 +360,12 @@ bd_status bd_chebyshev_backward(bd_plan *plan, const double *R, const void *D,
  *   3     the symmetric kernel: only the 128 x 128 tiles on and above the
  *         diagonal are read, each serving D_IJ X_J and D_IJ^T X_I (D is
  *         symmetric, Eq. DF), with a second kernel summing the partials in a
- *         fixed order and running the epilogue.
+ *         fixed order and running the epilogue.  With this shape set, the
+ *         assembly (bd_build_D, bd_step) writes D32 and D16 only on and above
+ *         the diagonal 128 x 128 tiles (the diagonal tiles whole) and the
+ *         FP64-residual refinement of D.F reads that half too; the rest of
+ *         the lower triangle is left as it was.  Set the shape before
+ *         assembling the D that a product will read.
  * All shapes give the same product up to FP32 summation order.            */
 #define BD_SHAPE_SYMMETRIC 3
 

@@ -19,6 +19,7 @@
 #include "recip_tc.cuh"
 #include "kspace.cuh"
 #include "spectral.cuh"
+#include "tc_gemm.cuh"
 
 namespace bd {
 
@@ -440,7 +441,8 @@ k_build_D(const double *__restrict__ pw, const float *__restrict__ pw32, int n,
           const __grid_constant__ EwaldT<T> c, const EwaldCoef *__restrict__ ewc,
           const T *__restrict__ tab, int tab_i0, int ntab, const T *__restrict__ km, int nk,
           const T *__restrict__ cs, const T *__restrict__ sn, int overlap_corr, float rc,
-          T *__restrict__ D, void *__restrict__ D16, int is_bf16, long ld, int recip_in_D)
+          T *__restrict__ D, void *__restrict__ D16, int is_bf16, long ld, int recip_in_D,
+          int upper_only)
 {
     __shared__ T tile[TS * TSP];
     __shared__ T s_tr[4][KC][TB];      // cos nu, sin nu, cos mu, sin mu for one k chunk
@@ -517,7 +519,11 @@ k_build_D(const double *__restrict__ pw, const float *__restrict__ pw32, int n,
             for (int k = 0; k < 4; k++)
                 if (c0 + cc + k < n3) Store<T>::put(D, D16, idx + k, v[k], is_bf16);
     }
-    if (I != J) {
+    // the mirror block (rows c0.., columns r0..) is skipped for the symmetric
+    // product's D when it lies wholly below the diagonal 128 x 128 tiles (those
+    // tiles are read whole; the rest of the lower triangle is never read)
+    const bool mirror = I != J && !(upper_only && c0 / 128 > (r0 + TS - 1) / 128);
+    if (mirror) {
         for (int e = threadIdx.x; e < TS * NQ; e += TB * TB) {
             // mirror: row c0 + r, columns r0 + cc .. r0 + cc + 3 = tile[cc + k][r]
             const int r = e / NQ, cc = 4 * (e - (e / NQ) * NQ);
@@ -631,7 +637,7 @@ void launch_build_D_f64(Plan &P, const double *R, double *D, cudaStream_t s)
     k_build_D<double><<<(unsigned)nb, TB * TB, 0, s>>>(
         P.d_pw64, P.d_pw32, P.n, P.h_ew64, P.d_ewc, P.d_tab, P.tab_i0, P.ntab, P.d_km64, P.nk,
         P.d_cos, P.d_sin, P.p.overlap_corr,
-        (float)P.p.r_c, D, nullptr, 0, P.ld, 0);
+        (float)P.p.r_c, D, nullptr, 0, P.ld, 0, 0);
     count_launches(1);
 }
 
@@ -650,7 +656,7 @@ bd_status launch_build_D_f32(Plan &P, const double *R, float *D32, void *D16, in
     k_build_D<float><<<(unsigned)nb, TB * TB, 0, s>>>(
         P.d_pw64, P.d_pw32, P.n, P.h_ew32, P.d_ewc, P.d_tab32, P.tab32_i0, P.ntab32, P.d_km32, nk,
         P.d_cos32, P.d_sin32, P.p.overlap_corr,
-        (float)P.p.r_c, D32, D16, is_bf16, P.ld, P.recip_tc);
+        (float)P.p.r_c, D32, D16, is_bf16, P.ld, P.recip_tc, P.tc_split == kSymShape ? 1 : 0);
     count_launches(1);
     return BD_OK;
 }

@@ -513,6 +513,173 @@ k_sym_reduce(Geo g, const float *__restrict__ part, int n3, tc::Epi e)
     else ((__half *)e.X16next)[xo] = __float2half_rn(sv);
 }
 
+// ---------------------------------------------------------------------------
+// FP64-residual refinement of one column from the FP32 D on and above the
+// diagonal (the symmetric shape's D carries no lower triangle): y = D x with
+// x = xh + xl split into FP32 words and every product d xh formed exactly as
+// the pair (p, fma(d, xh, -p)) plus d xl, summed as double-float (TwoSum).
+// One CTA per 128 x 128 tile (I, J), I <= J, each thread an 8 x 8 block;
+// a tile gives the row partial D_IJ x_J and, off the diagonal, the
+// column partial D_IJ^T x_I, both in FP32 pairs; a second kernel sums a row
+// block's partials in a fixed order (its row partials J = X .. T-1, then its
+// column partials I = 0 .. X-1).
+struct DF {
+    float s, c;
+};
+
+__device__ __forceinline__ void df_add(DF &a, float p, float e)
+{
+    const float t = a.s + p, z = t - a.s;
+    a.c += ((a.s - (t - z)) + (p - z)) + e;
+    a.s = t;
+}
+
+__device__ __forceinline__ void df_madd(DF &a, float d, float xh, float xl)
+{
+    const float p = d * xh;
+    const float e = fmaf(d, xl, fmaf(d, xh, -p));
+    df_add(a, p, e);
+}
+
+__device__ __forceinline__ void df_merge(DF &a, DF b)
+{
+    df_add(a, b.s, b.c);
+}
+
+__host__ __device__ inline void tile_of_index(long t, int *I, int *J)
+{
+    int j = (int)((sqrtf(8.0f * (float)t + 1.0f) - 1.0f) * 0.5f);
+    while ((long)j * (j + 1) / 2 > t) j--;
+    while ((long)(j + 1) * (j + 2) / 2 <= t) j++;
+    *J = j;
+    *I = (int)(t - (long)j * (j + 1) / 2);
+}
+
+__global__ void __launch_bounds__(256)
+k_sym_refine_tiles(const float *__restrict__ D32, long ld, int n3, const float *__restrict__ xs,
+                   float2 *__restrict__ part)
+{
+    // thread (tr, tc) owns rows 8 tr .. 8 tr + 7 and columns 8 tc .. 8 tc + 7
+    // of the tile; its row and column sums stay in registers, then 16 partials
+    // per row (and per column) are combined in shared memory in a fixed order
+    __shared__ float2 s_xi[BM], s_xj[BM];
+    __shared__ float2 s_red[16][BM + 1];
+    const long t = blockIdx.x;
+    int I, J;
+    tile_of_index(t, &I, &J);
+    const int tid = threadIdx.x, tr = tid >> 4, tc = tid & 15;
+    const float *xh = xs, *xl = xs + n3;
+    if (tid < BM) {
+        const long gi = (long)I * BM + tid, gj = (long)J * BM + tid;
+        s_xi[tid] = gi < n3 ? make_float2(xh[gi], xl[gi]) : make_float2(0.f, 0.f);
+        s_xj[tid] = gj < n3 ? make_float2(xh[gj], xl[gj]) : make_float2(0.f, 0.f);
+    }
+    __syncthreads();
+    const bool off = I != J;
+    const long c0 = (long)J * BM + 8 * tc;
+    float2 xj[8];
+#pragma unroll
+    for (int k = 0; k < 8; k++) xj[k] = s_xj[8 * tc + k];
+    DF rs[8], cs[8];
+#pragma unroll
+    for (int k = 0; k < 8; k++) {
+        rs[k] = DF{0.f, 0.f};
+        cs[k] = DF{0.f, 0.f};
+    }
+#pragma unroll
+    for (int i = 0; i < 8; i++) {
+        const int r = 8 * tr + i;
+        const long gr = (long)I * BM + r;
+        float d[8];
+#pragma unroll
+        for (int k = 0; k < 8; k++) d[k] = 0.f;
+        if (gr < n3) {
+            const float *src = D32 + gr * ld + c0;
+            if (c0 + 7 < n3) {
+                const float4 v0 = __ldcs((const float4 *)src), v1 = __ldcs((const float4 *)(src + 4));
+                d[0] = v0.x; d[1] = v0.y; d[2] = v0.z; d[3] = v0.w;
+                d[4] = v1.x; d[5] = v1.y; d[6] = v1.z; d[7] = v1.w;
+            } else {
+#pragma unroll
+                for (int k = 0; k < 8; k++)
+                    if (c0 + k < n3) d[k] = src[k];
+            }
+        }
+#pragma unroll
+        for (int k = 0; k < 8; k++) df_madd(rs[i], d[k], xj[k].x, xj[k].y);
+        if (off) {
+            const float2 xi = s_xi[r];
+#pragma unroll
+            for (int k = 0; k < 8; k++) df_madd(cs[k], d[k], xi.x, xi.y);
+        }
+    }
+    // row sums: 16 column groups per row
+#pragma unroll
+    for (int i = 0; i < 8; i++) s_red[tc][8 * tr + i] = make_float2(rs[i].s, rs[i].c);
+    __syncthreads();
+    if (tid < BM) {
+        DF a = {s_red[0][tid].x, s_red[0][tid].y};
+        for (int q = 1; q < 16; q++) df_merge(a, DF{s_red[q][tid].x, s_red[q][tid].y});
+        part[(t * 2) * BM + tid] = make_float2(a.s, a.c);
+    }
+    if (!off) return;
+    __syncthreads();
+    // column sums: 16 row groups per column
+#pragma unroll
+    for (int k = 0; k < 8; k++) s_red[tr][8 * tc + k] = make_float2(cs[k].s, cs[k].c);
+    __syncthreads();
+    if (tid < BM) {
+        DF a = {s_red[0][tid].x, s_red[0][tid].y};
+        for (int q = 1; q < 16; q++) df_merge(a, DF{s_red[q][tid].x, s_red[q][tid].y});
+        part[(t * 2 + 1) * BM + tid] = make_float2(a.s, a.c);
+    }
+}
+
+// y[row] += (D x)[row] - y[row] for the 128-row block X, the row block's
+// partials in a fixed order (deterministic)
+__global__ void __launch_bounds__(BM)
+k_sym_refine_reduce(const float2 *__restrict__ part, int T, int n3, double *__restrict__ y)
+{
+    const int X = blockIdx.x, r = threadIdx.x;
+    const long row = (long)X * BM + r;
+    DF a = {0.f, 0.f};
+    // row partials of tiles (X, J), J = X .. T-1: tile index J (J + 1) / 2 + X
+    int J = X;
+    for (; J + 4 <= T; J += 4) {
+        float2 v[4];
+#pragma unroll
+        for (int h = 0; h < 4; h++) {
+            const long tt = (long)(J + h) * (J + h + 1) / 2 + X;
+            v[h] = __ldcg(part + (tt * 2) * BM + r);
+        }
+#pragma unroll
+        for (int h = 0; h < 4; h++) df_merge(a, DF{v[h].x, v[h].y});
+    }
+    for (; J < T; J++) {
+        const long tt = (long)J * (J + 1) / 2 + X;
+        const float2 v = __ldcg(part + (tt * 2) * BM + r);
+        df_merge(a, DF{v.x, v.y});
+    }
+    // column partials of tiles (I, X), I = 0 .. X-1: tile index X (X + 1) / 2 + I
+    const long base = (long)X * (X + 1) / 2;
+    int I = 0;
+    for (; I + 4 <= X; I += 4) {
+        float2 v[4];
+#pragma unroll
+        for (int h = 0; h < 4; h++) v[h] = __ldcg(part + ((base + I + h) * 2 + 1) * BM + r);
+#pragma unroll
+        for (int h = 0; h < 4; h++) df_merge(a, DF{v[h].x, v[h].y});
+    }
+    for (; I < X; I++) {
+        const float2 v = __ldcg(part + ((base + I) * 2 + 1) * BM + r);
+        df_merge(a, DF{v.x, v.y});
+    }
+    if (row >= n3) return;
+    const double acc = (double)a.s + (double)a.c;
+    const double y0 = y[row];
+    y[row] = y0 + (acc - y0);
+}
+
 }  // namespace sy
 
 // ---------------------------------------------------------------------------
@@ -524,6 +691,7 @@ struct SymState {
     int *d_jbase;
     int *d_xstart, *d_xlist;
     float *d_part;
+    float2 *d_rpart;        // refinement partials [tiles][2][128]
 };
 
 static bd_status sym_oom(cudaError_t e)
@@ -591,7 +759,9 @@ bd_status sym_plan_init(Plan &P)
     if (e == cudaSuccess) e = cudaMalloc((void **)&S->d_xstart, sizeof(int) * (T + 1));
     if (e == cudaSuccess) e = cudaMalloc((void **)&S->d_xlist, sizeof(int) * (xlist.size() + 1));
     if (e == cudaSuccess) e = cudaMalloc((void **)&S->d_part, sizeof(float) * pool);
+    if (e == cudaSuccess) e = cudaMalloc((void **)&S->d_rpart, sizeof(float2) * 2 * BM * U);
     if (e != cudaSuccess) return sym_oom(e);
+    P.scratch_bytes += (int64_t)(sizeof(float2) * 2 * BM * U);
     P.scratch_bytes += (int64_t)(sizeof(long) * (nb + 1) + sizeof(int) * (nb + 1 + T + 1 + xlist.size()) +
                                  sizeof(float) * pool);
     cudaMemcpy(S->d_boff, boff.data(), sizeof(long) * (nb + 1), cudaMemcpyHostToDevice);
@@ -616,11 +786,22 @@ void sym_plan_free(Plan &P)
 {
     SymState *S = P.sym;
     if (!S) return;
-    void *ptrs[] = {S->d_boff, S->d_jbase, S->d_xstart, S->d_xlist, S->d_part};
+    void *ptrs[] = {S->d_boff, S->d_jbase, S->d_xstart, S->d_xlist, S->d_part, S->d_rpart};
     for (void *q : ptrs)
         if (q) cudaFree(q);
     delete S;
     P.sym = nullptr;
+}
+
+bd_status sym_refine(Plan &P, const float *D32, const float *xs, double *y, cudaStream_t s)
+{
+    bd_status st = sym_plan_init(P);
+    if (st != BD_OK) return st;
+    const SymState *S = P.sym;
+    sy::k_sym_refine_tiles<<<(unsigned)S->geo.U, 256, 0, s>>>(D32, P.ld, P.n3, xs, S->d_rpart);
+    sy::k_sym_refine_reduce<<<S->geo.T, sy::BM, 0, s>>>(S->d_rpart, S->geo.T, P.n3, y);
+    count_launches(2);
+    return check_launch("symmetric refinement");
 }
 
 bd_status sym_launch(Plan &P, const CUtensorMap &mapD, const CUtensorMap &mapX, int bn,

@@ -774,6 +774,15 @@ void launch_refine_f32(Plan &P, const float *D32, const double *X, int m, double
                        cudaStream_t s)
 {
     long threads = (long)P.n3 * 32;
+    if (P.tc_split == kSymShape) {
+        // the symmetric shape's D holds the tiles on and above the diagonal only
+        for (int j = 0; j < m; j++) {
+            k_split_x<<<(P.n3 + 255) / 256, 256, 0, s>>>(X + (long)j * P.n3, P.n3, P.d_xsplit);
+            count_launches(1);
+            sym_refine(P, D32, P.d_xsplit, Y + (long)j * P.n3, s);
+        }
+        return;
+    }
     for (int j = 0; j < m; j++) {
         k_split_x<<<(P.n3 + 255) / 256, 256, 0, s>>>(X + (long)j * P.n3, P.n3, P.d_xsplit);
         count_launches(1);
