@@ -41,9 +41,10 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--precision", default="both",
-                    choices=["both", "fp64", "mixed_f16", "mixed_bf16"],
-                    help="both: FP64 and mixed (IEEE-half) on the same system; the headline "
-                         "value is the mixed step, the FP64 step is reported beside it")
+                    choices=["both", "fp64", "fp64_df", "mixed_f16", "mixed_bf16"],
+                    help="both: FP64 (FP64 multiply-adds and double-float on the FP32 "
+                         "pipe) and mixed (IEEE-half) on the same system; the headline "
+                         "value is the mixed step, the FP64 steps are reported beside it")
     ap.add_argument("--nch", type=int, default=40)
     ap.add_argument("--m", type=int, default=16)
     ap.add_argument("--alpha-factor", default="auto",
@@ -233,8 +234,9 @@ def measured_peaks():
     return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}, "fallback"
 
 
-def probe_fp64_peak():
-    """FP64 DFMA throughput of this GPU (probe kernel), flop/s."""
+def probe_fp64_peak(which=0):
+    """FP64 DFMA (which=0) or FP32 FFMA (which=2) throughput of this GPU
+    (probe kernel), flop/s."""
     import ctypes
     from paper_1203_6208_gb300 import build
     L = ctypes.CDLL(build.PROBE_LIB)
@@ -243,7 +245,7 @@ def probe_fp64_peak():
     sms = 152
     best = 0.0
     for blocks_per_sm in (4, 8):
-        best = max(best, L.bd_probe_peak(0, 4096, sms * blocks_per_sm, 256))
+        best = max(best, L.bd_probe_peak(which, 4096, sms * blocks_per_sm, 256))
     return best
 
 
@@ -256,6 +258,7 @@ def kernel_source_hash(path, name):
 
 
 KERNELS = {"fp64": ("paper_1203_6208_gb300/csrc/dense_f64.cu", "k_gemm_f64"),
+           "fp64_df": ("paper_1203_6208_gb300/csrc/dense_f64.cu", "k_gemm_df"),
            "mixed": ("paper_1203_6208_gb300/csrc/tc_gemm.cu", "k_tc_gemm"),
            "sym": ("paper_1203_6208_gb300/csrc/sym_gemm.cu", "k_sym_gemm")}
 
@@ -294,19 +297,22 @@ def measure(args, precision, p, R0, rank, ws):
     """Warm up, then time exactly args.steps bd_step calls on the device."""
     import torch
     from paper_1203_6208_gb300 import binding as bnd
-    plan = bnd.Plan(p, precision, max_rhs=args.m, max_cheb=max(args.nch, 2))
+    is64 = precision.startswith("fp64")
+    plan = bnd.Plan(p, "fp64" if is64 else precision, max_rhs=args.m, max_cheb=max(args.nch, 2))
+    if precision == "fp64_df":
+        plan.set_shape(bnd.BD_SHAPE_F64_DOUBLE_FLOAT)
     R = torch.tensor(R0, device="cuda")
     D = plan.alloc_D()
     stats = bnd.new_stats()
     # mixed steps take their bounds from the previous step's Lanczos recurrence,
     # which rides as one extra column of the products (no extra pass over D)
-    bounds_mode = 1 if (precision != "fp64" and args.bounds == "lagged") else 0
+    bounds_mode = 1 if (not is64 and args.bounds == "lagged") else 0
     kw = dict(m=args.m, n_cheb=args.nch, lanczos_iters=args.lanczos, bound_safety=0.05,
               dmin_fraction=0.5, seed=4242 + rank, stats=stats, bounds_mode=bounds_mode)
     shape = None
     for w in range(args.warmup):
         plan.step(R, D, None, step_index=w, **kw)
-        if w == 0 and precision != "fp64":
+        if w == 0 and not is64:
             # launch shape of the tensor-core product, timed on this D (or fixed)
             if args.shape != "auto":
                 plan.set_shape(int(args.shape))
@@ -344,7 +350,7 @@ def measure(args, precision, p, R0, rank, ws):
     plan.set_phase_events(None)
     ms = e0.elapsed_time(e1)
     direct_ms = ms
-    graph = precision != "fp64" and not args.no_graph
+    graph = not is64 and not args.no_graph
     if graph:
         # the same step recorded once as a CUDA graph (noise from the device
         # step counter) and replayed: no host launch gaps between its kernels
@@ -390,6 +396,22 @@ def measure(args, precision, p, R0, rank, ws):
                 "peak_source": "FP64 DFMA probe (probe/peaks.cu) on this GPU (measured)",
                 "traffic": traffic_per_launch("fp64"),
                 "algorithmic_per_launch": f"2*(3N)^2*m = {flops:.3e} flop",
+                "launch_ms": cheb_launch_ms, "launches_timed": prod_n}
+    elif precision == "fp64_df":
+        # 12 FP32 lane instructions per multiply-add (exact hi x hi product,
+        # two cross terms, two-sum into the pair); peak = FFMA lanes x clock
+        ins = 12.0 * n3 * n3 * args.m
+        lane_peak = probe_fp64_peak(2) / 2.0
+        achieved = ins / (cheb_launch_ms * 1e-3) / 1e12
+        roof = {"bound": "alu", "kernel": "k_gemm_df<16,cheb>", "achieved": achieved,
+                "peak": lane_peak / 1e12, "unit": "T FP32 lane-instructions/s",
+                "frac": achieved * 1e12 / lane_peak,
+                "peak_source": "FP32 FFMA probe (probe/peaks.cu) on this GPU (measured), "
+                               "one FFMA = one lane instruction",
+                "traffic": traffic_per_launch("fp64_df"),
+                "algorithmic_per_launch": f"12*(3N)^2*m = {ins:.3e} FP32 lane instructions "
+                                          f"(2*(3N)^2*m = {2.0 * n3 * n3 * args.m:.3e} FP64-"
+                                          f"equivalent flop, {2.0 * n3 * n3 * args.m / (cheb_launch_ms * 1e-3) / 1e12:.3f} TFLOP/s)",
                 "launch_ms": cheb_launch_ms, "launches_timed": prod_n}
     else:
         lag = args.bounds == "lagged"
@@ -459,7 +481,8 @@ def measure(args, precision, p, R0, rank, ws):
 
 
 def dtype_of(precision):
-    return {"fp64": "f64", "mixed_f16": "f16+f32+f64", "mixed_bf16": "bf16+f32+f64"}[precision]
+    return {"fp64": "f64", "fp64_df": "f64 (double-float f32 products)", "mixed_f16": "f16+f32+f64",
+            "mixed_bf16": "bf16+f32+f64"}[precision]
 
 
 def run_ours(args):
@@ -473,14 +496,17 @@ def run_ours(args):
         torch.cuda.set_device(0)
     from paper_1203_6208_gb300 import build, inputs
     build.build()
-    precs = ["fp64", "mixed_f16"] if args.precision == "both" else [args.precision]
+    precs = ["fp64", "fp64_df", "mixed_f16"] if args.precision == "both" else [args.precision]
     cfg, p1 = system(1.0, args.chains)
     R0 = inputs.make_chains(cfg, seed=cfg.seed + 17 * rank)
     results, alphas = {}, {}
     for prec in precs:
-        Rt = torch.tensor(R0, device="cuda")
-        f, sweep = pick_alpha(args, p1, Rt, prec)
-        del Rt
+        if prec == "fp64_df" and "fp64" in alphas:
+            f, sweep = alphas["fp64"][0], "as fp64 (the same FP64 assembly)"
+        else:
+            Rt = torch.tensor(R0, device="cuda")
+            f, sweep = pick_alpha(args, p1, Rt, "fp64" if prec == "fp64_df" else prec)
+            del Rt
         _, p = system(f, args.chains)
         alphas[prec] = (f, sweep, p)
         results[prec] = measure(args, prec, p, R0, rank, ws)
@@ -499,21 +525,27 @@ def run_ours(args):
                        "alpha": p["alpha"], "alpha_factor": f, "alpha_sweep_ms": sweep,
                        "r_c": p["rc"], "n2max": p["n2max"], "n_kvec_half": r["n_kvec_half"],
                        "m": args.m, "n_cheb": args.nch, "lanczos_iters": args.lanczos,
-                       "bounds": args.bounds if head != "fp64" else "fresh",
+                       "bounds": args.bounds if not head.startswith("fp64") else "fresh",
                        "l2": "inputs larger than L2 (D alone is %.2f GB)" % r["d_gb"],
                        "parallelism": "replicas" if ws > 1 else "single",
                        "product_shape": r["product_shape"], "launch": r["launch"]},
             "direct_ms_per_step": r["direct_ms_per_step"],
             "phases_ms": r["phases_ms"], "step_stats": r["step_stats"], "roofline": r["roofline"],
             "gpu_launches": r["gpu_launches"], "clocks": r["clocks"], "e2e": r["e2e"]}
+    for key in ("fp64", "fp64_df"):
+        if key not in results or key == head:
+            continue
+        q = results[key]
+        fq, sq, pq = alphas[key]
+        line["fp64" if key == "fp64" else "fp64_double_float"] = {
+            "value": q["value"], "unit": "steps/s", "ms_per_step": q["ms_per_step"],
+            "products": "FP64 multiply-adds" if key == "fp64" else
+                        "double-float on the FP32 pipe (launch shape 4)",
+            "alpha_factor": fq, "alpha_sweep_ms": sq, "phases_ms": q["phases_ms"],
+            "step_stats": q["step_stats"], "roofline": q["roofline"],
+            "gpu_launches": q["gpu_launches"], "clocks": q["clocks"], "e2e": q["e2e"]}
     if "fp64" in results and head != "fp64":
-        q = results["fp64"]
-        fq, sq, pq = alphas["fp64"]
-        line["fp64"] = {"value": q["value"], "unit": "steps/s", "ms_per_step": q["ms_per_step"],
-                        "alpha_factor": fq, "alpha_sweep_ms": sq, "phases_ms": q["phases_ms"],
-                        "step_stats": q["step_stats"], "roofline": q["roofline"],
-                        "gpu_launches": q["gpu_launches"], "clocks": q["clocks"], "e2e": q["e2e"]}
-        line["mixed_speedup_over_fp64"] = r["value"] / q["value"]
+        line["mixed_speedup_over_fp64"] = r["value"] / results["fp64"]["value"]
     if ws == 1 and not args.no_cpu_baseline:
         import oracle
         oracle.build()

@@ -366,8 +366,26 @@ bd_status bd_chebyshev_backward(bd_plan *plan, const double *R, const void *D,
  *         FP64-residual refinement of D.F reads that half too; the rest of
  *         the lower triangle is left as it was.  Set the shape before
  *         assembling the D that a product will read.
- * All shapes give the same product up to FP32 summation order.            */
+ * All shapes give the same product up to FP32 summation order.
+ * Launch shapes of the FP64 plans' product Y = D X:
+ *   0     (default) FP64 multiply-adds;
+ *   4     double-float on the FP32 pipe: each FP64 entry of D and X is split
+ *         into two FP32 words (hi = the leading 24 significant bits, lo the
+ *         next 24), each product d x is formed from hi*hi exactly (FMA error
+ *         term) plus the cross terms hi*lo + lo*hi, and the products are
+ *         summed as an unevaluated FP32 pair (two-sum).  The result agrees
+ *         with the FP64 product to about 1e-13 of sum_k |D_ik x_k| (FP32
+ *         pair precision, 2^-46, times the growth of a 3N-term sum) and is
+ *         returned in FP64.  D, X and the products d x must lie in the
+ *         FP32 range: D entries below 2^-97 in magnitude count as zero,
+ *         entries of 2^128 or more overflow to an infinity, products below
+ *         about 2^-100 lose bits.  The D of a physical system in the plan's
+ *         units has entries of order one.  On a GPU whose FP64 pipe is a
+ *         small fraction of FP32 this is the faster shape.
+ * The shapes of one precision are rejected on a plan of the other
+ * (BD_ERR_INVALID for 4 on a mixed plan; an FP64 plan takes 1..3 as 0).   */
 #define BD_SHAPE_SYMMETRIC 3
+#define BD_SHAPE_F64_DOUBLE_FLOAT 4
 
 /* Autotuner: for a mixed plan, times the tensor-core product on D (its
  * contents do not matter) in shapes 1, 2 and 3 and keeps the fastest for all
@@ -376,10 +394,11 @@ bd_status bd_chebyshev_backward(bd_plan *plan, const double *R, const void *D,
 bd_status bd_plan_autotune(bd_plan *plan, void *D, int32_t *split_out, float *ms_out,
                            bd_stream stream);
 
-/* Set the launch shape (0..3, above) of the plan's later products without
- * timing.  Shape 3 allocates its schedule and partial buffers on first use
- * (synchronous, BD_ERR_OOM if they do not fit).  BD_ERR_INVALID outside 0..3;
- * FP64 plans accept and ignore it.                                        */
+/* Set the launch shape (0..4, above) of the plan's later products without
+ * timing.  Shape 3 allocates its schedule and partial buffers on first use,
+ * shape 4 its split operand (64 x 3N floats), both synchronous and
+ * BD_ERR_OOM if they do not fit.  BD_ERR_INVALID outside 0..4 and for 4 on a
+ * mixed plan; FP64 plans take 1..3 as 0 (FP64 multiply-adds).             */
 bd_status bd_plan_set_shape(bd_plan *plan, int32_t shape);
 
 /* Set the plan's device step counter used by BD_STEP_DEVICE_COUNTER (stream-

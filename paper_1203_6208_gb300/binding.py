@@ -27,6 +27,7 @@ BD_APPLY_REFINE = 1
 BD_STEP_DEVICE_COUNTER = 1
 BD_STEP_MATRIX_FREE = 2
 BD_SHAPE_SYMMETRIC = 3
+BD_SHAPE_F64_DOUBLE_FLOAT = 4
 BOUNDS_MODES = {"fresh": 0, "lagged": 1, "fixman_dilute": 2, "fixman_semidilute": 3}
 
 EXPORTS = ["bd_plan_create", "bd_plan_destroy", "bd_plan_query", "bd_forces", "bd_build_D",
@@ -293,8 +294,10 @@ class Plan:
         _check(load().bd_plan_set_step_counter(self._h, int(value), _stream(stream)))
 
     def set_shape(self, shape: int):
-        """Launch shape of the mixed product: 1/2 stream-K CTAs per SM, 3 the
-        symmetric kernel over the upper triangle (BD_SHAPE_SYMMETRIC)."""
+        """Launch shape of the product.  Mixed plans: 1/2 stream-K CTAs per
+        SM, 3 the symmetric kernel over the upper triangle (BD_SHAPE_SYMMETRIC).
+        FP64 plans: 0 FP64 multiply-adds, 4 double-float on the FP32 pipe
+        (BD_SHAPE_F64_DOUBLE_FLOAT)."""
         _check(load().bd_plan_set_shape(self._h, int(shape)))
 
     def autotune(self, D, stream=None):

@@ -77,7 +77,7 @@ static void free_plan(Plan &P)
                     P.d_coef, P.d_wdw, P.d_red, P.d_redpart, P.d_bounds, P.d_status, P.d_lq[0], P.d_lq[1],
                     P.d_lq[2], P.d_lab, P.d_x16, P.d_xscale, P.d_part, P.d_counters,
                     P.d_stats_scratch, P.d_y32, P.d_lag_bounds, P.d_step_ctr, P.d_vhist, P.d_xhist, P.d_ubuf[0], P.d_ubuf[1],
-                    P.d_ubuf[2], P.d_ubuf[3], P.d_Uh, P.d_Ul, P.d_rtiles, P.d_kbasis, P.d_lanpart, P.d_mom, P.d_sfac, P.d_mfW, P.d_mfpart};
+                    P.d_ubuf[2], P.d_ubuf[3], P.d_xdf, P.d_Uh, P.d_Ul, P.d_rtiles, P.d_kbasis, P.d_lanpart, P.d_mom, P.d_sfac, P.d_mfW, P.d_mfpart};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     if (P.h_est) cudaFreeHost(P.h_est);
@@ -534,9 +534,18 @@ bd_status bd_plan_autotune(bd_plan *plan, void *D, int32_t *split_out, float *ms
 bd_status bd_plan_set_shape(bd_plan *plan, int32_t shape)
 {
     if (!plan) return set_error(BD_ERR_INVALID, "NULL plan");
-    if (shape < 0 || shape > kSymShape) return set_error(BD_ERR_INVALID, "shape %d outside 0..3", shape);
+    if (shape < 0 || shape > kF64DoubleFloat) return set_error(BD_ERR_INVALID, "shape %d outside 0..4", shape);
     Plan &P = plan->P;
-    if (!is_mixed(P)) return BD_OK;
+    if (!is_mixed(P)) {
+        // FP64 plans: 4 selects the double-float products, anything else DFMA
+        if (shape == kF64DoubleFloat && !P.d_xdf) {
+            bd_status st = dmalloc(P, &P.d_xdf, (size_t)2 * kMaxRhs * P.n3);   // a step's products carry up to kMaxRhs columns
+            if (st != BD_OK) return st;
+        }
+        P.tc_split = shape == kF64DoubleFloat ? shape : 0;
+        return BD_OK;
+    }
+    if (shape == kF64DoubleFloat) return set_error(BD_ERR_INVALID, "shape 4 is for FP64 plans");
     if (shape == kSymShape) {
         bd_status st = sym_plan_init(P);
         if (st != BD_OK) return st;

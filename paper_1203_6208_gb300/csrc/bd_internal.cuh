@@ -118,6 +118,7 @@ struct Plan {
     int tc_split;                      // resident CTAs per SM of the tensor-core product (0: 2)
     int tc_maxslots;                   // partial slots per row block (stream-K schedule)
     SymState *sym;                     // symmetric product schedule (mixed plans)
+    float *d_xdf;                      // FP64 plans, shape 4: split operand [2][kMaxRhs][3N]
     cudaGraph_t step_graph;            // a captured bd_step (bd_step_capture)
     cudaGraphExec_t step_exec;
     int num_sms;                       // SM count of the plan's device
@@ -184,6 +185,9 @@ bd_status launch_apply_matfree(Plan &P, const double *X, int m, double *Y, cudaS
 bd_status matfree_product(Plan &P, const double *X, int m, double *Y, cudaStream_t s);
 
 // dense_f64.cu : Y = D X (FP64), epilogue variants
+// FP64 plans: launch shape of the double-float products on the FP32 pipe
+constexpr int kF64DoubleFloat = 4;
+
 struct ChebEpi {
     const double *coef;       // device coefficients
     const double *bounds;     // device {dmin, dmax}
