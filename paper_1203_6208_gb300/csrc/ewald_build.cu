@@ -435,8 +435,10 @@ __device__ __forceinline__ void pair_real(const double *__restrict__ pw,
 
 constexpr int KC = 64;                 // k-vectors per shared-memory chunk
 
+// FP32: 48 registers and 5 CTAs per SM (issue-bound; 4 CTAs took 6 % longer, 6 no
+// better); FP64: 4 CTAs (fewer registers spill)
 template <typename T>
-__global__ void __launch_bounds__(TB *TB, 4)
+__global__ void __launch_bounds__(TB *TB, sizeof(T) == 4 ? 5 : 4)
 k_build_D(const double *__restrict__ pw, const float *__restrict__ pw32, int n,
           const __grid_constant__ EwaldT<T> c, const EwaldCoef *__restrict__ ewc,
           const T *__restrict__ tab, int tab_i0, int ntab, const T *__restrict__ km, int nk,

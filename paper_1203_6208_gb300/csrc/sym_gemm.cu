@@ -555,7 +555,7 @@ __host__ __device__ inline void tile_of_index(long t, int *I, int *J)
     *I = (int)(t - (long)j * (j + 1) / 2);
 }
 
-__global__ void __launch_bounds__(256)
+__global__ void __launch_bounds__(256, 4)
 k_sym_refine_tiles(const float *__restrict__ D32, long ld, int n3, const float *__restrict__ xs,
                    float2 *__restrict__ part)
 {
