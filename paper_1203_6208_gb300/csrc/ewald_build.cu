@@ -175,8 +175,8 @@ __global__ void k_kvec_m(const KVec *kv, int nk, double *m64, float *m32)
     }
 }
 
-// cos/sin(k_t . r_nu) per bead and half-space k (FP64; FP32 copies for the
-// mixed build).  The pair factor cos(k.(r_nu - r_mu)) is then
+// cos/sin(k_t . r_nu) per bead and half-space k (FP64 plans; FP32 copies if
+// cs32 is given).  The pair factor cos(k.(r_nu - r_mu)) is then
 // c_nu c_mu + s_nu s_mu.
 __global__ void k_trig(const double *R, int n, const KVec *kv, int nk, double *cs, double *sn,
                        float *cs32, float *sn32)
@@ -611,11 +611,38 @@ void launch_kvec_table(Plan &P, cudaStream_t s)
     free(hn);
 }
 
+// FP32 tables only (mixed plans): the phase k.r is formed in FP64 and reduced
+// to the fraction f of a turn, f = k.r / 2 pi - rint(k.r / 2 pi) (exact
+// subtraction); 2 f is split into FP32 words x + x_lo and sin, cos of pi x
+// come from the FP32 sincospif, corrected to first order in x_lo (|pi x_lo|
+// <= 2e-7, the dropped term ~1e-14).  Seven FP64 instructions per entry
+// instead of an FP64 sincos on this GPU's slow FP64 pipe.
+__global__ void k_trig32(const double *R, int n, const KVec *kv, int nk, float *cs32, float *sn32)
+{
+    int nu = blockIdx.x * blockDim.x + threadIdx.x;
+    int t = blockIdx.y;
+    if (nu >= n || t >= nk) return;
+    constexpr double kInv2Pi = 0.15915494309189533577;
+    const double ph = kv[t].k[0] * R[3 * nu] + kv[t].k[1] * R[3 * nu + 1] + kv[t].k[2] * R[3 * nu + 2];
+    const double f = ph * kInv2Pi;
+    const double tf = 2.0 * (f - rint(f));                 // in [-1, 1]
+    const float x = (float)tf;
+    const float xl = (float)(tf - (double)x);
+    float sp, cp;
+    sincospif(x, &sp, &cp);
+    const float d = 3.14159265358979f * xl;
+    cs32[(size_t)t * n + nu] = fmaf(-d, sp, cp);
+    sn32[(size_t)t * n + nu] = fmaf(d, cp, sp);
+}
+
 void launch_trig_tables(Plan &P, const double *R, cudaStream_t s)
 {
     if (P.nk == 0) return;
     dim3 g((P.n + 127) / 128, P.nk);
-    k_trig<<<g, 128, 0, s>>>(R, P.n, P.d_kvec, P.nk, P.d_cos, P.d_sin, P.d_cos32, P.d_sin32);
+    if (is_mixed(P))
+        k_trig32<<<g, 128, 0, s>>>(R, P.n, P.d_kvec, P.nk, P.d_cos32, P.d_sin32);
+    else
+        k_trig<<<g, 128, 0, s>>>(R, P.n, P.d_kvec, P.nk, P.d_cos, P.d_sin, nullptr, nullptr);
     count_launches(1);
 }
 

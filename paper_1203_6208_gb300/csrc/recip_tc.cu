@@ -351,35 +351,55 @@ __device__ __forceinline__ uint2 pack4(float a, float b, float c, float d)
     return make_uint2(*(uint32_t *)&x, *(uint32_t *)&y);
 }
 
-__global__ void k_build_U(const float *__restrict__ cs, const float *__restrict__ sn,
-                          const float *__restrict__ basis, int n, int nk, int Kp,
-                          __half *__restrict__ Uh, __half *__restrict__ Ul)
+// One CTA per kUBeads beads: their cos/sin values for a chunk of kUChunk k
+// groups are staged in shared memory (bead-major), then the CTA writes that
+// chunk of its 3 kUBeads rows of Uh and Ul with consecutive threads on
+// consecutive k groups, so that each warp stores 256 contiguous bytes of a row
+// (a thread per (bead, k group) would scatter 8-byte stores 6 Kp bytes apart).
+constexpr int kUBeads = 8;
+constexpr int kUThreads = 256;
+constexpr int kUChunk = 512;
+
+__global__ void __launch_bounds__(kUThreads)
+k_build_U(const float *__restrict__ cs, const float *__restrict__ sn,
+          const float *__restrict__ basis, int n, int nk, int Kp,
+          __half *__restrict__ Uh, __half *__restrict__ Ul)
 {
-    const int nu = blockIdx.x * blockDim.x + threadIdx.x;
-    const int t = blockIdx.y;
-    if (nu >= n) return;
-    if (t >= nk) {                       // zero padding columns of this k group
-        for (int a = 0; a < 3; a++) {
-            size_t o = (size_t)(3 * nu + a) * Kp + 4 * t;
-            *(uint2 *)(Uh + o) = make_uint2(0u, 0u);
-            *(uint2 *)(Ul + o) = make_uint2(0u, 0u);
+    __shared__ float s_c[kUBeads][kUChunk], s_s[kUBeads][kUChunk];
+    const int nu0 = blockIdx.x * kUBeads;
+    const int nb = min(kUBeads, n - nu0);
+    const int ng = Kp / 4;                        // k groups (>= nk, the rest zero)
+    for (int t0 = 0; t0 < ng; t0 += kUChunk) {
+        const int tn = min(kUChunk, ng - t0);
+        __syncthreads();                          // the previous chunk is written
+        for (int i = threadIdx.x; i < kUBeads * tn; i += kUThreads) {
+            const int tt = i / kUBeads, b = i % kUBeads;     // 8 consecutive beads per k
+            const bool in = b < nb && t0 + tt < nk;
+            s_c[b][tt] = in ? cs[(size_t)(t0 + tt) * n + nu0 + b] : 0.f;
+            s_s[b][tt] = in ? sn[(size_t)(t0 + tt) * n + nu0 + b] : 0.f;
         }
-        return;
-    }
-    const float c = cs[(size_t)t * n + nu], s = sn[(size_t)t * n + nu];
-    const float *b = basis + 8 * t;
+        __syncthreads();
+        for (int i = threadIdx.x; i < 3 * nb * tn; i += kUThreads) {
+            const int row = i / tn, tt = i - row * tn, t = t0 + tt;
+            const int b = row / 3, a = row - 3 * b;
+            const size_t o = (size_t)(3 * (nu0 + b) + a) * Kp + 4 * t;
+            if (t >= nk) {
+                *(uint2 *)(Uh + o) = make_uint2(0u, 0u);
+                *(uint2 *)(Ul + o) = make_uint2(0u, 0u);
+                continue;
+            }
+            const float c = s_c[b][tt], sv = s_s[b][tt];
+            const float *bs = basis + 8 * t;
+            const float v[4] = {bs[a] * c, bs[a] * sv, bs[3 + a] * c, bs[3 + a] * sv};
+            float h[4], l[4];
 #pragma unroll
-    for (int a = 0; a < 3; a++) {
-        const float v[4] = {b[a] * c, b[a] * s, b[3 + a] * c, b[3 + a] * s};
-        float h[4], l[4];
-#pragma unroll
-        for (int j = 0; j < 4; j++) {
-            h[j] = to_tf32(v[j]);
-            l[j] = to_tf32(v[j] - h[j]);            // exact difference
+            for (int j = 0; j < 4; j++) {
+                h[j] = to_tf32(v[j]);
+                l[j] = to_tf32(v[j] - h[j]);            // exact difference
+            }
+            *(uint2 *)(Uh + o) = pack4(h[0], h[1], h[2], h[3]);
+            *(uint2 *)(Ul + o) = pack4(l[0], l[1], l[2], l[3]);
         }
-        size_t o = (size_t)(3 * nu + a) * Kp + 4 * t;
-        *(uint2 *)(Uh + o) = pack4(h[0], h[1], h[2], h[3]);
-        *(uint2 *)(Ul + o) = pack4(l[0], l[1], l[2], l[3]);
     }
 }
 
@@ -459,10 +479,8 @@ static bd_status map_U(CUtensorMap *m, const __half *base, int Kp, int n3, int r
 // D32 (band tiles) = U U^T, after the per-bead trig tables of this R are built
 bd_status launch_recip_tc(Plan &P, float *D32, cudaStream_t s)
 {
-    const int nkgroups = P.recip_kp / 4;             // >= nk, the rest zero
-    dim3 gu((P.n + 127) / 128, nkgroups);
-    k_build_U<<<gu, 128, 0, s>>>(P.d_cos32, P.d_sin32, P.d_kbasis, P.n, P.nk, P.recip_kp, P.d_Uh,
-                                 P.d_Ul);
+    k_build_U<<<(P.n + kUBeads - 1) / kUBeads, kUThreads, 0, s>>>(
+        P.d_cos32, P.d_sin32, P.d_kbasis, P.n, P.nk, P.recip_kp, P.d_Uh, P.d_Ul);
     count_launches(1);
     CUtensorMap mh, ml, mhb, mlb;
     bd_status st = map_U(&mh, P.d_Uh, P.recip_kp, P.n3, rt::BM);
