@@ -198,8 +198,9 @@ __global__ void k_cell_assign(const double *__restrict__ pw, int n, int nc, doub
     if (nu >= n) return;
     int ci[3];
     for (int s = 0; s < 3; s++) {
-        int c = (int)floor(pw[3 * nu + s] * nc / L);
-        ci[s] = c < 0 ? 0 : (c >= nc ? nc - 1 : c);
+        const double v = pw[3 * nu + s] * nc / L;
+        const int c = (v >= 0.0 && v < (double)nc) ? (int)v : 0;     // non-finite: cell 0
+        ci[s] = c >= nc ? nc - 1 : c;
     }
     const int c = (ci[0] * nc + ci[1]) * nc + ci[2];
     cell_of[nu] = c;
@@ -273,7 +274,8 @@ __global__ void k_tile_assign(const double *__restrict__ pw, int n, double L, in
     if (nu >= n) return;
     int ti[3];
     for (int d = 0; d < 3; d++) {
-        const double u = pw[3 * nu + d] * K / L;
+        double u = pw[3 * nu + d] * K / L;
+        if (!(u >= 0.0 && u < (double)K)) u = 0.0;        // non-finite position: a valid mesh cell
         const double fl = floor(u);
         T w[kMaxOrder];
         bspline_weights<T>((T)(u - fl), p, w);
