@@ -31,6 +31,8 @@ namespace rt {
 
 constexpr int BM = 128, BN = 256, BK = 64;     // BK in half elements (128 bytes)
 constexpr int STAGES = 4;
+// largest padded k width K_p (4 columns per half-space k) of the tensor-core path
+constexpr int kRecipTcMaxKp = 1024;
 constexpr int THREADS = 192;
 constexpr int A_BYTES = BM * BK * 2;           // 16 KB: 128 rows of U
 constexpr int B_BYTES = BN * BK * 2;           // 32 KB: 256 rows of U
@@ -358,7 +360,7 @@ __device__ __forceinline__ uint2 pack4(float a, float b, float c, float d)
 // (a thread per (bead, k group) would scatter 8-byte stores 6 Kp bytes apart).
 constexpr int kUBeads = 8;
 constexpr int kUThreads = 256;
-constexpr int kUChunk = 512;
+constexpr int kUChunk = 128;
 
 __global__ void __launch_bounds__(kUThreads)
 k_build_U(const float *__restrict__ cs, const float *__restrict__ sn,
@@ -430,6 +432,12 @@ bd_status recip_tc_init(Plan &P)
     double kmax2 = (2.0 * 3.14159265358979323846 / P.p.box_L) *
                    (2.0 * 3.14159265358979323846 / P.p.box_L) * P.p.n2max;
     if (!(kmax2 * P.p.a * P.p.a < 3.0)) return BD_OK;
+    // The tensor-core accumulator loses up to about half an ulp of the running
+    // sum at each of the 3 K_p / 16 MMA steps, always towards zero: on the
+    // positive diagonal sums the error grows with K_p (measured, 800 beads:
+    // 1.8e-6 of max|D| at K_p = 960, 3.4e-6 at 1856, 9.0e-6 at 3200).  Above
+    // K_p = 1024 the per-pair FP32 sum keeps D32 within 2e-6.
+    if (4 * P.nk > rt::kRecipTcMaxKp) return BD_OK;
     if (!g_enc) {
         cudaDriverEntryPointQueryResult q;
         void *fn = nullptr;

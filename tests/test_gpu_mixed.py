@@ -169,6 +169,33 @@ def test_build_D_f32_reciprocal_paths(bnd, n_chains, nb, alpha_factor):
     assert np.array_equal(D32, D32.T)
 
 
+@pytest.mark.parametrize("alpha_factor,nk,tol", [(2.0, 230, 2e-6), (3.0, 787, 5e-6)])
+def test_build_D_f32_dilute_k_sphere(bnd, alpha_factor, nk, tol):
+    """800 beads in a dilute box (L = 27.6) where k_max^2 a^2 < 3 holds up
+    to alpha = 3 sqrt(pi)/L.
+
+    At the benchmark's alpha = 2 sqrt(pi)/L (230 half-space k, K_p = 960)
+    the reciprocal sum is the tensor-core product, its U words staged in
+    two chunks, within the FP32 bar of the other tests (2e-6 of max|D|).
+
+    With 787 k (K_p = 3200) the product's accumulation error would grow to
+    9e-6 (measured), so the per-pair FP32 sum takes over.  That sum adds
+    787 terms per entry in FP32: its error bound is of order nk u (4.7e-5
+    worst case) and ~sqrt(nk) u typical; 2.7e-6 was measured.  Bar 5e-6."""
+    cfg = inputs.SystemConfig(n_chains=40, nb=20, c_over_cstar=0.25, alpha_factor=alpha_factor,
+                              seed=64)
+    p = cfg.params()
+    R = inputs.make_chains(cfg)
+    kmax2 = (2 * np.pi / p["L"]) ** 2 * p["n2max"]
+    assert kmax2 * p["a"] ** 2 < 3.0
+    plan, Rg, D = mixed(bnd, p, R)
+    assert plan.info.n_kvec == nk
+    Dr = oracle.build_D(p, R)
+    D32 = plan.D_view(D, "f32").cpu().numpy().astype(np.float64)
+    assert relerr(D32, Dr) <= tol
+    assert np.array_equal(D32, D32.T)
+
+
 def test_n8000_D32_sampled_rows(bnd):
     """FP32 D of the N = 8000 workload (16,000+ tensor-core tiles of the
     reciprocal product) against oracle rows of D."""
