@@ -189,6 +189,11 @@ bd_status bd_forces(bd_plan *plan, const double *R, double *F, int32_t *n_bad, b
  * reciprocal sum of M2(k) cos(k.(r_nu - r_mu)) over 0 < |k|, n.n <= n2max
  * (Eq. M2), and, for the image of a pair nu != mu closer than 2a, the
  * overlap correction M* = Omega_B - Omega_A (Eq. cor5).
+ * Mixed plans form the reciprocal sum as a tensor-core product U U^T of
+ * 16-bit words where 4 n_kvec <= 1024 and k_max^2 a^2 < 3, else per pair in
+ * FP32; FP64 plans per pair in FP64.  A non-finite position makes its own
+ * rows and columns of D non-finite and leaves the rest as for the other
+ * beads alone (its pairs contribute no real-space images).
  *   R   dev, 3N doubles
  *   D   dev, bd_plan_info.d_bytes bytes (output; layout in the header
  *       comment).  Padding columns [3N, ld) are not written.            */
