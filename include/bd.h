@@ -60,7 +60,7 @@ typedef enum {
     BD_ERR_FENE_STRETCH = 5,  /* a FENE spring reached |Q|^2 >= b                  */
     BD_ERR_CHEB_NOCONV = 6,   /* adaptive Chebyshev did not reach the tolerance    */
     BD_ERR_TIMEOUT = 7,       /* a bounded device-side wait gave up                */
-    BD_ERR_UNSUPPORTED = 8    /* request outside this build's supported range      */
+    BD_ERR_UNSUPPORTED = 8    /* request outside the library's supported range     */
 } bd_status;
 
 typedef enum {

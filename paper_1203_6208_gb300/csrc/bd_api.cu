@@ -96,7 +96,7 @@ static bd_status validate(const bd_params *p)
     if (p->beads_per_chain < 1 || p->n_beads % p->beads_per_chain != 0)
         return set_error(BD_ERR_INVALID, "n_beads must be a multiple of beads_per_chain >= 1");
     if ((int64_t)p->n_beads * 3 > (int64_t)1 << 20)
-        return set_error(BD_ERR_UNSUPPORTED, "3N = %lld exceeds this build's limit 2^20",
+        return set_error(BD_ERR_UNSUPPORTED, "3N = %lld exceeds the library's limit 2^20",
                          (long long)p->n_beads * 3);
     if (!(p->box_L > 0.0)) return set_error(BD_ERR_INVALID, "box_L must be > 0");
     if (!(p->a >= 0.0) || !(2.0 * p->a < p->box_L))
