@@ -86,6 +86,29 @@ def dist_env():
     return ws, rank, local
 
 
+def max_over_ranks(ms, ws, device):
+    """The slowest rank's time: every rank gets the max over ranks (one
+    all-reduce; no collective on the data path)."""
+    if ws <= 1:
+        return ms
+    import torch
+    t = torch.tensor([ms], dtype=torch.float64, device=device)
+    torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_value(ws, steps, ms):
+    """Whole-job throughput: every rank advances its own replica `steps`
+    times in the (max-over-ranks) time ms."""
+    return ws * steps / (ms * 1e-3)
+
+
+def replica_chains(cfg, rank):
+    """The rank's replica: the same system shape, its own seeded chains."""
+    from paper_1203_6208_gb300 import inputs
+    return inputs.make_chains(cfg, seed=cfg.seed + 17 * rank)
+
+
 def system(alpha_factor, chains=400):
     from paper_1203_6208_gb300 import inputs
     cfg, extra = inputs.preset("c4", alpha_factor=alpha_factor, n_chains=chains)
@@ -374,10 +397,7 @@ def measure(args, precision, p, R0, rank, ws):
     if ws > 1:
         torch.distributed.barrier()
     clk = clocks.stop()
-    if ws > 1:
-        t = torch.tensor([ms], device="cuda")
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = max_over_ranks(ms, ws, "cuda")
     st = bnd.read_stats(stats)
     phases = {name: sum(evs[k][i].elapsed_time(evs[k][i + 1]) for k in range(args.steps))
               / args.steps for i, name in enumerate(bnd.PHASES)}
@@ -467,7 +487,7 @@ def measure(args, precision, p, R0, rank, ws):
                "note": "per step: positions H2D from pinned memory, the step (bd_step_replay "
                        "of the captured step on mixed plans, else bd_step), positions + stats "
                        "D2H, stream sync (wall clock)"}
-    out = {"value": ws * args.steps / (ms * 1e-3), "ms_per_step": ms / args.steps,
+    out = {"value": job_value(ws, args.steps, ms), "ms_per_step": ms / args.steps,
            "launch": "CUDA graph replay (bd_step_capture / bd_step_replay)" if graph
                      else "direct bd_step calls",
            "direct_ms_per_step": direct_ms / args.steps,
@@ -498,7 +518,7 @@ def run_ours(args):
     build.build()
     precs = ["fp64", "fp64_df", "mixed_f16"] if args.precision == "both" else [args.precision]
     cfg, p1 = system(1.0, args.chains)
-    R0 = inputs.make_chains(cfg, seed=cfg.seed + 17 * rank)
+    R0 = replica_chains(cfg, rank)
     results, alphas = {}, {}
     for prec in precs:
         if prec == "fp64_df" and "fp64" in alphas:
