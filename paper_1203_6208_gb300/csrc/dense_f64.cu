@@ -427,6 +427,7 @@ static void dispatch(const Plan &P, const double *D, const double *X, int m, dou
     else if (m <= 4) BD_GEMM_CASE(4);
     else if (m <= 8) BD_GEMM_CASE(8);
     else if (m <= 16) BD_GEMM_CASE(16);
+    else if (m <= 24) BD_GEMM_CASE(24);      // a step's first product: 16 + 1 columns
     else BD_GEMM_CASE(32);
     count_launches(1);
 #undef BD_GEMM_CASE
@@ -453,6 +454,7 @@ static void dispatch_df(const Plan &P, const double *D, const double *X, int m, 
     else if (m <= 4) BD_GEMM_DF_CASE(4);
     else if (m <= 8) BD_GEMM_DF_CASE(8);
     else if (m <= 16) BD_GEMM_DF_CASE(16);
+    else if (m <= 24) BD_GEMM_DF_CASE(24);
     else BD_GEMM_DF_CASE(32);
     count_launches(1);
 #undef BD_GEMM_DF_CASE
