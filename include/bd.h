@@ -125,7 +125,8 @@ typedef struct {
     int32_t n_cheb;           /* Chebyshev terms N_Ch (2..max_cheb); 0 = adaptive  */
     int32_t lanczos_iters;    /* Lanczos steps for the bounds (4..128)            */
     double  bound_safety;     /* d_max = (1 + bound_safety) theta_max             */
-    double  dmin_fraction;    /* d_min = dmin_fraction theta_min (0 < f <= 1)     */
+    double  dmin_fraction;    /* d_min = dmin_fraction min(theta_min, theta_pair)
+                                 (0 < f <= 1; see bd_eig_bounds)                   */
     uint64_t seed;            /* Philox key when dW == NULL                        */
     uint64_t step_index;      /* Philox counter high word when dW == NULL          */
     int32_t bounds_mode;      /* BD_BOUNDS_FRESH, _LAGGED, _FIXMAN_DILUTE or
@@ -144,7 +145,9 @@ typedef struct {
                                      it, so a captured graph draws new noise on
                                      every replay; step_index is ignored           */
 
-#define BD_BOUNDS_FRESH 0     /* lanczos_iters Lanczos products every step          */
+#define BD_BOUNDS_FRESH 0     /* lanczos_iters Lanczos products every step, d_min
+                                 tightened by the pair estimate of this step's D
+                                 (bd_eig_bounds; not on matrix-free steps)          */
 #define BD_BOUNDS_FIXMAN_DILUTE 2     /* Eq. (lmax-lmin-dilute): lambda^F_max,min =
                                  U+-.D.U+- / 3N with U+ all ones and U- alternating
                                  +1, -1 (two extra columns of the first product);
@@ -155,7 +158,9 @@ typedef struct {
                                  d_max = lambda_max, d_min = lambda_min            */
 #define BD_BOUNDS_LAGGED 1    /* mixed plans: the Lanczos vector rides as one extra
                                  column of this step's products; its bounds serve
-                                 the next step (the first step runs fresh)          */
+                                 the next step (the first step runs fresh), d_min
+                                 tightened by the pair estimate of the current D,
+                                 which the assembly computes on the fly           */
 
 /* ---------------------------------------------------------------------------
  * Plan.  bd_plan_create validates the parameters, computes the reciprocal
@@ -174,7 +179,9 @@ bd_status bd_plan_query(const bd_plan *plan, bd_plan_info *out_info);
  * Springs: F^c(Q_mu) - F^c(Q_{mu-1}) with Hookean F^c(Q) = Q or FENE
  * F^c(Q) = Q/(1 - |Q|^2/b).  Excluded volume: narrow-Gaussian
  * F = sum (z_star/d_star^5) r exp(-r^2/(2 d_star^2)) over all pairs and periodic images
- * with |r| <= r_ev (not specified by the paper, which uses WCA; see DESIGN).
+ * with |r| <= r_ev.  The paper uses a WCA potential and does not define this
+ * narrow-Gaussian form; U/kT = (z_star/d_star^3) exp(-r^2/(2 d_star^2)) is the
+ * library's reading of the excluded volume the benchmarked systems switch on.
  *   R       dev, 3N doubles (input positions, unwrapped)
  *   F       dev, 3N doubles (output)
  *   n_bad   dev, one int32 (output, may be NULL): FENE springs with
@@ -191,9 +198,11 @@ bd_status bd_forces(bd_plan *plan, const double *R, double *F, int32_t *n_bad, b
  * overlap correction M* = Omega_B - Omega_A (Eq. cor5).
  * Mixed plans form the reciprocal sum as a tensor-core product U U^T of
  * 16-bit words where 4 n_kvec <= 1024 and k_max^2 a^2 < 3, else per pair in
- * FP32; FP64 plans per pair in FP64.  A non-finite position makes its own
- * rows and columns of D non-finite and leaves the rest as for the other
- * beads alone (its pairs contribute no real-space images).
+ * FP32; FP64 plans per pair in FP64.  Positions may be any finite doubles:
+ * unwrapped coordinates are reduced into [0, L) exactly (fmod) before use, so
+ * chains may travel any number of box lengths.  A non-finite position makes
+ * its own rows and columns of D non-finite and leaves the rest as for the
+ * other beads alone (its pairs contribute no real-space images).
  *   R   dev, 3N doubles
  *   D   dev, bd_plan_info.d_bytes bytes (output; layout in the header
  *       comment).  Padding columns [3N, ld) are not written.            */
@@ -215,19 +224,28 @@ bd_status bd_apply_D(bd_plan *plan, const void *D, const double *X, int32_t m, d
  * bd_eig_bounds -- bounds d_min <= lambda_min(D), d_max >= lambda_max(D)
  * required by the Chebyshev series (Sec. IV).  The paper estimates them from
  * Fixman's quadratic forms and empirical scalings (Eqs. lmax-lmin-dilute,
- * fmax, fmin); here they come from `iters` Lanczos steps (FP64 vectors and
- * recurrence, start vector from a fixed Philox stream) whose extreme Ritz
- * values theta are widened: d_max = (1 + safety_max) theta_max,
- * d_min = dmin_fraction theta_min.  theta_max converges to lambda_max from
- * below within a few tens of steps; theta_min approaches lambda_min slowly
- * (the bottom of the spectrum of D is clustered), which is why d_min takes a
- * multiplicative fraction rather than a small margin.  The tridiagonal
- * eigenvalues are found by bisection on the device; a Lanczos breakdown
- * (beta ~ 0) truncates the tridiagonal matrix.  1 <= iters <= 128 (clamped
- * to 3N).
+ * fmax, fmin); here they come from two upper estimates of the extreme
+ * eigenvalues, widened:
+ *   d_max = (1 + safety_max) theta_max,
+ *   d_min = dmin_fraction min(theta_min, theta_pair).
+ * theta_min, theta_max: the extreme Ritz values of `iters` Lanczos steps
+ * (FP64 vectors and recurrence, start vector from a fixed Philox stream).
+ * theta_max converges to lambda_max from below within a few tens of steps;
+ * theta_min approaches lambda_min slowly.
+ * theta_pair = d_s - max over pairs nu != mu of the spectral radius of the
+ * 3x3 block D_{nu mu}, with d_s I the (common) diagonal block: the smallest
+ * eigenvalue of the pair's 6x6 principal submatrix, >= lambda_min by Cauchy
+ * interlacing.  In dense solutions the lowest modes of D are the relative
+ * motions of the closest overlapping pairs, so theta_pair lies within a few
+ * per cent of lambda_min (measured at N = 3000 and 8000, c/c* = 4).
+ * theta_pair <= 0 proves D indefinite.  The pair estimate reads the
+ * strictly upper 3x3 blocks of D (FP64, or D32 of a mixed plan) once; the
+ * tridiagonal eigenvalues are found by bisection on the device; a Lanczos
+ * breakdown (beta ~ 0) truncates the tridiagonal matrix.  1 <= iters <= 128
+ * (clamped to 3N).
  *   bounds  dev, 2 doubles (output): {d_min, d_max}
  *   status  dev, one int32 (output, may be NULL): BD_ERR_NOT_PD when
- *           d_min <= 0, else BD_OK.                                       */
+ *           d_min <= 0 or d_max <= d_min, else BD_OK.                     */
 bd_status bd_eig_bounds(bd_plan *plan, const void *D, int32_t iters, double safety_max,
                         double dmin_fraction, double *bounds, int32_t *status, bd_stream stream);
 

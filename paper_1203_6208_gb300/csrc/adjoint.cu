@@ -114,7 +114,7 @@ k_pair_adjoint(const double *__restrict__ R, int n, const EwaldCoef *__restrict_
         double d[3];
         for (int s = 0; s < 3; s++) {
             double x = R[3 * nu + s] - R[3 * mu + s];
-            d[s] = x - L * rint(x * invL);
+            d[s] = remainder(x, L);      // exact, in [-L/2, L/2] for any finite x
         }
         const T rc2 = (T)c.rc2, four_a2 = (T)c.four_a2, Lt = (T)L;
         const T dx = (T)d[0], dy = (T)d[1], dz = (T)d[2];

@@ -76,7 +76,7 @@ static void free_plan(Plan &P)
                     P.d_Rnew, P.d_V[0], P.d_V[1], P.d_V[2], P.d_X0, P.d_Y0, P.d_dS, P.d_dW,
                     P.d_coef, P.d_wdw, P.d_red, P.d_redpart, P.d_bounds, P.d_status, P.d_lq[0], P.d_lq[1],
                     P.d_lq[2], P.d_lab, P.d_x16, P.d_xscale, P.d_part, P.d_counters,
-                    P.d_stats_scratch, P.d_y32, P.d_lag_bounds, P.d_step_ctr, P.d_vhist, P.d_xhist, P.d_ubuf[0], P.d_ubuf[1],
+                    P.d_stats_scratch, P.d_y32, P.d_lag_bounds, P.d_pairw, P.d_step_ctr, P.d_vhist, P.d_xhist, P.d_ubuf[0], P.d_ubuf[1],
                     P.d_ubuf[2], P.d_ubuf[3], P.d_xdf, P.d_Uh, P.d_Ul, P.d_rtiles, P.d_kbasis, P.d_lanpart, P.d_mom, P.d_sfac, P.d_mfW, P.d_mfpart};
     for (void *p : ptrs)
         if (p) cudaFree(p);
@@ -214,6 +214,7 @@ bd_status bd_plan_create(const bd_params *params, bd_plan **out_plan)
     TRY(dmalloc(P, &P.d_X0, n3 * (R + 3)));
     TRY(dmalloc(P, &P.d_Y0, n3 * (R + 3)));
     TRY(dmalloc(P, &P.d_lag_bounds, 2));
+    TRY(dmalloc(P, &P.d_pairw, 2));
     TRY(dmalloc(P, &P.d_step_ctr, 1));
     TRY(dmalloc(P, &P.d_dS, n3 * R));
     TRY(dmalloc(P, &P.d_dW, n3 * R));
@@ -367,10 +368,16 @@ bd_status bd_apply_D(bd_plan *plan, const void *D, const double *X, int32_t m, d
     return apply_core(P, D, X, m, Y, flags, stream);
 }
 
+// where the pair estimate of lambda_min comes from (pair_bound.cuh)
+enum PairSource { kPairNone = 0, kPairFromBuild = 1, kPairScanD = 2 };
+
+// Lanczos bounds, then d_min = min(d_min, f theta_pair) unless pair == kPairNone
 static bd_status eig_bounds_core(Plan &P, const void *D, int iters, double smax, double fmin_,
-                                 double *bounds, int32_t *status, cudaStream_t s)
+                                 double *bounds, int32_t *status, cudaStream_t s,
+                                 int pair = kPairScanD)
 {
     int k = iters < P.n3 ? iters : P.n3;
+    if (pair == kPairScanD) launch_pair_radius_scan(D, is_mixed(P), P.n, P.ld, P.d_pairw, s);
     launch_lanczos_init(P, s);
     for (int j = 0; j < k; j++) {
         bd_status st = apply_core(P, D, P.d_lq[1], 1, P.d_lq[2], 0, s);
@@ -378,6 +385,7 @@ static bd_status eig_bounds_core(Plan &P, const void *D, int iters, double smax,
         launch_lanczos_update(P, j, s);
     }
     launch_lanczos_finish(P, k, smax, fmin_, bounds, status, s);
+    if (pair != kPairNone) launch_bounds_pair(bounds, P.d_pairw, fmin_, status, s);
     return check_launch("bd_eig_bounds");
 }
 
@@ -691,6 +699,9 @@ bd_status bd_step(bd_plan *plan, double *R, void *D, const double *dW, const bd_
     if (matfree) {
         st = launch_matfree_tables(P, R, s);
         if (st != BD_OK) return st;
+        // the pair estimate of the bounds from D(R) (pair sums only; the
+        // spectral path has no per-pair reciprocal tables)
+        if (!P.pme && !fix) launch_pair_estimate(P, s);
     } else {
         st = bd_build_D(plan, R, D, s);
         if (st != BD_OK) return st;
@@ -703,11 +714,14 @@ bd_status bd_step(bd_plan *plan, double *R, void *D, const double *dW, const bd_
     if (fix) {
         // Fixman's estimates come from the first product below
     } else if (lag && P.lag_valid) {
+        // the previous step's Lanczos bounds, d_min tightened by this step's
+        // pair estimate (computed by the assembly above)
         cudaMemcpyAsync(P.d_bounds, P.d_lag_bounds, 2 * sizeof(double), cudaMemcpyDeviceToDevice, s);
-        launch_check_bounds(P.d_bounds, P.d_status + 3, s);
+        launch_bounds_pair(P.d_bounds, P.d_pairw, o->dmin_fraction, P.d_status + 3, s);
     } else {
         st = eig_bounds_core(P, D, o->lanczos_iters, o->bound_safety, o->dmin_fraction,
-                             P.d_bounds, P.d_status + 3, s);
+                             P.d_bounds, P.d_status + 3, s,
+                             (matfree && P.pme) ? kPairNone : kPairFromBuild);
         if (st != BD_OK) return st;
     }
     if (!fix) launch_stats_bounds(st_dev, P.d_bounds, P.d_status + 3, s);

@@ -128,6 +128,9 @@ struct Plan {
     cudaEvent_t *prod_ev;              // product timing: event pairs around each
     int prod_cap, prod_n, prod_on;     //   Chebyshev-product kernel launch
     double *d_lag_bounds;              // bounds from the previous step's lagged Lanczos
+    unsigned *d_pairw;                 // pair estimate words (pair_bound.cuh), float bits:
+                                       //   [0] max over pairs of the block spectral radius,
+                                       //   [1] d_s; written by the last assembly
     unsigned long long *d_step_ctr;    // device step counter (BD_STEP_DEVICE_COUNTER)
     int lag_valid;                     // host flag: d_lag_bounds was produced
     int phase_on;
@@ -179,6 +182,8 @@ bd_status launch_build_D_f32(Plan &P, const double *R, float *D32, void *D16, in
 
 // matrix-free Y = D(R) X (ewald_build.cu); the tables of R must be current
 bd_status launch_matfree_tables(Plan &P, const double *R, cudaStream_t s);
+// pair estimate words of D(R) without storing D (after launch_matfree_tables)
+void launch_pair_estimate(Plan &P, cudaStream_t s);
 bd_status matfree_init(Plan &P);
 bd_status launch_apply_matfree(Plan &P, const double *X, int m, double *Y, cudaStream_t s);
 // the matrix-free product of the plan: spectral (pme_grid > 0) or pair sums
@@ -218,7 +223,15 @@ void launch_lanczos_update(Plan &P, int j, cudaStream_t s);
 void launch_lanczos_finish(Plan &P, int k, double safety_max, double dmin_fraction,
                            double *bounds, int32_t *status, cudaStream_t s);
 void launch_stats_begin(bd_step_stats *st, int nch, cudaStream_t s);
-void launch_check_bounds(const double *bounds, int32_t *status, cudaStream_t s);
+// the pair estimate (pair_bound.cuh): word[0] = max over pairs of rho(D_{nu mu})
+// read from a stored D (FP64, or the FP32 D32 when f32), upper triangle only;
+// word[1] = d_s = D[0][0]
+void launch_pair_radius_scan(const void *D, int f32, int n, long ld, unsigned *word,
+                             cudaStream_t s);
+// bounds[0] = min(bounds[0], dmin_fraction (d_s - rho_max)) from word;
+// status (may be NULL) = BD_OK, or BD_ERR_NOT_PD when d_min <= 0 or d_max <= d_min
+void launch_bounds_pair(double *bounds, const unsigned *word, double dmin_fraction,
+                        int32_t *status, cudaStream_t s);
 // Fixman estimates: U+, U- into two columns of X; bounds from X2 . Y2 (Y2 = D X2)
 void launch_fixman_fill(double *X, int n3, cudaStream_t s);
 void launch_fixman_bounds(Plan &P, const double *X2, const double *Y2, int mode, double C,

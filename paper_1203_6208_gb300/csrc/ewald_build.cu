@@ -16,6 +16,7 @@
 
 #include "bd_internal.cuh"
 #include "pair_common.cuh"
+#include "pair_bound.cuh"
 #include "recip_tc.cuh"
 #include "kspace.cuh"
 #include "spectral.cuh"
@@ -73,13 +74,16 @@ __global__ void k_ewald_typed(const EwaldCoef *c, EwaldT<double> *o64, EwaldT<fl
     if (o32) fill_ewt<float>(*c, o32);
 }
 
-// positions wrapped into [0, L): FP64, and as FP32 hi/lo words
+// positions wrapped into [0, L): FP64, and as FP32 hi/lo words.  fmod is
+// exact (the remainder of a binary64 division is representable), so an
+// unwrapped coordinate of any finite magnitude lands in [0, L); x - L floor(x/L)
+// would leave a residual many box lengths long once x/L is not exact.
 __global__ void k_wrap(const double *R, int n3, double L, double *pw, float *pw32)
 {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n3) return;
-    double x = R[i];
-    x -= L * floor(x / L);
+    double x = fmod(R[i], L);
+    if (x < 0.0) x += L;
     if (x >= L) x -= L;
     pw[i] = x;
     if (pw32) {
@@ -444,7 +448,7 @@ k_build_D(const double *__restrict__ pw, const float *__restrict__ pw32, int n,
           const T *__restrict__ tab, int tab_i0, int ntab, const T *__restrict__ km, int nk,
           const T *__restrict__ cs, const T *__restrict__ sn, int overlap_corr, float rc,
           T *__restrict__ D, void *__restrict__ D16, int is_bf16, long ld, int recip_in_D,
-          int upper_only)
+          int upper_only, unsigned *__restrict__ pairw)
 {
     __shared__ T tile[TS * TSP];
     __shared__ T s_tr[4][KC][TB];      // cos nu, sin nu, cos mu, sin mu for one k chunk
@@ -493,6 +497,18 @@ k_build_D(const double *__restrict__ pw, const float *__restrict__ pw32, int n,
             }
         }
     }
+    // the pair estimate of lambda_min (pair_bound.cuh): pairw[0] = max over
+    // nu != mu of the spectral radius of the block, pairw[1] = d_s (the
+    // diagonal block of bead 0)
+    {
+        const float rho = (active && nu != mu)
+            ? pair_block_radius((float)acc[0], (float)acc[1], (float)acc[2], (float)acc[3],
+                                (float)acc[4], (float)acc[5])
+            : 0.f;
+        warp_max_to_word(rho, pairw);
+        if (active && nu == 0 && mu == 0) pairw[1] = __float_as_uint((float)acc[0]);
+    }
+    if (D == nullptr) return;           // pair estimate only (matrix-free steps)
     __syncthreads();
     // stage the 3x3 block: rows 3ty+a, cols 3tx+b
     {
@@ -635,14 +651,25 @@ __global__ void k_trig32(const double *R, int n, const KVec *kv, int nk, float *
     sn32[(size_t)t * n + nu] = fmaf(d, cp, sp);
 }
 
+static void launch_wrap(Plan &P, const double *R, cudaStream_t s)
+{
+    k_wrap<<<(P.n3 + 255) / 256, 256, 0, s>>>(R, P.n3, P.p.box_L, P.d_pw64, P.d_pw32);
+    count_launches(1);
+}
+
+// wrapped positions (P.d_pw64, P.d_pw32), then the per-bead cos/sin tables
+// from them: the phases k.r of coordinates reduced exactly into [0, L) keep
+// their digits however far the unwrapped chains have travelled
 void launch_trig_tables(Plan &P, const double *R, cudaStream_t s)
 {
+    launch_wrap(P, R, s);
     if (P.nk == 0) return;
     dim3 g((P.n + 127) / 128, P.nk);
     if (is_mixed(P))
-        k_trig32<<<g, 128, 0, s>>>(R, P.n, P.d_kvec, P.nk, P.d_cos32, P.d_sin32);
+        k_trig32<<<g, 128, 0, s>>>(P.d_pw64, P.n, P.d_kvec, P.nk, P.d_cos32, P.d_sin32);
     else
-        k_trig<<<g, 128, 0, s>>>(R, P.n, P.d_kvec, P.nk, P.d_cos, P.d_sin, nullptr, nullptr);
+        k_trig<<<g, 128, 0, s>>>(P.d_pw64, P.n, P.d_kvec, P.nk, P.d_cos, P.d_sin, nullptr,
+                                 nullptr);
     count_launches(1);
 }
 
@@ -652,21 +679,15 @@ static long tile_pairs(int n)
     return T * (T + 1) / 2;
 }
 
-static void launch_wrap(Plan &P, const double *R, cudaStream_t s)
-{
-    k_wrap<<<(P.n3 + 255) / 256, 256, 0, s>>>(R, P.n3, P.p.box_L, P.d_pw64, P.d_pw32);
-    count_launches(1);
-}
-
 void launch_build_D_f64(Plan &P, const double *R, double *D, cudaStream_t s)
 {
     launch_trig_tables(P, R, s);
-    launch_wrap(P, R, s);
+    cudaMemsetAsync(P.d_pairw, 0, 2 * sizeof(unsigned), s);
     long nb = tile_pairs(P.n);
     k_build_D<double><<<(unsigned)nb, TB * TB, 0, s>>>(
         P.d_pw64, P.d_pw32, P.n, P.h_ew64, P.d_ewc, P.d_tab, P.tab_i0, P.ntab, P.d_km64, P.nk,
         P.d_cos, P.d_sin, P.p.overlap_corr,
-        (float)P.p.r_c, D, nullptr, 0, P.ld, 0, 0);
+        (float)P.p.r_c, D, nullptr, 0, P.ld, 0, 0, P.d_pairw);
     count_launches(1);
 }
 
@@ -674,20 +695,41 @@ bd_status launch_build_D_f32(Plan &P, const double *R, float *D32, void *D16, in
                         cudaStream_t s)
 {
     launch_trig_tables(P, R, s);
-    launch_wrap(P, R, s);
     int nk = P.nk;
     if (P.recip_tc) {
         bd_status st = launch_recip_tc(P, D32, s);
         if (st != BD_OK) return st;
         nk = 0;
     }
+    cudaMemsetAsync(P.d_pairw, 0, 2 * sizeof(unsigned), s);
     long nb = tile_pairs(P.n);
     k_build_D<float><<<(unsigned)nb, TB * TB, 0, s>>>(
         P.d_pw64, P.d_pw32, P.n, P.h_ew32, P.d_ewc, P.d_tab32, P.tab32_i0, P.ntab32, P.d_km32, nk,
         P.d_cos32, P.d_sin32, P.p.overlap_corr,
-        (float)P.p.r_c, D32, D16, is_bf16, P.ld, P.recip_tc, P.tc_split == kSymShape ? 1 : 0);
+        (float)P.p.r_c, D32, D16, is_bf16, P.ld, P.recip_tc, P.tc_split == kSymShape ? 1 : 0,
+        P.d_pairw);
     count_launches(1);
     return BD_OK;
+}
+
+// the pair estimate of D(R) without storing D (matrix-free steps): the
+// assembly kernel with no output, the reciprocal sum per pair from the trig
+// tables (launch_matfree_tables must have run for R)
+void launch_pair_estimate(Plan &P, cudaStream_t s)
+{
+    cudaMemsetAsync(P.d_pairw, 0, 2 * sizeof(unsigned), s);
+    long nb = tile_pairs(P.n);
+    if (is_mixed(P))
+        k_build_D<float><<<(unsigned)nb, TB * TB, 0, s>>>(
+            P.d_pw64, P.d_pw32, P.n, P.h_ew32, P.d_ewc, P.d_tab32, P.tab32_i0, P.ntab32,
+            P.d_km32, P.nk, P.d_cos32, P.d_sin32, P.p.overlap_corr, (float)P.p.r_c, nullptr,
+            nullptr, 0, P.ld, 0, 0, P.d_pairw);
+    else
+        k_build_D<double><<<(unsigned)nb, TB * TB, 0, s>>>(
+            P.d_pw64, P.d_pw32, P.n, P.h_ew64, P.d_ewc, P.d_tab, P.tab_i0, P.ntab, P.d_km64,
+            P.nk, P.d_cos, P.d_sin, P.p.overlap_corr, (float)P.p.r_c, nullptr, nullptr, 0,
+            P.ld, 0, 0, P.d_pairw);
+    count_launches(1);
 }
 
 // ---------------------------------------------------------------------------
@@ -876,7 +918,6 @@ bd_status launch_matfree_tables(Plan &P, const double *R, cudaStream_t s)
         return spectral_tables(P, s);
     }
     launch_trig_tables(P, R, s);
-    launch_wrap(P, R, s);
     return BD_OK;
 }
 

@@ -26,9 +26,9 @@ namespace bd {
 constexpr int kNoAllocMaxN3 = 24576;
 // q_{j-1}, q_j, w (3 x 3N), the tridiagonal alpha/beta (2 x kMaxLanczos), the
 // reduction words (4 x kMaxRhs) and their per-block partials (kRedBlocks x
-// kMaxRhs), laid out as in a plan
+// kMaxRhs), laid out as in a plan, and one slot for the two pair-estimate words
 constexpr size_t kNoAllocDoubles = 3 * (size_t)kNoAllocMaxN3 + 2 * kMaxLanczos + 4 * kMaxRhs +
-                                   (size_t)kRedBlocks * kMaxRhs;
+                                   (size_t)kRedBlocks * kMaxRhs + 1;
 
 static __device__ __align__(256) double g_noalloc_scratch[kNoAllocDoubles];
 
@@ -92,13 +92,17 @@ extern "C" bd_status bd_eig_bounds_noalloc(const double *D, int32_t n3, int32_t 
     P.d_lab = scr + 3 * (size_t)kNoAllocMaxN3;
     P.d_red = P.d_lab + 2 * kMaxLanczos;
     P.d_redpart = P.d_red + 4 * kMaxRhs;
+    unsigned *pair_word = (unsigned *)(scr + kNoAllocDoubles - 1);
     cudaStream_t s = stream;
     int k = iters < n3 ? iters : n3;
+    // the pair estimate of lambda_min from D's blocks (clears its word first)
+    launch_pair_radius_scan(D, 0, P.n, ld, pair_word, s);
     launch_lanczos_init(P, s);          // overwrites q and q_prev, clears its reduction word
     for (int j = 0; j < k; j++) {
         launch_gemm_f64(P, D, P.d_lq[1], 1, P.d_lq[2], s);
         launch_lanczos_update(P, j, s); // clears the words it accumulates into
     }
     launch_lanczos_finish(P, k, safety_max, dmin_fraction, bounds, status, s);
+    launch_bounds_pair(bounds, pair_word, dmin_fraction, status, s);
     return check_launch("bd_eig_bounds_noalloc");
 }

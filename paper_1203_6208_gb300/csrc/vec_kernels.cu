@@ -6,6 +6,7 @@
 #include <math.h>
 
 #include "bd_internal.cuh"
+#include "pair_bound.cuh"
 
 namespace bd {
 
@@ -76,7 +77,6 @@ __global__ void k_ev(const double *R, int n, double L, double pref, double inv2d
     double rn[3] = {0, 0, 0};
     if (nu < n) for (int s = 0; s < 3; s++) rn[s] = R[3 * nu + s];
     double acc[3] = {0.0, 0.0, 0.0};
-    const double invL = 1.0 / L;
     for (int base = 0; base < n; base += 128) {
         __syncthreads();
         for (int i = threadIdx.x; i < 3 * 128; i += blockDim.x) {
@@ -92,7 +92,7 @@ __global__ void k_ev(const double *R, int n, double L, double pref, double inv2d
                 double d[3];
                 for (int s = 0; s < 3; s++) {
                     double x = rn[s] - sr[3 * q + s];
-                    d[s] = x - L * rint(x * invL);
+                    d[s] = remainder(x, L);   // exact minimum image
                 }
                 for (int ix = -nmax; ix <= nmax; ix++) {
                     double vx = d[0] + ix * L;
@@ -544,14 +544,56 @@ void launch_fixman_bounds(Plan &P, const double *X2, const double *Y2, int mode,
 }
 
 // status of given bounds (lagged mode)
-__global__ void k_check_bounds(const double *b, int32_t *status)
+
+// the pair estimate from a stored D: one thread per block (nu, mu), nu < mu
+// (the strictly upper blocks, which every layout of D holds), block rows nu =
+// blockIdx.y + k gridDim.y; the symmetric part of the block is used
+template <typename T>
+__global__ void k_pair_radius_scan(const T *__restrict__ D, int n, long ld, unsigned *word)
 {
-    *status = (b[0] > 0.0 && b[1] > b[0]) ? BD_OK : BD_ERR_NOT_PD;
+    const int mu = blockIdx.x * blockDim.x + threadIdx.x;
+    float rho = 0.f;
+    for (int nu = blockIdx.y; nu < n - 1; nu += gridDim.y) {
+        if (mu > nu && mu < n) {
+            const T *b = D + (size_t)3 * nu * ld + 3 * mu;
+            const float a00 = (float)b[0], a11 = (float)b[ld + 1], a22 = (float)b[2 * ld + 2];
+            const float a01 = 0.5f * ((float)b[1] + (float)b[ld]);
+            const float a02 = 0.5f * ((float)b[2] + (float)b[2 * ld]);
+            const float a12 = 0.5f * ((float)b[ld + 2] + (float)b[2 * ld + 1]);
+            rho = fmaxf(rho, pair_block_radius(a00, a01, a02, a11, a12, a22));
+        }
+    }
+    warp_max_to_word(rho, word);
+    if (blockIdx.x == 0 && blockIdx.y == 0 && threadIdx.x == 0) word[1] = __float_as_uint((float)D[0]);
 }
 
-void launch_check_bounds(const double *bounds, int32_t *status, cudaStream_t s)
+void launch_pair_radius_scan(const void *D, int f32, int n, long ld, unsigned *word,
+                             cudaStream_t s)
 {
-    k_check_bounds<<<1, 1, 0, s>>>(bounds, status);
+    cudaMemsetAsync(word, 0, 2 * sizeof(unsigned), s);
+    dim3 g((unsigned)((n + 255) / 256), (unsigned)(n - 1 < 1 ? 1 : (n - 1 < 65535 ? n - 1 : 65535)));
+    if (f32) k_pair_radius_scan<float><<<g, 256, 0, s>>>((const float *)D, n, ld, word);
+    else k_pair_radius_scan<double><<<g, 256, 0, s>>>((const double *)D, n, ld, word);
+    count_launches(1);
+}
+
+// d_min = min(d_min, f theta_pair), theta_pair = d_s - rho_max (pair_bound.cuh).
+// theta_pair <= 0 means a 6 x 6 principal submatrix of D is not positive
+// definite, and then neither is D: the status says so.
+__global__ void k_bounds_pair(double *b, const unsigned *word, double f, int32_t *status)
+{
+    const double ds = (double)__uint_as_float(word[1]);
+    const double rho = (double)__uint_as_float(word[0]);
+    const double th = ds - rho;
+    const double dmin = th > 0.0 ? fmin(b[0], f * th) : f * th;
+    b[0] = dmin;
+    if (status) *status = (dmin > 0.0 && b[1] > dmin) ? BD_OK : BD_ERR_NOT_PD;
+}
+
+void launch_bounds_pair(double *bounds, const unsigned *word, double dmin_fraction,
+                        int32_t *status, cudaStream_t s)
+{
+    k_bounds_pair<<<1, 1, 0, s>>>(bounds, word, dmin_fraction, status);
     count_launches(1);
 }
 
