@@ -84,7 +84,7 @@ def build(verbose: bool = False, force: bool = False) -> str:
         raise RuntimeError(f"nvcc failed:\n{msg}")
     if force or procs or not os.path.exists(LIB):
         tmp = LIB + f".tmp{os.getpid()}"
-        cmd = [nvcc, *ARCH, "-shared", "-o", tmp, *objs, "-lcufft"]
+        cmd = [nvcc, *ARCH, "-shared", "-o", tmp, *objs]
         subprocess.run(cmd, check=True)
         os.replace(tmp, LIB)
     if force or not os.path.exists(PROBE_LIB) or (

@@ -8,7 +8,8 @@
 //     r_c / 2, searched two cells deep;
 //   * the reciprocal sum of the same truncated k-sphere as the dense D by
 //     smooth particle-mesh Ewald: the operand is spread onto a K^3 mesh with
-//     cardinal B-splines of order p, transformed (cuFFT, batched R2C), each
+//     cardinal B-splines of order p, transformed (fft.cu, real to half
+//     complex), each
 //     mesh wave vector m multiplied by G(m) |b(m)|^2 with G = M2(2 pi m / L)
 //     of Eq. (M2) for |m|^2 <= n2max (zero otherwise and at m = 0) and b the
 //     Euler exponential-spline factors, transformed back and interpolated
@@ -149,6 +150,8 @@ bd_status spectral_init(Plan &P)
     if (e == cudaSuccess) e = cudaMallocHost((void **)&S->h_npair, sizeof(long long));
     if (e != cudaSuccess) return oom("mesh", e);
     P.scratch_bytes += (int64_t)bytes;
+    bd_status fst = fft_plan_init(S->fft, S->K);
+    if (fst != BD_OK) return fst;
     // influence function (plan constant)
     std::vector<double> bm(3 * (size_t)S->K);
     for (int d = 0; d < 3; d++)
@@ -180,10 +183,7 @@ void spectral_free(Plan &P)
     for (void *q : ptrs)
         if (q) cudaFree(q);
     if (S->h_npair) cudaFreeHost(S->h_npair);
-    if (S->plan_m) {
-        cufftDestroy(S->fwd);
-        cufftDestroy(S->inv);
-    }
+    fft_free(S->fft);
     delete S;
     P.pme = nullptr;
 }
@@ -565,31 +565,6 @@ static void launch_gather(const PmeState *S, int n, int m, double *Y, cudaStream
 #undef GATHER
 }
 
-static bd_status cufft_plans(Plan &P, int m)
-{
-    PmeState *S = P.pme;
-    if (S->plan_m == m) return BD_OK;
-    if (S->plan_m) {
-        cufftDestroy(S->fwd);
-        cufftDestroy(S->inv);
-        S->plan_m = 0;
-    }
-    int dims[3] = {S->K, S->K, S->K};
-    const bool dbl = !is_mixed(P);
-    cufftResult r1 = cufftPlanMany(&S->fwd, 3, dims, nullptr, 1, (int)S->K3, nullptr, 1, (int)S->Kh,
-                                   dbl ? CUFFT_D2Z : CUFFT_R2C, 3 * m);
-    cufftResult r2 = cufftPlanMany(&S->inv, 3, dims, nullptr, 1, (int)S->Kh, nullptr, 1, (int)S->K3,
-                                   dbl ? CUFFT_Z2D : CUFFT_C2R, 3 * m);
-    if (r1 != CUFFT_SUCCESS || r2 != CUFFT_SUCCESS) {
-        if (r1 == CUFFT_SUCCESS) cufftDestroy(S->fwd);
-        if (r2 == CUFFT_SUCCESS) cufftDestroy(S->inv);
-        return set_error(BD_ERR_CUDA, "cuFFT plan for a %d^3 mesh x %d failed (%d, %d)", S->K, 3 * m,
-                         (int)r1, (int)r2);
-    }
-    S->plan_m = m;
-    return BD_OK;
-}
-
 bd_status launch_apply_spectral(Plan &P, const double *X, int m, double *Y, cudaStream_t s)
 {
     PmeState *S = P.pme;
@@ -598,36 +573,34 @@ bd_status launch_apply_spectral(Plan &P, const double *X, int m, double *Y, cuda
     bd_status st = launch_real_pairs(P, X, m, Y, s);
     if (st != BD_OK) return st;
     if (P.p.n2max <= 0) return BD_OK;
-    st = cufft_plans(P, m);
-    if (st != BD_OK) return st;
     const unsigned ntiles = (unsigned)S->ntile;
     const unsigned nh = (unsigned)((S->Kh * m + 255) / 256);
     constexpr int kTileThreads = kMeshTile * kMeshTile * kMeshTile;
-    cufftSetStream(S->fwd, s);
-    cufftSetStream(S->inv, s);
-    cufftResult r1, r2;
+    const int B = 3 * m;                 // three component meshes per column
     if (!is_mixed(P)) {
         k_pme_spread<double, 6><<<ntiles, kTileThreads, 0, s>>>(
             P.n, S->K, S->p, S->tpd, S->d_tile_start, S->d_tile_beads, S->d_bfl,
             (const double *)S->d_bw, X, m, (double *)S->d_qreal);
-        r1 = cufftExecD2Z(S->fwd, (cufftDoubleReal *)S->d_qreal, (cufftDoubleComplex *)S->d_qhat);
-        k_pme_influence_apply<double, cufftDoubleComplex><<<nh, 256, 0, s>>>(
-            (const double *)S->d_infl, S->Kh, m, (cufftDoubleComplex *)S->d_qhat);
-        r2 = cufftExecZ2D(S->inv, (cufftDoubleComplex *)S->d_qhat, (cufftDoubleReal *)S->d_qreal);
+        st = fft3_r2c<double>(S->fft, (const double *)S->d_qreal, S->d_qhat, B, s);
+        if (st != BD_OK) return st;
+        k_pme_influence_apply<double, double2><<<nh, 256, 0, s>>>(
+            (const double *)S->d_infl, S->Kh, m, (double2 *)S->d_qhat);
+        st = fft3_c2r<double>(S->fft, S->d_qhat, (double *)S->d_qreal, B, s);
+        if (st != BD_OK) return st;
         launch_gather<double>(S, P.n, m, Y, s);
     } else {
         k_pme_spread<float, 9><<<ntiles, kTileThreads, 0, s>>>(
             P.n, S->K, S->p, S->tpd, S->d_tile_start, S->d_tile_beads, S->d_bfl,
             (const float *)S->d_bw, X, m, (float *)S->d_qreal);
-        r1 = cufftExecR2C(S->fwd, (cufftReal *)S->d_qreal, (cufftComplex *)S->d_qhat);
-        k_pme_influence_apply<float, cufftComplex><<<nh, 256, 0, s>>>(
-            (const float *)S->d_infl, S->Kh, m, (cufftComplex *)S->d_qhat);
-        r2 = cufftExecC2R(S->inv, (cufftComplex *)S->d_qhat, (cufftReal *)S->d_qreal);
+        st = fft3_r2c<float>(S->fft, (const float *)S->d_qreal, S->d_qhat, B, s);
+        if (st != BD_OK) return st;
+        k_pme_influence_apply<float, float2><<<nh, 256, 0, s>>>(
+            (const float *)S->d_infl, S->Kh, m, (float2 *)S->d_qhat);
+        st = fft3_c2r<float>(S->fft, S->d_qhat, (float *)S->d_qreal, B, s);
+        if (st != BD_OK) return st;
         launch_gather<float>(S, P.n, m, Y, s);
     }
     count_launches(3);
-    if (r1 != CUFFT_SUCCESS || r2 != CUFFT_SUCCESS)
-        return set_error(BD_ERR_CUDA, "cuFFT execution failed (%d, %d)", (int)r1, (int)r2);
     return check_launch("spectral product");
 }
 

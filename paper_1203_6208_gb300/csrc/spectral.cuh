@@ -1,9 +1,9 @@
 // spectral.cuh -- the spectral matrix-free product (sparse real space over
 // cell lists, reciprocal sum on a mesh): plan state and launchers.
 #pragma once
-#include <cufft.h>
 
 #include "bd_internal.cuh"
+#include "fft.cuh"
 
 namespace bd {
 
@@ -47,8 +47,7 @@ struct PmeState {
     void *d_bw;                   // [n][3][p] spline weights M_p(u_d - floor(u_d) + j)
     void *d_qreal;                // [3 mcap][K3] real mesh (working precision)
     void *d_qhat;                 // [3 mcap][Kh] complex mesh
-    cufftHandle fwd, inv;         // batched R2C / C2R plans for plan_m columns
-    int plan_m;                   // 0: no cuFFT plans yet
+    FftPlan fft;                  // the mesh transforms (fft.cu)
 };
 
 // the spectral product needs pme_grid > 0 in the plan parameters; creates the

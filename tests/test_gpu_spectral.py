@@ -102,5 +102,5 @@ def test_spectral_step_vs_oracle(bnd):
     assert st["status"] == 0 and st["accepted"] == 1
     R_ref, st_ref, DF_r, dS_r, _ = oracle.step(p, R, dW, st["d_min"], st["d_max"], nch)
     assert st_ref == 0
-    assert relerr(DF.cpu().numpy(), DF_r) <= 1e-10
-    assert relerr(dS.cpu().numpy(), dS_r) <= 1e-9
+    e = {"DF": relerr(DF.cpu().numpy(), DF_r), "dS": relerr(dS.cpu().numpy(), dS_r)}
+    assert e["DF"] <= 1e-11 and e["dS"] <= 1e-11, e
