@@ -134,22 +134,40 @@ def oracle_sample_step(p, R, m, nch, rows):
     return time.perf_counter() - t0
 
 
-def cpu_baseline(p, R, m, nch, target_s=12.0):
+# Ewald splits the oracle is tried at (alpha = f sqrt(pi)/L)
+ORACLE_ALPHAS = (0.75, 1.0, 1.25, 1.5)
+
+
+def oracle_alpha(chains, R, rows=16):
+    """The oracle's own best Ewald split: the factor f whose D rows the oracle
+    (as it stands) builds fastest on this system; the products do not depend
+    on alpha.  Both CPU figures of the benchmark use it."""
     import oracle
+    best = None
+    for f in ORACLE_ALPHAS:
+        _, p = system(f, chains)
+        t0 = time.perf_counter()
+        oracle.build_D_rows(p, R, 0, rows)
+        t = time.perf_counter() - t0
+        if best is None or t < best[1]:
+            best = (f, t)
+    return best[0]
+
+
+def cpu_baseline(chains, R, m, nch, target_s=12.0):
+    import oracle
+    f = oracle_alpha(chains, R)
+    _, p = system(f, chains)
     n = p["n"]
     t_small = oracle_sample_step(p, R, m, nch, 32)
     rows = int(min(n, max(32, 32 * target_s / max(t_small, 1e-3))))
     t = oracle_sample_step(p, R, m, nch, rows)
     step_s = t * n / rows
     return {"value": 1.0 / step_s, "unit": "steps/s", "cores": oracle.num_threads(),
-            "kind": "oracle",
+            "kind": "oracle", "alpha_factor": f,
             "sample": f"D rows and the {nch - 1} products for {rows} of {n} beads "
-                      f"({t:.1f} s), scaled by N/rows to one step ({step_s:.1f} s)"}
-
-
-# alpha factor the oracle arm uses when --alpha-factor is auto: the balanced
-# split f = 1 of the input recipe (the oracle is timed as it stands, untuned)
-REFERENCE_ALPHA = 1.0
+                      f"({t:.1f} s), scaled by N/rows to one step ({step_s:.1f} s); "
+                      f"alpha = {f} sqrt(pi)/L, the oracle's fastest of {list(ORACLE_ALPHAS)}"}
 
 
 def run_reference(args):
@@ -159,9 +177,10 @@ def run_reference(args):
     from paper_1203_6208_gb300 import inputs
     import oracle
     oracle.build()
-    f = REFERENCE_ALPHA if args.alpha_factor == "auto" else float(args.alpha_factor)
-    cfg, p = system(f, args.chains)
+    cfg, _ = system(1.0, args.chains)
     R = inputs.make_chains(cfg)
+    f = oracle_alpha(args.chains, R) if args.alpha_factor == "auto" else float(args.alpha_factor)
+    cfg, p = system(f, args.chains)
     n = p["n"]
     rows = 64
     for _ in range(args.warmup):
@@ -176,8 +195,10 @@ def run_reference(args):
             "config": {"workload": WORKLOAD, "precision": "fp64 oracle", "alpha_factor": f},
             "cpu_baseline": {"value": v, "unit": "steps/s", "cores": oracle.num_threads(),
                              "kind": "oracle",
+                             "alpha_factor": f,
                              "sample": f"each step: D rows + {args.nch - 1} products for {rows} "
-                                       f"of {n} beads, scaled by N/rows"},
+                                       f"of {n} beads, scaled by N/rows; alpha = {f} sqrt(pi)/L, "
+                                       f"the oracle's fastest of {list(ORACLE_ALPHAS)}"},
             "e2e": {"value": v, "unit": "steps/s", "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
@@ -316,6 +337,117 @@ def pick_alpha(args, p, R, precision):
     return best, {str(k): round(v, 3) for k, v in times.items()}
 
 
+def spectrum_check(plan, D, st, is64):
+    """Sec. IV's bound condition d_min <= lambda_min, d_max >= lambda_max on
+    the D of the last timed step (exact extremes from an FP32 symmetric
+    eigensolver on the device, upper triangle; for mixed plans also of the
+    16-bit copy the Chebyshev products multiply by).  Untimed."""
+    import torch
+    out = {"d_min": st["d_min"], "d_max": st["d_max"],
+           "eigensolver": "torch.linalg.eigvalsh (FP32, upper triangle) of the step's D"}
+    for which in (("f32",) if is64 else ("f32", "f16")):
+        try:
+            w = torch.linalg.eigvalsh(plan.D_view(D, which).float(), UPLO="U")
+        except RuntimeError as e:          # a missing dense eigensolver must not end the run
+            out["error"] = str(e).splitlines()[0]
+            return out
+        lmin, lmax = float(w[0]), float(w[-1])
+        del w
+        torch.cuda.empty_cache()
+        key = "" if which == "f32" else "_f16"
+        out["lambda_min" + key] = lmin
+        out["lambda_max" + key] = lmax
+        out["d_min_over_lambda_min" + key] = st["d_min"] / lmin
+        out["d_max_over_lambda_max" + key] = st["d_max"] / lmax
+        out["brackets" + key] = bool(st["d_min"] <= lmin and lmax <= st["d_max"])
+    return out
+
+
+def mixed_error_vs_fp64(args, p, R0, shape_code):
+    """Error of the benchmark's mixed step against the FP64 path on the same
+    configuration: two lagged mixed steps with given Wiener increments (the
+    second uses the first's Lanczos bounds, as in the timed loop), then the
+    FP64 plan's D.F and Chebyshev dS for the positions, dW and bounds of that
+    second step.  Max-norm relative errors."""
+    import torch
+    from paper_1203_6208_gb300 import binding as bnd, inputs
+    n3, m, nch = 3 * p["n"], args.m, args.nch
+    dW = torch.tensor(inputs.make_wiener(n3, m, p["dt"], 4343), device="cuda")
+    plan = bnd.Plan(p, "mixed_f16", max_rhs=m, max_cheb=nch)
+    if shape_code:
+        plan.set_shape(shape_code)
+    R = torch.tensor(R0, device="cuda")
+    D = plan.alloc_D()
+    stats = bnd.new_stats()
+    DF = torch.empty(n3, dtype=torch.float64, device="cuda")
+    dS = torch.empty(m, n3, dtype=torch.float64, device="cuda")
+    kw = dict(m=m, n_cheb=nch, lanczos_iters=args.lanczos, bound_safety=0.05,
+              dmin_fraction=0.5, bounds_mode=1, stats=stats)
+    plan.step(R, D, dW, **kw)
+    R1 = R.clone()
+    plan.step(R, D, dW, DF=DF, dS=dS, **kw)
+    torch.cuda.synchronize()
+    st = bnd.read_stats(stats)
+    plan.close()
+    del D
+    torch.cuda.empty_cache()
+    ref = bnd.Plan(p, "fp64", max_rhs=m, max_cheb=nch)
+    D64 = ref.alloc_D()
+    ref.build_D(R1, D64)
+    F = torch.empty(n3, dtype=torch.float64, device="cuda")
+    ref.forces(R1, F)
+    DF64 = torch.empty_like(F)
+    ref.apply(D64, F, DF64)
+    bounds = torch.tensor([st["d_min"], st["d_max"]], dtype=torch.float64, device="cuda")
+    dS64 = torch.empty_like(dS)
+    ref.chebyshev(D64, bounds, nch, dW, dS64)
+    torch.cuda.synchronize()
+    rel = lambda a, b: float((a - b).abs().max() / b.abs().max())
+    out = {"DF": rel(DF, DF64), "dS": rel(dS, dS64), "norm": "max|mixed - FP64| / max|FP64|",
+           "reference": "the FP64 GPU path (parity with the FP64 oracle at 1e-11) on the same "
+                        "positions, dW and bounds", "bounds": [st["d_min"], st["d_max"]],
+           "targets": {"DF": 1e-5, "dS": 1e-3}}
+    ref.close()
+    del D64
+    torch.cuda.empty_cache()
+    return out
+
+
+def adaptive_figure(args, p, R0, shape_code, tol=1e-3, steps=3, precision="mixed_f16"):
+    """Sec. IV's adaptive N_Ch on the benchmark's system: N_Ch starts at
+    Eq. (nint) and grows until E_f < tol (fresh Lanczos + pair bounds, as the
+    lagged recurrence needs a fixed N_Ch).  The adaptive series reads E_f back
+    on the host per candidate, so the step time is host wall clock."""
+    import torch
+    from paper_1203_6208_gb300 import binding as bnd
+    plan = bnd.Plan(p, precision, max_rhs=args.m, max_cheb=256)
+    if shape_code:
+        plan.set_shape(shape_code)
+    R = torch.tensor(R0, device="cuda")
+    D = plan.alloc_D()
+    stats = bnd.new_stats()
+    kw = dict(m=args.m, n_cheb=0, ef_tol=tol, lanczos_iters=args.lanczos, bound_safety=0.05,
+              dmin_fraction=0.5, seed=99, bounds_mode=0, stats=stats)
+    plan.step(R, D, None, step_index=0, **kw)
+    torch.cuda.synchronize()
+    rows = []
+    t0 = time.perf_counter()
+    for k in range(steps):
+        plan.step(R, D, None, step_index=1 + k, **kw)
+        torch.cuda.synchronize()
+        st = bnd.read_stats(stats)
+        rows.append({"n_cheb": st["n_cheb"], "ef_max": st["ef_max"], "status": st["status"]})
+    ms = (time.perf_counter() - t0) / steps * 1e3
+    plan.close()
+    del D
+    torch.cuda.empty_cache()
+    return {"precision": precision, "ef_tol": tol, "ms_per_step": ms, "steps_per_s": 1e3 / ms,
+            "steps": rows, "max_cheb": 256, "bounds": "fresh Lanczos (30 steps) + pair estimate",
+            "note": "status 6 = BD_ERR_CHEB_NOCONV (max_cheb reached); E_f is recomputed "
+                    "from the final dS (the moment estimate that stops the growth is "
+                    "taken on the same products)"}
+
+
 def measure(args, precision, p, R0, rank, ws):
     """Warm up, then time exactly args.steps bd_step calls on the device."""
     import torch
@@ -399,6 +531,9 @@ def measure(args, precision, p, R0, rank, ws):
     clk = clocks.stop()
     ms = max_over_ranks(ms, ws, "cuda")
     st = bnd.read_stats(stats)
+    # the exact spectrum is checked on the benchmark's own system only (the
+    # reduced sizes serve profiler captures)
+    bounds_check = spectrum_check(plan, D, st, is64) if args.chains == 400 else None
     phases = {name: sum(evs[k][i].elapsed_time(evs[k][i + 1]) for k in range(args.steps))
               / args.steps for i, name in enumerate(bnd.PHASES)}
 
@@ -493,6 +628,7 @@ def measure(args, precision, p, R0, rank, ws):
            "direct_ms_per_step": direct_ms / args.steps,
            "phases_ms": phases, "step_stats": st, "roofline": roof, "gpu_launches": launches,
            "clocks": clk, "e2e": e2e, "n_kvec_half": plan.info.n_kvec,
+           "bounds_check": bounds_check,
            "d_gb": plan.info.d_bytes / 1e9, "product_shape": shape}
     del D
     plan.close()
@@ -550,7 +686,8 @@ def run_ours(args):
                        "parallelism": "replicas" if ws > 1 else "single",
                        "product_shape": r["product_shape"], "launch": r["launch"]},
             "direct_ms_per_step": r["direct_ms_per_step"],
-            "phases_ms": r["phases_ms"], "step_stats": r["step_stats"], "roofline": r["roofline"],
+            "phases_ms": r["phases_ms"], "step_stats": r["step_stats"],
+            "bounds_check": r["bounds_check"], "roofline": r["roofline"],
             "gpu_launches": r["gpu_launches"], "clocks": r["clocks"], "e2e": r["e2e"]}
     for key in ("fp64", "fp64_df"):
         if key not in results or key == head:
@@ -562,14 +699,26 @@ def run_ours(args):
             "products": "FP64 multiply-adds" if key == "fp64" else
                         "double-float on the FP32 pipe (launch shape 4)",
             "alpha_factor": fq, "alpha_sweep_ms": sq, "phases_ms": q["phases_ms"],
-            "step_stats": q["step_stats"], "roofline": q["roofline"],
+            "step_stats": q["step_stats"], "bounds_check": q["bounds_check"],
+            "roofline": q["roofline"],
             "gpu_launches": q["gpu_launches"], "clocks": q["clocks"], "e2e": q["e2e"]}
     if "fp64" in results and head != "fp64":
         line["mixed_speedup_over_fp64"] = r["value"] / results["fp64"]["value"]
+    if head.startswith("mixed") and args.chains == 400:
+        sh = r["product_shape"] or {}
+        code = 3 if "ctas_per_sm" not in sh else int(sh["ctas_per_sm"])
+        line["error_vs_fp64"] = mixed_error_vs_fp64(args, p, R0, code)
+        line["adaptive_nch"] = adaptive_figure(args, p, R0, code)
+        if "fp64_df" in alphas:
+            # the same series in FP64 (double-float products), where E_f can
+            # reach the tolerance (the 16-bit D of the mixed products sets a
+            # floor near 2e-3)
+            line["adaptive_nch_fp64"] = adaptive_figure(args, alphas["fp64_df"][2], R0, 4,
+                                                        steps=1, precision="fp64")
     if ws == 1 and not args.no_cpu_baseline:
         import oracle
         oracle.build()
-        line["cpu_baseline"] = cpu_baseline(p, R0, args.m, args.nch)
+        line["cpu_baseline"] = cpu_baseline(args.chains, R0, args.m, args.nch)
     print(json.dumps(line), flush=True)
 
 
@@ -614,6 +763,36 @@ def run_batch(args):
     st = [bnd.BdStepStats.from_buffer_copy(bytes(stats[i * bnd.STATS_BYTES:(i + 1) * bnd.STATS_BYTES]
                                                  .cpu().numpy().tobytes())) for i in range(b.count)]
     nbeads = sum(c.n for c in cfgs)
+    # the batched Chebyshev loop alone: the same batch at N_Ch = nch and at
+    # N_Ch = 8 (the smallest with the lagged Lanczos column), the difference
+    # over the terms between (each term streams every replica's D16 once)
+    def batch_ms(n_cheb, reps):
+        bb = bnd.Batch(plist, "mixed_f16", max_rhs=m, max_cheb=nch)
+        kk = dict(kw, n_cheb=n_cheb)
+        for _ in range(3):
+            bb.step(R, D, **kk)
+        torch.cuda.synchronize()
+        a, z = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        for _ in range(reps):
+            bb.step(R, D, **kk)
+        z.record()
+        torch.cuda.synchronize()
+        bb.close()
+        return a.elapsed_time(z) / reps
+    t_long, t_short = batch_ms(nch, args.steps), batch_ms(8, args.steps)
+    term_ms = (t_long - t_short) / (nch - 8)
+    d16 = sum(9.0 * c.n * c.n * 2.0 for c in cfgs)
+    vec = sum(3.0 * c.n * (m * (8 * 5 + 4 * 2) + (8 * 5 + 4)) for c in cfgs)
+    peaks, peak_src = measured_peaks()
+    achieved = (d16 + vec) / (term_ms * 1e-3) / 1e9
+    roof = {"bound": "hbm", "kernel": "k_rows_cheb (all replicas' Chebyshev terms, one launch)",
+            "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+            "frac": achieved / peaks["hbm_gbs"],
+            "peak_source": f"hbm_gbs ({peak_src} copy bandwidth)", "traffic": None,
+            "algorithmic_per_term": f"every replica's 16-bit D + vectors = {d16 + vec:.3e} B",
+            "term_ms": term_ms,
+            "how": f"(step at N_Ch = {nch} - step at N_Ch = 8) / {nch - 8} terms, graph replays"}
     line = {"metric": "batched replica steps/sec (64 replicas, N ~ U[200, 2000], mixed)",
             "value": b.count * args.steps / (ms * 1e-3), "unit": "replica-steps/s",
             "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
@@ -626,7 +805,7 @@ def run_batch(args):
             "bead_steps_per_s": nbeads * args.steps / (ms * 1e-3),
             "graph_launches": host_launches,
             "accepted": sum(x.accepted for x in st), "max_ef": max(x.ef_max for x in st),
-            "clocks": clk}
+            "roofline": roof, "clocks": clk}
     print(json.dumps(line), flush=True)
 
 
@@ -697,8 +876,8 @@ def run_theta(args):
 
 
 def fft_size(k):
-    """Smallest multiple of 8 >= k whose prime factors are 2, 3 and 5 (cuFFT
-    runs such sizes fastest; a factor 7 measured ~40 % slower)."""
+    """Smallest multiple of 8 >= k whose prime factors are 2, 3 and 5 (the
+    mesh transforms take radix-2, 3, 4 and 5 passes)."""
     K = int(math.ceil(k / 8.0)) * 8
     while True:
         r = K

@@ -67,7 +67,10 @@ typedef enum {
     BD_FP64 = 0,        /* FP64 everywhere                                          */
     BD_MIXED_F16 = 1,   /* FP32 D assembly; products on tensor cores with IEEE-half
                            operands and FP32 accumulation; FP64 vectors/scalars     */
-    BD_MIXED_BF16 = 2   /* as BD_MIXED_F16 with bfloat16 operands                  */
+    BD_MIXED_BF16 = 2   /* as BD_MIXED_F16 with bfloat16 operands.  bfloat16 keeps 8
+                           significant bits (IEEE half 11): the Brownian term lands
+                           near 5e-3 of the FP64 result, above the 1e-3 bound the
+                           half-precision mode meets; kept for comparison only    */
 } bd_precision;
 
 /* Model and method parameters.  Units: lengths in l_H = sqrt(kT/H), time in
@@ -93,7 +96,8 @@ typedef struct {
     int32_t pme_grid;         /* > 0: matrix-free products use the spectral path:
                                  real space over cell lists (needs r_c < L/2) and the
                                  reciprocal sum on a pme_grid^3 mesh (a multiple
-                                 of 8, >= 2 ceil(sqrt(n2max)) + 2, <= 512); 0: off */
+                                 of 8 with no prime factor above 5, >= 2
+                                 ceil(sqrt(n2max)) + 2, <= 512); 0: off        */
     int32_t pme_order;        /* B-spline order of the mesh, 4..10 and <= pme_grid */
 } bd_params;
 
@@ -389,7 +393,14 @@ bd_status bd_chebyshev_backward(bd_plan *plan, const double *R, const void *D,
  *         FP64-residual refinement of D.F reads that half too; the rest of
  *         the lower triangle is left as it was.  Set the shape before
  *         assembling the D that a product will read.
- * All shapes give the same product up to FP32 summation order.
+ *   5     row-streamed products for a few columns (plans with max_rhs <= 4):
+ *         D16 is read row by row on the CUDA cores with the operand in FP32
+ *         (no 16-bit quantisation of X), FP32 sums in an order fixed by the
+ *         row, and a step's whole Chebyshev series (with the lagged Lanczos
+ *         column) runs as one persistent cooperative launch.  Mixed batches
+ *         (bd_batch_*) of such plans take this shape and run the series of
+ *         all their replicas in that one launch.
+ * Shapes 1-3 give the same product up to FP32 summation order.
  * Launch shapes of the FP64 plans' product Y = D X:
  *   0     (default) FP64 multiply-adds;
  *   4     double-float on the FP32 pipe: each FP64 entry of D and X is split
@@ -409,20 +420,38 @@ bd_status bd_chebyshev_backward(bd_plan *plan, const double *R, const void *D,
  * (BD_ERR_INVALID for 4 on a mixed plan; an FP64 plan takes 1..3 as 0).   */
 #define BD_SHAPE_SYMMETRIC 3
 #define BD_SHAPE_F64_DOUBLE_FLOAT 4
+#define BD_SHAPE_ROWS 5
 
-/* Autotuner: for a mixed plan, times the tensor-core product on D (its
- * contents do not matter) in shapes 1, 2 and 3 and keeps the fastest for all
- * later products of this plan; returns the choice in *split_out and the time
- * per product (ms).  Synchronous.  FP64 plans: no-op (0).                 */
+/* Autotuner: for a mixed plan, times the product of max_rhs + 1 columns on D
+ * (its contents do not matter) in shapes 1, 2, 3 and, when max_rhs <= 4, 5,
+ * and keeps the fastest for all later products of this plan; returns the
+ * choice in *split_out and the time per product (ms).  Synchronous.  FP64
+ * plans: no-op (0).                                                       */
 bd_status bd_plan_autotune(bd_plan *plan, void *D, int32_t *split_out, float *ms_out,
                            bd_stream stream);
 
-/* Set the launch shape (0..4, above) of the plan's later products without
+/* Set the launch shape (0..5, above) of the plan's later products without
  * timing.  Shape 3 allocates its schedule and partial buffers on first use,
- * shape 4 its split operand (64 x 3N floats), both synchronous and
- * BD_ERR_OOM if they do not fit.  BD_ERR_INVALID outside 0..4 and for 4 on a
- * mixed plan; FP64 plans take 1..3 as 0 (FP64 multiply-adds).             */
+ * shape 4 its split operand (64 x 3N floats), shape 5 its FP32 operand and
+ * work-queue tables, all synchronous and BD_ERR_OOM if they do not fit.
+ * BD_ERR_INVALID outside 0..5, for 4 on a mixed plan and for 5 on a mixed
+ * plan with max_rhs > 4; FP64 plans take 1..3 and 5 as 0 (FP64
+ * multiply-adds).                                                         */
 bd_status bd_plan_set_shape(bd_plan *plan, int32_t shape);
+
+/* Test hook for the device-side failure path (the paper has no counterpart;
+ * it exercises the bounded waits of the tensor-core kernels without a GPU
+ * fault).  Arms the next symmetric product that the plan launches or records
+ * (a mixed plan in launch shape 3): in that product, CTA `cta` (0 <= cta <
+ * SM count) waits on an mbarrier that nothing completes, gives up after a
+ * bounded spin as any wait that ran out does, and takes the abort path: it
+ * records BD_ERR_TIMEOUT in the plan's status word, lets its copies in
+ * flight land, frees its TMEM and returns.  That product's output is
+ * invalid; a bd_step containing it rejects the proposal (R unchanged,
+ * stats.status = BD_ERR_TIMEOUT, accepted = 0).  The hook disarms itself
+ * after one product; cta < 0 disarms it.  BD_ERR_INVALID on an FP64 plan,
+ * in another shape, or for cta >= the SM count.                           */
+bd_status bd_plan_test_stall(bd_plan *plan, int32_t cta);
 
 /* Set the plan's device step counter used by BD_STEP_DEVICE_COUNTER (stream-
  * ordered write of one uint64). */
@@ -440,7 +469,14 @@ bd_status bd_plan_set_step_counter(bd_plan *plan, uint64_t value, bd_stream stre
  * batched step into one CUDA graph (one branch per replica on its own stream,
  * forked from and joined back to `stream`), and every later call with the
  * same arguments is a single graph launch.  Changing R, D, opts or stats
- * pointers re-records the graph.  Not thread-safe per batch.            */
+ * pointers re-records the graph.  Mixed batches whose replicas have
+ * max_rhs <= 4 put every plan in launch shape 5: each replica's step then
+ * runs its front (forces, D, bounds, first product) on its branch, the
+ * Chebyshev series of ALL replicas runs as one persistent launch over a work
+ * queue of {replica, 64-row block} items (a bounded grid barrier between
+ * terms), and each replica's back (E_f, lagged bounds, Euler update) follows
+ * on its branch; a replica's results are bitwise those of its plan alone in
+ * the same shape.  Not thread-safe per batch.                            */
 typedef struct bd_batch bd_batch;
 bd_status bd_batch_create(const bd_params *params, int32_t count, bd_batch **out_batch);
 void bd_batch_destroy(bd_batch *batch);

@@ -33,7 +33,8 @@ BOUNDS_MODES = {"fresh": 0, "lagged": 1, "fixman_dilute": 2, "fixman_semidilute"
 EXPORTS = ["bd_plan_create", "bd_plan_destroy", "bd_plan_query", "bd_forces", "bd_build_D",
            "bd_apply_D", "bd_eig_bounds", "bd_chebyshev_sqrt", "bd_step", "bd_wiener",
            "bd_set_phase_events", "bd_kernel_launches", "bd_eig_bounds_noalloc",
-           "bd_apply_D_backward", "bd_chebyshev_backward", "bd_plan_autotune", "bd_plan_set_shape", "bd_step_capture", "bd_step_replay", "bd_product_timing",
+           "bd_apply_D_backward", "bd_chebyshev_backward", "bd_plan_autotune", "bd_plan_set_shape",
+           "bd_plan_test_stall", "bd_step_capture", "bd_step_replay", "bd_product_timing",
            "bd_plan_set_step_counter", "bd_batch_create", "bd_batch_destroy", "bd_batch_query",
            "bd_batch_step", "bd_chebyshev_sqrt_adaptive", "bd_apply_D_matfree",
            "bd_last_error", "bd_version"]
@@ -108,6 +109,7 @@ def load(path: str = LIB_PATH):
     L.bd_apply_D_backward.argtypes = [_vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp]
     L.bd_plan_set_shape.argtypes = [_vp, i32]
     L.bd_plan_set_shape.restype = i32
+    L.bd_plan_test_stall.argtypes = [_vp, i32]
     L.bd_plan_autotune.argtypes = [_vp, _vp, ctypes.POINTER(i32), ctypes.POINTER(ctypes.c_float),
                                    _vp]
     L.bd_plan_set_step_counter.argtypes = [_vp, u64, _vp]
@@ -299,6 +301,11 @@ class Plan:
         FP64 plans: 0 FP64 multiply-adds, 4 double-float on the FP32 pipe
         (BD_SHAPE_F64_DOUBLE_FLOAT)."""
         _check(load().bd_plan_set_shape(self._h, int(shape)))
+
+    def test_stall(self, cta: int):
+        """bd_plan_test_stall: the next symmetric product's CTA `cta` takes the
+        bounded-wait failure path (a test of the device-side error handling)."""
+        _check(load().bd_plan_test_stall(self._h, int(cta)))
 
     def autotune(self, D, stream=None):
         sp = ctypes.c_int32()

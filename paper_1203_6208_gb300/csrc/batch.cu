@@ -1,12 +1,15 @@
 // batch.cu -- many independent replicas (uneven N) advanced together.
 //
 // One plan per replica.  A step of the batch forks `count` branches from the
-// caller's stream (one non-blocking stream per replica), runs bd_step for
-// each replica on its branch and joins them back.  From the second call on,
-// that whole fork/step/join sequence is recorded once into a CUDA graph and
-// replayed with a single cudaGraphLaunch per step, so the host issues one
-// launch per batched step and the GPU runs the replicas' kernels
-// concurrently (small replicas do not fill the GPU on their own).  Wiener
+// caller's stream (one non-blocking stream per replica) and joins them back.
+// Mixed plans with a few Wiener columns (max_rhs <= 4) take the row-streamed
+// product shape, and their step runs in three parts: every replica's front
+// (forces, D(R), bounds, the first product, V_1) on its branch; then the
+// Chebyshev loops of ALL replicas in one persistent launch, a work queue over
+// {replica, 64-row block} (rows_gemm.cu); then every replica's back (E_f,
+// lagged bounds, Euler update) on its branch.  Otherwise each branch runs a
+// whole bd_step.  From the second call on, the sequence is recorded once into
+// a CUDA graph and replayed with a single cudaGraphLaunch per step.  Wiener
 // increments are drawn on the device with the plan's device step counter,
 // so every replay draws new noise.
 #include <string.h>
@@ -15,6 +18,7 @@
 #include <vector>
 
 #include "bd_internal.cuh"
+#include "rows_gemm.cuh"
 
 struct bd_batch {
     int count = 0;
@@ -32,6 +36,14 @@ struct bd_batch {
     bd_step_stats *key_stats = nullptr;
     bd_step_opts key_opts;
     int calls = 0;
+    // the batched Chebyshev loop (all plans in the row-streamed shape)
+    int rows = 0;                    // 1: the plans use launch shape 5
+    std::vector<int> item0;          // first work item of each replica
+    int nitems = 0;
+    bd::RowsRep *d_reps = nullptr;   // [count] table entries, written by each front part
+    int *d_items = nullptr;          // item -> replica
+    unsigned *d_bar = nullptr;       // grid barrier words
+    cudaEvent_t mid_ev = nullptr;    // fork of the back parts
 };
 
 using namespace bd;
@@ -44,6 +56,10 @@ static void destroy_batch(bd_batch *b)
     for (auto s : b->streams) if (s) cudaStreamDestroy(s);
     for (auto e : b->join_ev) if (e) cudaEventDestroy(e);
     if (b->fork_ev) cudaEventDestroy(b->fork_ev);
+    if (b->mid_ev) cudaEventDestroy(b->mid_ev);
+    if (b->d_reps) cudaFree(b->d_reps);
+    if (b->d_items) cudaFree(b->d_items);
+    if (b->d_bar) cudaFree(b->d_bar);
     if (b->origin) cudaStreamDestroy(b->origin);
     for (auto p : b->plans) bd_plan_destroy(p);
     delete b;
@@ -82,9 +98,43 @@ bd_status bd_batch_create(const bd_params *params, int32_t count, bd_batch **out
         }
     }
     if (cudaEventCreateWithFlags(&b->fork_ev, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&b->mid_ev, cudaEventDisableTiming) != cudaSuccess ||
         cudaStreamCreateWithFlags(&b->origin, cudaStreamNonBlocking) != cudaSuccess) {
         destroy_batch(b);
         return set_error(BD_ERR_CUDA, "event creation failed");
+    }
+    // mixed replicas with few columns: the row-streamed shape and one
+    // persistent Chebyshev launch for all of them
+    bool rows = true;
+    for (int i = 0; i < count; i++)
+        rows = rows && params[i].precision != BD_FP64 && params[i].max_rhs + 4 <= kRowsMaxCols;
+    if (rows) {
+        for (int i = 0; i < count; i++) {
+            bd_status st = bd_plan_set_shape(b->plans[i], kRowsShape);
+            if (st != BD_OK) {
+                destroy_batch(b);
+                return st;
+            }
+        }
+        std::vector<int> items;
+        for (int i = 0; i < count; i++) {
+            b->item0.push_back(b->nitems);
+            const int k = step_part_items(b->plans[i]);
+            for (int t = 0; t < k; t++) items.push_back(i);
+            b->nitems += k;
+        }
+        cudaError_t e = cudaMalloc(&b->d_reps, sizeof(RowsRep) * count);
+        if (e == cudaSuccess) e = cudaMalloc(&b->d_items, sizeof(int) * items.size());
+        if (e == cudaSuccess) e = cudaMalloc(&b->d_bar, 4 * sizeof(unsigned));
+        if (e == cudaSuccess)
+            e = cudaMemcpy(b->d_items, items.data(), sizeof(int) * items.size(), cudaMemcpyHostToDevice);
+        if (e == cudaSuccess) e = cudaMemset(b->d_bar, 0, 4 * sizeof(unsigned));
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            destroy_batch(b);
+            return set_error(BD_ERR_OOM, "batch work queue: %s", cudaGetErrorString(e));
+        }
+        b->rows = 1;
     }
     *out_batch = b;
     return BD_OK;
@@ -106,10 +156,48 @@ bd_status bd_batch_query(const bd_batch *b, int32_t index, bd_plan_info *info, i
     return BD_OK;
 }
 
+// fork from `stream`, the replicas' fronts, one launch of all their
+// Chebyshev loops, the replicas' backs, join back
+static bd_status batch_body_rows(bd_batch *b, double *R, void *D, const bd_step_opts *opts,
+                                 bd_step_stats *stats, cudaStream_t stream)
+{
+    if (cudaEventRecord(b->fork_ev, stream) != cudaSuccess) return check_launch("batch fork");
+    int lag = 0;
+    for (int i = 0; i < b->count; i++) {
+        cudaStreamWaitEvent(b->streams[i], b->fork_ev, 0);
+        bd_step_opts o = *opts;
+        o.seed = opts->seed + (uint64_t)i;
+        o.flags |= BD_STEP_DEVICE_COUNTER;
+        bd_status st = step_part(b->plans[i], R + b->r_off[i], (char *)D + b->d_off[i], &o,
+                                 stats ? stats + i : nullptr, b->streams[i], 1, b->d_reps + i,
+                                 b->item0[i]);
+        if (st != BD_OK) return st;
+        lag = step_part_lag(b->plans[i]);
+        cudaEventRecord(b->join_ev[i], b->streams[i]);
+        cudaStreamWaitEvent(stream, b->join_ev[i], 0);
+    }
+    bd_status st = rows_cheb_launch(b->d_reps, b->count, b->d_items, b->nitems, opts->m + lag,
+                                    opts->n_cheb, lag ? 0 : -1, b->d_bar,
+                                    plan_device(b->plans[0]), stream);
+    if (st != BD_OK) return st;
+    if (cudaEventRecord(b->mid_ev, stream) != cudaSuccess) return check_launch("batch fork");
+    for (int i = 0; i < b->count; i++) {
+        cudaStreamWaitEvent(b->streams[i], b->mid_ev, 0);
+        st = step_part(b->plans[i], R + b->r_off[i], (char *)D + b->d_off[i], opts,
+                       stats ? stats + i : nullptr, b->streams[i], 2, nullptr, 0);
+        if (st != BD_OK) return st;
+        cudaEventRecord(b->join_ev[i], b->streams[i]);
+        cudaStreamWaitEvent(stream, b->join_ev[i], 0);
+    }
+    return check_launch("batch step");
+}
+
 // fork from `stream`, one bd_step per replica on its branch, join back
 static bd_status batch_body(bd_batch *b, double *R, void *D, const bd_step_opts *opts,
                             bd_step_stats *stats, cudaStream_t stream)
 {
+    if (b->rows && step_batchable(b->plans[0], opts))
+        return batch_body_rows(b, R, D, opts, stats, stream);
     if (cudaEventRecord(b->fork_ev, stream) != cudaSuccess) return check_launch("batch fork");
     for (int i = 0; i < b->count; i++) {
         cudaStreamWaitEvent(b->streams[i], b->fork_ev, 0);

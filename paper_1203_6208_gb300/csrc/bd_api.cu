@@ -9,6 +9,7 @@
 #include "bd_internal.cuh"
 #include "sym_gemm.cuh"
 #include "tc_gemm.cuh"
+#include "rows_gemm.cuh"
 #include "adjoint.cuh"
 #include "recip_tc.cuh"
 #include "adaptive.cuh"
@@ -77,7 +78,8 @@ static void free_plan(Plan &P)
                     P.d_coef, P.d_wdw, P.d_red, P.d_redpart, P.d_bounds, P.d_status, P.d_lq[0], P.d_lq[1],
                     P.d_lq[2], P.d_lab, P.d_x16, P.d_xscale, P.d_part, P.d_counters,
                     P.d_stats_scratch, P.d_y32, P.d_lag_bounds, P.d_pairw, P.d_step_ctr, P.d_vhist, P.d_xhist, P.d_ubuf[0], P.d_ubuf[1],
-                    P.d_ubuf[2], P.d_ubuf[3], P.d_xdf, P.d_Uh, P.d_Ul, P.d_rtiles, P.d_kbasis, P.d_lanpart, P.d_mom, P.d_sfac, P.d_mfW, P.d_mfpart};
+                    P.d_ubuf[2], P.d_ubuf[3], P.d_xdf, P.d_Uh, P.d_Ul, P.d_rtiles, P.d_kbasis, P.d_lanpart, P.d_mom, P.d_sfac, P.d_mfW, P.d_mfpart,
+                    P.d_x32, P.d_rows_part, P.d_rows_rep, P.d_rows_items, P.d_rows_bar};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     if (P.h_est) cudaFreeHost(P.h_est);
@@ -113,6 +115,11 @@ static bd_status validate(const bd_params *p)
         if (p->pme_grid % 8 != 0 || p->pme_grid > 512 || p->pme_grid < 2 * kmax + 2)
             return set_error(BD_ERR_INVALID, "pme_grid must be a multiple of 8, <= 512 and >= 2 "
                              "sqrt(n2max) + 2 = %d", 2 * kmax + 2);
+        int r = p->pme_grid;
+        for (int f : {2, 3, 5})
+            while (r % f == 0) r /= f;
+        if (r != 1)
+            return set_error(BD_ERR_INVALID, "pme_grid must have no prime factor other than 2, 3, 5");
         if (p->pme_order < 4 || p->pme_order > 10 || p->pme_order > p->pme_grid)
             return set_error(BD_ERR_INVALID, "pme_order must be in [4, 10] and <= pme_grid");
         if (!(p->r_c < 0.5 * p->box_L))
@@ -336,7 +343,8 @@ static bd_status apply_core(Plan &P, const void *D, const double *X, int m, doub
     float *D32;
     void *D16;
     split_mixed(P, (void *)D, &D32, &D16);
-    bd_status st = tc_apply(P, D16, X, m, Y, s);
+    bd_status st = P.tc_split == kRowsShape && m <= kRowsMaxCols ? rows_apply(P, D16, X, m, Y, s)
+                                                                   : tc_apply(P, D16, X, m, Y, s);
     if (st != BD_OK) return st;
     if (flags & BD_APPLY_REFINE) {
         launch_refine_f32(P, D32, X, m, Y, s);
@@ -400,16 +408,46 @@ bd_status bd_eig_bounds(bd_plan *plan, const void *D, int32_t iters, double safe
     return eig_bounds_core(plan->P, D, iters, safety_max, dmin_fraction, bounds, status, stream);
 }
 
-// Chebyshev recurrence given W = D dW; dS and E_f outputs
+// parts of a Chebyshev series / of a step: the batch runs the front of every
+// replica, then all replicas' loops in one launch, then the backs
+enum StepPart { kPartAll = 0, kPartFront = 1, kPartBack = 2 };
+
+// the plan's products run the whole loop in one launch (shape 5, dense D)
+static bool rows_loop(const Plan &P) { return is_mixed(P) && !P.matfree_R && P.tc_split == kRowsShape; }
+
+// Chebyshev recurrence given W = D dW; dS and E_f outputs.  kPartFront stops
+// after V_1 (and, in shape 5, writes the loop's table entry to *slot);
+// kPartBack runs only E_f.
 static bd_status cheb_core(Plan &P, const void *D, const double *bounds, int nch,
                            const double *dW, const double *W, int m, double *dS, double *Ef,
-                           bd_step_stats *stats, cudaStream_t s, int lanczos_from = -1)
+                           bd_step_stats *stats, cudaStream_t s, int lanczos_from = -1,
+                           int part = kPartAll, RowsRep *slot = nullptr, int item0 = 0)
 {
     // lanczos_from >= 0: a Lanczos recurrence (its step lanczos_from already
     // taken) rides as an extra column of every product (mixed plans only)
+    if (part == kPartBack) {
+        launch_ef(P, dW, W, dS, m, Ef, stats, s);
+        return check_launch("chebyshev");
+    }
     launch_cheb_coeffs(P, bounds, nch, s);
     double *A = P.d_V[0], *B = P.d_V[1];
     launch_cheb_first(P, bounds, dW, W, m, A, B, dS, s);   // A = V0, B = V1
+    if (rows_loop(P)) {
+        float *D32;
+        void *D16;
+        split_mixed(P, (void *)D, &D32, &D16);
+        const int lan = lanczos_from >= 0 ? 1 : 0;
+        RowsRep rep = rows_rep(P, D16, P.d_coef, bounds, m, lan, dS);
+        rep.item0 = item0;
+        rows_cheb_prepare(P, rep, slot ? slot : (RowsRep *)P.d_rows_rep, B, lan, s);
+        if (part == kPartFront) return check_launch("chebyshev");
+        bd_status st = rows_cheb_launch((const RowsRep *)P.d_rows_rep, 1, P.d_rows_items,
+                                        rep.nitems, m + lan, nch, lanczos_from, P.d_rows_bar,
+                                        P.device, s);
+        if (st != BD_OK) return st;
+        launch_ef(P, dW, W, dS, m, Ef, stats, s);
+        return check_launch("chebyshev");
+    }
     double *prev2 = A, *prev1 = B;
     for (int p = 2; p < nch; p++) {
         if (P.matfree_R) {
@@ -542,8 +580,9 @@ bd_status bd_plan_autotune(bd_plan *plan, void *D, int32_t *split_out, float *ms
 bd_status bd_plan_set_shape(bd_plan *plan, int32_t shape)
 {
     if (!plan) return set_error(BD_ERR_INVALID, "NULL plan");
-    if (shape < 0 || shape > kF64DoubleFloat) return set_error(BD_ERR_INVALID, "shape %d outside 0..4", shape);
+    if (shape < 0 || shape > kRowsShape) return set_error(BD_ERR_INVALID, "shape %d outside 0..5", shape);
     Plan &P = plan->P;
+    if (!is_mixed(P) && shape == kRowsShape) shape = 0;
     if (!is_mixed(P)) {
         // FP64 plans: 4 selects the double-float products, anything else DFMA
         if (shape == kF64DoubleFloat && !P.d_xdf) {
@@ -554,11 +593,34 @@ bd_status bd_plan_set_shape(bd_plan *plan, int32_t shape)
         return BD_OK;
     }
     if (shape == kF64DoubleFloat) return set_error(BD_ERR_INVALID, "shape 4 is for FP64 plans");
+    if (shape == kRowsShape) {
+        // a step's first product carries m + 4 columns at most (F, the Lanczos
+        // vector, Fixman's two vectors)
+        if (P.p.max_rhs + 4 > kRowsMaxCols)
+            return set_error(BD_ERR_INVALID, "shape 5 needs max_rhs <= %d", kRowsMaxCols - 4);
+        bd_status st = rows_plan_init(P);
+        if (st != BD_OK) return st;
+    }
     if (shape == kSymShape) {
         bd_status st = sym_plan_init(P);
         if (st != BD_OK) return st;
     }
     P.tc_split = shape;
+    return BD_OK;
+}
+
+bd_status bd_plan_test_stall(bd_plan *plan, int32_t cta)
+{
+    if (!plan) return set_error(BD_ERR_INVALID, "NULL plan");
+    Plan &P = plan->P;
+    if (cta < 0) {
+        P.test_stall = 0;
+        return BD_OK;
+    }
+    if (!is_mixed(P) || P.tc_split != kSymShape)
+        return set_error(BD_ERR_INVALID, "the stall hook needs a mixed plan in the symmetric shape");
+    if (cta >= P.num_sms) return set_error(BD_ERR_INVALID, "cta %d outside the product's grid", cta);
+    P.test_stall = cta + 1;
     return BD_OK;
 }
 
@@ -646,8 +708,73 @@ bd_status bd_wiener(bd_plan *plan, uint64_t seed, uint64_t step_index, int64_t c
     return check_launch("bd_wiener");
 }
 
+}  // extern "C"
+
+namespace bd {
+
+// the end of a step after its Chebyshev series: the lagged Lanczos bounds of
+// the next step, the Euler update with FENE rejection, the drift copy-out
+static bd_status step_finish(Plan &P, const StepCtx &c, cudaStream_t s)
+{
+    if (c.lag) {             // N_Ch - 1 Lanczos steps -> bounds of the next step
+        launch_lanczos_finish(P, c.nch - 1, c.bound_safety, c.dmin_fraction, P.d_lag_bounds,
+                              nullptr, s);
+        P.lag_valid = 1;
+    }
+    if (P.phase_on) cudaEventRecord(P.phase_ev[5], s);
+    // (a8) Euler update with FENE rejection
+    launch_euler(P, c.R, c.DFd, c.dSd, c.st_dev, s);
+    if (P.phase_on) cudaEventRecord(P.phase_ev[6], s);
+    if (c.DF) cudaMemcpyAsync(c.DF, c.DFd, (size_t)P.n3 * sizeof(double), cudaMemcpyDeviceToDevice, s);
+    return check_launch("bd_step");
+}
+
+static bd_status step_run(bd_plan *plan, double *R, void *D, const double *dW,
+                          const bd_step_opts *o, double *DF, double *dS, bd_step_stats *stats,
+                          cudaStream_t stream, int part, RowsRep *slot, int item0);
+
+bool step_batchable(bd_plan *plan, const bd_step_opts *o)
+{
+    const Plan &P = plan->P;
+    return o && is_mixed(P) && P.tc_split == kRowsShape && o->n_cheb >= 3 &&
+           !(o->flags & BD_STEP_MATRIX_FREE) && o->m >= 1 && o->m + 1 <= kRowsMaxCols;
+}
+
+int step_part_lag(bd_plan *plan) { return plan->P.step_ctx.lag; }
+int step_part_items(bd_plan *plan) { return rows_items(plan->P.n3); }
+int plan_device(bd_plan *plan) { return plan->P.device; }
+
+bd_status step_part(bd_plan *plan, double *R, void *D, const bd_step_opts *o,
+                    bd_step_stats *stats, cudaStream_t s, int part, RowsRep *slot, int item0)
+{
+    if (part == kPartBack) {
+        Plan &P = plan->P;
+        const StepCtx &c = P.step_ctx;
+        bd_status st = cheb_core(P, c.D, P.d_bounds, c.nch, c.w, c.Wcols, c.m, c.dSd, nullptr,
+                                 c.st_dev, s, c.lag ? 0 : -1, kPartBack);
+        if (st != BD_OK) return st;
+        return step_finish(P, c, s);
+    }
+    return step_run(plan, R, D, nullptr, o, nullptr, nullptr, stats, s, part, slot, item0);
+}
+
+}  // namespace bd
+
+extern "C" {
+
 bd_status bd_step(bd_plan *plan, double *R, void *D, const double *dW, const bd_step_opts *o,
                   double *DF, double *dS, bd_step_stats *stats, bd_stream stream)
+{
+    return step_run(plan, R, D, dW, o, DF, dS, stats, stream, kPartAll, nullptr, 0);
+}
+
+}  // extern "C"
+
+namespace bd {
+
+static bd_status step_run(bd_plan *plan, double *R, void *D, const double *dW,
+                          const bd_step_opts *o, double *DF, double *dS, bd_step_stats *stats,
+                          cudaStream_t stream, int part, RowsRep *slot, int item0)
 {
     if (!plan || !R || !o) return set_error(BD_ERR_INVALID, "NULL argument");
     Plan &P = plan->P;
@@ -781,28 +908,29 @@ bd_status bd_step(bd_plan *plan, double *R, void *D, const double *dW, const bd_
     PHASE(4);
     // (a7) Chebyshev
     double *dSd = dS ? dS : P.d_dS;
+    StepCtx c{R, D, w, Wcols, dSd, st_dev, DFd, DF, m, o->n_cheb, lag ? 1 : 0, o->bound_safety,
+              o->dmin_fraction};
+#undef PHASE
     if (adaptive) {
         int N = 0, conv = 0;
         st = cheb_adaptive_core(P, D, P.d_bounds, o->ef_tol, w, Wcols, m, dSd, nullptr, st_dev, s,
                                 &N, &conv);
+    } else if (part == kPartFront) {
+        // the batch runs every replica's loop in one launch, then the backs
+        P.step_ctx = c;
+        return cheb_core(P, D, P.d_bounds, o->n_cheb, w, Wcols, m, dSd, nullptr, st_dev, s,
+                         lag ? 0 : -1, kPartFront, slot, item0);
     } else {
         st = cheb_core(P, D, P.d_bounds, o->n_cheb, w, Wcols, m, dSd, nullptr, st_dev, s,
                        lag ? 0 : -1);
     }
     if (st != BD_OK) return st;
-    if (lag) {               // N_Ch - 1 Lanczos steps -> bounds of the next step
-        launch_lanczos_finish(P, o->n_cheb - 1, o->bound_safety, o->dmin_fraction,
-                              P.d_lag_bounds, nullptr, s);
-        P.lag_valid = 1;
-    }
-    PHASE(5);
-    // (a8) Euler update with FENE rejection
-    launch_euler(P, R, DFd, dSd, st_dev, s);
-    PHASE(6);
-#undef PHASE
-    if (DF) cudaMemcpyAsync(DF, DFd, n3 * sizeof(double), cudaMemcpyDeviceToDevice, s);
-    return check_launch("bd_step");
+    return step_finish(P, c, s);
 }
+
+}  // namespace bd
+
+extern "C" {
 
 static bd_status ensure_backward_scratch(Plan &P)
 {

@@ -68,6 +68,20 @@ constexpr int kLdAlign = 64;          // D leading dimension multiple (elements)
 struct PmeState;
 struct SymState;
 
+// what a step's front part leaves for its back part (the batched loop runs
+// in between)
+struct StepCtx {
+    double *R;
+    const void *D;
+    const double *w, *Wcols;
+    double *dSd;
+    bd_step_stats *st_dev;
+    const double *DFd;
+    double *DF;
+    int m, nch, lag;
+    double bound_safety, dmin_fraction;
+};
+
 struct Plan {
     bd_params p;
     int device;
@@ -116,6 +130,8 @@ struct Plan {
     double *d_lanpart;                 // Lanczos dot partials per row block [3 * blocks]
     int ldx;                           // leading dimension of d_x16 (elements)
     int tc_split;                      // resident CTAs per SM of the tensor-core product (0: 2)
+    int test_stall;                    // bd_plan_test_stall: CTA + 1 of the next symmetric
+                                       //   product that stalls (0: none; one-shot)
     int tc_maxslots;                   // partial slots per row block (stream-K schedule)
     SymState *sym;                     // symmetric product schedule (mixed plans)
     float *d_xdf;                      // FP64 plans, shape 4: split operand [2][kMaxRhs][3N]
@@ -158,6 +174,14 @@ struct Plan {
     __half *d_Uh, *d_Ul;               // U as hi/lo words, half(word 2^8) [3N][recip_kp]
     int2 *d_rtiles;                    // block list (128-row tile, 256-column block)
     float *d_kbasis;                   // per k: w u1, w u2 (FP32) [nk][8]
+    // launch shape 5 (rows_gemm.cu): row-streamed products of a few columns
+    float *d_x32;                      // FP32 operand, 2 x [kRowsMaxCols][x32_stride]
+    int x32_stride;                    // 3N rounded up to 8
+    double *d_rows_part;               // Lanczos dot partials per 64-row item
+    void *d_rows_rep;                  // the plan's one-replica table (RowsRep)
+    int *d_rows_items;                 // item -> replica (all 0 for a single plan)
+    unsigned *d_rows_bar;              // grid barrier {count, generation}, Lanczos item count
+    StepCtx step_ctx;                  // kept between the parts of a batched step
 };
 
 inline bool is_mixed(const Plan &P) { return P.p.precision != BD_FP64; }

@@ -194,9 +194,10 @@ k_recip_syrk(const __grid_constant__ CUtensorMap mapH, const __grid_constant__ C
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     const uint32_t tmem = tmem_base_sh;
 
+    int issued = 0;                      // the producer's loads, for the drain after an abort
     if (warp == 0 && lane == 0) {
         // ---- TMA producer
-        int it = 0, issued = 0;
+        int it = 0;
         for (int bi = c; bi < nblocks && !abort_flag; bi += G) {
             const int2 t2 = blocks[bi];
             for (int i = 0; i < nsteps; i++, it++) {
@@ -212,13 +213,6 @@ k_recip_syrk(const __grid_constant__ CUtensorMap mapH, const __grid_constant__ C
                 tma_load_2d(a, ma, kk * BK, t2.x * BM, fb);
                 tma_load_2d(b, mb, kk * BK, t2.y * BN, fb);
                 issued = it + 1;
-            }
-        }
-        if (abort_flag) {
-            for (int i = (issued > STAGES ? issued - STAGES : 0); i < issued; i++) {
-                const int st = i % STAGES;
-                const uint32_t ph = (uint32_t)(i / STAGES) & 1u;
-                for (uint32_t t = 0; t < kWaitLimit && !mbar_try(smem_u32(&full_bar[st]), ph); t++) {}
             }
         }
     } else if (warp == 1 && lane == 0) {
@@ -289,7 +283,18 @@ k_recip_syrk(const __grid_constant__ CUtensorMap mapH, const __grid_constant__ C
             mbar_arrive_cta(smem_u32(&acc_empty[buf]));
         }
     }
-    if (threadIdx.x == 0 && abort_flag) atomicExch(err, (int32_t)BD_ERR_TIMEOUT);
+    // teardown: abort_flag is final once every thread is here; after an abort
+    // the producer lets every load it issued land before the CTA exits
+    __syncthreads();
+    if (abort_flag) {
+        if (warp == 0 && lane == 0)
+            for (int i = (issued > STAGES ? issued - STAGES : 0); i < issued; i++) {
+                const int st = i % STAGES;
+                const uint32_t ph = (uint32_t)(i / STAGES) & 1u;
+                for (uint32_t t = 0; t < kWaitLimit && !mbar_try(smem_u32(&full_bar[st]), ph); t++) {}
+            }
+        if (threadIdx.x == 0) atomicExch(err, (int32_t)BD_ERR_TIMEOUT);
+    }
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
     if (warp == 1) {

@@ -147,7 +147,8 @@ __device__ __forceinline__ uint64_t sw128_desc_mn(uint32_t addr, uint32_t lbo)
 template <int BN>
 __global__ void __launch_bounds__(THREADS, 1)
 k_sym_gemm(const __grid_constant__ CUtensorMap mapD, const __grid_constant__ CUtensorMap mapX,
-           Geo g, int m, int is_bf16, float *__restrict__ part, int32_t *__restrict__ err)
+           Geo g, int m, int is_bf16, float *__restrict__ part, int32_t *__restrict__ err,
+           int stall_cta)
 {
     constexpr int ST = stages<BN>();
     constexpr int XB = xbox<BN>();
@@ -164,7 +165,7 @@ k_sym_gemm(const __grid_constant__ CUtensorMap mapD, const __grid_constant__ CUt
     uint8_t *vband = smem + ST * STAGE;
     __shared__ __align__(8) uint64_t full_bar[ST], empty_bar[ST];
     __shared__ __align__(8) uint64_t vb_full, vb_empty, row_full, row_empty, col_full[2],
-        col_empty[2], drain_bar;
+        col_empty[2], drain_bar, stall_bar;
     __shared__ uint32_t tmem_base_sh;
     __shared__ volatile int abort_flag;
 
@@ -189,6 +190,7 @@ k_sym_gemm(const __grid_constant__ CUtensorMap mapD, const __grid_constant__ CUt
             tc::mbar_init(tc::smem_u32(&col_empty[q]), 128);
         }
         tc::mbar_init(tc::smem_u32(&drain_bar), 1);
+        tc::mbar_init(tc::smem_u32(&stall_bar), 1);          // never completed
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     }
@@ -203,13 +205,21 @@ k_sym_gemm(const __grid_constant__ CUtensorMap mapD, const __grid_constant__ CUt
     __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     const uint32_t tmem = tmem_base_sh;
+    // launched as a programmatic dependent of the kernel before it: the set-up
+    // above overlapped that kernel's tail; its outputs (the operand X, and the
+    // partial slots this kernel overwrites) are used only after this wait
+    tc::grid_dep_wait();
+    if (threadIdx.x == 0) tc::grid_dep_launch();
+    // the producer's record of its loads, for the drain after an abort
+    int issued = 0, pseg = 0;
+    bool vb_pending = false;
 
     if (warp == 0 && lane == 0) {
         // ---- TMA producer
+        const uint64_t pol_d = tc::l2_evict_first_policy();
         It t;
         it_seek(t, u0, g.boff, g.nb, T);
-        int issued = 0, seg = 0, pb = -1;
-        bool vb_pending = false;
+        int seg = 0, pb = -1;
         for (int i = 0; i < nunits; i++) {
             if (t.b != pb) {
                 // the band's operand rows X_I, once the previous band's MMAs are done
@@ -233,24 +243,14 @@ k_sym_gemm(const __grid_constant__ CUtensorMap mapD, const __grid_constant__ CUt
             const uint32_t a = tc::smem_u32(smem + s * STAGE);
             const uint32_t fb = tc::smem_u32(&full_bar[s]);
             tc::mbar_expect_tx(fb, STAGE);
-            tc::tma_load_2d(a, &mapD, t.J * BM, t.I * BM, fb);
-            tc::tma_load_2d(a + BM * BK * 2, &mapD, t.J * BM + BK, t.I * BM, fb);
+            tc::tma_load_2d_hint(a, &mapD, t.J * BM, t.I * BM, fb, pol_d);
+            tc::tma_load_2d_hint(a + BM * BK * 2, &mapD, t.J * BM + BK, t.I * BM, fb, pol_d);
             tc::tma_load_2d(a + A_TILE, &mapX, t.J * BM, 0, fb);
             tc::tma_load_2d(a + A_TILE + XB, &mapX, t.J * BM + BK, 0, fb);
             issued = i + 1;
             it_next(t, T);
         }
-        if (abort_flag) {
-            // let every load issued land before the CTA can exit
-            for (int i = (issued > ST ? issued - ST : 0); i < issued; i++) {
-                const int s = i % ST;
-                const uint32_t ph = (uint32_t)(i / ST) & 1u;
-                for (uint32_t k = 0; k < kWaitLimit && !tc::mbar_try(tc::smem_u32(&full_bar[s]), ph); k++) {}
-            }
-            if (vb_pending)
-                for (uint32_t k = 0;
-                     k < kWaitLimit && !tc::mbar_try(tc::smem_u32(&vb_full), (uint32_t)(seg - 1) & 1u); k++) {}
-        }
+        pseg = seg;
     } else if (warp == 1 && lane == 0) {
         // ---- MMA issuer
         It t;
@@ -259,6 +259,14 @@ k_sym_gemm(const __grid_constant__ CUtensorMap mapD, const __grid_constant__ CUt
         int seg = 0, jsteps = 0, pb = -1, pJ = -1;
         uint32_t started = 0;
         bool col_on = false;
+        if ((int)blockIdx.x == stall_cta) {
+            // test hook (bd_plan_test_stall): a wait on a barrier that nothing
+            // completes, given up after a bounded spin like any wait that ran
+            // out; the CTA then takes the abort path below
+            for (uint32_t k = 0; k < 4096u && !tc::mbar_try(tc::smem_u32(&stall_bar), 0); k++) {}
+            abort_flag = 1;
+            ok = false;
+        }
         for (int i = 0; i < nunits && ok; i++) {
             It nx = t;
             it_next(nx, T);
@@ -406,8 +414,24 @@ k_sym_gemm(const __grid_constant__ CUtensorMap mapD, const __grid_constant__ CUt
             t = nx;
         }
     }
-    // ---- teardown
-    if (threadIdx.x == 0 && abort_flag) atomicExch(err, (int32_t)BD_ERR_TIMEOUT);
+    // ---- teardown.  Every role has left its loop once all threads are here,
+    // so abort_flag is final: after an abort (which may come after the
+    // producer issued its last load) the producer lets every load it issued
+    // land before the CTA exits, and the status word records the timeout.
+    __syncthreads();
+    if (abort_flag) {
+        if (warp == 0 && lane == 0) {
+            for (int i = (issued > ST ? issued - ST : 0); i < issued; i++) {
+                const int s = i % ST;
+                const uint32_t ph = (uint32_t)(i / ST) & 1u;
+                for (uint32_t k = 0; k < kWaitLimit && !tc::mbar_try(tc::smem_u32(&full_bar[s]), ph); k++) {}
+            }
+            if (vb_pending)
+                for (uint32_t k = 0;
+                     k < kWaitLimit && !tc::mbar_try(tc::smem_u32(&vb_full), (uint32_t)(pseg - 1) & 1u); k++) {}
+        }
+        if (threadIdx.x == 0) atomicExch(err, (int32_t)BD_ERR_TIMEOUT);
+    }
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
     if (warp == 1) {
@@ -432,6 +456,9 @@ k_sym_reduce(Geo g, const float *__restrict__ part, int n3, tc::Epi e)
     constexpr int kList = 256;
     __shared__ double lan_red[4][3];
     __shared__ int s_list[kList];
+    // a programmatic dependent of the product kernel: scheduled while the
+    // product's CTAs finish, it reads their partial slots only after this wait
+    tc::grid_dep_wait();
     const int X = blockIdx.x, cc = blockIdx.y, r = threadIdx.x;
     const int q = r >> 5, lane = r & 31;
     const long row = (long)X * BM + r;
@@ -813,16 +840,41 @@ bd_status sym_launch(Plan &P, const CUtensorMap &mapD, const CUtensorMap &mapX, 
     const sy::Geo &g = S->geo;
     const int cols = e.m + (e.lan_col >= 0 ? 1 : 0);
     int32_t *err = P.d_status + 6;
+    const int stall = P.test_stall - 1;          // -1: no stall (the hook is one-shot)
+    P.test_stall = 0;
+    // both kernels are programmatic dependents of the kernel before them:
+    // each is scheduled while its predecessor's CTAs drain and waits
+    // (griddepcontrol.wait) before it reads anything that kernel wrote
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cudaLaunchConfig_t cg = {};
+    cg.gridDim = dim3(g.G);
+    cg.blockDim = dim3(sy::THREADS);
+    cg.stream = s;
+    cg.attrs = attr;
+    cg.numAttrs = 1;
+    cudaLaunchConfig_t cr = cg;
+    cr.gridDim = dim3(g.T, cols);
+    cr.blockDim = dim3(128);
+    cr.dynamicSmemBytes = 0;
+    cudaError_t le;
     if (bn == 16) {
-        sy::k_sym_gemm<16><<<g.G, sy::THREADS, sy::smem_bytes<16>(), s>>>(
-            mapD, mapX, g, cols, e.is_bf16, S->d_part, err);
-        sy::k_sym_reduce<16><<<dim3(g.T, cols), 128, 0, s>>>(g, S->d_part, P.n3, e);
+        cg.dynamicSmemBytes = sy::smem_bytes<16>();
+        le = cudaLaunchKernelEx(&cg, sy::k_sym_gemm<16>, mapD, mapX, g, cols, e.is_bf16,
+                                S->d_part, err, stall);
+        if (le == cudaSuccess)
+            le = cudaLaunchKernelEx(&cr, sy::k_sym_reduce<16>, g, (const float *)S->d_part, P.n3, e);
     } else {
-        sy::k_sym_gemm<32><<<g.G, sy::THREADS, sy::smem_bytes<32>(), s>>>(
-            mapD, mapX, g, cols, e.is_bf16, S->d_part, err);
-        sy::k_sym_reduce<32><<<dim3(g.T, cols), 128, 0, s>>>(g, S->d_part, P.n3, e);
+        cg.dynamicSmemBytes = sy::smem_bytes<32>();
+        le = cudaLaunchKernelEx(&cg, sy::k_sym_gemm<32>, mapD, mapX, g, cols, e.is_bf16,
+                                S->d_part, err, stall);
+        if (le == cudaSuccess)
+            le = cudaLaunchKernelEx(&cr, sy::k_sym_reduce<32>, g, (const float *)S->d_part, P.n3, e);
     }
     count_launches(2);
+    if (le != cudaSuccess) return set_error(BD_ERR_CUDA, "symmetric product launch: %s",
+                                            cudaGetErrorString(le));
     return check_launch("symmetric product");
 }
 

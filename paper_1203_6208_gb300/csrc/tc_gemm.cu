@@ -25,6 +25,7 @@
 #include "sym_gemm.cuh"
 #include "tc_common.cuh"
 #include "tc_gemm.cuh"
+#include "rows_gemm.cuh"
 
 namespace bd {
 
@@ -104,9 +105,9 @@ k_tc_gemm(const __grid_constant__ CUtensorMap mapD, const __grid_constant__ CUte
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     const uint32_t tmem = tmem_base_sh;
 
+    int issued = 0;                      // the producer's loads, for the drain after an abort
     if (warp == 0 && lane == 0) {
         // ---- TMA producer: every unit of the range, in order
-        int issued = 0;
         int mb = (int)(u0 / ktiles), kt = (int)(u0 % ktiles);
         for (int i = 0; i < nunits; i++, kt = (kt + 1 == ktiles) ? 0 : kt + 1, mb += (kt == 0)) {
             int s = i % ST;
@@ -118,14 +119,6 @@ k_tc_gemm(const __grid_constant__ CUtensorMap mapD, const __grid_constant__ CUte
             tma_load_2d(a, &mapD, kt * BK, mb * BM, fb);
             tma_load_2d(b, &mapX, kt * BK, 0, fb);
             issued = i + 1;
-        }
-        if (abort_flag) {
-            // let every load issued land before the CTA can exit
-            for (int i = (issued > ST ? issued - ST : 0); i < issued; i++) {
-                int s = i % ST;
-                uint32_t ph = (uint32_t)(i / ST) & 1u;
-                for (uint32_t t = 0; t < kWaitLimit && !mbar_try(smem_u32(&full_bar[s]), ph); t++) {}
-            }
         }
     } else if (warp == 1 && lane == 0) {
         // ---- MMA issuer: segment j accumulates in TMEM buffer j & 1
@@ -291,8 +284,19 @@ k_tc_gemm(const __grid_constant__ CUtensorMap mapD, const __grid_constant__ CUte
             }
         }
     }
-    // ---- teardown
-    if (threadIdx.x == 0 && abort_flag) atomicExch(err, (int32_t)BD_ERR_TIMEOUT);
+    // ---- teardown.  Every role has left its loop once all threads are here,
+    // so abort_flag is final: after an abort the producer lets every load it
+    // issued land before the CTA exits, and the status word records it.
+    __syncthreads();
+    if (abort_flag) {
+        if (warp == 0 && lane == 0)
+            for (int i = (issued > ST ? issued - ST : 0); i < issued; i++) {
+                int s = i % ST;
+                uint32_t ph = (uint32_t)(i / ST) & 1u;
+                for (uint32_t t = 0; t < kWaitLimit && !mbar_try(smem_u32(&full_bar[s]), ph); t++) {}
+            }
+        if (threadIdx.x == 0) atomicExch(err, (int32_t)BD_ERR_TIMEOUT);
+    }
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
     if (warp == 1) {
@@ -545,8 +549,9 @@ bd_status tc_apply(Plan &P, const void *D16, const double *X, int m, double *Y, 
 // Autotuner of the product's launch shape: time Y = D16 X with the column
 // count of a lagged Chebyshev product (max_rhs + 1, the Lanczos vector riding
 // along) with 2 resident CTAs per SM (shallower ring), 1 (ring twice as
-// deep), and the symmetric product over the upper triangle (shape 3), on this
-// plan's own matrix, and keep the fastest.  Synchronous.
+// deep), the symmetric product over the upper triangle (shape 3) and, for
+// plans with max_rhs <= 4, the row-streamed CUDA-core product (shape 5), on
+// this plan's own matrix, and keep the fastest.  Synchronous.
 bd_status tc_autotune(Plan &P, const void *D16, cudaStream_t s, int *best_out, float *ms_out)
 {
     const int m = P.p.max_rhs + 1 < kMaxRhs ? P.p.max_rhs + 1 : kMaxRhs;
@@ -558,12 +563,17 @@ bd_status tc_autotune(Plan &P, const void *D16, cudaStream_t s, int *best_out, f
     int best = 0;
     float best_ms = 1e30f;
     const int saved = P.tc_split;
-    for (int cps = 1; cps <= kSymShape; cps++) {
+    const bool rows_ok = P.p.max_rhs + 4 <= kRowsMaxCols;
+    for (int cps = 1; cps <= kRowsShape; cps++) {
+        if (cps == kF64DoubleFloat || (cps == kRowsShape && !rows_ok)) continue;
         P.tc_split = cps;
-        bd_status st = tc_apply(P, D16, X, m, Y, s);      // warm-up
+        auto product = [&]() {
+            return cps == kRowsShape ? rows_apply(P, D16, X, m, Y, s) : tc_apply(P, D16, X, m, Y, s);
+        };
+        bd_status st = product();                          // warm-up
         if (st != BD_OK) { P.tc_split = saved; cudaEventDestroy(e0); cudaEventDestroy(e1); return st; }
         cudaEventRecord(e0, s);
-        for (int r = 0; r < 3; r++) tc_apply(P, D16, X, m, Y, s);
+        for (int r = 0; r < 3; r++) product();
         cudaEventRecord(e1, s);
         cudaEventSynchronize(e1);
         float ms = 0.f;

@@ -68,51 +68,48 @@ __global__ void k_springs(const double *R, int n, int nb, int fene, double b, do
 }
 
 // narrow-Gaussian excluded volume over all pairs and periodic images with
-// |r| <= r_ev: F_nu += (z*/d*^5) r exp(-r^2/(2 d*^2))
-__global__ void k_ev(const double *R, int n, double L, double pref, double inv2d2, double rev2,
-                     int nmax, double *F)
+// |r| <= r_ev: F_nu += (z*/d*^5) r exp(-r^2/(2 d*^2)).  One warp per bead nu,
+// its lanes over the other beads mu (coalesced position loads), the images of
+// each pair's minimum-image separation (exact remainder) within r_ev; the
+// lanes' partial forces are then combined by a butterfly of shuffles, the
+// same order on every run.
+constexpr int kEvWarps = 4;
+
+__global__ void __launch_bounds__(32 * kEvWarps)
+k_ev(const double *__restrict__ R, int n, double L, double pref, double inv2d2, double rev2,
+     int nmax, double *__restrict__ F)
 {
-    __shared__ double sr[3 * 128];
-    int nu = blockIdx.x * blockDim.x + threadIdx.x;
-    double rn[3] = {0, 0, 0};
-    if (nu < n) for (int s = 0; s < 3; s++) rn[s] = R[3 * nu + s];
+    const int nu = blockIdx.x * kEvWarps + (threadIdx.x >> 5), lane = threadIdx.x & 31;
+    if (nu >= n) return;                           // the whole warp leaves together
+    const double rn0 = R[3 * nu], rn1 = R[3 * nu + 1], rn2 = R[3 * nu + 2];
     double acc[3] = {0.0, 0.0, 0.0};
-    for (int base = 0; base < n; base += 128) {
-        __syncthreads();
-        for (int i = threadIdx.x; i < 3 * 128; i += blockDim.x) {
-            int b = base * 3 + i;
-            sr[i] = b < 3 * n ? R[b] : 0.0;
-        }
-        __syncthreads();
-        if (nu < n) {
-            int lim = min(128, n - base);
-            for (int q = 0; q < lim; q++) {
-                int mu = base + q;
-                if (mu == nu) continue;
-                double d[3];
-                for (int s = 0; s < 3; s++) {
-                    double x = rn[s] - sr[3 * q + s];
-                    d[s] = remainder(x, L);   // exact minimum image
-                }
-                for (int ix = -nmax; ix <= nmax; ix++) {
-                    double vx = d[0] + ix * L;
-                    if (vx * vx > rev2) continue;
-                    for (int iy = -nmax; iy <= nmax; iy++) {
-                        double vy = d[1] + iy * L;
-                        if (vx * vx + vy * vy > rev2) continue;
-                        for (int iz = -nmax; iz <= nmax; iz++) {
-                            double vz = d[2] + iz * L;
-                            double u = vx * vx + vy * vy + vz * vz;
-                            if (u > rev2) continue;
-                            double w = pref * exp(-u * inv2d2);
-                            acc[0] += w * vx; acc[1] += w * vy; acc[2] += w * vz;
-                        }
-                    }
+    for (int mu = lane; mu < n; mu += 32) {
+        if (mu == nu) continue;
+        const double d0 = remainder(rn0 - R[3 * mu], L);      // exact minimum image
+        const double d1 = remainder(rn1 - R[3 * mu + 1], L);
+        const double d2 = remainder(rn2 - R[3 * mu + 2], L);
+        for (int ix = -nmax; ix <= nmax; ix++) {
+            const double vx = d0 + ix * L;
+            if (vx * vx > rev2) continue;
+            for (int iy = -nmax; iy <= nmax; iy++) {
+                const double vy = d1 + iy * L;
+                if (vx * vx + vy * vy > rev2) continue;
+                for (int iz = -nmax; iz <= nmax; iz++) {
+                    const double vz = d2 + iz * L;
+                    const double u = vx * vx + vy * vy + vz * vz;
+                    if (u > rev2) continue;
+                    const double w = pref * exp(-u * inv2d2);
+                    acc[0] += w * vx; acc[1] += w * vy; acc[2] += w * vz;
                 }
             }
         }
     }
-    if (nu < n) for (int s = 0; s < 3; s++) F[3 * nu + s] += acc[s];
+#pragma unroll
+    for (int s = 0; s < 3; s++)
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) acc[s] += __shfl_xor_sync(0xffffffffu, acc[s], o);
+    if (lane == 0)
+        for (int s = 0; s < 3; s++) F[3 * nu + s] += acc[s];
 }
 
 void launch_forces(Plan &P, const double *R, double *F, int32_t *n_bad, cudaStream_t s)
@@ -125,8 +122,8 @@ void launch_forces(Plan &P, const double *R, double *F, int32_t *n_bad, cudaStre
         double d = P.p.d_star;
         double pref = P.p.z_star / (d * d * d * d * d);
         int nmax = (int)floor(P.p.r_ev / P.p.box_L + 0.5) + 1;
-        k_ev<<<(n + 127) / 128, 128, 0, s>>>(R, n, P.p.box_L, pref, 1.0 / (2.0 * d * d),
-                                              P.p.r_ev * P.p.r_ev, nmax, F);
+        k_ev<<<(n + kEvWarps - 1) / kEvWarps, 32 * kEvWarps, 0, s>>>(
+            R, n, P.p.box_L, pref, 1.0 / (2.0 * d * d), P.p.r_ev * P.p.r_ev, nmax, F);
         count_launches(1);
     }
 }

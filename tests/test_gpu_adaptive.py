@@ -129,12 +129,12 @@ def test_step_adaptive_fene_ev(bnd):
     dS_r, Ef_r, n_r, ok_r = oracle.cheb_sqrt_adaptive(Dr, st["d_min"], st["d_max"], dW, tol, 100)
     assert st["n_cheb"] == n_r
     assert (st["status"] == 0) == ok_r
-    assert relerr(dS.cpu().numpy(), dS_r) <= 1e-10
+    assert relerr(dS.cpu().numpy(), dS_r) <= 1e-11
     R_ref, st_ref, _, _, _ = oracle.step(p, R, dW, st["d_min"], st["d_max"], n_r)
     if st_ref == 0:
         assert st["accepted"] == 1
         disp = Rg.cpu().numpy() - R.reshape(-1)
-        assert relerr(disp, R_ref.reshape(-1) - R.reshape(-1)) <= 1e-9
+        assert relerr(disp, R_ref.reshape(-1) - R.reshape(-1)) <= 1e-11
 
 
 def test_adaptive_mixed_close_to_oracle(bnd):

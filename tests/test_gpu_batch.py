@@ -1,8 +1,10 @@
 """Batched replicas (bd_batch_*): uneven N, one plan per replica, one graph
-launch per step after the first two calls.
+launch per step after the first two calls; mixed replicas with few Wiener
+columns run their Chebyshev loops together in one persistent launch.
 
 The replicas advanced by the batch must be bitwise the replicas advanced one
-plan at a time with the same options (the batch records the same kernels);
+plan at a time with the same options and launch shape (every sum of the
+batched loop is taken in an order fixed by the row alone);
 the mixed batch is checked against the FP64 oracle; the autotuner keeps a
 valid split and the product stays within the mixed tolerance.
 """
@@ -48,6 +50,8 @@ def test_batch_equals_single_plans(bnd, prec):
     torch.cuda.synchronize()
     for i, (p, R) in enumerate(zip(plist, Rs)):
         plan = bnd.Plan(p, prec, max_rhs=2, max_cheb=16)
+        if prec != "fp64":
+            plan.set_shape(5)      # the batch's shape: its Chebyshev loops run in one launch
         plan.set_step_counter(kw["step_index"])
         D = plan.alloc_D()
         Rg = torch.tensor(R, device="cuda")

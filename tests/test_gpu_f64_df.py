@@ -178,7 +178,7 @@ def test_df_shape_rules(bnd):
         mixed.set_shape(bnd.BD_SHAPE_F64_DOUBLE_FLOAT)
     mixed.close()
     with pytest.raises(bnd.BDError):
-        bnd.Plan(p, "fp64", max_rhs=2).set_shape(5)
+        bnd.Plan(p, "fp64", max_rhs=2).set_shape(6)
     R = inputs.make_chains(cfg)
     plan, Rg, D = df_plan(bnd, p, R, max_rhs=4)
     X = inputs.make_wiener(3 * cfg.n, 4, 1.0, 67)

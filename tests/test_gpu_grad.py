@@ -57,7 +57,7 @@ def test_drift_gradient_vs_oracle(mods, n_chains):
     plan.apply_backward(Rg, D, torch.tensor(F, device="cuda"), torch.tensor(g, device="cuda"),
                         gR, gF)
     gR_ref, gF_ref = oracle.grad_DF(p, R, F, g)
-    assert relerr(gR.cpu().numpy().reshape(-1, 3), gR_ref) <= 1e-10
+    assert relerr(gR.cpu().numpy().reshape(-1, 3), gR_ref) <= 1e-11
     assert relerr(gF.cpu().numpy(), gF_ref) <= 1e-11
 
 
@@ -115,7 +115,7 @@ def test_chebyshev_gradient_vs_oracle(mods, n_chains):
                             torch.tensor(h, device="cuda"), gR, gdW)
     X, Y, U0 = oracle.cheb_adjoint(D, dmin, dmax, nch, dW, h)
     gR_ref = oracle.grad_pairs(p, R, X, Y)
-    assert relerr(gR.cpu().numpy().reshape(-1, 3), gR_ref) <= 1e-10
+    assert relerr(gR.cpu().numpy().reshape(-1, 3), gR_ref) <= 1e-11
     assert relerr(gdW.cpu().numpy(), U0) <= 1e-11
 
 

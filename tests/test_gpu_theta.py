@@ -68,3 +68,59 @@ def test_theta_statics_batched():
         for k in (1, 2):
             assert abs(mean[k] - ref[k]) < 4.0 * se[k], (ci, k, mean, se)
             assert abs(mean[k] / ref[k] - 1) < 0.20, (ci, k, mean)
+
+
+def test_theta_relaxation_from_off_equilibrium_starts():
+    """Chains started far from the theta statics relax to them: bonds
+    stretched twofold (<Q^2> = 12) or compressed to 0.3 (<Q^2> = 0.27).
+    A uniform rescaling of the bonds puts the same share of the excess into
+    every Rouse mode, and the bond statistic follows their average, so the
+    slowest mode sets the pace: for 4-bead chains its rate is
+    sin^2(pi/8) = 0.15 per time unit (free draining), and 15 time units
+    (1500 steps of dt = 0.01) leave ~1 % of the excess.  From there both
+    starts must sit at <Q^2> = 3 (Eq. Re2 per bond: the fluctuation-
+    dissipation balance of the drift D.F against the noise sqrt(D) dW); a
+    wrong drift factor or noise amplitude moves that limit, from either
+    side.  Dilute and semidilute boxes (0.03 and 0.3 c*) with N_Ch = 40, so
+    that the Chebyshev error stays below 1 % (checked) and the limit tests
+    the dynamics, not the series.  <R_e^2> = 3 (N_b - 1) is reached too (within its sampling error,
+    ~4 % per group of eight replicas)."""
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1203_6208_gb300 import binding as bnd, build
+    build.build()
+    bnd.load()
+    nb = 4
+    cfgs = inputs.theta_systems(nb=nb, concentrations=(0.03, 0.3), replicas=8, seed=2100)
+    scale = [2.0 if i % 2 == 0 else 0.3 for i in range(len(cfgs))]
+    starts = []
+    for c, f in zip(cfgs, scale):
+        r = inputs.make_chains(c).reshape(c.n_chains, nb, 3)
+        bonds = np.diff(r, axis=1) * f
+        r[:, 1:] = r[:, :1] + np.cumsum(bonds, axis=1)
+        starts.append(r.reshape(-1))
+    b = bnd.Batch([c.params() for c in cfgs], "mixed_f16", max_rhs=1, max_cheb=40)
+    R = torch.tensor(np.concatenate(starts), device="cuda")
+    D = b.alloc_D()
+    stats = torch.zeros(b.count * bnd.STATS_BYTES, dtype=torch.uint8, device="cuda")
+    q0 = chain_stats(R, b, cfgs)[:, 0].cpu().numpy()
+    acc = torch.zeros(b.count, 3, dtype=torch.float64, device="cuda")
+    nsamp = 0
+    for k in range(3000):
+        b.step(R, D, m=1, n_cheb=40, seed=41, stats=stats, bounds_mode=1)
+        if k >= 1500 and k % 10 == 0:
+            acc += chain_stats(R, b, cfgs)
+            nsamp += 1
+    torch.cuda.synchronize()
+    per = (acc / nsamp).cpu().numpy()
+    q = per[:, 0]
+    st = [bnd.BdStepStats.from_buffer_copy(bytes(stats[i * bnd.STATS_BYTES:(i + 1) * bnd.STATS_BYTES]
+                                                 .cpu().numpy().tobytes())) for i in range(b.count)]
+    assert all(x.status == 0 and x.accepted == 1 for x in st)
+    assert max(x.ef_max for x in st) < 0.01, [x.ef_max for x in st]
+    stretched, compressed = q[0::2], q[1::2]
+    assert np.all(q0[0::2] > 8.0) and np.all(q0[1::2] < 0.5)
+    assert abs(stretched.mean() / 3.0 - 1) < 0.03, stretched
+    assert abs(compressed.mean() / 3.0 - 1) < 0.03, compressed
+    re2 = per[:, 1] / (3.0 * (nb - 1))
+    assert abs(re2[0::2].mean() - 1) < 0.15 and abs(re2[1::2].mean() - 1) < 0.15, re2
