@@ -247,7 +247,10 @@ k_gemm_df(const double *__restrict__ D, long ld, int n3, const float *__restrict
 {
     using S = ShapeDF<MC>;
     // row stride MC + 4: 16-byte aligned rows, and the fill below (8 k x 4
-    // columns per warp) lands on 32 distinct banks
+    // columns per warp) lands on 32 distinct banks for MC = 8, 16, 24 and 32
+    // (one warp's 32 addresses enumerated: XS = 12, 20, 28, 36); MC = 4 takes
+    // two words per bank.  MC = 24 gives CPT = 6 columns per thread, which
+    // load_cols reads element by element (no 16-byte vector of 6)
     constexpr int XS = MC >= 4 ? MC + 4 : MC;
     constexpr int JG = MC >= 4 ? 4 : MC;
     __shared__ float2 sD[BM][BK + 1];
