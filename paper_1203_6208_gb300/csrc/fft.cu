@@ -86,6 +86,22 @@ struct Radices {
     int r[16];
 };
 
+// n / d and n % d for 0 <= n < 2^22 and a runtime d: the quotient from an
+// FP32 reciprocal, corrected by one step either way (integer division would
+// cost ~20 instructions per element in the load and store loops)
+struct FastDiv {
+    int d;
+    float inv;
+    __device__ explicit FastDiv(int d_) : d(d_), inv(1.0f / (float)d_) {}
+    __device__ __forceinline__ int div(int n) const
+    {
+        int q = (int)((float)n * inv);
+        const int r = n - q * d;
+        q += r >= d ? 1 : (r < 0 ? -1 : 0);
+        return q;
+    }
+};
+
 // one Stockham pass of radix R over NL lines of length K (line stride K + 1
 // in shared memory), src -> dst; consecutive threads take the same butterfly
 // of consecutive lines (each thread keeps its line), so the padded stride
@@ -109,11 +125,14 @@ __device__ __forceinline__ void fft_pass(const C2<T> *src, C2<T> *dst, const C2<
     for (; j < nb; j += step) {
         C2<T> a[R];
 #pragma unroll
-        for (int r = 0; r < R; r++) {
-            const C2<T> v = s[j + r * nb];
-            C2<T> w = tw[r * jm * tstep];
-            w.y *= -sg;                   // the table holds e^{-2 pi i t/K}; sg = +1 conjugates
-            a[r] = r ? cmul(v, w) : v;
+        for (int r = 0; r < R; r++) a[r] = s[j + r * nb];
+        if (Ns > 1) {                     // the first pass has no twiddles
+#pragma unroll
+            for (int r = 1; r < R; r++) {
+                C2<T> w = tw[r * jm * tstep];
+                w.y *= -sg;               // the table holds e^{-2 pi i t/K}; sg = +1 conjugates
+                a[r] = cmul(a[r], w);
+            }
         }
         dft<T, R>(a, sg);
         C2<T> *d = dl + jd * Ns * R + jm;
@@ -168,10 +187,11 @@ k_fft_z_r2c(const T *__restrict__ in, C2<T> *__restrict__ out, long npairs, int 
     const int nl = (int)min((long)kLines, npairs - p0);
     const int H = K / 2 + 1;
     for (int t = threadIdx.x; t < K; t += blockDim.x) tw[t] = twg[t];
+    const FastDiv dK(K), dH(H);
     // lines 2 p0 .. 2 (p0 + nl) - 1 are one contiguous run of reals
     const T *src = in + (size_t)2 * p0 * K;
     for (int e = threadIdx.x; e < 2 * nl * K; e += blockDim.x) {
-        const int line = e / K, k = e - line * K;
+        const int line = dK.div(e), k = e - line * K;
         const T v = src[e];
         C2<T> &c = b0[(size_t)(line >> 1) * (K + 1) + k];
         if (line & 1) c.y = v;
@@ -181,9 +201,9 @@ k_fft_z_r2c(const T *__restrict__ in, C2<T> *__restrict__ out, long npairs, int 
     const C2<T> *res = fft_lines<T>(b0, b1, tw, K, rd, (T)-1);
     C2<T> *dst = out + (size_t)2 * p0 * H;
     for (int e = threadIdx.x; e < 2 * nl * H; e += blockDim.x) {
-        const int line = e / H, k = e - line * H;
+        const int line = dH.div(e), k = e - line * H;
         const C2<T> *c = res + (size_t)(line >> 1) * (K + 1);
-        const C2<T> ck = c[k], cm = c[(K - k) % K];          // C_k, C_{-k}
+        const C2<T> ck = c[k], cm = c[k ? K - k : 0];        // C_k, C_{-k}
         C2<T> v;
         if (line & 1) v = {(T)0.5 * (ck.y + cm.y), (T)-0.5 * (ck.x - cm.x)};   // (C_k - conj C_-k)/(2i)
         else v = {(T)0.5 * (ck.x + cm.x), (T)0.5 * (ck.y - cm.y)};             // (C_k + conj C_-k)/2
@@ -205,10 +225,11 @@ k_fft_z_c2r(const C2<T> *__restrict__ in, T *__restrict__ out, long npairs, int 
     const int nl = (int)min((long)kLines, npairs - p0);
     const int H = K / 2 + 1;
     for (int t = threadIdx.x; t < K; t += blockDim.x) tw[t] = twg[t];
+    const FastDiv dK(K);
     const C2<T> *src = in + (size_t)2 * p0 * H;
     // C_k = A_k + i B_k over the whole line, the upper half from conjugates
     for (int e = threadIdx.x; e < nl * K; e += blockDim.x) {
-        const int pr = e / K, k = e - pr * K;
+        const int pr = dK.div(e), k = e - pr * K;
         const bool lo = k < H;
         const int kk = lo ? k : K - k;
         C2<T> a = src[(size_t)(2 * pr) * H + kk], b = src[(size_t)(2 * pr + 1) * H + kk];
@@ -222,7 +243,7 @@ k_fft_z_c2r(const C2<T> *__restrict__ in, T *__restrict__ out, long npairs, int 
     const C2<T> *res = fft_lines<T>(b0, b1, tw, K, rd, (T)1);
     T *dst = out + (size_t)2 * p0 * K;
     for (int e = threadIdx.x; e < 2 * nl * K; e += blockDim.x) {
-        const int line = e / K, k = e - line * K;
+        const int line = dK.div(e), k = e - line * K;
         const C2<T> c = res[(size_t)(line >> 1) * (K + 1) + k];
         dst[e] = (line & 1) ? c.y : c.x;
     }
