@@ -20,6 +20,7 @@ import hashlib
 import json
 import math
 import os
+import re
 import statistics
 import subprocess
 import sys
@@ -294,11 +295,15 @@ def probe_fp64_peak(which=0):
 
 
 def kernel_source_hash(path, name):
-    """sha256 (16 hex) of the source between the kernel's begin/end markers."""
+    """sha256 (16 hex) of the code between the kernel's begin/end markers,
+    comments and whitespace removed (a comment edit leaves the kernel, and
+    its recorded traffic, as it was)."""
     txt = open(os.path.join(ROOT, path)).read()
     a = txt.index(f"// -- kernel begin: {name}")
     b = txt.index(f"// -- kernel end: {name}")
-    return hashlib.sha256(txt[a:b].encode()).hexdigest()[:16]
+    code = re.sub(r"/\*.*?\*/", " ", txt[a:b], flags=re.S)
+    code = re.sub(r"//[^\n]*", " ", code)
+    return hashlib.sha256(" ".join(code.split()).encode()).hexdigest()[:16]
 
 
 KERNELS = {"fp64": ("paper_1203_6208_gb300/csrc/dense_f64.cu", "k_gemm_f64"),
