@@ -441,17 +441,20 @@ bd_status bd_plan_set_shape(bd_plan *plan, int32_t shape);
 
 /* Test hook for the device-side failure path (the paper has no counterpart;
  * it exercises the bounded waits of the tensor-core kernels without a GPU
- * fault).  Arms the next symmetric product that the plan launches or records
- * (a mixed plan in launch shape 3): in that product, CTA `cta` (0 <= cta <
- * SM count) waits on an mbarrier that nothing completes, gives up after a
- * bounded spin as any wait that ran out does, and takes the abort path: it
- * records BD_ERR_TIMEOUT in the plan's status word, lets its copies in
- * flight land, frees its TMEM and returns.  That product's output is
- * invalid; a bd_step containing it rejects the proposal (R unchanged,
- * stats.status = BD_ERR_TIMEOUT, accepted = 0).  The hook disarms itself
- * after one product; cta < 0 disarms it.  BD_ERR_INVALID on an FP64 plan,
- * in another shape, or for cta >= the SM count.                           */
-bd_status bd_plan_test_stall(bd_plan *plan, int32_t cta);
+ * fault).  Arms a symmetric product that the plan launches or records (a
+ * mixed plan in launch shape 3): the next one for term = 0, else the
+ * term-th product of a Chebyshev series from now (term = 1: the series'
+ * first product, the one that forms V_2; those products load their first D
+ * tiles before the previous kernel's results are visible).  In that product,
+ * CTA `cta` (0 <= cta < SM count) waits on an mbarrier that nothing
+ * completes, gives up after a bounded spin as any wait that ran out does,
+ * and takes the abort path: it records BD_ERR_TIMEOUT in the plan's status
+ * word, lets its copies in flight land, frees its TMEM and returns.  That
+ * product's output is invalid; a bd_step containing it rejects the proposal
+ * (R unchanged, stats.status = BD_ERR_TIMEOUT, accepted = 0).  The hook
+ * disarms itself after one product; cta < 0 disarms it.  BD_ERR_INVALID on
+ * an FP64 plan, in another shape, for cta >= the SM count or term < 0.     */
+bd_status bd_plan_test_stall(bd_plan *plan, int32_t cta, int32_t term);
 
 /* Set the plan's device step counter used by BD_STEP_DEVICE_COUNTER (stream-
  * ordered write of one uint64). */

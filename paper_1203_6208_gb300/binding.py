@@ -109,7 +109,7 @@ def load(path: str = LIB_PATH):
     L.bd_apply_D_backward.argtypes = [_vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp]
     L.bd_plan_set_shape.argtypes = [_vp, i32]
     L.bd_plan_set_shape.restype = i32
-    L.bd_plan_test_stall.argtypes = [_vp, i32]
+    L.bd_plan_test_stall.argtypes = [_vp, i32, i32]
     L.bd_plan_autotune.argtypes = [_vp, _vp, ctypes.POINTER(i32), ctypes.POINTER(ctypes.c_float),
                                    _vp]
     L.bd_plan_set_step_counter.argtypes = [_vp, u64, _vp]
@@ -302,10 +302,11 @@ class Plan:
         (BD_SHAPE_F64_DOUBLE_FLOAT)."""
         _check(load().bd_plan_set_shape(self._h, int(shape)))
 
-    def test_stall(self, cta: int):
-        """bd_plan_test_stall: the next symmetric product's CTA `cta` takes the
+    def test_stall(self, cta: int, term: int = 0):
+        """bd_plan_test_stall: CTA `cta` of the next symmetric product (term 0)
+        or of the term-th product of a Chebyshev series from now takes the
         bounded-wait failure path (a test of the device-side error handling)."""
-        _check(load().bd_plan_test_stall(self._h, int(cta)))
+        _check(load().bd_plan_test_stall(self._h, int(cta), int(term)))
 
     def autotune(self, D, stream=None):
         sp = ctypes.c_int32()

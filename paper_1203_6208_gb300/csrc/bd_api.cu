@@ -609,18 +609,21 @@ bd_status bd_plan_set_shape(bd_plan *plan, int32_t shape)
     return BD_OK;
 }
 
-bd_status bd_plan_test_stall(bd_plan *plan, int32_t cta)
+bd_status bd_plan_test_stall(bd_plan *plan, int32_t cta, int32_t term)
 {
     if (!plan) return set_error(BD_ERR_INVALID, "NULL plan");
     Plan &P = plan->P;
     if (cta < 0) {
         P.test_stall = 0;
+        P.test_stall_term = 0;
         return BD_OK;
     }
+    if (term < 0) return set_error(BD_ERR_INVALID, "term %d < 0", term);
     if (!is_mixed(P) || P.tc_split != kSymShape)
         return set_error(BD_ERR_INVALID, "the stall hook needs a mixed plan in the symmetric shape");
     if (cta >= P.num_sms) return set_error(BD_ERR_INVALID, "cta %d outside the product's grid", cta);
     P.test_stall = cta + 1;
+    P.test_stall_term = term;
     return BD_OK;
 }
 

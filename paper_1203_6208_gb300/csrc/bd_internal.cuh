@@ -130,6 +130,7 @@ struct Plan {
     double *d_lanpart;                 // Lanczos dot partials per row block [3 * blocks]
     int ldx;                           // leading dimension of d_x16 (elements)
     int tc_split;                      // resident CTAs per SM of the tensor-core product (0: 2)
+    int test_stall_term;               // bd_plan_test_stall: Chebyshev-series products to let pass
     int test_stall;                    // bd_plan_test_stall: CTA + 1 of the next symmetric
                                        //   product that stalls (0: none; one-shot)
     int tc_maxslots;                   // partial slots per row block (stream-K schedule)

@@ -148,7 +148,7 @@ template <int BN>
 __global__ void __launch_bounds__(THREADS, 1)
 k_sym_gemm(const __grid_constant__ CUtensorMap mapD, const __grid_constant__ CUtensorMap mapX,
            Geo g, int m, int is_bf16, float *__restrict__ part, int32_t *__restrict__ err,
-           int stall_cta)
+           int stall_cta, int pre_d)
 {
     constexpr int ST = stages<BN>();
     constexpr int XB = xbox<BN>();
@@ -207,18 +207,41 @@ k_sym_gemm(const __grid_constant__ CUtensorMap mapD, const __grid_constant__ CUt
     const uint32_t tmem = tmem_base_sh;
     // launched as a programmatic dependent of the kernel before it: the set-up
     // above overlapped that kernel's tail; its outputs (the operand X, and the
-    // partial slots this kernel overwrites) are used only after this wait
-    tc::grid_dep_wait();
-    if (threadIdx.x == 0) tc::grid_dep_launch();
-    // the producer's record of its loads, for the drain after an abort
-    int issued = 0, pseg = 0;
+    // partial slots this kernel overwrites) are used only after this wait.
+    // The producer waits later, after its first D tiles (below).
+    const bool producer = warp == 0 && lane == 0;
+    if (!producer) tc::grid_dep_wait();
+    if (threadIdx.x == 32) tc::grid_dep_launch();
+    // the producer's record of its loads, for the drain after an abort: stages
+    // issued, band segments, and the first stages' D tiles loaded ahead
+    // (npre, their J in pre_j) of which the first xdone have their X_J too
+    int issued = 0, pseg = 0, npre = 0, xdone = 0;
+    int pre_j[ST];
     bool vb_pending = false;
 
-    if (warp == 0 && lane == 0) {
+    if (producer) {
         // ---- TMA producer
         const uint64_t pol_d = tc::l2_evict_first_policy();
         It t;
         it_seek(t, u0, g.boff, g.nb, T);
+        if (pre_d) {
+            // D was complete before the previous kernel started (the products
+            // of a Chebyshev series): the D tiles of the first stages stream in
+            // while that kernel finishes; each stage's barrier expects the
+            // whole stage, so it completes only once X_J lands as well
+            It tp = t;
+            for (; npre < ST && npre < nunits; npre++) {
+                const uint32_t a = tc::smem_u32(smem + npre * STAGE);
+                const uint32_t fb = tc::smem_u32(&full_bar[npre]);
+                tc::mbar_expect_tx(fb, STAGE);
+                tc::tma_load_2d_hint(a, &mapD, tp.J * BM, tp.I * BM, fb, pol_d);
+                tc::tma_load_2d_hint(a + BM * BK * 2, &mapD, tp.J * BM + BK, tp.I * BM, fb, pol_d);
+                pre_j[npre] = tp.J;
+                it_next(tp, T);
+            }
+            issued = npre;
+        }
+        tc::grid_dep_wait();
         int seg = 0, pb = -1;
         for (int i = 0; i < nunits; i++) {
             if (t.b != pb) {
@@ -239,9 +262,17 @@ k_sym_gemm(const __grid_constant__ CUtensorMap mapD, const __grid_constant__ CUt
             }
             const int s = i % ST;
             const uint32_t ph = (uint32_t)(i / ST) & 1u;
-            if (!tc::mbar_wait(tc::smem_u32(&empty_bar[s]), ph ^ 1u, &abort_flag)) break;
             const uint32_t a = tc::smem_u32(smem + s * STAGE);
             const uint32_t fb = tc::smem_u32(&full_bar[s]);
+            if (i < npre) {
+                // D already on its way: X_J completes the stage
+                tc::tma_load_2d(a + A_TILE, &mapX, t.J * BM, 0, fb);
+                tc::tma_load_2d(a + A_TILE + XB, &mapX, t.J * BM + BK, 0, fb);
+                xdone = i + 1;
+                it_next(t, T);
+                continue;
+            }
+            if (!tc::mbar_wait(tc::smem_u32(&empty_bar[s]), ph ^ 1u, &abort_flag)) break;
             tc::mbar_expect_tx(fb, STAGE);
             tc::tma_load_2d_hint(a, &mapD, t.J * BM, t.I * BM, fb, pol_d);
             tc::tma_load_2d_hint(a + BM * BK * 2, &mapD, t.J * BM + BK, t.I * BM, fb, pol_d);
@@ -421,6 +452,16 @@ k_sym_gemm(const __grid_constant__ CUtensorMap mapD, const __grid_constant__ CUt
     __syncthreads();
     if (abort_flag) {
         if (warp == 0 && lane == 0) {
+            // stages loaded ahead whose X_J was never issued: issue it (the
+            // dependency wait is behind the producer whenever it can abort) so
+            // that their barriers complete and the drain below can see the D
+            // tiles land
+            for (int i = xdone; i < npre; i++) {
+                const uint32_t a = tc::smem_u32(smem + i * STAGE);
+                const uint32_t fb = tc::smem_u32(&full_bar[i]);
+                tc::tma_load_2d(a + A_TILE, &mapX, pre_j[i] * BM, 0, fb);
+                tc::tma_load_2d(a + A_TILE + XB, &mapX, pre_j[i] * BM + BK, 0, fb);
+            }
             for (int i = (issued > ST ? issued - ST : 0); i < issued; i++) {
                 const int s = i % ST;
                 const uint32_t ph = (uint32_t)(i / ST) & 1u;
@@ -457,7 +498,10 @@ k_sym_reduce(Geo g, const float *__restrict__ part, int n3, tc::Epi e)
     __shared__ double lan_red[4][3];
     __shared__ int s_list[kList];
     // a programmatic dependent of the product kernel: scheduled while the
-    // product's CTAs finish, it reads their partial slots only after this wait
+    // product's CTAs finish, it reads their partial slots only after this
+    // wait; the kernel after it may be scheduled as soon as every CTA of this
+    // one has started (it waits for this one's results itself)
+    tc::grid_dep_launch();
     tc::grid_dep_wait();
     const int X = blockIdx.x, cc = blockIdx.y, r = threadIdx.x;
     const int q = r >> 5, lane = r & 31;
@@ -491,15 +535,14 @@ k_sym_reduce(Geo g, const float *__restrict__ part, int n3, tc::Epi e)
     }
     // the operand's column scales are powers of two: undone exactly in FP32
     const float isc = e.inv_scale[cc];
-    const double w = (double)(sh * isc) + (double)(sl * isc);
     if (e.mode == 0) {
-        if (row < n3) e.Y[(long)cc * n3 + row] = w;
+        if (row < n3) e.Y[(long)cc * n3 + row] = tc::f32_to_f64(sh * isc) + tc::f32_to_f64(sl * isc);
         return;
     }
     if (cc == e.lan_col) {
         // the Lanczos column: w = D q_j and this row block's share of q_j.w,
         // q_{j-1}.w and w.w, reduced in a fixed order (deterministic)
-        const double lw = w;
+        const double lw = tc::f32_to_f64(sh * isc) + tc::f32_to_f64(sl * isc);
         if (row < n3) e.lan_w[row] = lw;
         double t[3] = {row < n3 ? e.lan_q[row] * lw : 0.0, row < n3 ? e.lan_qp[row] * lw : 0.0,
                        row < n3 ? lw * lw : 0.0};
@@ -518,23 +561,26 @@ k_sym_reduce(Geo g, const float *__restrict__ part, int n3, tc::Epi e)
     // Chebyshev term of Eqs. (cheb2)/(cheb3): V_p = 2 (s W - t V_{p-1}) - V_{p-2},
     // dS += c_p V_p, and the scaled 16-bit V_p as the next product's operand.
     // The interval map s, t is formed once per CTA (FP64 divisions run on
-    // this GPU's slow FP64 pipe).
-    __shared__ double s_map[2];
+    // this GPU's slow FP64 pipe), folded with the factor 2 and the column's
+    // inverse scale (a power of two) so that each element costs four FP64
+    // fused multiply-adds: V_p = 2s isc (sh + sl) - (2t V_{p-1} + V_{p-2}).
+    __shared__ double s_map[3];
     if (r == 0) {
         const double dmin = e.bounds[0], dmax = e.bounds[1];
         const double iw = 1.0 / (dmax - dmin);
-        s_map[0] = 2.0 * iw;
-        s_map[1] = (dmax + dmin) * iw;
+        s_map[0] = 4.0 * iw * (double)isc;
+        s_map[1] = 2.0 * (dmax + dmin) * iw;
+        s_map[2] = e.coef[e.p];
     }
     __syncthreads();
     if (row >= n3) return;
-    const double ys = s_map[0], yt = s_map[1];
+    const double ya = s_map[0], yb = s_map[1], cp = s_map[2];
     const long o = (long)cc * n3 + row;
     const double p1 = e.Vprev1[o], p2 = e.Vprev2[o], d0 = e.dS[o];
-    const double v = 2.0 * (ys * w - yt * p1) - p2;
+    const double v = fma(ya, tc::f32_to_f64(sh), fma(ya, tc::f32_to_f64(sl), -fma(yb, p1, p2)));
     e.Vprev2[o] = v;
-    e.dS[o] = d0 + e.coef[e.p] * v;
-    const float sv = (float)v * e.scale[cc];
+    e.dS[o] = fma(cp, v, d0);
+    const float sv = tc::f64_to_f32_rz(v) * e.scale[cc];
     const size_t xo = (size_t)cc * e.ldx + row;
     if (e.is_bf16) ((__nv_bfloat16 *)e.X16next)[xo] = __float2bfloat16_rn(sv);
     else ((__half *)e.X16next)[xo] = __float2half_rn(sv);
@@ -840,8 +886,21 @@ bd_status sym_launch(Plan &P, const CUtensorMap &mapD, const CUtensorMap &mapX, 
     const sy::Geo &g = S->geo;
     const int cols = e.m + (e.lan_col >= 0 ? 1 : 0);
     int32_t *err = P.d_status + 6;
-    const int stall = P.test_stall - 1;          // -1: no stall (the hook is one-shot)
-    P.test_stall = 0;
+    // the stall hook (one-shot): armed for this product unless it waits for
+    // a later product of a Chebyshev series
+    int stall = -1;
+    if (P.test_stall > 0) {
+        if (P.test_stall_term > 0 && e.mode == 1) P.test_stall_term--;
+        if (P.test_stall_term == 0) {
+            stall = P.test_stall - 1;
+            P.test_stall = 0;
+        }
+    }
+    // a Chebyshev series' product follows kernels that do not write D, and D
+    // was complete before they started: its first D tiles may be loaded
+    // before the dependency wait.  A plain product may follow the kernel that
+    // wrote D, so it loads nothing before that wait.
+    const int pre_d = e.mode == 1 ? 1 : 0;
     // both kernels are programmatic dependents of the kernel before them:
     // each is scheduled while its predecessor's CTAs drain and waits
     // (griddepcontrol.wait) before it reads anything that kernel wrote
@@ -862,13 +921,13 @@ bd_status sym_launch(Plan &P, const CUtensorMap &mapD, const CUtensorMap &mapX, 
     if (bn == 16) {
         cg.dynamicSmemBytes = sy::smem_bytes<16>();
         le = cudaLaunchKernelEx(&cg, sy::k_sym_gemm<16>, mapD, mapX, g, cols, e.is_bf16,
-                                S->d_part, err, stall);
+                                S->d_part, err, stall, pre_d);
         if (le == cudaSuccess)
             le = cudaLaunchKernelEx(&cr, sy::k_sym_reduce<16>, g, (const float *)S->d_part, P.n3, e);
     } else {
         cg.dynamicSmemBytes = sy::smem_bytes<32>();
         le = cudaLaunchKernelEx(&cg, sy::k_sym_gemm<32>, mapD, mapX, g, cols, e.is_bf16,
-                                S->d_part, err, stall);
+                                S->d_part, err, stall, pre_d);
         if (le == cudaSuccess)
             le = cudaLaunchKernelEx(&cr, sy::k_sym_reduce<32>, g, (const float *)S->d_part, P.n3, e);
     }

@@ -112,6 +112,34 @@ __device__ __forceinline__ uint64_t l2_evict_first_policy()
     return p;
 }
 
+// FP32 <-> FP64 conversions on the integer pipe.  On this GPU the hardware
+// conversions issue on the FP64 pipe (1/64 of the FP32 rate), where the
+// products' epilogues are short of throughput.  The IEEE binary32 fields are
+// moved into the binary64 fields (exponent rebiased by 1023 - 127 = 896):
+// exact for every normal FP32 value and for zero; other inputs (subnormal,
+// infinite, NaN) take the hardware conversion.
+__device__ __forceinline__ double f32_to_f64(float f)
+{
+    const unsigned u = __float_as_uint(f);
+    const unsigned ex = (u >> 23) & 0xFFu;
+    if (ex == 0u && (u << 1) == 0u) return __hiloint2double((int)(u & 0x80000000u), 0);
+    if (ex == 0u || ex == 0xFFu) return (double)f;
+    const unsigned hi = (u & 0x80000000u) | ((ex + 896u) << 20) | ((u & 0x7FFFFFu) >> 3);
+    return __hiloint2double((int)hi, (int)(u << 29));
+}
+
+// FP64 -> FP32 rounded toward zero (the 29 low fraction bits dropped), for
+// values in the normal FP32 range; others take the hardware conversion.  Used
+// where the result is rounded again to 16 bits.
+__device__ __forceinline__ float f64_to_f32_rz(double d)
+{
+    const unsigned hi = (unsigned)__double2hiint(d), lo = (unsigned)__double2loint(d);
+    const unsigned ex = (hi >> 20) & 0x7FFu;
+    if (ex < 897u || ex > 1150u) return (float)d;
+    return __uint_as_float((hi & 0x80000000u) | ((ex - 896u) << 23) | ((hi & 0xFFFFFu) << 3) |
+                           (lo >> 29));
+}
+
 // programmatic dependent launch: wait for the grids this one depends on
 // (and their memory) before touching their outputs; let the next grid be
 // scheduled once every CTA of this one has run this far

@@ -617,6 +617,9 @@ __global__ void k_lanczos_step(double *qprev, double *q, const double *w, int n3
                                const double *part, int nparts, double *lab, int j, void *X16col,
                                int is_bf16)
 {
+    // a programmatic dependent of the product's last kernel (see tc_cheb)
+    tc::grid_dep_launch();
+    tc::grid_dep_wait();
     __shared__ double sh[3];
     if (threadIdx.x < 32) {
         double t[3] = {0.0, 0.0, 0.0};
@@ -692,10 +695,26 @@ bd_status tc_cheb(Plan &P, const void *D16, int m, const double *coef, const dou
     e.lan_part = P.d_lanpart;
     bd_status st = launch_tc(P, D16, cur, bn, e, s);
     if (st != BD_OK || !lan) return st;
-    k_lanczos_step<<<(P.n3 + 255) / 256, 256, 0, s>>>(
-        P.d_lq[0], P.d_lq[1], P.d_lq[2], P.n3, P.d_lanpart, mblocks(P), P.d_lab, lan_step,
-        (char *)nxt + (size_t)m * P.ldx * 2, is_bf16);
+    // launched as a programmatic dependent: scheduled while the product
+    // finishes, it reads the product's outputs after its dependency wait, and
+    // the next product may in turn be scheduled while it runs
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cudaLaunchConfig_t cl = {};
+    cl.gridDim = dim3((P.n3 + 255) / 256);
+    cl.blockDim = dim3(256);
+    cl.stream = s;
+    cl.attrs = attr;
+    cl.numAttrs = 1;
+    const cudaError_t le = cudaLaunchKernelEx(&cl, k_lanczos_step, P.d_lq[0], P.d_lq[1],
+                                              (const double *)P.d_lq[2], P.n3,
+                                              (const double *)P.d_lanpart, mblocks(P), P.d_lab,
+                                              lan_step, (void *)((char *)nxt + (size_t)m * P.ldx * 2),
+                                              is_bf16);
     count_launches(1);
+    if (le != cudaSuccess)
+        return set_error(BD_ERR_CUDA, "lanczos step launch: %s", cudaGetErrorString(le));
     return check_launch("lanczos step");
 }
 
