@@ -288,6 +288,36 @@ __device__ __forceinline__ void add_m1_tab(T vx, T vy, T vz, T u, const T *__res
     acc[5] += c1 + g * vz * vz;
 }
 
+// The same for the image loop of the dense assembly, where the caller has
+// already checked 4a^2 <= u <= r_c^2 in the working precision: the interval
+// index then lies in [0, ntab) without a clamp (the table range is built from
+// the same FP32 values, 4a^2 and r_c^2 (1 + 1e-6)).  The isotropic part c1 is
+// summed into c1sum (added to the three diagonal components once per pair).
+template <typename T>
+__device__ __forceinline__ void add_m1_tab_in_range(T vx, T vy, T vz, T u, const T *__restrict__ tab,
+                                                    int i0, T acc[6], T &c1sum)
+{
+    constexpr int DEG = TabFmt<T>::DEG;
+    const int i = (int)(__float_as_uint((float)u) >> TabFmt<T>::SHIFT) - i0;
+    const TabRow<T> r(tab + (size_t)i * TabFmt<T>::STRIDE);
+    T t = (u - r.v[0]) * r.v[1];
+    const T *a = r.v + 2, *b = r.v + 2 + (DEG + 1);
+    T c1 = a[DEG], g = b[DEG];
+#pragma unroll
+    for (int k = DEG - 1; k >= 0; k--) {
+        c1 = c1 * t + a[k];
+        g = g * t + b[k];
+    }
+    const T gx = g * vx, gy = g * vy, gz = g * vz;
+    acc[0] += gx * vx;
+    acc[1] += gx * vy;
+    acc[2] += gx * vz;
+    acc[3] += gy * vy;
+    acc[4] += gy * vz;
+    acc[5] += gz * vz;
+    c1sum += c1;
+}
+
 template <typename T>
 __device__ __forceinline__ T horner(const double *cf, T x)
 {
@@ -419,18 +449,29 @@ __device__ __forceinline__ void pair_real(const double *__restrict__ pw,
     T d[3];
     Sep<T>::get(pw, pw32, n3, nu, mu, c, d);
     const bool same = (nu == mu);
+    T c1sum = 0;
     ImageCursor cur;
     cur.start((float)d[0], (float)d[1], (float)d[2], c.Lf, c.invLf, rc);
     while (!cur.done) {
         T vx = d[0] + (T)cur.nx * c.L, vy = d[1] + (T)cur.ny * c.L, vz = d[2] + (T)cur.nz * c.L;
         T u = vx * vx + vy * vy + vz * vz;
-        bool zero_image = same && cur.at_origin();
+        // the bead's own zero image (nu = mu, n = 0) is the one image of a
+        // diagonal pair with u = 0 (its separation is exactly zero)
+        const bool zero_image = same && u == (T)0;
         if (u <= c.rc2 && !zero_image) {
-            if (u >= c.four_a2) add_m1_tab<T>(vx, vy, vz, u, tab, tab_i0, ntab, acc);
+            // FP32: the leaner table step (the FP64 kernel keeps the plain one,
+            // whose registers fit its 4 CTAs per SM without spills)
+            if (u >= c.four_a2) {
+                if constexpr (sizeof(T) == 4) add_m1_tab_in_range<T>(vx, vy, vz, u, tab, tab_i0, acc, c1sum);
+                else add_m1_tab<T>(vx, vy, vz, u, tab, tab_i0, ntab, acc);
+            }
             else if (!same && overlap_corr) add_overlap<T>(vx, vy, vz, u, c, acc);
             else add_m1<T>(vx, vy, vz, u, c, acc);
         }
         cur.advance();
+    }
+    if constexpr (sizeof(T) == 4) {
+        acc[0] += c1sum; acc[3] += c1sum; acc[5] += c1sum;
     }
     if (same) {
         acc[0] += c.self; acc[3] += c.self; acc[5] += c.self;
