@@ -11,6 +11,7 @@
 // symmetric and each 3x3 block is a symmetric tensor).  The same template
 // runs in FP64 (BD_FP64) and FP32 (mixed plans, which also write the 16-bit
 // tensor-core copy of D).
+#include <limits.h>
 #include <math.h>
 #include <string.h>
 
@@ -367,6 +368,7 @@ __device__ void add_overlap(T vx, T vy, T vz, T u, const EwaldT<T> &c, T acc[6])
 
 
 constexpr int TB = 16;                 // beads per tile side
+static_assert(TB == 16, "the assembly's warp layout takes 16 x 16 pairs per CTA");
 constexpr int TS = 3 * TB;             // matrix rows per tile side
 constexpr int TSP = TS + 1;            // padded smem row
 
@@ -478,6 +480,89 @@ __device__ __forceinline__ void pair_real(const double *__restrict__ pw,
     }
 }
 
+// M1 (or M1 + M* for an overlapping pair) of one image closer than 2a, for
+// the warp loop below: rare, and kept out of line so that its registers (the
+// series and erfc/exp evaluation) do not weigh on the loop's allocation
+struct Six {
+    float v[6];
+};
+__device__ __noinline__ Six near_image(float vx, float vy, float vz, float u, const EwaldT<float> &c,
+                                       bool overlap)
+{
+    float a[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+    if (overlap) add_overlap<float>(vx, vy, vz, u, c, a);
+    else add_m1<float>(vx, vy, vz, u, c, a);
+    Six r;
+#pragma unroll
+    for (int k = 0; k < 6; k++) r.v[k] = a[k];
+    return r;
+}
+
+// The same sum for the FP32 dense assembly, taken by the 32 pairs of a warp
+// together: the lanes walk one common set of lattice candidates n (the union
+// of their per-axis ranges, FP32 bounds widened by a margin as in the image
+// cursor) in lockstep, skip the rows and candidates that no lane keeps (a
+// vote), and a lane evaluates only the images inside its own sphere
+// |d + nL| <= r_c.  The per-lane cursor's nested loops put the lanes of a warp
+// at different loop levels (row set-up on some, image evaluation on others);
+// here the control flow is uniform and only the evaluation is masked.  Every
+// lane of the warp must call this (it holds warp votes); lanes without images
+// (inactive, or with a non-finite or farther than 2^20 L separation) pass
+// active = false and take no candidate.
+__device__ __forceinline__ void pair_real_warp(const float *__restrict__ pw32, long n3, int nu, int mu,
+                                               bool active, const EwaldT<float> &c,
+                                               const float *__restrict__ tab, int tab_i0,
+                                               int overlap_corr, float rc, float acc[6])
+{
+    constexpr unsigned kAll = 0xffffffffu;
+    float d[3] = {0.f, 0.f, 0.f};
+    if (active) Sep<float>::get(nullptr, pw32, n3, nu, mu, c, d);
+    const bool same = (nu == mu);
+    const float L = c.Lf, invL = c.invLf, rc2 = c.rc2;
+    const bool ok = active && isfinite(d[0] + d[1] + d[2]) &&
+                    fabsf(d[0]) + fabsf(d[1]) + fabsf(d[2]) <= 0x1p20f * L;
+    int lo[3], hi[3];
+#pragma unroll
+    for (int s = 0; s < 3; s++) {
+        const float l = ok ? ceilf((-rc - d[s]) * invL - 1e-4f) : 0.f;
+        const float h = ok ? floorf((rc - d[s]) * invL + 1e-4f) : 0.f;
+        lo[s] = __reduce_min_sync(kAll, ok ? (int)l : INT_MAX);
+        hi[s] = __reduce_max_sync(kAll, ok ? (int)h : INT_MIN);
+    }
+    float c1sum = 0.f;
+    for (int ix = lo[0]; ix <= hi[0]; ix++) {
+        const float vx = fmaf((float)ix, L, d[0]);
+        const float rx = vx * vx;
+        if (!__any_sync(kAll, ok && rx <= rc2)) continue;
+        for (int iy = lo[1]; iy <= hi[1]; iy++) {
+            const float vy = fmaf((float)iy, L, d[1]);
+            const float rxy = fmaf(vy, vy, rx);
+            if (!__any_sync(kAll, ok && rxy <= rc2)) continue;
+            for (int iz = lo[2]; iz <= hi[2]; iz++) {
+                const float vz = fmaf((float)iz, L, d[2]);
+                const float u = fmaf(vz, vz, rxy);
+                // the bead's own zero image (nu = mu, n = 0) is the one
+                // image of a diagonal pair with u = 0
+                const bool take = ok && u <= rc2 && !(same && u == 0.f);
+                if (!__any_sync(kAll, take)) continue;
+                if (take) {
+                    if (u >= c.four_a2) {
+                        add_m1_tab_in_range<float>(vx, vy, vz, u, tab, tab_i0, acc, c1sum);
+                    } else {
+                        const Six r = near_image(vx, vy, vz, u, c, !same && overlap_corr);
+#pragma unroll
+                        for (int k = 0; k < 6; k++) acc[k] += r.v[k];
+                    }
+                }
+            }
+        }
+    }
+    acc[0] += c1sum; acc[3] += c1sum; acc[5] += c1sum;
+    if (same && active) {
+        acc[0] += c.self; acc[3] += c.self; acc[5] += c.self;
+    }
+}
+
 constexpr int KC = 64;                 // k-vectors per shared-memory chunk
 
 // FP32: 48 registers and 5 CTAs per SM (issue-bound; 4 CTAs took 6 % longer, 6 no
@@ -502,7 +587,11 @@ k_build_D(const double *__restrict__ pw, const float *__restrict__ pw32, int n,
     while ((long)(J + 1) * (J + 2) / 2 <= idx) J++;
     int I = (int)(idx - (long)J * (J + 1) / 2);
     (void)ewc;
-    int ty = threadIdx.x / TB, tx = threadIdx.x % TB;
+    // each warp takes 4 consecutive beads nu x 8 consecutive beads mu (beads
+    // in chain order, so the warp's separations are close together and their
+    // periodic images overlap: fewer candidates for the warp image loop)
+    const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+    const int ty = 4 * (w & 3) + (l >> 3), tx = 8 * (w >> 2) + (l & 7);
     int nu = I * TB + ty, mu = J * TB + tx;
     T acc[6] = {0, 0, 0, 0, 0, 0};
     // diagonal tiles compute nu <= mu only; the rest is mirrored on write,
@@ -516,7 +605,10 @@ k_build_D(const double *__restrict__ pw, const float *__restrict__ pw32, int n,
         acc[0] = b[0]; acc[1] = b[1]; acc[2] = b[2];
         acc[3] = b[ld + 1]; acc[4] = b[ld + 2]; acc[5] = b[2 * ld + 2];
     }
-    if (active) pair_real<T>(pw, pw32, n3, nu, mu, c, tab, tab_i0, ntab, overlap_corr, rc, acc);
+    if constexpr (sizeof(T) == 4)
+        pair_real_warp(pw32, n3, nu, mu, active, c, tab, tab_i0, overlap_corr, rc, acc);
+    else if (active)
+        pair_real<T>(pw, pw32, n3, nu, mu, c, tab, tab_i0, ntab, overlap_corr, rc, acc);
     // reciprocal sum over half-space k (each folded with -k), staged per chunk
     for (int t0 = 0; t0 < nk; t0 += KC) {
         const int kc = min(KC, nk - t0);

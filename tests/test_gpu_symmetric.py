@@ -142,18 +142,21 @@ def test_symmetric_lagged_steps(bnd):
             assert st["status"] == 0 and st["accepted"] == 1
         res.append((st, DF.cpu().numpy(), dS.cpu().numpy(), R_before, dW))
         plan.close()
-    (s1, DF1, dS1, _, _), (s3, DF3, dS3, Rb, dW) = res
+    (s1, DF1, dS1, Rb1, dW), (s3, DF3, dS3, Rb3, _) = res
     # the bottom Ritz value of a few dozen lagged Lanczos steps has not
     # converged (clustered small eigenvalues) and moves with the summation
     # order of the products (measured 2.4e-4 relative); the top one converges
     assert abs(s3["d_min"] - s1["d_min"]) <= 2e-3 * s1["d_min"]
     assert abs(s3["d_max"] - s1["d_max"]) <= 1e-4 * s1["d_max"]
     assert relerr(DF3, DF1) <= 1e-5
-    assert relerr(dS3, dS1) <= 1e-4
-    R_ref, code, DF_r, dS_r, _ = oracle.step(p, Rb.reshape(R.shape), dW, s3["d_min"], s3["d_max"], nch)
-    assert code == 0
-    assert relerr(DF3, DF_r) <= 1e-5
-    assert relerr(dS3, dS_r) <= 1e-3
+    # each shape's Brownian term is taken on its own Chebyshev interval, so the
+    # two agree only to the mixed-mode bar; each matches the oracle at its bounds
+    assert relerr(dS3, dS1) <= 1e-3
+    for st, DFg, dSg, Rb in ((s1, DF1, dS1, Rb1), (s3, DF3, dS3, Rb3)):
+        R_ref, code, DF_r, dS_r, _ = oracle.step(p, Rb.reshape(R.shape), dW, st["d_min"], st["d_max"], nch)
+        assert code == 0
+        assert relerr(DFg, DF_r) <= 1e-5
+        assert relerr(dSg, dS_r) <= 1e-3
 
 
 def test_symmetric_n8000_sampled_rows(bnd):
