@@ -643,12 +643,18 @@ k_build_D(const double *__restrict__ pw, const float *__restrict__ pw32, int n,
     }
     if (D == nullptr) return;           // pair estimate only (matrix-free steps)
     __syncthreads();
-    // stage the 3x3 block: rows 3ty+a, cols 3tx+b
+    // stage the 3x3 block: rows 3ty+a, cols 3tx+b.  In a diagonal tile the
+    // block below the diagonal (ty > tx) is the mirror of (tx, ty): the block
+    // is symmetric, so the thread of (tx, ty) writes the same six values there
     {
-        T *b = &tile[(3 * ty) * TSP + 3 * tx];
-        b[0] = acc[0]; b[1] = acc[1]; b[2] = acc[2];
-        b[TSP] = acc[1]; b[TSP + 1] = acc[3]; b[TSP + 2] = acc[4];
-        b[2 * TSP] = acc[2]; b[2 * TSP + 1] = acc[4]; b[2 * TSP + 2] = acc[5];
+        auto put_block = [&](int by, int bx) {
+            T *b = &tile[(3 * by) * TSP + 3 * bx];
+            b[0] = acc[0]; b[1] = acc[1]; b[2] = acc[2];
+            b[TSP] = acc[1]; b[TSP + 1] = acc[3]; b[TSP + 2] = acc[4];
+            b[2 * TSP] = acc[2]; b[2 * TSP + 1] = acc[4]; b[2 * TSP + 2] = acc[5];
+        };
+        if (I != J || ty <= tx) put_block(ty, tx);
+        if (I == J && ty < tx) put_block(tx, ty);
     }
     __syncthreads();
     // four consecutive columns per thread and store (rows start 256-byte
@@ -662,8 +668,7 @@ k_build_D(const double *__restrict__ pw, const float *__restrict__ pw32, int n,
         if (r0 + r >= n3) continue;
         T v[4];
 #pragma unroll
-        for (int k = 0; k < 4; k++)
-            v[k] = (I == J && r / 3 > (cc + k) / 3) ? tile[(cc + k) * TSP + r] : tile[r * TSP + cc + k];
+        for (int k = 0; k < 4; k++) v[k] = tile[r * TSP + cc + k];
         const size_t idx = (size_t)((r0 + r) * ld + c0 + cc);
         if (c0 + cc + 4 <= n3) Store<T>::put4(D, D16, idx, v, is_bf16);
         else
