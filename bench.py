@@ -736,9 +736,13 @@ def run_batch(args):
     from paper_1203_6208_gb300 import binding as bnd, build, inputs
     build.build()
     cfgs = inputs.batch_systems(count=args.replicas)
+    # the Ewald split of every replica at 1.75 sqrt(pi)/L: the fastest batched
+    # step of a sweep over 1.5 .. 2.5 (beyond 2.0 the reciprocal sum leaves
+    # the tensor-core product)
+    alpha_factor = 1.75
     plist = []
     for c in cfgs:
-        c.alpha_factor = 1.5
+        c.alpha_factor = alpha_factor
         plist.append(c.params())
     m = 1
     nch = 30
@@ -805,7 +809,7 @@ def run_batch(args):
             "vs_baseline": None, "dtype": "f16+f32+f64", "data": "synthetic",
             "config": {"workload": "batch", "replicas": b.count, "beads_total": nbeads,
                        "n_range": [min(c.n for c in cfgs), max(c.n for c in cfgs)],
-                       "m": m, "n_cheb": nch, "bounds": "lagged", "alpha_factor": 1.5,
+                       "m": m, "n_cheb": nch, "bounds": "lagged", "alpha_factor": alpha_factor,
                        "d_arena_gb": b.d_total / 1e9},
             "bead_steps_per_s": nbeads * args.steps / (ms * 1e-3),
             "graph_launches": host_launches,
