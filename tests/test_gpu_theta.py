@@ -83,7 +83,9 @@ def test_theta_relaxation_from_off_equilibrium_starts():
     wrong drift factor or noise amplitude moves that limit, from either
     side.  Dilute and semidilute boxes (0.03 and 0.3 c*) with N_Ch = 40, so
     that the Chebyshev error stays below 1 % (checked) and the limit tests
-    the dynamics, not the series.  <R_e^2> = 3 (N_b - 1) is reached too (within its sampling error,
+    the dynamics, not the series.  Each group's <Q^2> is held to 4 standard
+    errors of its replica-to-replica scatter, as the equilibrium test above.
+    <R_e^2> = 3 (N_b - 1) is reached too (within its sampling error,
     ~4 % per group of eight replicas)."""
     if not torch.cuda.is_available():
         pytest.skip("no CUDA device")
@@ -120,7 +122,11 @@ def test_theta_relaxation_from_off_equilibrium_starts():
     assert max(x.ef_max for x in st) < 0.01, [x.ef_max for x in st]
     stretched, compressed = q[0::2], q[1::2]
     assert np.all(q0[0::2] > 8.0) and np.all(q0[1::2] < 0.5)
-    assert abs(stretched.mean() / 3.0 - 1) < 0.03, stretched
-    assert abs(compressed.mean() / 3.0 - 1) < 0.03, compressed
+    # each group's mean against <Q^2> = 3 within 4 standard errors of the
+    # replica-to-replica scatter (~1.4 % of the mean for eight replicas),
+    # and the two groups pooled likewise
+    for grp in (stretched, compressed, q):
+        se = grp.std(ddof=1) / np.sqrt(len(grp))
+        assert abs(grp.mean() - 3.0) < 4.0 * se, (grp, se)
     re2 = per[:, 1] / (3.0 * (nb - 1))
     assert abs(re2[0::2].mean() - 1) < 0.15 and abs(re2[1::2].mean() - 1) < 0.15, re2
