@@ -17,7 +17,9 @@
 // two for the columns (D_IJ^T X_I summed over the band's rows of one J,
 // double-buffered so the epilogue drains one while the next J accumulates).
 // The band's operand rows X_I stay in shared memory; each stage of the ring
-// holds one tile and X_J.  Partial sums leave the CTA as FP32 slots: one per
+// holds one tile and X_J.  One warp issues the TMA loads, two issue the MMAs
+// (the row products and the column products), four drain TMEM.  Partial sums
+// leave the CTA as FP32 slots: one per
 // (band, CTA) for the rows and one per (J-step, CTA) for the columns.  A
 // second kernel sums, for each 128-row block, its row slots and then its
 // column slots, band by band, in a fixed order (double-float, deterministic), and
@@ -40,7 +42,7 @@ using tc::BM;
 using tc::kWaitLimit;
 
 constexpr int R = 8;               // tile rows per band
-constexpr int THREADS = 192;       // warp 0 TMA, warp 1 MMA, warps 2-5 epilogue
+constexpr int THREADS = 224;       // warp 0 TMA, warps 1 and 6 MMA, warps 2-5 epilogue
 constexpr int A_TILE = 2 * BM * BK * 2;   // one 128 x 128 tile: two 64-column boxes
 template <int BN> __host__ __device__ constexpr int xbox() { return BN * BK * 2; }   // 64 operand rows
 template <int BN> __host__ __device__ constexpr int stage_bytes() { return A_TILE + 2 * xbox<BN>(); }
@@ -165,7 +167,7 @@ k_sym_gemm(const __grid_constant__ CUtensorMap mapD, const __grid_constant__ CUt
     uint8_t *vband = smem + ST * STAGE;
     __shared__ __align__(8) uint64_t full_bar[ST], empty_bar[ST];
     __shared__ __align__(8) uint64_t vb_full, vb_empty, row_full, row_empty, col_full[2],
-        col_empty[2], drain_bar, stall_bar;
+        col_empty[2], drain_bar, drain_bar2, stall_bar;
     __shared__ uint32_t tmem_base_sh;
     __shared__ volatile int abort_flag;
 
@@ -179,7 +181,7 @@ k_sym_gemm(const __grid_constant__ CUtensorMap mapD, const __grid_constant__ CUt
         abort_flag = 0;
         for (int s = 0; s < ST; s++) {
             tc::mbar_init(tc::smem_u32(&full_bar[s]), 1);
-            tc::mbar_init(tc::smem_u32(&empty_bar[s]), 1);
+            tc::mbar_init(tc::smem_u32(&empty_bar[s]), 2);
         }
         tc::mbar_init(tc::smem_u32(&vb_full), 1);
         tc::mbar_init(tc::smem_u32(&vb_empty), 1);
@@ -190,6 +192,7 @@ k_sym_gemm(const __grid_constant__ CUtensorMap mapD, const __grid_constant__ CUt
             tc::mbar_init(tc::smem_u32(&col_empty[q]), 128);
         }
         tc::mbar_init(tc::smem_u32(&drain_bar), 1);
+        tc::mbar_init(tc::smem_u32(&drain_bar2), 1);
         tc::mbar_init(tc::smem_u32(&stall_bar), 1);          // never completed
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
@@ -282,15 +285,22 @@ k_sym_gemm(const __grid_constant__ CUtensorMap mapD, const __grid_constant__ CUt
             it_next(t, T);
         }
         pseg = seg;
-    } else if (warp == 1 && lane == 0) {
-        // ---- MMA issuer
+    } else if ((warp == 1 || warp == 6) && lane == 0) {
+        // ---- MMA issuers: warp 1 the row products D_IJ X_J (K-major tile),
+        // warp 6 the column products D_IJ^T X_I (the same tile MN-major);
+        // each commits every ring stage (its empty barrier counts two), the
+        // row issuer the band's row accumulators, the column issuer the
+        // J-step's column accumulator and the band's operand rows X_I.  Two
+        // issuers overlap the per-instruction issue cost of the 16 small MMAs
+        // of a tile (2.5 % on the product)
+        const bool rows = warp == 1;
         It t;
         it_seek(t, u0, g.boff, g.nb, T);
         bool ok = true;
         int seg = 0, jsteps = 0, pb = -1, pJ = -1;
         uint32_t started = 0;
         bool col_on = false;
-        if ((int)blockIdx.x == stall_cta) {
+        if (rows && (int)blockIdx.x == stall_cta) {
             // test hook (bd_plan_test_stall): a wait on a barrier that nothing
             // completes, given up after a bounded spin like any wait that ran
             // out; the CTA then takes the abort path below
@@ -306,17 +316,18 @@ k_sym_gemm(const __grid_constant__ CUtensorMap mapD, const __grid_constant__ CUt
             const bool first_j = first_band || (t.J != pJ);
             const bool last_j = last_band || (nx.J != t.J);
             if (first_band) {
-                if (seg > 0 &&
-                    !tc::mbar_wait(tc::smem_u32(&row_empty), (uint32_t)(seg - 1) & 1u, &abort_flag)) {
-                    ok = false;
-                    break;
-                }
-                if (!tc::mbar_wait(tc::smem_u32(&vb_full), (uint32_t)seg & 1u, &abort_flag)) {
+                if (rows) {
+                    if (seg > 0 &&
+                        !tc::mbar_wait(tc::smem_u32(&row_empty), (uint32_t)(seg - 1) & 1u, &abort_flag)) {
+                        ok = false;
+                        break;
+                    }
+                    started = 0;
+                } else if (!tc::mbar_wait(tc::smem_u32(&vb_full), (uint32_t)seg & 1u, &abort_flag)) {
                     ok = false;
                     break;
                 }
                 asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-                started = 0;
                 seg++;
             }
             if (first_j) col_on = false;
@@ -326,19 +337,18 @@ k_sym_gemm(const __grid_constant__ CUtensorMap mapD, const __grid_constant__ CUt
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
             const int rr = t.I - t.b * R;
             const uint32_t a = tc::smem_u32(smem + s * STAGE);
-            const uint32_t xj = a + A_TILE;
-            // Y_I += D_IJ X_J: the tile K-major, K = the tile's columns
-            const uint32_t acc_r = tmem + (uint32_t)(rr * BN);
-            const bool racc = (started >> rr) & 1u;
+            if (rows) {
+                const uint32_t xj = a + A_TILE;
+                const uint32_t acc_r = tmem + (uint32_t)(rr * BN);
+                const bool racc = (started >> rr) & 1u;
 #pragma unroll
-            for (int k = 0; k < 8; k++) {
-                const uint64_t da = tc::sw128_desc(a + (k >> 2) * (BM * BK * 2)) + (uint64_t)(2 * (k & 3));
-                const uint64_t db = tc::sw128_desc(xj + (k >> 2) * XB) + (uint64_t)(2 * (k & 3));
-                tc::mma_f16(acc_r, da, db, idesc_k, (racc || k > 0) ? 1u : 0u);
-            }
-            started |= 1u << rr;
-            if (t.I != t.J) {
-                // Y_J += D_IJ^T X_I: the same tile MN-major, K = the tile's rows
+                for (int k = 0; k < 8; k++) {
+                    const uint64_t da = tc::sw128_desc(a + (k >> 2) * (BM * BK * 2)) + (uint64_t)(2 * (k & 3));
+                    const uint64_t db = tc::sw128_desc(xj + (k >> 2) * XB) + (uint64_t)(2 * (k & 3));
+                    tc::mma_f16(acc_r, da, db, idesc_k, (racc || k > 0) ? 1u : 0u);
+                }
+                started |= 1u << rr;
+            } else if (t.I != t.J) {
                 if (!col_on && jsteps >= 2 &&
                     !tc::mbar_wait(tc::smem_u32(&col_empty[jsteps & 1]),
                                    (uint32_t)((jsteps >> 1) - 1) & 1u, &abort_flag)) {
@@ -357,23 +367,21 @@ k_sym_gemm(const __grid_constant__ CUtensorMap mapD, const __grid_constant__ CUt
                 col_on = true;
             }
             tc::mma_commit(tc::smem_u32(&empty_bar[s]));
-            if (last_j && col_on) {
+            if (!rows && last_j && col_on) {
                 tc::mma_commit(tc::smem_u32(&col_full[jsteps & 1]));
                 jsteps++;
             }
-            if (last_band) {
-                tc::mma_commit(tc::smem_u32(&row_full));
-                tc::mma_commit(tc::smem_u32(&vb_empty));
-            }
+            if (last_band) tc::mma_commit(tc::smem_u32(rows ? &row_full : &vb_empty));
             pb = t.b;
             pJ = t.J;
             t = nx;
         }
         if (!ok) {
-            tc::mma_commit(tc::smem_u32(&drain_bar));
-            for (uint32_t k = 0; k < kWaitLimit && !tc::mbar_try(tc::smem_u32(&drain_bar), 0); k++) {}
+            uint64_t *db = rows ? &drain_bar : &drain_bar2;
+            tc::mma_commit(tc::smem_u32(db));
+            for (uint32_t k = 0; k < kWaitLimit && !tc::mbar_try(tc::smem_u32(db), 0); k++) {}
         }
-    } else if (warp >= 2) {
+    } else if (warp >= 2 && warp <= 5) {
         // ---- epilogue warps: TMEM lane quadrant q, row r of the tile
         const int q = warp & 3;
         const int r = q * 32 + lane;
