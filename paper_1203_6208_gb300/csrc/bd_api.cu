@@ -225,7 +225,7 @@ bd_status bd_plan_create(const bd_params *params, bd_plan **out_plan)
     TRY(dmalloc(P, &P.d_step_ctr, 1));
     TRY(dmalloc(P, &P.d_dS, n3 * R));
     TRY(dmalloc(P, &P.d_dW, n3 * R));
-    TRY(dmalloc(P, &P.d_coef, kMaxCheb));
+    TRY(dmalloc(P, &P.d_coef, kMaxCheb + 2));
     TRY(dmalloc(P, &P.d_wdw, kMaxRhs));
     TRY(dmalloc(P, &P.d_red, 4 * kMaxRhs));
     TRY(dmalloc(P, &P.d_redpart, (size_t)kRedBlocks * kMaxRhs));

@@ -62,6 +62,12 @@ template <typename T> struct EwaldT {
 constexpr int kMaxKvec = 4096;        // half-space k-vectors a plan may use
 constexpr int kMaxRhs = 32;           // Wiener columns per product
 constexpr int kMaxCheb = 256;         // Chebyshev terms
+// The interval map of a Chebyshev series (Eq. cheb2: y = s x - t with
+// s = 2 / (d_max - d_min), t = (d_max + d_min) / (d_max - d_min)), formed once
+// per series beside its coefficients: coef[kChebMapS], coef[kChebMapT].  FP64
+// divisions are long sequences on this GPU's slow FP64 pipe; the products'
+// epilogues read the two values instead of dividing per CTA or per element.
+constexpr int kChebMapS = kMaxCheb, kChebMapT = kMaxCheb + 1;
 constexpr int kMaxLanczos = 128;      // Lanczos steps
 constexpr int kLdAlign = 64;          // D leading dimension multiple (elements)
 
@@ -113,7 +119,7 @@ struct Plan {
     double *d_X0, *d_Y0;               // first product [F, dW, extra] and its image (3N x (max_rhs+3))
     double *d_dS;                      // noise when the caller passes no dS
     double *d_dW;                      // Wiener block when generated on device
-    double *d_coef;                    // Chebyshev coefficients [kMaxCheb]
+    double *d_coef;                    // Chebyshev coefficients [kMaxCheb], then the interval map
     double *d_wdw;                     // dW.D.dW per column [kMaxRhs]
     double *d_red;                     // reduction results [4*kMaxRhs]
     double *d_redpart;                 // per-block partial sums [kRedBlocks * kMaxRhs]

@@ -87,8 +87,7 @@ k_gemm_f64(const double *__restrict__ D, long ld, int n3, const double *__restri
             if (j < m) Y[(long)j * n3 + gr] = acc[c];
         }
     } else {
-        const double dmin = e.bounds[0], dmax = e.bounds[1];
-        const double ys = 2.0 / (dmax - dmin), yt = (dmax + dmin) / (dmax - dmin);
+        const double ys = e.coef[kChebMapS], yt = e.coef[kChebMapT];
         const double cp = e.coef[e.p];
 #pragma unroll
         for (int c = 0; c < S::CPT; c++) {
@@ -348,9 +347,7 @@ k_gemm_df(const double *__restrict__ D, long ld, int n3, const float *__restrict
             if (j < m) Y[(long)j * n3 + gr] = (double)acc[c].s + (double)acc[c].c;
         }
     } else {
-        const double dmin = e.bounds[0], dmax = e.bounds[1];
-        const double iw = 1.0 / (dmax - dmin);
-        const double ys = 2.0 * iw, yt = (dmax + dmin) * iw;
+        const double ys = e.coef[kChebMapS], yt = e.coef[kChebMapT];
         const double cp = e.coef[e.p];
 #pragma unroll
         for (int c = 0; c < S::CPT; c++) {

@@ -249,9 +249,7 @@ k_rows_cheb(const RowsRep *__restrict__ reps, int nreps, const int *__restrict__
             const double *V1 = (p & 1) ? R.VA : R.VB;
             float sums[WRC][C];
             rows_dot<C, WRC>(R.D16, R.ld, R.n3, X, R.xs, row0, R.is_bf16, sums, sx);
-            const double dmin = R.bounds[0], dmax = R.bounds[1];
-            const double iw = 1.0 / (dmax - dmin);
-            const double ys = 2.0 * iw, yt = (dmax + dmin) * iw;
+            const double ys = R.coef[kChebMapS], yt = R.coef[kChebMapT];
             const double cp = R.coef[p];
             for (int e = lane; e < WRC * C; e += 32) {
                 const int r = e / C, c = e % C;

@@ -568,21 +568,13 @@ k_sym_reduce(Geo g, const float *__restrict__ part, int n3, tc::Epi e)
     }
     // Chebyshev term of Eqs. (cheb2)/(cheb3): V_p = 2 (s W - t V_{p-1}) - V_{p-2},
     // dS += c_p V_p, and the scaled 16-bit V_p as the next product's operand.
-    // The interval map s, t is formed once per CTA (FP64 divisions run on
-    // this GPU's slow FP64 pipe), folded with the factor 2 and the column's
-    // inverse scale (a power of two) so that each element costs four FP64
-    // fused multiply-adds: V_p = 2s isc (sh + sl) - (2t V_{p-1} + V_{p-2}).
-    __shared__ double s_map[3];
-    if (r == 0) {
-        const double dmin = e.bounds[0], dmax = e.bounds[1];
-        const double iw = 1.0 / (dmax - dmin);
-        s_map[0] = 4.0 * iw * (double)isc;
-        s_map[1] = 2.0 * (dmax + dmin) * iw;
-        s_map[2] = e.coef[e.p];
-    }
-    __syncthreads();
+    // The interval map s, t (formed once per series beside the coefficients)
+    // is folded with the factor 2 and the column's inverse scale (a power of
+    // two) so that each element costs four FP64 fused multiply-adds:
+    // V_p = 2s isc (sh + sl) - (2t V_{p-1} + V_{p-2}).
     if (row >= n3) return;
-    const double ya = s_map[0], yb = s_map[1], cp = s_map[2];
+    const double ya = 2.0 * e.coef[kChebMapS] * (double)isc, yb = 2.0 * e.coef[kChebMapT];
+    const double cp = e.coef[e.p];
     const long o = (long)cc * n3 + row;
     const double p1 = e.Vprev1[o], p2 = e.Vprev2[o], d0 = e.dS[o];
     const double v = fma(ya, tc::f32_to_f64(sh), fma(ya, tc::f32_to_f64(sl), -fma(yb, p1, p2)));

@@ -222,8 +222,7 @@ k_tc_gemm(const __grid_constant__ CUtensorMap mapD, const __grid_constant__ CUte
                     for (int cc = 0; cc < BN; cc++)
                         if (cc < e.m) e.Y[(long)cc * n3 + row] = y[cc] * (double)e.inv_scale[cc];
                 } else {
-                    const double dmin = e.bounds[0], dmax = e.bounds[1];
-                    const double ys = 2.0 / (dmax - dmin), yt = (dmax + dmin) / (dmax - dmin);
+                    const double ys = e.coef[kChebMapS], yt = e.coef[kChebMapT];
                     const double cp = e.coef[e.p];
                     // columns in chunks of 8: every load of a chunk is issued
                     // before its stores (the vectors may alias as far as the

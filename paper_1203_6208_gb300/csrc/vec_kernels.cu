@@ -154,6 +154,10 @@ __global__ void k_cheb_coeffs(const double *bounds, int nch, double *c)
         __syncthreads();
     }
     if (threadIdx.x == 0) c[p] = 2.0 * red[0] / nch;
+    if (p == 0 && threadIdx.x == 0) {
+        c[kChebMapS] = 2.0 / (dmax - dmin);
+        c[kChebMapT] = (dmax + dmin) / (dmax - dmin);
+    }
 }
 
 void launch_cheb_coeffs(Plan &P, const double *bounds, int nch, cudaStream_t s)
@@ -168,8 +172,8 @@ __global__ void k_cheb_first(const double *dW, const double *DW, long len, const
 {
     long i = (long)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= len) return;
-    double dmin = bounds[0], dmax = bounds[1];
-    double ys = 2.0 / (dmax - dmin), yt = (dmax + dmin) / (dmax - dmin);
+    (void)bounds;
+    const double ys = coef[kChebMapS], yt = coef[kChebMapT];
     double w = dW[i];
     double v1 = ys * DW[i] - yt * w;
     V0[i] = w;
@@ -193,8 +197,8 @@ __global__ void k_cheb_term(const double *W, const double *V1, double *V2, long 
 {
     long i = (long)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= len) return;
-    double dmin = bounds[0], dmax = bounds[1];
-    double ys = 2.0 / (dmax - dmin), yt = (dmax + dmin) / (dmax - dmin);
+    (void)bounds;
+    const double ys = coef[kChebMapS], yt = coef[kChebMapT];
     double v = 2.0 * (ys * W[i] - yt * V1[i]) - V2[i];
     V2[i] = v;
     dS[i] += coef[p] * v;
