@@ -500,9 +500,11 @@ def measure(args, precision, p, R0, rank, ws):
     l0 = bnd.kernel_launches()
     plan.product_timing(True)
     e0.record(stream)
+    torch.cuda.nvtx.range_push("timed_direct_steps")
     for k in range(args.steps):
         plan.set_phase_events(evs[k])
         plan.step(R, D, None, step_index=args.warmup + k, **kw)
+    torch.cuda.nvtx.range_pop()
     e1.record(stream)
     torch.cuda.synchronize()
     prod_ms, prod_n = plan.product_timing(False)
@@ -526,8 +528,10 @@ def measure(args, precision, p, R0, rank, ws):
             torch.distributed.barrier()
         torch.cuda.synchronize()
         e0.record(stream)
+        torch.cuda.nvtx.range_push("timed_steps")     # a profiler can select these launches
         for k in range(args.steps):
             plan.step_replay()
+        torch.cuda.nvtx.range_pop()
         e1.record(stream)
         torch.cuda.synchronize()
         ms = e0.elapsed_time(e1)
