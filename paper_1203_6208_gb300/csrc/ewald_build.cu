@@ -289,27 +289,34 @@ __device__ __forceinline__ void add_m1_tab(T vx, T vy, T vz, T u, const T *__res
     acc[5] += c1 + g * vz * vz;
 }
 
-// The same for the image loop of the dense assembly, where the caller has
-// already checked 4a^2 <= u <= r_c^2 in the working precision: the interval
-// index then lies in [0, ntab) without a clamp (the table range is built from
-// the same FP32 values, 4a^2 and r_c^2 (1 + 1e-6)).  The isotropic part c1 is
+// The same for the image loop of the FP32 dense assembly, where the caller
+// has already checked 4a^2 <= u <= r_c^2: the interval index then lies in
+// [0, ntab) without a clamp (the table range is built from the same FP32
+// values, 4a^2 and r_c^2 (1 + 1e-6)).  The intervals split each binade into
+// 2^BITS equal parts, so the low 23 - BITS fraction bits of u are its offset
+// in its interval: 1 + offset / 2^(23 - BITS) is built as a float f in
+// [1, 2) and t = 2 f - 3 equals (u - mid) / hw exactly, so only the row's ten
+// coefficients are loaded (40 of its 48 bytes).  The isotropic part c1 is
 // summed into c1sum (added to the three diagonal components once per pair).
-template <typename T>
-__device__ __forceinline__ void add_m1_tab_in_range(T vx, T vy, T vz, T u, const T *__restrict__ tab,
-                                                    int i0, T acc[6], T &c1sum)
+__device__ __forceinline__ void add_m1_tab_in_range(float vx, float vy, float vz, float u,
+                                                    const float *__restrict__ tab, int i0,
+                                                    float acc[6], float &c1sum)
 {
-    constexpr int DEG = TabFmt<T>::DEG;
-    const int i = (int)(__float_as_uint((float)u) >> TabFmt<T>::SHIFT) - i0;
-    const TabRow<T> r(tab + (size_t)i * TabFmt<T>::STRIDE);
-    T t = (u - r.v[0]) * r.v[1];
-    const T *a = r.v + 2, *b = r.v + 2 + (DEG + 1);
-    T c1 = a[DEG], g = b[DEG];
-#pragma unroll
-    for (int k = DEG - 1; k >= 0; k--) {
-        c1 = c1 * t + a[k];
-        g = g * t + b[k];
-    }
-    const T gx = g * vx, gy = g * vy, gz = g * vz;
+    constexpr int BITS = TabFmt<float>::BITS, SHIFT = TabFmt<float>::SHIFT;
+    static_assert(TabFmt<float>::DEG == 4 && TabFmt<float>::STRIDE == 12,
+                  "row layout: mid, 1/hw, a0 .. a4, b0 .. b4");
+    const unsigned ub = __float_as_uint(u);
+    const float *row = tab + (size_t)((int)(ub >> SHIFT) - i0) * TabFmt<float>::STRIDE;
+    const float2 q0 = __ldg((const float2 *)(row + 2));      // a0 a1
+    const float4 q1 = __ldg((const float4 *)(row + 4));      // a2 a3 a4 b0
+    const float4 q2 = __ldg((const float4 *)(row + 8));      // b1 b2 b3 b4
+    const float t = fmaf(2.f, __uint_as_float(0x3F800000u | ((ub << BITS) & 0x7FFFFFu)), -3.f);
+    float c1 = q1.z, g = q2.w;
+    c1 = c1 * t + q1.y; g = g * t + q2.z;
+    c1 = c1 * t + q1.x; g = g * t + q2.y;
+    c1 = c1 * t + q0.y; g = g * t + q2.x;
+    c1 = c1 * t + q0.x; g = g * t + q1.w;
+    const float gx = g * vx, gy = g * vy, gz = g * vz;
     acc[0] += gx * vx;
     acc[1] += gx * vy;
     acc[2] += gx * vz;
@@ -464,7 +471,7 @@ __device__ __forceinline__ void pair_real(const double *__restrict__ pw,
             // FP32: the leaner table step (the FP64 kernel keeps the plain one,
             // whose registers fit its 4 CTAs per SM without spills)
             if (u >= c.four_a2) {
-                if constexpr (sizeof(T) == 4) add_m1_tab_in_range<T>(vx, vy, vz, u, tab, tab_i0, acc, c1sum);
+                if constexpr (sizeof(T) == 4) add_m1_tab_in_range(vx, vy, vz, u, tab, tab_i0, acc, c1sum);
                 else add_m1_tab<T>(vx, vy, vz, u, tab, tab_i0, ntab, acc);
             }
             else if (!same && overlap_corr) add_overlap<T>(vx, vy, vz, u, c, acc);
@@ -547,7 +554,7 @@ __device__ __forceinline__ void pair_real_warp(const float *__restrict__ pw32, l
                 if (!__any_sync(kAll, take)) continue;
                 if (take) {
                     if (u >= c.four_a2) {
-                        add_m1_tab_in_range<float>(vx, vy, vz, u, tab, tab_i0, acc, c1sum);
+                        add_m1_tab_in_range(vx, vy, vz, u, tab, tab_i0, acc, c1sum);
                     } else {
                         const Six r = near_image(vx, vy, vz, u, c, !same && overlap_corr);
 #pragma unroll
