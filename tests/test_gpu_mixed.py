@@ -169,6 +169,30 @@ def test_build_D_f32_reciprocal_paths(bnd, n_chains, nb, alpha_factor):
     assert np.array_equal(D32, D32.T)
 
 
+@pytest.mark.parametrize("alpha_factor", [0.5, 2.0])
+def test_build_D_f32_warp_image_loop(bnd, alpha_factor):
+    """The FP32 image sum taken by the 32 pairs of a warp together: 35 beads
+    (warps with inactive lanes, diagonal tiles), a wide real-space sphere at
+    alpha = 0.5 sqrt(pi)/L (r_c = 4.8 L: up to 11 lattice candidates per axis)
+    and the benchmark's 2 sqrt(pi)/L; images inside 2a (the out-of-line
+    branch, one of them through a periodic image) and two coincident beads
+    (u = 0 for a pair of distinct beads: the overlap limit, not the skipped
+    zero image of a bead with itself)."""
+    cfg = inputs.SystemConfig(n_chains=5, nb=7, c_over_cstar=1.0, seed=73, alpha_factor=alpha_factor)
+    p = cfg.params()
+    R = inputs.make_chains(cfg)
+    a = p["a"]
+    e = np.array([0.6, -0.48, 0.64])
+    R[3] = R[2] + 0.05 * a * e
+    R[12] = R[4] + 0.7 * a * e + p["L"] * np.array([1.0, -2.0, 0.0])
+    R[30] = R[29]
+    plan, Rg, D = mixed(bnd, p, R)
+    Dr = oracle.build_D(p, R)
+    D32 = plan.D_view(D, "f32").cpu().numpy().astype(np.float64)
+    assert relerr(D32, Dr) <= 2e-6
+    assert np.array_equal(D32, D32.T)
+
+
 @pytest.mark.parametrize("alpha_factor,nk,tol", [(2.0, 230, 2e-6), (3.0, 787, 5e-6)])
 def test_build_D_f32_dilute_k_sphere(bnd, alpha_factor, nk, tol):
     """800 beads in a dilute box (L = 27.6) where k_max^2 a^2 < 3 holds up
