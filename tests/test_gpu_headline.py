@@ -72,14 +72,16 @@ def test_headline_mixed_step_and_replay_vs_oracle(bnd):
     torch.cuda.synchronize()
     st0 = bnd.read_stats(stats)
     # rows of the FP32 D of that step (R0): tiles on and above the diagonal
+    # (the symmetric shape leaves the rest of the lower triangle unwritten,
+    # so only those columns are read back)
     D32 = plan.D_view(D, "f32")
     for b0 in (0, 3997, 7992):
         rows = oracle.build_D_rows(p, R0, b0, b0 + 8)
-        got = D32[3 * b0:3 * b0 + 24].cpu().numpy().astype(np.float64)
         for i in range(24):
             r = 3 * b0 + i
             c0 = (r // 128) * 128
-            assert relerr(got[i, c0:], rows[i, c0:]) <= 2e-6, (b0, i)
+            got = D32[r, c0:].cpu().numpy().astype(np.float64)
+            assert relerr(got, rows[i, c0:]) <= 2e-6, (b0, i)
     R1 = R.cpu().numpy().copy()
     e0 = check_step(p, R0, R1, dW0, st0, DF.cpu().numpy(), dS.cpu().numpy())
 
