@@ -14,6 +14,7 @@
 // so every replay draws new noise.
 #include <string.h>
 
+#include <algorithm>
 #include <new>
 #include <vector>
 
@@ -116,19 +117,26 @@ bd_status bd_batch_create(const bd_params *params, int32_t count, bd_batch **out
                 return st;
             }
         }
-        std::vector<int> items;
-        for (int i = 0; i < count; i++) {
-            b->item0.push_back(b->nitems);
+        // the item table lists the replicas with the longest rows (largest N)
+        // first: items are claimed in table order, so the long ones start
+        // early and the short ones fill in at the end of each term
+        std::vector<int> order(count), items;
+        for (int i = 0; i < count; i++) order[i] = i;
+        std::stable_sort(order.begin(), order.end(),
+                         [&](int x, int y) { return params[x].n_beads > params[y].n_beads; });
+        b->item0.assign(count, 0);
+        for (int i : order) {
+            b->item0[i] = b->nitems;
             const int k = step_part_items(b->plans[i]);
             for (int t = 0; t < k; t++) items.push_back(i);
             b->nitems += k;
         }
         cudaError_t e = cudaMalloc(&b->d_reps, sizeof(RowsRep) * count);
         if (e == cudaSuccess) e = cudaMalloc(&b->d_items, sizeof(int) * items.size());
-        if (e == cudaSuccess) e = cudaMalloc(&b->d_bar, 4 * sizeof(unsigned));
+        if (e == cudaSuccess) e = cudaMalloc(&b->d_bar, kRowsBarAlloc * sizeof(unsigned));
         if (e == cudaSuccess)
             e = cudaMemcpy(b->d_items, items.data(), sizeof(int) * items.size(), cudaMemcpyHostToDevice);
-        if (e == cudaSuccess) e = cudaMemset(b->d_bar, 0, 4 * sizeof(unsigned));
+        if (e == cudaSuccess) e = cudaMemset(b->d_bar, 0, kRowsBarAlloc * sizeof(unsigned));
         if (e != cudaSuccess) {
             cudaGetLastError();
             destroy_batch(b);

@@ -19,7 +19,10 @@
 // FP32 operand, the Lanczos product w and its per-item dot partials); a
 // grid barrier; phase B (with the Lanczos column), every item's rows of
 // q_{j+1}, with alpha_j, beta_j reduced from the replica's partials in a
-// fixed order; a grid barrier.  The barriers spin with a bound: a CTA that
+// fixed order; a grid barrier.  In phase A the CTAs claim items from a
+// per-term counter (an item's rows cost as much as its replica's row length,
+// 600 to 6000 entries in a batch; the item table lists the largest replicas
+// first); which CTA takes an item does not change its result.  The barriers spin with a bound: a CTA that
 // gives up records BD_ERR_TIMEOUT and goes on (the results are then invalid,
 // nothing hangs).
 #include <math.h>
@@ -233,13 +236,19 @@ k_rows_cheb(const RowsRep *__restrict__ reps, int nreps, const int *__restrict__
             int nitems, int p_first, int p_end, int lan_from, unsigned *bar)
 {
     __shared__ double s_lan[RBC][3];
-    __shared__ int s_last;
+    __shared__ int s_last, s_item;
     __shared__ __align__(16) float sx[C * KC];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    unsigned *work = bar + kRowsBarWords;          // one item counter per term, zeroed per launch
     for (int p = p_first; p < p_end; p++) {
         const int j = lan_from + p - 1;
-        // ---- phase A: products and their epilogues
-        for (int it = blockIdx.x; it < nitems; it += gridDim.x) {
+        // ---- phase A: products and their epilogues, items claimed in turn
+        for (;;) {
+            if (threadIdx.x == 0) s_item = (int)atomicAdd(&work[p], 1u);
+            __syncthreads();
+            const int it = s_item;
+            __syncthreads();
+            if (it >= nitems) break;
             const RowsRep &R = reps[item_rep[it]];
             const int loc = it - R.item0;
             const int row0 = loc * RBC + warp * WRC;
@@ -339,16 +348,16 @@ bd_status rows_plan_init(Plan &P)
     if (e == cudaSuccess) e = cudaMalloc(&P.d_rows_part, (size_t)3 * items * sizeof(double));
     if (e == cudaSuccess) e = cudaMalloc(&P.d_rows_rep, sizeof(RowsRep));
     if (e == cudaSuccess) e = cudaMalloc(&P.d_rows_items, (size_t)items * sizeof(int));
-    if (e == cudaSuccess) e = cudaMalloc(&P.d_rows_bar, 4 * sizeof(unsigned));
+    if (e == cudaSuccess) e = cudaMalloc(&P.d_rows_bar, kRowsBarAlloc * sizeof(unsigned));
     if (e != cudaSuccess) {
         cudaGetLastError();
         return set_error(BD_ERR_OOM, "row-streamed product scratch: %s", cudaGetErrorString(e));
     }
     P.scratch_bytes += (int64_t)(nx * sizeof(float) + 3 * items * sizeof(double) +
-                                 sizeof(RowsRep) + items * sizeof(int) + 4 * sizeof(unsigned));
+                                 sizeof(RowsRep) + items * sizeof(int) + kRowsBarAlloc * sizeof(unsigned));
     cudaMemset(P.d_x32, 0, nx * sizeof(float));
     cudaMemset(P.d_rows_items, 0, (size_t)items * sizeof(int));
-    cudaMemset(P.d_rows_bar, 0, 4 * sizeof(unsigned));
+    cudaMemset(P.d_rows_bar, 0, kRowsBarAlloc * sizeof(unsigned));
     return check_launch("row-streamed product init");
 }
 
@@ -433,6 +442,7 @@ bd_status rows_cheb_launch(const RowsRep *reps, int nreps, const int *item_rep, 
     if (grid > nitems) grid = nitems;
     if (grid < 1) return set_error(BD_ERR_CUDA, "no resident CTA for the batched Chebyshev loop");
     cudaMemsetAsync(bar, 0, sizeof(unsigned), s);      // arrival count (a timed-out launch may leave it)
+    cudaMemsetAsync(bar + kRowsBarWords, 0, sizeof(unsigned) * kMaxCheb, s);   // per-term item counters
     cudaLaunchAttribute attr[1];
     attr[0].id = cudaLaunchAttributeCooperative;
     attr[0].val.cooperative = 1;

@@ -8,6 +8,10 @@ namespace bd {
 constexpr int kRowsShape = 5;
 constexpr int kRowsMaxCols = 8;   // columns of one row-streamed product
 constexpr int kRowsMaxLoopCols = 5;   // columns of the Chebyshev loop (m <= 4 and the Lanczos vector)
+// the loop's control words: grid-barrier count and generation, the Lanczos
+// item count, a spare word, then one item counter per Chebyshev term
+constexpr int kRowsBarWords = 4;
+constexpr int kRowsBarAlloc = kRowsBarWords + kMaxCheb;
 
 // one replica of a batched Chebyshev loop (device table entry)
 struct RowsRep {
