@@ -25,7 +25,7 @@
 
 namespace bd {
 
-constexpr double kPiA = 3.14159265358979323846;
+constexpr int kEfRun = 8;            // consecutive N whose E_f estimates one host wait reads
 
 // partial sums of a.a, a.b and b.b per column (block b of kRedBlocks)
 __global__ void k_moment_part(const double *A, const double *B, int n3, double *part)
@@ -78,51 +78,56 @@ __global__ void k_moment_update(const double *part, int nparts, int m, int p, do
     }
 }
 
-// E_f(N) of every column from the moments (one block of 256 threads,
-// N <= 256): c_p of the N-term interpolant, the quadratic form above, and
-// the maximum over columns in est[m]
-__global__ void k_ef_estimate(const double *mom, int m, const double *bounds, int N, double *est)
+// E_f(N) of one column from the moments: block (j, b) takes column j at
+// N = N0 + b (N <= 256, 256 threads), so one launch gives the estimates of a
+// run of N values for every column.  The interpolant's c_t = (2/N) sum_k f_k
+// cos(pi t (k + 1/2) / N), f_k = sqrt(h cos(pi (k + 1/2) / N) + mid): the f_k
+// once per block, the cosines of thread t by rotating (cos, sin) through
+// the N nodes (four FP64 multiply-adds a node instead of a cosine; the FP64
+// pipe of this GPU runs at 1/64 of FP32), then the quadratic form above and
+// est[b m + j] = E_f.
+__global__ void k_ef_estimate(const double *mom, int m, const double *bounds, int N0, double *est)
 {
     __shared__ double c[kMaxCheb];
+    __shared__ double f[kMaxCheb];
     __shared__ double red[256];
-    const int t = threadIdx.x;
+    const int t = threadIdx.x, j = blockIdx.x, N = N0 + (int)blockIdx.y;
     const double dmin = bounds[0], dmax = bounds[1];
     const double h = 0.5 * (dmax - dmin), mid = 0.5 * (dmax + dmin);
+    if (t < N) f[t] = sqrt(h * cospi((t + 0.5) / N) + mid);
+    __syncthreads();
     if (t < N) {
+        double cd, sd, cr, sr;
+        sincospi((double)t / N, &sd, &cd);              // the step between nodes
+        sincospi(0.5 * t / N, &sr, &cr);                // the first node
         double s = 0.0;
-        for (int j = 0; j < N; j++) {
-            double th = kPiA * (j + 0.5) / N;
-            s += sqrt(h * cos(th) + mid) * cos(t * th);
+        for (int k = 0; k < N; k++) {
+            s += f[k] * cr;
+            const double cn = cr * cd - sr * sd;
+            sr = fma(sr, cd, cr * sd);
+            cr = cn;
         }
-        c[t] = 2.0 * s / N;
+        c[t] = (t == 0 ? 1.0 : 2.0) * s / N;            // c_0 halved in the series
     }
     __syncthreads();
-    if (t == 0) c[0] *= 0.5;
+    double v = 0.0;
+    if (t < N) {
+        for (int q = 0; q < N; q++) {
+            const int d = t > q ? t - q : q - t;
+            v += c[q] * 0.5 * (mom[(size_t)(t + q) * m + j] + mom[(size_t)d * m + j]);
+        }
+        v *= c[t];
+    }
+    red[t] = v;
     __syncthreads();
-    double mx = 0.0;
-    for (int j = 0; j < m; j++) {
-        double v = 0.0;
-        if (t < N) {
-            for (int q = 0; q < N; q++) {
-                int d = t > q ? t - q : q - t;
-                v += c[q] * 0.5 * (mom[(size_t)(t + q) * m + j] + mom[(size_t)d * m + j]);
-            }
-            v *= c[t];
-        }
-        red[t] = v;
+    for (int w = 128; w > 0; w >>= 1) {
+        if (t < w) red[t] += red[t + w];
         __syncthreads();
-        for (int w = 128; w > 0; w >>= 1) {
-            if (t < w) red[t] += red[t + w];
-            __syncthreads();
-        }
-        const double ss = red[0];
+    }
+    if (t == 0) {
         const double wdw = h * mom[1 * m + j] + mid * mom[0 * m + j];
-        const double e = sqrt(fabs(ss - wdw) / wdw);
-        if (t == 0) est[j] = e;
-        mx = fmax(mx, e);
-        __syncthreads();
+        est[(size_t)blockIdx.y * m + j] = sqrt(fabs(red[0] - wdw) / wdw);
     }
-    if (t == 0) est[m] = mx;
 }
 
 // dS = (c_0/2) V_0 + c_1 V_1 + sum_{p>=2} c_p V_p, the terms added in the
@@ -159,13 +164,13 @@ static bd_status ensure_adaptive_scratch(Plan &P)
     if (!P.d_mom) {
         size_t nm = (size_t)2 * kMaxCheb * kMaxRhs, np = (size_t)3 * kRedBlocks * kMaxRhs;
         size_t nw = (size_t)P.n3 * P.p.max_rhs;
-        cudaError_t e = cudaMalloc(&P.d_mom, (nm + np + kMaxRhs + 1 + nw) * sizeof(double));
-        if (e == cudaSuccess) e = cudaMallocHost(&P.h_est, (kMaxRhs + 1) * sizeof(double));
+        cudaError_t e = cudaMalloc(&P.d_mom, (nm + np + kEfRun * kMaxRhs + nw) * sizeof(double));
+        if (e == cudaSuccess) e = cudaMallocHost(&P.h_est, kEfRun * kMaxRhs * sizeof(double));
         if (e != cudaSuccess) {
             cudaGetLastError();
             return set_error(BD_ERR_OOM, "adaptive Chebyshev scratch: %s", cudaGetErrorString(e));
         }
-        P.scratch_bytes += (int64_t)((nm + np + kMaxRhs + 1 + nw) * sizeof(double));
+        P.scratch_bytes += (int64_t)((nm + np + kEfRun * kMaxRhs + nw) * sizeof(double));
     }
     return BD_OK;
 }
@@ -180,8 +185,8 @@ bd_status cheb_adaptive_core(Plan &P, const void *D, const double *bounds, doubl
     const long blk = (long)n3 * m;
     double *mom = P.d_mom;
     double *part = mom + (size_t)2 * kMaxCheb * kMaxRhs;
-    double *est = part + (size_t)3 * kRedBlocks * kMaxRhs;
-    double *Wp = est + kMaxRhs + 1;                     // D V_{p-1}, 3N x m
+    double *est = part + (size_t)3 * kRedBlocks * kMaxRhs;   // [kEfRun][m]
+    double *Wp = est + (size_t)kEfRun * kMaxRhs;        // D V_{p-1}, 3N x m
     auto V = [&](int p) -> const double * { return p == 0 ? dW : P.d_vhist + (long)(p - 1) * blk; };
     const unsigned gl = (unsigned)((blk + 255) / 256);
     const int nparts = kRedBlocks < (n3 + 255) / 256 ? kRedBlocks : (n3 + 255) / 256;
@@ -203,8 +208,13 @@ bd_status cheb_adaptive_core(Plan &P, const void *D, const double *bounds, doubl
     moments(1);
     int p = 1;                       // highest V computed
     int conv = 0;
+    // N grows by one until E_f < tol; the estimates of a run of up to kEfRun
+    // consecutive N are taken in one launch and read with one host wait, and
+    // the first N of the run below tol is the answer (the same N as one
+    // check per term; the few extra terms of the run are left unused)
     for (;;) {
-        while (p < N - 1) {          // V_p = 2 (D V_{p-1} - sigma V_{p-1})/h - V_{p-2}
+        const int Nhi = N + kEfRun - 1 < nmax ? N + kEfRun - 1 : nmax;
+        while (p < Nhi - 1) {        // V_p = 2 (D V_{p-1} - sigma V_{p-1})/h - V_{p-2}
             p++;
             st = apply_dense(P, D, V(p - 1), m, Wp, s);
             if (st != BD_OK) return st;
@@ -212,13 +222,27 @@ bd_status cheb_adaptive_core(Plan &P, const void *D, const double *bounds, doubl
                                P.d_vhist + (long)(p - 1) * blk, s);
             moments(p);
         }
-        k_ef_estimate<<<1, 256, 0, s>>>(mom, m, bounds, N, est);
+        const int run = Nhi - N + 1;
+        k_ef_estimate<<<dim3(m, run), 256, 0, s>>>(mom, m, bounds, N, est);
         count_launches(1);
-        cudaMemcpyAsync(P.h_est, est + m, sizeof(double), cudaMemcpyDeviceToHost, s);
+        cudaMemcpyAsync(P.h_est, est, sizeof(double) * run * m, cudaMemcpyDeviceToHost, s);
         if (cudaStreamSynchronize(s) != cudaSuccess) return check_launch("adaptive Chebyshev");
-        if (P.h_est[0] < tol) { conv = 1; break; }
-        if (N >= nmax) break;
-        N++;
+        int hit = -1;
+        for (int b = 0; b < run && hit < 0; b++) {
+            double mx = 0.0;
+            for (int j = 0; j < m; j++) mx = fmax(mx, P.h_est[b * m + j]);
+            if (mx < tol) hit = b;
+        }
+        if (hit >= 0) {
+            N += hit;
+            conv = 1;
+            break;
+        }
+        if (Nhi >= nmax) {
+            N = nmax;
+            break;
+        }
+        N = Nhi + 1;
     }
     launch_cheb_coeffs(P, bounds, N, s);
     k_cheb_combine<<<gl, 256, 0, s>>>(dW, P.d_vhist, blk, P.d_coef, N, blk, dS);
