@@ -309,6 +309,26 @@ bd_status bd_apply_D_matfree(bd_plan *plan, const double *R, const double *X, in
                              double *Y, bd_stream stream);
 
 /* ---------------------------------------------------------------------------
+ * bd_mesh_fft -- the 3-D mesh transforms of the spectral product (Sec. VIII:
+ * the Fourier part of the Ewald sum by FFT), on their own.  B real meshes
+ * [B][K][K][K] (row-major, last index fastest) <-> their half spectra
+ * [B][K][K][K/2 + 1] of (re, im) pairs, unnormalised:
+ *   forward (inverse = 0): out_k = sum_j in_j e^{-2 pi i j.k / K}
+ *   inverse (inverse = 1): out_j = sum over the full spectrum of in_k
+ *                          e^{+2 pi i j.k / K}, the missing half taken as the
+ *                          Hermitian conjugate (so inverse(forward(x)) = K^3 x)
+ *   K          even, 2..512, no prime factor above 5 (else BD_ERR_UNSUPPORTED)
+ *   B          meshes, >= 1
+ *   precision  BD_FP64: doubles; BD_MIXED_F16 / BD_MIXED_BF16: floats
+ *   in, out    dev, must not overlap; the inverse overwrites `in`
+ * Forms its twiddle tables on every call and returns after the transform has
+ * finished on `stream` (synchronous).  BD_ERR_INVALID for NULL pointers,
+ * B < 1, an unknown precision or overlapping buffers; BD_ERR_OOM or
+ * BD_ERR_CUDA from the device.                                            */
+bd_status bd_mesh_fft(int32_t K, int32_t B, int32_t precision, int32_t inverse, void *in,
+                      void *out, bd_stream stream);
+
+/* ---------------------------------------------------------------------------
  * bd_step -- one Euler step of Eq. (sde) with kappa = 0:
  *   r(t+dt) = r + (dt/4) D.F + (1/sqrt 2) dS[:,0],
  * i.e. bd_forces, bd_build_D, bd_eig_bounds, the product D.[F, dW] and

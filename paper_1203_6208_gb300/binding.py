@@ -37,7 +37,7 @@ EXPORTS = ["bd_plan_create", "bd_plan_destroy", "bd_plan_query", "bd_forces", "b
            "bd_plan_test_stall", "bd_step_capture", "bd_step_replay", "bd_product_timing",
            "bd_plan_set_step_counter", "bd_batch_create", "bd_batch_destroy", "bd_batch_query",
            "bd_batch_step", "bd_chebyshev_sqrt_adaptive", "bd_apply_D_matfree",
-           "bd_last_error", "bd_version"]
+           "bd_mesh_fft", "bd_last_error", "bd_version"]
 PHASES = ["forces", "build_D", "bounds", "first_product", "chebyshev", "update"]
 
 
@@ -122,6 +122,7 @@ def load(path: str = LIB_PATH):
     L.bd_batch_step.argtypes = [_vp, _vp, _vp, ctypes.POINTER(BdStepOpts), _vp, _vp]
     L.bd_chebyshev_backward.argtypes = [_vp, _vp, _vp, _vp, i32, _vp, i32, _vp, _vp, _vp, _vp]
     L.bd_apply_D_matfree.argtypes = [_vp, _vp, _vp, i32, _vp, _vp]
+    L.bd_mesh_fft.argtypes = [i32, i32, i32, i32, _vp, _vp, _vp]
     L.bd_chebyshev_sqrt_adaptive.argtypes = [_vp, _vp, _vp, f64, _vp, i32, _vp, _vp,
                                              ctypes.POINTER(i32), _vp]
     L.bd_eig_bounds_noalloc.argtypes = [_vp, i32, i32, i32, f64, f64, _vp, _vp, _vp]
@@ -338,6 +339,13 @@ def eig_bounds_noalloc(D, n3, ld, iters, safety_max, dmin_fraction, bounds, stat
     _check(load().bd_eig_bounds_noalloc(_p(D), int(n3), int(ld), int(iters), float(safety_max),
                                         float(dmin_fraction), _p(bounds), _p(status),
                                         _stream(stream)))
+
+
+def mesh_fft(K, B, precision, inverse, x, y, stream=None):
+    """bd_mesh_fft: B real K^3 meshes <-> their half spectra (unnormalised;
+    synchronous).  x and y are device tensors of the input and output."""
+    _check(load().bd_mesh_fft(int(K), int(B), PRECISIONS[precision], int(inverse), _p(x), _p(y),
+                              _stream(stream)))
 
 
 class Batch:

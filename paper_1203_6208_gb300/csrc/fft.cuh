@@ -8,8 +8,7 @@ constexpr int kFftMaxK = 512;     // mesh points per edge
 
 struct FftPlan {
     int K;                        // mesh points per edge, 2^a 3^b 5^c
-    int nrad;                     // radix passes
-    int rad[16];
+    unsigned code32, code64;      // radix passes, 5 bits each from the low end (FP32, FP64)
     void *d_tw64, *d_tw32;        // e^{-2 pi i t/K}, t < K (FP64 and FP32 pairs)
 };
 
