@@ -1,13 +1,17 @@
 // fft.cu -- the 3-D mesh transforms of the spectral product (Sec. VIII
 // outlook: the Fourier part of the Ewald sum by FFT): a batch of real K^3
 // meshes to their half spectra K x K x (K/2 + 1) and back, unnormalised
-// (forward e^{-2 pi i jk/K}, inverse e^{+2 pi i jk/K}), K = 2^a 3^b 5^c.
+// (forward e^{-2 pi i jk/K}, inverse e^{+2 pi i jk/K}), K an even
+// 2^a 3^b 5^c <= 512.
 //
 // Each 1-D transform runs in shared memory as a Stockham (self-sorting)
-// sequence of radix-4, 2, 3 and 5 passes: pass q with radix R and Ns = the
-// product of the earlier radices reads R values K/R apart, turns them by the
-// twiddles w^{r (j mod Ns) K/(Ns R)}, takes the R-point DFT and writes them Ns
-// apart at (j div Ns) Ns R + (j mod Ns); the output is in natural order.
+// sequence of radix passes: pass q with radix R and Ns = the product of the
+// earlier radices reads R values K/R apart, turns them by the twiddles
+// w^{r (j mod Ns) K/(Ns R)}, takes the R-point DFT and writes them Ns apart
+// at (j div Ns) Ns R + (j mod Ns); the output is in natural order.  The
+// radices are 16 (FP32 only), 8, 4, 2, 9, 3 and 5, largest first; 8, 9 and
+// 16 are one Cooley-Tukey split done in registers, so fewer passes go
+// through shared memory (K = 144 = 16 9: two).
 //   z (contiguous) : two real lines a, b form c = a + i b; after the complex
 //                    transform A_k = (C_k + conj C_{-k})/2 and
 //                    B_k = (C_k - conj C_{-k})/(2i), k = 0 .. K/2 (the inverse
