@@ -318,7 +318,7 @@ bd_status bd_apply_D_matfree(bd_plan *plan, const double *R, const double *X, in
  *                          e^{+2 pi i j.k / K}, the missing half taken as the
  *                          Hermitian conjugate (so inverse(forward(x)) = K^3 x)
  *   K          even, 2..512, no prime factor above 5 (else BD_ERR_UNSUPPORTED)
- *   B          meshes, >= 1
+ *   B          meshes, 1..65535 (BD_ERR_UNSUPPORTED above)
  *   precision  BD_FP64: doubles; BD_MIXED_F16 / BD_MIXED_BF16: floats
  *   in, out    dev, must not overlap; the inverse overwrites `in`
  * Forms its twiddle tables on every call and returns after the transform has

@@ -581,6 +581,7 @@ extern "C" bd_status bd_mesh_fft(int32_t K, int32_t B, int32_t precision, int32_
 {
     if (!in || !out) return set_error(BD_ERR_INVALID, "NULL argument");
     if (B < 1) return set_error(BD_ERR_INVALID, "B=%d < 1", B);
+    if (B > 65535) return set_error(BD_ERR_UNSUPPORTED, "B=%d > 65535 meshes in one call", B);
     if (precision != BD_FP64 && precision != BD_MIXED_F16 && precision != BD_MIXED_BF16)
         return set_error(BD_ERR_INVALID, "unknown precision %d", precision);
     if (K < 2 || K % 2) return set_error(BD_ERR_UNSUPPORTED, "mesh size %d is not even", K);

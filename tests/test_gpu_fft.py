@@ -87,7 +87,7 @@ def test_largest_meshes_and_most_passes(bnd, prec, K, B):
 def test_rejects_bad_arguments(bnd):
     x = torch.zeros(2 * 15 ** 3, dtype=torch.float64, device="cuda")
     y = torch.zeros(2 * 16 ** 3, dtype=torch.float64, device="cuda")
-    for K, B in ((15, 1), (14, 1), (1024, 1), (8, 0)):   # odd, factor 7, too large, B < 1
+    for K, B in ((15, 1), (14, 1), (1024, 1), (8, 0), (8, 70000)):   # odd, factor 7, too large, B out of range
         with pytest.raises(bnd.BDError):
             bnd.mesh_fft(K, B, "fp64", 0, x, y)
     with pytest.raises(bnd.BDError):                     # overlapping buffers
