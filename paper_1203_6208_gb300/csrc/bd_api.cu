@@ -728,7 +728,7 @@ static bd_status step_finish(Plan &P, const StepCtx &c, cudaStream_t s)
     // (a8) Euler update with FENE rejection
     launch_euler(P, c.R, c.DFd, c.dSd, c.st_dev, s);
     if (P.phase_on) cudaEventRecord(P.phase_ev[6], s);
-    if (c.DF) cudaMemcpyAsync(c.DF, c.DFd, (size_t)P.n3 * sizeof(double), cudaMemcpyDeviceToDevice, s);
+    if (c.DF) launch_copy_f64(c.DF, c.DFd, (size_t)P.n3, s);
     return check_launch("bd_step");
 }
 
@@ -821,7 +821,7 @@ static bd_status step_run(bd_plan *plan, double *R, void *D, const double *dW,
     do { if (P.phase_on) cudaEventRecord(P.phase_ev[i], s); } while (0)
     PHASE(0);
     launch_stats_begin(st_dev, o->n_cheb, s);
-    cudaMemsetAsync(P.d_status, 0, 8 * sizeof(int32_t), s);
+    launch_zero_i32(P.d_status, 8, s);
     // (a1) forces; input over-stretch count in status word 2
     launch_forces(P, R, P.d_F, P.d_status + 2, s);
     PHASE(1);
@@ -846,7 +846,7 @@ static bd_status step_run(bd_plan *plan, double *R, void *D, const double *dW,
     } else if (lag && P.lag_valid) {
         // the previous step's Lanczos bounds, d_min tightened by this step's
         // pair estimate (computed by the assembly above)
-        cudaMemcpyAsync(P.d_bounds, P.d_lag_bounds, 2 * sizeof(double), cudaMemcpyDeviceToDevice, s);
+        launch_copy_f64(P.d_bounds, P.d_lag_bounds, 2, s);
         launch_bounds_pair(P.d_bounds, P.d_pairw, o->dmin_fraction, P.d_status + 3, s);
     } else {
         st = eig_bounds_core(P, D, o->lanczos_iters, o->bound_safety, o->dmin_fraction,
@@ -870,12 +870,11 @@ static bd_status step_run(bd_plan *plan, double *R, void *D, const double *dW,
     const int fcols = fix ? 2 : 0;         // Fixman's U+, U- ride along
     if (m + 1 + fcols <= kMaxRhs) {
         const int extra = lag ? 1 : 0;     // the Lanczos start vector q_1
-        cudaMemcpyAsync(P.d_X0, P.d_F, n3 * sizeof(double), cudaMemcpyDeviceToDevice, s);
-        cudaMemcpyAsync(P.d_X0 + n3, w, n3 * m * sizeof(double), cudaMemcpyDeviceToDevice, s);
+        launch_copy_f64(P.d_X0, P.d_F, n3, s);
+        launch_copy_f64(P.d_X0 + n3, w, n3 * m, s);
         if (lag) {
             launch_lanczos_init(P, s);
-            cudaMemcpyAsync(P.d_X0 + n3 * (m + 1), P.d_lq[1], n3 * sizeof(double),
-                            cudaMemcpyDeviceToDevice, s);
+            launch_copy_f64(P.d_X0 + n3 * (m + 1), P.d_lq[1], n3, s);
         }
         if (fix) launch_fixman_fill(P.d_X0 + n3 * (m + 1), n3, s);
         st = apply_core(P, D, P.d_X0, m + 1 + extra + fcols, P.d_Y0, 0, s);
@@ -888,8 +887,7 @@ static bd_status step_run(bd_plan *plan, double *R, void *D, const double *dW,
             launch_refine_f32(P, (const float *)D, P.d_F, 1, P.d_Y0, s);
         }
         if (lag) {           // Lanczos step 0 from the product's last column
-            cudaMemcpyAsync(P.d_lq[2], P.d_Y0 + n3 * (m + 1), n3 * sizeof(double),
-                            cudaMemcpyDeviceToDevice, s);
+            launch_copy_f64(P.d_lq[2], P.d_Y0 + n3 * (m + 1), n3, s);
             launch_lanczos_update(P, 0, s);
         }
     } else {

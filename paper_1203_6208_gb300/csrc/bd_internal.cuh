@@ -276,5 +276,6 @@ constexpr int kRedBlocks = 64;
 void launch_dot_cols(const double *A, const double *B, int n3, int m, double *out, double *part,
                      cudaStream_t s);
 void launch_zero_i32(int32_t *p, int n, cudaStream_t s);
+void launch_copy_f64(double *dst, const double *src, size_t n, cudaStream_t s);
 
 }  // namespace bd

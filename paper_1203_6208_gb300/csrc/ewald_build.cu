@@ -827,7 +827,7 @@ static long tile_pairs(int n)
 void launch_build_D_f64(Plan &P, const double *R, double *D, cudaStream_t s)
 {
     launch_trig_tables(P, R, s);
-    cudaMemsetAsync(P.d_pairw, 0, 2 * sizeof(unsigned), s);
+    launch_zero_i32((int32_t *)P.d_pairw, 2, s);
     long nb = tile_pairs(P.n);
     k_build_D<double><<<(unsigned)nb, TB * TB, 0, s>>>(
         P.d_pw64, P.d_pw32, P.n, P.h_ew64, P.d_ewc, P.d_tab, P.tab_i0, P.ntab, P.d_km64, P.nk,
@@ -846,7 +846,7 @@ bd_status launch_build_D_f32(Plan &P, const double *R, float *D32, void *D16, in
         if (st != BD_OK) return st;
         nk = 0;
     }
-    cudaMemsetAsync(P.d_pairw, 0, 2 * sizeof(unsigned), s);
+    launch_zero_i32((int32_t *)P.d_pairw, 2, s);
     long nb = tile_pairs(P.n);
     k_build_D<float><<<(unsigned)nb, TB * TB, 0, s>>>(
         P.d_pw64, P.d_pw32, P.n, P.h_ew32, P.d_ewc, P.d_tab32, P.tab32_i0, P.ntab32, P.d_km32, nk,
@@ -862,7 +862,7 @@ bd_status launch_build_D_f32(Plan &P, const double *R, float *D32, void *D16, in
 // tables (launch_matfree_tables must have run for R)
 void launch_pair_estimate(Plan &P, cudaStream_t s)
 {
-    cudaMemsetAsync(P.d_pairw, 0, 2 * sizeof(unsigned), s);
+    launch_zero_i32((int32_t *)P.d_pairw, 2, s);
     long nb = tile_pairs(P.n);
     if (is_mixed(P))
         k_build_D<float><<<(unsigned)nb, TB * TB, 0, s>>>(

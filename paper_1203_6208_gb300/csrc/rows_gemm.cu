@@ -418,7 +418,7 @@ void rows_cheb_prepare(Plan &P, const RowsRep &rep, RowsRep *dst, const double *
                                                           P.d_x32 + (size_t)rep.m * P.x32_stride,
                                                           P.x32_stride);
     k_rep_set<<<1, 1, 0, s>>>(dst, rep);
-    cudaMemsetAsync(rep.lan_count, 0, sizeof(unsigned), s);
+    launch_zero_i32((int32_t *)rep.lan_count, 1, s);
     count_launches(lan ? 3 : 2);
 }
 
@@ -441,8 +441,8 @@ bd_status rows_cheb_launch(const RowsRep *reps, int nreps, const int *item_rep, 
     int grid = per_sm * sms;
     if (grid > nitems) grid = nitems;
     if (grid < 1) return set_error(BD_ERR_CUDA, "no resident CTA for the batched Chebyshev loop");
-    cudaMemsetAsync(bar, 0, sizeof(unsigned), s);      // arrival count (a timed-out launch may leave it)
-    cudaMemsetAsync(bar + kRowsBarWords, 0, sizeof(unsigned) * kMaxCheb, s);   // per-term item counters
+    launch_zero_i32((int32_t *)bar, 1, s);      // arrival count (a timed-out launch may leave it)
+    launch_zero_i32((int32_t *)(bar + kRowsBarWords), kMaxCheb, s);   // per-term item counters
     cudaLaunchAttribute attr[1];
     attr[0].id = cudaLaunchAttributeCooperative;
     attr[0].val.cooperative = 1;

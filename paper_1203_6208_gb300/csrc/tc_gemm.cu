@@ -481,7 +481,7 @@ static void *x16_buf(Plan &P, int which)
 static void prepare_operand(Plan &P, const double *X, int m, int bn, void *X16, cudaStream_t s)
 {
     unsigned long long *bits = (unsigned long long *)(P.d_xscale + 2 * kMaxRhs);
-    cudaMemsetAsync(bits, 0, sizeof(unsigned long long) * kMaxRhs, s);
+    launch_zero_i32((int32_t *)bits, 2 * kMaxRhs, s);
     k_col_absmax<<<dim3(64, m), 256, 0, s>>>(X, P.n3, m, bits);
     count_launches(1);
     k_col_scale<<<1, 32, 0, s>>>(bits, m, bn, P.d_xscale, P.d_xscale + kMaxRhs);
@@ -510,7 +510,7 @@ static bd_status launch_tc(Plan &P, const void *D16, const void *X16, int bn, co
     const int G = sk_grid(P, P.tc_split > 0 ? P.tc_split : tc::kMaxCtasPerSm);
     // the arrival counters reset themselves; a plain product (the first of
     // every step) also clears them in case an earlier launch gave up
-    if (e.mode == 0) cudaMemsetAsync(P.d_counters, 0, sizeof(int32_t) * mbk, s);
+    if (e.mode == 0) launch_zero_i32(P.d_counters, mbk, s);
     int32_t *err = P.d_status + 6;
     if (e.mode == 1) prod_mark(P, 0, s);
     const bool two = (P.tc_split > 0 ? P.tc_split : tc::kMaxCtasPerSm) == 2;

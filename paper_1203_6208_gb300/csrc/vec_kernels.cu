@@ -571,7 +571,7 @@ __global__ void k_pair_radius_scan(const T *__restrict__ D, int n, long ld, unsi
 void launch_pair_radius_scan(const void *D, int f32, int n, long ld, unsigned *word,
                              cudaStream_t s)
 {
-    cudaMemsetAsync(word, 0, 2 * sizeof(unsigned), s);
+    launch_zero_i32((int32_t *)word, 2, s);
     dim3 g((unsigned)((n + 255) / 256), (unsigned)(n - 1 < 1 ? 1 : (n - 1 < 65535 ? n - 1 : 65535)));
     if (f32) k_pair_radius_scan<float><<<g, 256, 0, s>>>((const float *)D, n, ld, word);
     else k_pair_radius_scan<double><<<g, 256, 0, s>>>((const double *)D, n, ld, word);
@@ -670,7 +670,7 @@ void launch_euler(Plan &P, double *R, const double *DF, const double *dS, bd_ste
     k_euler_propose<<<(n3 + 255) / 256, 256, 0, s>>>(R, DF, dS, n3, P.p.dt, P.d_Rnew);
     count_launches(1);
     int32_t *over = P.d_status + 1;
-    cudaMemsetAsync(over, 0, sizeof(int32_t), s);
+    launch_zero_i32(over, 1, s);
     if (P.p.spring == 1) {
         k_fene_check<<<(P.n + 127) / 128, 128, 0, s>>>(P.d_Rnew, P.n, P.p.beads_per_chain,
                                                       P.p.fene_b, over);
@@ -697,6 +697,22 @@ __global__ void k_zero_i32(int32_t *p, int n)
 void launch_zero_i32(int32_t *p, int n, cudaStream_t s)
 {
     k_zero_i32<<<(n + 255) / 256, 256, 0, s>>>(p, n);
+    count_launches(1);
+}
+
+// device-to-device copies of the step as kernels: in a captured step they
+// are kernel nodes, where copy nodes would queue on the copy engines (a batch
+// of replicas issues several small copies per replica and step)
+__global__ void k_copy_f64(double *__restrict__ dst, const double *__restrict__ src, long n)
+{
+    for (long i = (long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x)
+        dst[i] = src[i];
+}
+
+void launch_copy_f64(double *dst, const double *src, size_t n, cudaStream_t s)
+{
+    const long blocks = ((long)n + 255) / 256;
+    k_copy_f64<<<(unsigned)(blocks < 1216 ? (blocks > 0 ? blocks : 1) : 1216), 256, 0, s>>>(dst, src, (long)n);
     count_launches(1);
 }
 
