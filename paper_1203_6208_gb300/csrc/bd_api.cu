@@ -820,8 +820,7 @@ static bd_status step_run(bd_plan *plan, double *R, void *D, const double *dW,
 #define PHASE(i) \
     do { if (P.phase_on) cudaEventRecord(P.phase_ev[i], s); } while (0)
     PHASE(0);
-    launch_stats_begin(st_dev, o->n_cheb, s);
-    launch_zero_i32(P.d_status, 8, s);
+    launch_step_begin(st_dev, o->n_cheb, P.d_status, s);
     // (a1) forces; input over-stretch count in status word 2
     launch_forces(P, R, P.d_F, P.d_status + 2, s);
     PHASE(1);
@@ -841,20 +840,21 @@ static bd_status step_run(bd_plan *plan, double *R, void *D, const double *dW,
     const bool lag = !adaptive && !matfree && o->bounds_mode == BD_BOUNDS_LAGGED && is_mixed(P) &&
                      o->n_cheb >= 8 &&
                      o->n_cheb - 1 <= kMaxLanczos && m + 2 <= kMaxRhs;
+    const bool lagged_now = lag && P.lag_valid;
     if (fix) {
         // Fixman's estimates come from the first product below
-    } else if (lag && P.lag_valid) {
+    } else if (lagged_now) {
         // the previous step's Lanczos bounds, d_min tightened by this step's
-        // pair estimate (computed by the assembly above)
-        launch_copy_f64(P.d_bounds, P.d_lag_bounds, 2, s);
-        launch_bounds_pair(P.d_bounds, P.d_pairw, o->dmin_fraction, P.d_status + 3, s);
+        // pair estimate (computed by the assembly above), and the statistics
+        launch_bounds_lagged(P.d_bounds, P.d_lag_bounds, P.d_pairw, o->dmin_fraction,
+                             P.d_status + 3, st_dev, s);
     } else {
         st = eig_bounds_core(P, D, o->lanczos_iters, o->bound_safety, o->dmin_fraction,
                              P.d_bounds, P.d_status + 3, s,
                              (matfree && P.pme) ? kPairNone : kPairFromBuild);
         if (st != BD_OK) return st;
     }
-    if (!fix) launch_stats_bounds(st_dev, P.d_bounds, P.d_status + 3, s);
+    if (!fix && !lagged_now) launch_stats_bounds(st_dev, P.d_bounds, P.d_status + 3, s);
     PHASE(3);
     // Wiener increments
     const double *w = dW;
@@ -870,12 +870,9 @@ static bd_status step_run(bd_plan *plan, double *R, void *D, const double *dW,
     const int fcols = fix ? 2 : 0;         // Fixman's U+, U- ride along
     if (m + 1 + fcols <= kMaxRhs) {
         const int extra = lag ? 1 : 0;     // the Lanczos start vector q_1
-        launch_copy_f64(P.d_X0, P.d_F, n3, s);
-        launch_copy_f64(P.d_X0 + n3, w, n3 * m, s);
-        if (lag) {
-            launch_lanczos_init(P, s);
-            launch_copy_f64(P.d_X0 + n3 * (m + 1), P.d_lq[1], n3, s);
-        }
+        // X0 = [F, dW, q_1]
+        if (lag) launch_lanczos_init(P, s);
+        launch_copy3_f64(P.d_X0, P.d_F, n3, w, n3 * m, P.d_lq[1], lag ? n3 : 0, s);
         if (fix) launch_fixman_fill(P.d_X0 + n3 * (m + 1), n3, s);
         st = apply_core(P, D, P.d_X0, m + 1 + extra + fcols, P.d_Y0, 0, s);
         if (st != BD_OK) return st;
@@ -886,10 +883,8 @@ static bd_status step_run(bd_plan *plan, double *R, void *D, const double *dW,
         if (is_mixed(P) && !matfree) {   // refine the drift column only
             launch_refine_f32(P, (const float *)D, P.d_F, 1, P.d_Y0, s);
         }
-        if (lag) {           // Lanczos step 0 from the product's last column
-            launch_copy_f64(P.d_lq[2], P.d_Y0 + n3 * (m + 1), n3, s);
-            launch_lanczos_update(P, 0, s);
-        }
+        if (lag)             // Lanczos step 0 from the product's last column (used in place)
+            launch_lanczos_update(P, 0, s, P.d_Y0 + n3 * (m + 1));
     } else {
         st = apply_core(P, D, P.d_F, 1, P.d_Y0, BD_APPLY_REFINE, s);
         if (st != BD_OK) return st;

@@ -250,10 +250,13 @@ void launch_wiener(Plan &P, uint64_t seed, uint64_t step, int64_t count, double 
                    cudaStream_t s, const unsigned long long *step_dev = nullptr);
 void launch_counter_add(unsigned long long *ctr, cudaStream_t s);
 void launch_lanczos_init(Plan &P, cudaStream_t s);
-void launch_lanczos_update(Plan &P, int j, cudaStream_t s);
+void launch_lanczos_update(Plan &P, int j, cudaStream_t s, double *w = nullptr);
 void launch_lanczos_finish(Plan &P, int k, double safety_max, double dmin_fraction,
                            double *bounds, int32_t *status, cudaStream_t s);
 void launch_stats_begin(bd_step_stats *st, int nch, cudaStream_t s);
+void launch_step_begin(bd_step_stats *st, int nch, int32_t *status, cudaStream_t s);
+void launch_bounds_lagged(double *bounds, const double *lag, const unsigned *word,
+                          double dmin_fraction, int32_t *status, bd_step_stats *st, cudaStream_t s);
 // the pair estimate (pair_bound.cuh): word[0] = max over pairs of rho(D_{nu mu})
 // read from a stored D (FP64, or the FP32 D32 when f32), upper triangle only;
 // word[1] = d_s = D[0][0]
@@ -277,5 +280,7 @@ void launch_dot_cols(const double *A, const double *B, int n3, int m, double *ou
                      cudaStream_t s);
 void launch_zero_i32(int32_t *p, int n, cudaStream_t s);
 void launch_copy_f64(double *dst, const double *src, size_t n, cudaStream_t s);
+void launch_copy3_f64(double *dst, const double *a, size_t na, const double *b, size_t nb,
+                      const double *c, size_t nc, cudaStream_t s);
 
 }  // namespace bd

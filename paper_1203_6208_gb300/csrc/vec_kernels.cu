@@ -376,21 +376,21 @@ __global__ void k_lanczos_shift(double *qprev, double *q, const double *w, int n
     q[i] = bj > 0.0 ? w[i] / bj : 0.0;
 }
 
-// called after d_lq[2] = D q_j
-void launch_lanczos_update(Plan &P, int j, cudaStream_t s)
+// called after w = D q_j (w: d_lq[2] unless given; it is overwritten)
+void launch_lanczos_update(Plan &P, int j, cudaStream_t s, double *w)
 {
     int n3 = P.n3;
+    if (!w) w = P.d_lq[2];
     double *alpha = P.d_lab + j, *beta = P.d_lab + kMaxLanczos + j;
     double *beta_prev = j > 0 ? P.d_lab + kMaxLanczos + j - 1 : nullptr;
-    launch_dot_cols(P.d_lq[1], P.d_lq[2], n3, 1, alpha, P.d_redpart, s);
+    launch_dot_cols(P.d_lq[1], w, n3, 1, alpha, P.d_redpart, s);
     double *part = P.d_redpart;
     int bx = min(kRedBlocks, (n3 + 255) / 256);
-    k_lanczos_orth<<<bx, 256, 0, s>>>(P.d_lq[2], P.d_lq[1], P.d_lq[0], n3, alpha, beta_prev,
-                                      part);
+    k_lanczos_orth<<<bx, 256, 0, s>>>(w, P.d_lq[1], P.d_lq[0], n3, alpha, beta_prev, part);
     count_launches(1);
     k_sum_parts<<<1, 32, 0, s>>>(part, bx, P.d_red + 1);
     count_launches(1);
-    k_lanczos_shift<<<(n3 + 255) / 256, 256, 0, s>>>(P.d_lq[0], P.d_lq[1], P.d_lq[2], n3,
+    k_lanczos_shift<<<(n3 + 255) / 256, 256, 0, s>>>(P.d_lq[0], P.d_lq[1], w, n3,
                                                      P.d_red + 1, beta);
     count_launches(1);
 }
@@ -618,6 +618,50 @@ void launch_stats_begin(bd_step_stats *st, int nch, cudaStream_t s)
     count_launches(1);
 }
 
+// the start of a step in one launch: the statistics record and the plan's
+// eight status words
+__global__ void k_step_begin(bd_step_stats *st, int nch, int32_t *status)
+{
+    if (threadIdx.x == 0) {
+        st->d_min = 0.0; st->d_max = 0.0; st->ef_max = 0.0;
+        st->n_cheb = nch; st->n_overstretched = 0; st->accepted = 0; st->status = BD_OK;
+    }
+    if (threadIdx.x < 8) status[threadIdx.x] = 0;
+}
+
+void launch_step_begin(bd_step_stats *st, int nch, int32_t *status, cudaStream_t s)
+{
+    k_step_begin<<<1, 32, 0, s>>>(st, nch, status);
+    count_launches(1);
+}
+
+// the lagged bounds of a step in one launch: the previous step's Lanczos
+// interval, d_min tightened by this step's pair estimate (as k_bounds_pair),
+// and the statistics record
+__global__ void k_bounds_lagged(double *b, const double *lag, const unsigned *word, double f,
+                                int32_t *status, bd_step_stats *st)
+{
+    const double ds = (double)__uint_as_float(word[1]);
+    const double rho = (double)__uint_as_float(word[0]);
+    const double th = ds - rho;
+    const double dmin = th > 0.0 ? fmin(lag[0], f * th) : f * th;
+    const double dmax = lag[1];
+    b[0] = dmin;
+    b[1] = dmax;
+    const int32_t bs = (dmin > 0.0 && dmax > dmin) ? BD_OK : BD_ERR_NOT_PD;
+    *status = bs;
+    st->d_min = dmin;
+    st->d_max = dmax;
+    if (bs != BD_OK) st->status = bs;
+}
+
+void launch_bounds_lagged(double *bounds, const double *lag, const unsigned *word,
+                          double dmin_fraction, int32_t *status, bd_step_stats *st, cudaStream_t s)
+{
+    k_bounds_lagged<<<1, 1, 0, s>>>(bounds, lag, word, dmin_fraction, status, st);
+    count_launches(1);
+}
+
 void launch_stats_bounds(bd_step_stats *st, const double *bounds, const int32_t *bstatus,
                          cudaStream_t s)
 {
@@ -707,6 +751,24 @@ __global__ void k_copy_f64(double *__restrict__ dst, const double *__restrict__ 
 {
     for (long i = (long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x)
         dst[i] = src[i];
+}
+
+// dst = [a (na) | b (nb) | c (nc)]: up to three contiguous copies in one launch
+__global__ void k_copy3_f64(double *__restrict__ dst, const double *__restrict__ a, long na,
+                            const double *__restrict__ b, long nb, const double *__restrict__ c, long nc)
+{
+    const long n = na + nb + nc;
+    for (long i = (long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x)
+        dst[i] = i < na ? a[i] : (i < na + nb ? b[i - na] : c[i - na - nb]);
+}
+
+void launch_copy3_f64(double *dst, const double *a, size_t na, const double *b, size_t nb,
+                      const double *c, size_t nc, cudaStream_t s)
+{
+    const long blocks = ((long)(na + nb + nc) + 255) / 256;
+    k_copy3_f64<<<(unsigned)(blocks < 1216 ? (blocks > 0 ? blocks : 1) : 1216), 256, 0, s>>>(
+        dst, a, (long)na, b, (long)nb, c, (long)nc);
+    count_launches(1);
 }
 
 void launch_copy_f64(double *dst, const double *src, size_t n, cudaStream_t s)
