@@ -83,3 +83,23 @@ def test_struct_layouts_match_binding():
             os.remove(exe)
     assert sizes == [ctypes.sizeof(b.BdParams), ctypes.sizeof(b.BdPlanInfo),
                      ctypes.sizeof(b.BdStepStats), ctypes.sizeof(b.BdStepOpts)]
+
+
+def test_mesh_fft_rejects_bad_arguments_before_any_device_call(libpath):
+    """bd_mesh_fft checks its arguments on the host before it touches the
+    device: NULL buffers, B outside 1..65535 and unknown precisions are
+    BD_ERR_INVALID / BD_ERR_UNSUPPORTED, and so is an odd mesh size (the
+    real-to-complex pass packs two real lines into one complex line)."""
+    from paper_1203_6208_gb300 import binding
+    L = binding.load(libpath)
+    INVALID, UNSUPPORTED = 1, 8      # bd_status codes (include/bd.h)
+    fake = ctypes.c_void_p(0x1000)   # never dereferenced: every call below fails its checks first
+    cases = [((8, 1, 0, 0, None, fake), INVALID),
+             ((8, 0, 0, 0, fake, ctypes.c_void_p(0x2000)), INVALID),
+             ((8, 70000, 0, 0, fake, ctypes.c_void_p(0x2000)), UNSUPPORTED),
+             ((8, 1, 7, 0, fake, ctypes.c_void_p(0x2000)), INVALID),
+             ((15, 1, 0, 0, fake, ctypes.c_void_p(0x2000)), UNSUPPORTED),
+             ((0, 1, 1, 1, fake, ctypes.c_void_p(0x2000)), UNSUPPORTED)]
+    for args, want in cases:
+        assert L.bd_mesh_fft(*args, None) == want, args
+        assert L.bd_last_error() != b""
