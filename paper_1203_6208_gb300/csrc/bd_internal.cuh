@@ -253,7 +253,6 @@ void launch_lanczos_init(Plan &P, cudaStream_t s);
 void launch_lanczos_update(Plan &P, int j, cudaStream_t s, double *w = nullptr);
 void launch_lanczos_finish(Plan &P, int k, double safety_max, double dmin_fraction,
                            double *bounds, int32_t *status, cudaStream_t s);
-void launch_stats_begin(bd_step_stats *st, int nch, cudaStream_t s);
 void launch_step_begin(bd_step_stats *st, int nch, int32_t *status, cudaStream_t s);
 void launch_bounds_lagged(double *bounds, const double *lag, const unsigned *word,
                           double dmin_fraction, int32_t *status, bd_step_stats *st, cudaStream_t s);

@@ -599,23 +599,11 @@ void launch_bounds_pair(double *bounds, const unsigned *word, double dmin_fracti
 }
 
 // stats bookkeeping for bd_step
-__global__ void k_stats_begin(bd_step_stats *st, int nch)
-{
-    st->d_min = 0.0; st->d_max = 0.0; st->ef_max = 0.0;
-    st->n_cheb = nch; st->n_overstretched = 0; st->accepted = 0; st->status = BD_OK;
-}
-
 __global__ void k_stats_bounds(bd_step_stats *st, const double *bounds, const int32_t *bstatus)
 {
     st->d_min = bounds[0];
     st->d_max = bounds[1];
     if (*bstatus != BD_OK) st->status = *bstatus;
-}
-
-void launch_stats_begin(bd_step_stats *st, int nch, cudaStream_t s)
-{
-    k_stats_begin<<<1, 1, 0, s>>>(st, nch);
-    count_launches(1);
 }
 
 // the start of a step in one launch: the statistics record and the plan's
