@@ -99,7 +99,11 @@ def test_mesh_fft_rejects_bad_arguments_before_any_device_call(libpath):
              ((8, 70000, 0, 0, fake, ctypes.c_void_p(0x2000)), UNSUPPORTED),
              ((8, 1, 7, 0, fake, ctypes.c_void_p(0x2000)), INVALID),
              ((15, 1, 0, 0, fake, ctypes.c_void_p(0x2000)), UNSUPPORTED),
-             ((0, 1, 1, 1, fake, ctypes.c_void_p(0x2000)), UNSUPPORTED)]
+             ((0, 1, 1, 1, fake, ctypes.c_void_p(0x2000)), UNSUPPORTED),
+             # even sizes the radix plan refuses (prime factor 7; above 512): the
+             # plan is formed before any allocation
+             ((14, 1, 0, 0, fake, ctypes.c_void_p(0x2000)), UNSUPPORTED),
+             ((1024, 1, 1, 0, fake, ctypes.c_void_p(1 << 44)), UNSUPPORTED)]
     for args, want in cases:
         assert L.bd_mesh_fft(*args, None) == want, args
         assert L.bd_last_error() != b""
