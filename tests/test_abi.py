@@ -102,7 +102,7 @@ def test_mesh_fft_rejects_bad_arguments_before_any_device_call(libpath):
              ((0, 1, 1, 1, fake, ctypes.c_void_p(0x2000)), UNSUPPORTED),
              # even sizes the radix plan refuses (prime factor 7; above 512): the
              # plan is formed before any allocation
-             ((14, 1, 0, 0, fake, ctypes.c_void_p(0x2000)), UNSUPPORTED),
+             ((14, 1, 0, 0, fake, ctypes.c_void_p(1 << 44)), UNSUPPORTED),
              ((1024, 1, 1, 0, fake, ctypes.c_void_p(1 << 44)), UNSUPPORTED)]
     for args, want in cases:
         assert L.bd_mesh_fft(*args, None) == want, args
